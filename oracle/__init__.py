@@ -1,0 +1,209 @@
+"""FP64 CPU oracle for the NEP3 energy/force/virial evaluation of arXiv:2205.10046.
+
+TEST INFRASTRUCTURE ONLY. The test-suite, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` are the only code that may import this package. The CUDA
+path never imports it and shares no code with it; the two meet only in the seeded
+input generators of ``paper_2205_10046_gb300.workloads``.
+
+The arithmetic lives in ``nep_oracle.cpp`` (plain FP64 C++, see its header for the
+definitions it follows and the readings of the paper it takes). This module compiles it
+with g++ on first use (or via :func:`build`) and wraps it with ctypes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "nep_oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile nep_oracle.cpp into liboracle.so (portable flags: no -march)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared",
+                               _SRC, "-o", tmp])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Model(C.Structure):
+    _fields_ = [("n_types", C.c_int), ("n_max_r", C.c_int), ("n_max_a", C.c_int),
+                ("basis_r", C.c_int), ("basis_a", C.c_int), ("l_max_3b", C.c_int),
+                ("l_max_4b", C.c_int), ("l_max_5b", C.c_int), ("n_neuron", C.c_int),
+                ("rc_r", C.c_double), ("rc_a", C.c_double),
+                ("c_r", C.c_void_p), ("c_a", C.c_void_p), ("w0", C.c_void_p),
+                ("b0", C.c_void_p), ("w1", C.c_void_p), ("b1", C.c_double)]
+
+
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            lib.oracle_n_des.argtypes = [C.POINTER(_Model)]
+            lib.oracle_radial_basis.argtypes = [C.c_double, C.c_int, C.c_double, _dp]
+            lib.oracle_radial_basis.restype = None
+            lib.oracle_angular_polynomials.argtypes = [C.c_double, C.c_double, C.c_double, _dp]
+            lib.oracle_angular_polynomials.restype = None
+            lib.oracle_neighbor_counts.argtypes = [C.c_int, _dp, _dp, C.c_double, _ip]
+            lib.oracle_neighbors.argtypes = [C.c_int, _dp, _dp, C.c_double, C.c_int, C.c_int,
+                                             _ip, _ip, _dp]
+            lib.oracle_descriptors.argtypes = [C.POINTER(_Model), C.c_int, _dp, _ip, _dp, C.c_int,
+                                               C.c_void_p, _dp, C.c_int]
+            lib.oracle_ann.argtypes = [C.POINTER(_Model), _dp, C.POINTER(C.c_double)]
+            lib.oracle_compute.argtypes = [C.POINTER(_Model), C.c_int, _dp, _ip, _dp, C.c_int,
+                                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+            lib.oracle_md.argtypes = [C.POINTER(_Model), C.c_int, _dp, _dp, _ip, _dp, _dp, C.c_int,
+                                      C.c_double, C.c_void_p, C.c_void_p, C.c_int]
+            lib.oracle_max_threads.argtypes = []
+            _lib = lib
+    return _lib
+
+
+class _Bound:
+    """Keeps the numpy arrays alive while the C struct points at them."""
+
+    def __init__(self, model):
+        self.arrays = [np.ascontiguousarray(a, dtype=np.float64) for a in
+                       (model.c_radial, model.c_angular, model.w0, model.b0, model.w1)]
+        cr, ca, w0, b0, w1 = self.arrays
+        self.s = _Model(model.n_types, model.n_max_radial, model.n_max_angular, model.basis_radial,
+                        model.basis_angular, model.l_max_3b, model.l_max_4b, model.l_max_5b,
+                        model.n_neuron, model.rc_radial, model.rc_angular,
+                        cr.ctypes.data, ca.ctypes.data, w0.ctypes.data, b0.ctypes.data,
+                        w1.ctypes.data, float(model.b1))
+
+    def ref(self):
+        return C.byref(self.s)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a if shape is None else a.reshape(shape)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+def n_des(model) -> int:
+    b = _Bound(model)
+    return int(_load().oracle_n_des(b.ref()))
+
+
+def radial_basis(rc: float, K: int, r: float) -> np.ndarray:
+    out = np.zeros(K + 1)
+    _load().oracle_radial_basis(float(rc), int(K), float(r), out)
+    return out
+
+
+def angular_polynomials(d) -> np.ndarray:
+    out = np.zeros(24)
+    _load().oracle_angular_polynomials(float(d[0]), float(d[1]), float(d[2]), out)
+    return out
+
+
+def neighbor_counts(pos, box, rc) -> np.ndarray:
+    pos = _f64(pos, (-1, 3))
+    out = np.zeros(pos.shape[0], np.int32)
+    rc_ = _load().oracle_neighbor_counts(pos.shape[0], pos, _f64(box, (3, 3)), float(rc), out)
+    if rc_ != 0:
+        raise ValueError("oracle_neighbor_counts failed")
+    return out
+
+
+def neighbors(pos, box, rc, i, cap=4096):
+    """(j [M], n [M, 3], d [M, 3]) of atom i within rc, brute force over all images."""
+    pos = _f64(pos, (-1, 3))
+    j = np.zeros(cap, np.int32)
+    n = np.zeros(cap * 3, np.int32)
+    d = np.zeros(cap * 3)
+    cnt = _load().oracle_neighbors(pos.shape[0], pos, _f64(box, (3, 3)), float(rc), int(i), cap, j, n, d)
+    if cnt < 0 or cnt > cap:
+        raise ValueError("oracle_neighbors failed")
+    return j[:cnt].copy(), n[:cnt * 3].reshape(-1, 3).copy(), d[:cnt * 3].reshape(-1, 3).copy()
+
+
+def descriptors(model, pos, types, box, sel=None, n_threads=0) -> np.ndarray:
+    """Descriptor vectors q^i [n_sel, N_des] (all atoms when sel is None)."""
+    pos = _f64(pos, (-1, 3))
+    types = _i32(types)
+    b = _Bound(model)
+    D = model.n_des
+    sel_a = None if sel is None else _i32(sel)
+    ns = pos.shape[0] if sel is None else sel_a.shape[0]
+    out = np.zeros((ns, D))
+    rc = _load().oracle_descriptors(b.ref(), pos.shape[0], pos, types, _f64(box, (3, 3)), ns,
+                                    _ptr(sel_a), out, int(n_threads))
+    if rc != 0:
+        raise ValueError("oracle_descriptors failed")
+    return out
+
+
+def site_energy(model, q) -> float:
+    b = _Bound(model)
+    out = C.c_double(0.0)
+    if _load().oracle_ann(b.ref(), _f64(q), C.byref(out)) != 0:
+        raise ValueError("oracle_ann failed")
+    return float(out.value)
+
+
+def compute(model, pos, types, box, sel=None, n_threads=0):
+    """Site energies U [n_sel], forces F [n_sel, 3] and per-atom virials W [n_sel, 9]
+    (xx, yy, zz, xy, xz, yz, yx, zx, zy) of the selected atoms (all when sel is None)."""
+    pos = _f64(pos, (-1, 3))
+    types = _i32(types)
+    b = _Bound(model)
+    sel_a = None if sel is None else _i32(sel)
+    ns = pos.shape[0] if sel is None else sel_a.shape[0]
+    U = np.zeros(ns)
+    F = np.zeros((ns, 3))
+    W = np.zeros((ns, 9))
+    rc = _load().oracle_compute(b.ref(), pos.shape[0], pos, types, _f64(box, (3, 3)), ns, _ptr(sel_a),
+                                U.ctypes.data, F.ctypes.data, W.ctypes.data, int(n_threads))
+    if rc != 0:
+        raise ValueError("oracle_compute failed")
+    return U, F, W
+
+
+def energy(model, pos, types, box, n_threads=0) -> float:
+    U, _, _ = compute(model, pos, types, box, n_threads=n_threads)
+    return float(np.sum(U))
+
+
+def md(model, pos, vel, types, box, n_steps, dt, n_threads=0):
+    """Velocity-Verlet NVE run. Returns (pos, vel, thermo [n_steps+1, 3] = (E_pot, E_kin, T),
+    final forces [N, 3])."""
+    pos = _f64(pos, (-1, 3)).copy()
+    vel = _f64(vel, (-1, 3)).copy()
+    types = _i32(types)
+    b = _Bound(model)
+    thermo = np.zeros((n_steps + 1, 3))
+    F = np.zeros_like(pos)
+    mass = _f64(model.mass)
+    rc = _load().oracle_md(b.ref(), pos.shape[0], pos, vel, types, mass, _f64(box, (3, 3)), int(n_steps),
+                           float(dt), thermo.ctypes.data, F.ctypes.data, int(n_threads))
+    if rc != 0:
+        raise ValueError("oracle_md failed")
+    return pos, vel, thermo, F
