@@ -1,0 +1,193 @@
+/*
+ * libnep: GB300 (sm_103a) evaluation of the NEP3 machine-learned potential of
+ * arXiv:2205.10046 (energy, forces, virials) and a velocity-Verlet NVE driver.
+ *
+ * What the library computes (all of it in its own CUDA kernels):
+ *   - cell-list neighbour search into a radial list (r < r_c^R + skin) and an angular
+ *     list (r < r_c^A + skin), all periodic images included (the quantities NN_i^R,
+ *     NN_i^A, NL_im^R, NL_im^A listed at the start of Appendix B);
+ *   - the radial descriptor of Eq. qin with the Chebyshev radial functions of Eqs. g_n
+ *     and f_n and per-ordered-type-pair coefficients c_nk^{t_i t_j} (Sec. II B);
+ *   - the angular sums S_{n,k} of Eq. S_nk and the 3-body (q_nl, l <= 4), 4-body (q_n222)
+ *     and 5-body (q_n1111) components with the pre-computed coefficients of Sec. II D;
+ *   - the single-hidden-layer tanh network of Eq. Ui and its gradient dU_i/dq;
+ *   - the partial forces of Eq. partial_force, gathered into F_i (Eqs. F_ij, F_i) and
+ *     the per-atom virial W_i (Eq. virial) without atomics;
+ *   - a velocity-Verlet NVE step (the NVE ensemble named in Sec. III A).
+ *
+ * Units: Angstrom, fs, eV, atomic mass unit, K.
+ * Conventions:
+ *   positions  [N][3] FP64, any values (they are wrapped into the cell internally);
+ *   cell       `box` [3][3] FP64, ROWS are the cell vectors a, b, c; r = s . box for
+ *              fractional s; any right- or left-handed non-degenerate cell;
+ *   types      [N] int32 in [0, n_types);
+ *   forces     [N][3] FP64;
+ *   virials    [N][9] FP64 in the order xx, yy, zz, xy, xz, yz, yx, zx, zy with
+ *              W_i[a][b] = sum_j (r_j - r_i)_a (dU_j/dr_ji)_b (Eq. virial); the total
+ *              is -(dE/d eps)^T for an affine strain r -> (I + eps) r;
+ *   energies   per-atom site energies U_i and their FP64 sum.
+ * Arithmetic: pair vectors, descriptors, network and partial forces in FP32; positions,
+ * velocities, integration and the energy/virial totals in FP64 (the mixed precision
+ * of Sec. II G: FP64 inputs/outputs, FP32 internals).
+ *
+ * Descriptor layout (the paper fixes the components, not their order):
+ *   q = [ q_n (n = 0..n_R) | q_n1 (n = 0..n_A) | q_n2 | q_n3 | q_n4 | q_n222 | q_n1111 ].
+ *
+ * Errors: every call returns NEP_OK (0) or a negative NEP_ERR_* code; nothing throws
+ * across the ABI. nep_last_error() gives a message for the last failed call on a handle.
+ * A handle is not thread-safe: serialise calls that share one.
+ */
+#ifndef NEP_H
+#define NEP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NEP_OK 0
+#define NEP_ERR_ARG (-1)               /* invalid argument (null pointer, bad size, bad type) */
+#define NEP_ERR_OOM (-2)               /* device allocation failed */
+#define NEP_ERR_CUDA (-3)              /* a CUDA runtime call failed */
+#define NEP_ERR_NEIGHBOR_OVERFLOW (-4) /* an atom has more neighbours than the list can hold */
+#define NEP_ERR_NONFINITE (-5)         /* non-finite position, force or energy */
+#define NEP_ERR_UNSUPPORTED (-6)       /* hyper-parameters without a compiled kernel, or a cell
+                                          thinner than a third of the list radius */
+#define NEP_ERR_STATE (-7)             /* call out of order (e.g. md_run before md_init) */
+
+#define NEP_MAX_TYPES 8
+
+/* Opaque library state: model, device workspace, neighbour lists, MD state. */
+typedef struct nep_handle nep_handle;
+
+/* Stream type without pulling in the CUDA headers: pass a cudaStream_t (0 = legacy
+ * default stream). */
+typedef void *nep_stream_t;
+
+/* Model hyper-parameters and weights (the nep.in keywords of Sec. III A plus the
+ * trained parameters). All pointers are HOST pointers; nep_create copies everything,
+ * the caller keeps ownership. */
+typedef struct {
+  int version;          /* must be 3 (NEP3) */
+  int n_types;          /* 1..NEP_MAX_TYPES */
+  double rc_radial;     /* r_c^R > 0 (Angstrom) */
+  double rc_angular;    /* 0 < r_c^A <= r_c^R */
+  int n_max_radial;     /* n_max^R >= 0 */
+  int n_max_angular;    /* n_max^A >= 0 */
+  int basis_radial;     /* N_bas^R >= 0 (K_R + 1 Chebyshev functions) */
+  int basis_angular;    /* N_bas^A >= 0 */
+  int l_max_3b;         /* 1..4 */
+  int l_max_4b;         /* 0 (off) or 2 (q_n222; l = 1 and l = 3 vanish, Sec. II D) */
+  int l_max_5b;         /* 0 (off) or 1 (q_n1111) */
+  int n_neuron;         /* N_neu >= 1 */
+  const double *c_radial;  /* [T][T][n_max_radial+1][basis_radial+1], ordered (t_i, t_j) */
+  const double *c_angular; /* [T][T][n_max_angular+1][basis_angular+1] */
+  const double *w0;        /* [n_neuron][N_des], neuron-major (w^(0)_{mu nu} of Eq. Ui) */
+  const double *b0;        /* [n_neuron] */
+  const double *w1;        /* [n_neuron] */
+  double b1;
+  const double *mass;      /* [T] in u; needed by md_* only (may be NULL otherwise) */
+  double skin;             /* neighbour-list skin in Angstrom; <= 0 selects 1.0 */
+} nep_params;
+
+/* Create a handle for one model. Validates the parameters (NEP_ERR_ARG) and checks that
+ * a kernel is compiled for (n_max^R, N_bas^R, n_max^A, N_bas^A, N_neu, l_max's)
+ * (NEP_ERR_UNSUPPORTED otherwise; nep_supported() lists them). Allocates nothing on
+ * the device until the first compute or md_init. Uses the current CUDA device. */
+int nep_create(const nep_params *params, nep_handle **out);
+
+/* Release the handle and all device memory it owns. NULL is accepted. */
+int nep_destroy(nep_handle *h);
+
+/* Message for the last failed call on h (or for the last failed nep_create when h is NULL).
+ * Valid until the next call on the handle. */
+const char *nep_last_error(const nep_handle *h);
+
+/* One NEP3 evaluation (Sec. II; the four-kernel scheme of Sec. II G / Appendix B,
+ * re-organised for GB300: neighbour build, one fused per-atom kernel for descriptor,
+ * network and angular partial forces, one gather kernel for F and W).
+ * DEVICE pointers, stream-ordered on `stream`: pos [N][3], types [N]; outputs
+ * energy [N] (or NULL), energy_total [1] (or NULL), force [N][3] (required),
+ * virial [N][9] (or NULL), virial_total [9] (or NULL). `box` is a HOST pointer [3][3].
+ * The neighbour lists are rebuilt on every call. The call synchronises `stream` once
+ * (to size the neighbour lists) and returns with the kernels queued on `stream`.
+ * n_atoms == 0 is valid and writes zero totals. The library owns its workspace. */
+int nep_compute(nep_handle *h, int n_atoms, const double *pos, const int *types, const double *box,
+                double *energy, double *energy_total, double *force, double *virial,
+                double *virial_total, nep_stream_t stream);
+
+/* nep_compute with HOST pointers for every array (synchronous; copies in and out). */
+int nep_compute_host(nep_handle *h, int n_atoms, const double *pos, const int *types, const double *box,
+                     double *energy, double *energy_total, double *force, double *virial,
+                     double *virial_total);
+
+/* Descriptor vectors q^i (Eqs. qin and S_nk with the explicit components of Sec. II D)
+ * into q [N][N_des] FP64 (DEVICE pointers, as nep_compute). */
+int nep_descriptors(nep_handle *h, int n_atoms, const double *pos, const int *types, const double *box,
+                    double *q, nep_stream_t stream);
+
+/* Descriptor length N_des of the handle's model (Sec. II D). */
+int nep_n_des(const nep_handle *h);
+
+/* Load an MD state (DEVICE pointers): positions [N][3], types [N], velocities [N][3]
+ * (Angstrom/fs; NULL = zero) and the HOST cell [3][3]. Builds the neighbour lists and
+ * the initial forces. The state then stays on the device. Needs params->mass. */
+int md_init(nep_handle *h, int n_atoms, const double *pos, const int *types, const double *box,
+            const double *vel, nep_stream_t stream);
+
+/* md_init from HOST arrays (synchronous). */
+int md_init_host(nep_handle *h, int n_atoms, const double *pos, const int *types, const double *box,
+                 const double *vel);
+
+/* Advance n_steps velocity-Verlet NVE steps of dt_fs: v += dt/2 F/m; x += dt v;
+ * [neighbour rebuild when an atom moved more than skin/2 since the last build];
+ * F = F(x); v += dt/2 F/m. Every `thermo_every` steps (>= 1) one row of `thermo`
+ * (DEVICE pointer, or NULL) receives {E_pot, E_kin, T, P} in eV, eV, K, GPa for the
+ * state after that step (row r = step (r+1)*thermo_every of this call); thermo must hold
+ * n_steps / thermo_every rows of 4 doubles. Each step replays one captured CUDA graph.
+ * Returns NEP_ERR_NEIGHBOR_OVERFLOW if a rebuild found more neighbours than the lists
+ * hold (the state is then unusable; call md_init again). */
+int md_run(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *thermo, nep_stream_t stream);
+
+/* Copy the MD state out (DEVICE pointers; any may be NULL): positions wrapped into the
+ * cell [N][3], velocities [N][3], forces of the current positions [N][3]. */
+int md_get_state(nep_handle *h, double *pos, double *vel, double *force, nep_stream_t stream);
+
+/* md_get_state into HOST arrays (synchronous). */
+int md_get_state_host(nep_handle *h, double *pos, double *vel, double *force);
+
+/* Statistics of the last neighbour build and of the MD run so far. */
+typedef struct {
+  int n_atoms;
+  int cap_radial, cap_angular;   /* list capacity per atom */
+  int max_radial, max_angular;   /* largest list length at the last build */
+  double mean_radial, mean_angular;            /* mean list length (r < r_c + skin) */
+  double mean_radial_in_rc, mean_angular_in_rc; /* mean count with r < r_c (last build) */
+  long long n_rebuilds;          /* neighbour rebuilds since md_init */
+  long long md_steps;            /* MD steps since md_init */
+  int cells[3];                  /* cell grid */
+} nep_stats;
+
+int nep_get_stats(nep_handle *h, nep_stats *out);
+
+/* Kernel timing for roofline reports. When enabled, md_run and nep_compute record CUDA
+ * events around each library kernel on the launching stream. nep_kernel_times returns,
+ * for the most recent call, the device time in ms of each kernel slot (names via
+ * nep_kernel_name; slots that did not run report 0). */
+int nep_set_profiling(nep_handle *h, int enable);
+int nep_kernel_slots(void);
+const char *nep_kernel_name(int slot);
+int nep_kernel_times(nep_handle *h, float *ms_out, int n_slots);
+
+/* Compiled hyper-parameter shapes: writes up to `max` rows of 8 ints
+ * (n_max^R, N_bas^R, n_max^A, N_bas^A, N_neu, l_max^3b, l_max^4b, l_max^5b) and
+ * returns the number of shapes. */
+int nep_supported(int *shapes, int max);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NEP_H */

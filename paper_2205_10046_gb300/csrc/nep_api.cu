@@ -1,0 +1,814 @@
+// libnep C ABI (include/nep.h): handle management, validation, device workspace,
+// neighbour-list sizing, the compute pipeline and the captured MD step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/nep.h"
+#include "nep_internal.cuh"
+
+namespace nep {
+void launch_rebuild(int N, int T, const Grid &g, const float4 *dtab, float rlR2, float rlA2, int cap_r, int cap_a,
+                    int count_only, double *x, double *x_ref, double *origin, const int *types, float4 *pos4,
+                    int *cell_of, int *cell_count, int *cell_cursor, int *cell_start, int *cell_atoms,
+                    unsigned *nl_r, int *nn_r, unsigned *nl_a, int *nn_a, int *rev_a, BuildStatus *st,
+                    cudaStream_t s);
+void launch_drift(int N, double *x, double *v, const double *F, float4 *pos4, const double *x_ref,
+                  const double *origin, const double *inv_mass_kappa, double dt, double half_skin2, BuildStatus *st,
+                  cudaStream_t s);
+void launch_wrap(int N, const double *x, const Grid &g, double *out, cudaStream_t s);
+void launch_finalize(int nb_atom, const double *partial_atom, int nb_gather, const double *partial_gather,
+                     double *energy_total, double *virial_total, double *thermo_stage, int *thermo_ctl, int N,
+                     double volume, cudaStream_t s);
+const ShapeOps *shape_si();
+const ShapeOps *shape_pbte();
+const ShapeOps *shape_mixed();
+
+int shape_count() { return 3; }
+const ShapeOps *shape_at(int i) {
+  switch (i) {
+    case 0: return shape_si();
+    case 1: return shape_pbte();
+    case 2: return shape_mixed();
+    default: return nullptr;
+  }
+}
+}  // namespace nep
+
+using namespace nep;
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+// 1 u * A^2 / fs^2 in eV from the CODATA 2018 atomic mass unit and elementary charge.
+const double kKappa = 1.66053906660e-27 * 1e-20 / 1e-30 / 1.602176634e-19;
+
+enum Slot { SLOT_DRIFT = 0, SLOT_REBUILD, SLOT_ATOM, SLOT_GATHER, SLOT_FINAL, N_SLOTS };
+const char *kSlotNames[N_SLOTS] = {"md_drift", "neighbor_rebuild", "nep_atom", "nep_gather", "finalize"};
+
+std::string g_create_error;
+
+template <class Tp>
+struct DevBuf {
+  Tp *p = nullptr;
+  size_t n = 0;
+  cudaError_t ensure(size_t want) {
+    if (want <= n && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    if (want == 0) want = 1;
+    cudaError_t e = cudaMalloc(&p, want * sizeof(Tp));
+    if (e == cudaSuccess) n = want;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+// The paper's 3-body (C3b), 4-body (C4b) and 5-body (C5b) coefficients (Sec. II D),
+// evaluated here from the printed expressions.
+void model_constants(ModelF &m) {
+  const double p = kPi;
+  const double c3[24] = {3.0 / (4 * p), 3.0 / (4 * p), 3.0 / (4 * p),
+                         5.0 / (16 * p), 15.0 / (4 * p), 15.0 / (4 * p), 15.0 / (16 * p), 15.0 / (16 * p),
+                         7.0 / (16 * p), 21.0 / (32 * p), 21.0 / (32 * p), 105.0 / (16 * p), 105.0 / (16 * p),
+                         35.0 / (32 * p), 35.0 / (32 * p),
+                         9.0 / (256 * p), 45.0 / (32 * p), 45.0 / (32 * p), 45.0 / (64 * p), 45.0 / (64 * p),
+                         315.0 / (32 * p), 315.0 / (32 * p), 315.0 / (256 * p), 315.0 / (256 * p)};
+  for (int k = 0; k < 24; ++k) m.c3b[k] = (float)c3[k];
+  const double y20 = 0.25 * std::sqrt(5.0 / p), y21 = 0.5 * std::sqrt(7.5 / p), y22 = 0.25 * std::sqrt(7.5 / p);
+  m.c4b[0] = (float)(-std::sqrt(2.0 / 35.0) * y20 * y20 * y20);
+  m.c4b[1] = (float)(-6.0 * std::sqrt(1.0 / 70.0) * y20 * y21 * y21);
+  m.c4b[2] = (float)(6.0 * std::sqrt(2.0 / 35.0) * y20 * y22 * y22);
+  m.c4b[3] = (float)(6.0 * std::sqrt(3.0 / 35.0) * y21 * y21 * y22);
+  m.c4b[4] = (float)(-12.0 * std::sqrt(3.0 / 35.0) * y21 * y21 * y22);
+  m.c5b[0] = (float)(21.0 / (80.0 * p * p));
+  m.c5b[1] = (float)(21.0 / (40.0 * p * p));
+  m.c5b[2] = (float)(21.0 / (80.0 * p * p));
+}
+
+}  // namespace
+
+struct nep_handle {
+  // model
+  int T = 0, nR = 0, nA = 0, KR = 0, KA = 0, L3 = 0, L4 = 0, L5 = 0, H = 0, n_des = 0;
+  double rcR = 0, rcA = 0, skin = 1.0;
+  std::vector<float> w0, b0, w1, cR, cA;
+  float b1 = 0;
+  std::vector<double> mass;
+  ModelF mf;
+  const ShapeOps *ops = nullptr;
+  int device = 0;
+  std::string err;
+  // device model copies
+  DevBuf<float> d_cR, d_cA;
+  DevBuf<double> d_inv_mk, d_mk_half;
+  // workspace
+  int N = 0;
+  int cap_r = 0, cap_a = 0;
+  Grid grid;
+  double volume = 0;
+  DevBuf<double> x, v, F, x_ref, origin, partial_atom, partial_gather, thermo_stage;
+  DevBuf<int> types, cell_of, cell_count, cell_cursor, cell_start, cell_atoms, nn_r, nn_a, rev_a, thermo_ctl;
+  DevBuf<unsigned> nl_r, nl_a;
+  DevBuf<float4> pos4, dtab, p_ang;
+  DevBuf<float> e_rad;
+  DevBuf<BuildStatus> status;
+  BuildStatus *h_status = nullptr;  // pinned mirror
+  // md
+  bool md_ready = false;
+  cudaGraphExec_t graph = nullptr;
+  double graph_dt = 0;
+  bool graph_prof = false;
+  const double *graph_thermo = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  // profiling
+  bool prof = false;
+  cudaEvent_t ev[N_SLOTS][2] = {};
+  bool slot_ran[N_SLOTS] = {};
+  nep_stats stats_cache{};
+};
+
+namespace {
+
+int fail(nep_handle *h, int code, const std::string &msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(nep_handle *h, cudaError_t e, const char *where) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(h, NEP_ERR_OOM, std::string(where) + ": out of device memory");
+  }
+  return fail(h, NEP_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                  \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
+  } while (0)
+
+void ev_record(nep_handle *h, int slot, int which, cudaStream_t s, bool capturing) {
+  if (!h->prof) return;
+  if (capturing) cudaEventRecordWithFlags(h->ev[slot][which], s, cudaEventRecordExternal);
+  else cudaEventRecord(h->ev[slot][which], s);
+  if (which == 1) h->slot_ran[slot] = true;
+}
+
+bool mat_inverse(const double H[3][3], double Hinv[3][3], double *det_out) {
+  double cof[3][3];
+  cof[0][0] = H[1][1] * H[2][2] - H[1][2] * H[2][1];
+  cof[0][1] = H[1][2] * H[2][0] - H[1][0] * H[2][2];
+  cof[0][2] = H[1][0] * H[2][1] - H[1][1] * H[2][0];
+  cof[1][0] = H[2][1] * H[0][2] - H[2][2] * H[0][1];
+  cof[1][1] = H[2][2] * H[0][0] - H[2][0] * H[0][2];
+  cof[1][2] = H[2][0] * H[0][1] - H[2][1] * H[0][0];
+  cof[2][0] = H[0][1] * H[1][2] - H[0][2] * H[1][1];
+  cof[2][1] = H[0][2] * H[1][0] - H[0][0] * H[1][2];
+  cof[2][2] = H[0][0] * H[1][1] - H[0][1] * H[1][0];
+  const double det = H[0][0] * cof[0][0] + H[0][1] * cof[0][1] + H[0][2] * cof[0][2];
+  if (!(std::fabs(det) > 1e-12) || !std::isfinite(det)) return false;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) Hinv[a][b] = cof[b][a] / det;
+  *det_out = det;
+  return true;
+}
+
+// Cell grid, image range and shift table for a cell `box` and list radius rc_list.
+int setup_grid(nep_handle *h, int N, const double *box, std::vector<float4> &dtab) {
+  Grid &g = h->grid;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) g.H[a][b] = box[3 * a + b];
+  double det;
+  if (!mat_inverse(g.H, g.Hinv, &det)) return fail(h, NEP_ERR_ARG, "box is singular or non-finite");
+  h->volume = std::fabs(det);
+  const double rl = h->rcR + h->skin;
+  double th[3];
+  for (int a = 0; a < 3; ++a) {
+    // face distance along axis a: |det| / |row b x row c| = 1 / |column a of Hinv|
+    const double n = std::sqrt(g.Hinv[0][a] * g.Hinv[0][a] + g.Hinv[1][a] * g.Hinv[1][a] + g.Hinv[2][a] * g.Hinv[2][a]);
+    th[a] = 1.0 / n;
+    g.nc[a] = std::max(1, (int)std::floor(th[a] / rl));
+  }
+  // keep the grid no larger than about 4 cells per atom (coarser cells stay valid)
+  const long long limit = std::max<long long>(64, 4LL * N);
+  while ((long long)g.nc[0] * g.nc[1] * g.nc[2] > limit) {
+    int a = 0;
+    for (int b = 1; b < 3; ++b)
+      if (g.nc[b] > g.nc[a]) a = b;
+    g.nc[a] = std::max(1, g.nc[a] / 2);
+  }
+  int rmax = 0;
+  for (int a = 0; a < 3; ++a) {
+    g.R[a] = (int)std::ceil(rl * g.nc[a] / th[a] - 1e-12);
+    if (g.R[a] < 1) g.R[a] = 1;
+    rmax = std::max(rmax, g.R[a]);
+  }
+  if (rmax > kMaxImage)
+    return fail(h, NEP_ERR_UNSUPPORTED,
+                "cell thinner than a third of r_c^R + skin; replicate the cell before calling");
+  g.ncell = g.nc[0] * g.nc[1] * g.nc[2];
+  g.obits = rmax <= 1 ? 2 : 3;
+  int jb = 1;
+  while ((1LL << jb) < (long long)std::max(N, 2)) ++jb;
+  if (jb + 3 * g.obits > 32) return fail(h, NEP_ERR_UNSUPPORTED, "too many atoms for the packed neighbour entries");
+  g.jbits = jb;
+  g.jmask = (jb >= 32) ? 0xffffffffu : ((1u << jb) - 1u);
+  g.ncode = 1 << (3 * g.obits);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) g.Hc[a][b] = g.H[a][b] / g.nc[a];
+  dtab.assign(g.ncode, make_float4(0.f, 0.f, 0.f, 0.f));
+  for (int ox = -g.R[0]; ox <= g.R[0]; ++ox)
+    for (int oy = -g.R[1]; oy <= g.R[1]; ++oy)
+      for (int oz = -g.R[2]; oz <= g.R[2]; ++oz) {
+        const unsigned code = (unsigned)(ox + g.R[0]) | ((unsigned)(oy + g.R[1]) << g.obits) |
+                              ((unsigned)(oz + g.R[2]) << (2 * g.obits));
+        double D[3];
+        for (int b = 0; b < 3; ++b) D[b] = ox * g.Hc[0][b] + oy * g.Hc[1][b] + oz * g.Hc[2][b];
+        dtab[code] = make_float4((float)D[0], (float)D[1], (float)D[2], 0.f);
+      }
+  return NEP_OK;
+}
+
+int ensure_atoms(nep_handle *h, int N) {
+  const size_t n = (size_t)std::max(N, 1);
+  CK(h->x.ensure(3 * n), "alloc");
+  CK(h->v.ensure(3 * n), "alloc");
+  CK(h->F.ensure(3 * n), "alloc");
+  CK(h->x_ref.ensure(3 * n), "alloc");
+  CK(h->origin.ensure(3 * n), "alloc");
+  CK(h->types.ensure(n), "alloc");
+  CK(h->cell_of.ensure(n), "alloc");
+  CK(h->cell_atoms.ensure(n), "alloc");
+  CK(h->pos4.ensure(n), "alloc");
+  CK(h->nn_r.ensure(n * h->T), "alloc");
+  CK(h->nn_a.ensure(n), "alloc");
+  CK(h->e_rad.ensure(n * h->T * (size_t)(((h->KR + 2) + 3) / 4 * 4)), "alloc");
+  CK(h->partial_atom.ensure(h->ops->atom_blocks(N) + 1), "alloc");
+  CK(h->partial_gather.ensure((size_t)(h->ops->gather_blocks(N) + 1) * kReduceSlots), "alloc");
+  CK(h->status.ensure(1), "alloc");
+  CK(h->thermo_ctl.ensure(4), "alloc");
+  return NEP_OK;
+}
+
+int ensure_lists(nep_handle *h, int N, int cap_r, int cap_a) {
+  const size_t n = (size_t)std::max(N, 1);
+  CK(h->nl_r.ensure(n * cap_r), "alloc lists");
+  CK(h->nl_a.ensure(n * cap_a), "alloc lists");
+  CK(h->rev_a.ensure(n * cap_a), "alloc lists");
+  CK(h->p_ang.ensure(n * cap_a), "alloc lists");
+  h->cap_r = cap_r;
+  h->cap_a = cap_a;
+  return NEP_OK;
+}
+
+int read_status(nep_handle *h, cudaStream_t s) {
+  CK(cudaMemcpyAsync(h->h_status, h->status.p, sizeof(BuildStatus), cudaMemcpyDeviceToHost, s), "status");
+  CK(cudaStreamSynchronize(s), "sync");
+  return NEP_OK;
+}
+
+void reset_status_counts(nep_handle *h) {
+  h->h_status->overflow = 0;
+  h->h_status->max_r = 0;
+  h->h_status->max_a = 0;
+  h->h_status->rev_missing = 0;
+  h->h_status->sum_r = 0;
+  h->h_status->sum_a = 0;
+  h->h_status->bad_input = 0;
+}
+
+int round_cap(int m) { return std::min(kListBuf, ((m * 5) / 4 + 8 + 3) / 4 * 4); }
+
+// Bin, size and build the neighbour lists for the positions in h->x (forced rebuild).
+int rebuild_lists(nep_handle *h, int N, cudaStream_t s) {
+  Grid &g = h->grid;
+  CK(h->cell_count.ensure(g.ncell + 1), "alloc cells");
+  CK(h->cell_cursor.ensure(g.ncell + 1), "alloc cells");
+  CK(h->cell_start.ensure(g.ncell + 1), "alloc cells");
+  const float rlR = (float)(h->rcR + h->skin), rlA = (float)(h->rcA + h->skin);
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    const bool count_only = (h->cap_r == 0 || h->cap_a == 0);
+    CK(cudaMemcpyAsync(h->h_status, h->status.p, sizeof(BuildStatus), cudaMemcpyDeviceToHost, s), "status");
+    CK(cudaStreamSynchronize(s), "sync");
+    reset_status_counts(h);
+    h->h_status->rebuild = 1;
+    CK(cudaMemcpyAsync(h->status.p, h->h_status, sizeof(BuildStatus), cudaMemcpyHostToDevice, s), "status");
+    launch_rebuild(N, h->T, g, h->dtab.p, rlR * rlR, rlA * rlA, h->cap_r, h->cap_a, count_only ? 1 : 0, h->x.p,
+                   h->x_ref.p, h->origin.p, h->types.p, h->pos4.p, h->cell_of.p, h->cell_count.p, h->cell_cursor.p,
+                   h->cell_start.p, h->cell_atoms.p, h->nl_r.p, h->nn_r.p, h->nl_a.p, h->nn_a.p, h->rev_a.p,
+                   h->status.p, s);
+    CK(cudaGetLastError(), "launch rebuild");
+    int rc = read_status(h, s);
+    if (rc) return rc;
+    const BuildStatus &st = *h->h_status;
+    if (st.bad_input & 1) return fail(h, NEP_ERR_ARG, "atom type out of range");
+    if (st.bad_input & 2) return fail(h, NEP_ERR_NONFINITE, "non-finite position");
+    if (st.max_r > kListBuf || st.max_a > kListBuf)
+      return fail(h, NEP_ERR_NEIGHBOR_OVERFLOW, "more than " + std::to_string(kListBuf) +
+                                                    " neighbours within r_c + skin for one atom");
+    if (count_only || st.overflow) {
+      rc = ensure_lists(h, N, round_cap(std::max(1, st.max_r)), round_cap(std::max(1, st.max_a)));
+      if (rc) return rc;
+      continue;
+    }
+    if (st.rev_missing) return fail(h, NEP_ERR_CUDA, "angular neighbour list is not symmetric");
+    h->stats_cache.max_radial = st.max_r;
+    h->stats_cache.max_angular = st.max_a;
+    h->stats_cache.mean_radial = N ? (double)st.sum_r / N : 0.0;
+    h->stats_cache.mean_angular = N ? (double)st.sum_a / N : 0.0;
+    return NEP_OK;
+  }
+  return fail(h, NEP_ERR_NEIGHBOR_OVERFLOW, "neighbour lists could not be sized");
+}
+
+AtomArgs make_args(nep_handle *h, int N) {
+  AtomArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.N = N;
+  a.T = h->T;
+  a.jbits = h->grid.jbits;
+  a.jmask = h->grid.jmask;
+  a.ncode = h->grid.ncode;
+  a.rcR = (float)h->rcR;
+  a.rcA = (float)h->rcA;
+  a.pos4 = h->pos4.p;
+  a.dtab = h->dtab.p;
+  a.nl_r = h->nl_r.p;
+  a.nn_r = h->nn_r.p;
+  a.nl_a = h->nl_a.p;
+  a.nn_a = h->nn_a.p;
+  a.rev_a = h->rev_a.p;
+  a.c_r = h->d_cR.p;
+  a.c_a = h->d_cA.p;
+  a.e_rad = h->e_rad.p;
+  a.est = ((h->KR + 2) + 3) / 4 * 4;
+  a.p_ang = h->p_ang.p;
+  a.partial_atom = h->partial_atom.p;
+  a.partial_gather = h->partial_gather.p;
+  a.inv_mass_kappa = h->d_inv_mk.p;
+  a.mass_kappa_half = h->d_mk_half.p;
+  a.vel = h->v.p;
+  return a;
+}
+
+// Load positions (device, [N][3]) and types, set up the grid and build the lists.
+int load_structure(nep_handle *h, int N, const double *pos, const int *types, const double *box, cudaStream_t s) {
+  int rc = ensure_atoms(h, N);
+  if (rc) return rc;
+  std::vector<float4> dtab;
+  rc = setup_grid(h, N, box, dtab);
+  if (rc) return rc;
+  CK(h->dtab.ensure(dtab.size()), "alloc");
+  CK(cudaMemcpyAsync(h->dtab.p, dtab.data(), dtab.size() * sizeof(float4), cudaMemcpyHostToDevice, s), "copy");
+  CK(cudaMemcpyAsync(h->x.p, pos, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s), "copy pos");
+  CK(cudaMemcpyAsync(h->types.p, types, sizeof(int) * N, cudaMemcpyDeviceToDevice, s), "copy types");
+  h->N = N;
+  h->stats_cache.n_atoms = N;
+  for (int a = 0; a < 3; ++a) h->stats_cache.cells[a] = h->grid.nc[a];
+  return rebuild_lists(h, N, s);
+}
+
+int run_forces(nep_handle *h, int N, double *energy, double *force, double *virial, int md_kick, double half_dt,
+               cudaStream_t s, bool capturing) {
+  AtomArgs a = make_args(h, N);
+  a.energy = energy;
+  a.force = force;
+  a.virial = virial;
+  a.md_kick = md_kick;
+  a.half_dt = half_dt;
+  ev_record(h, SLOT_ATOM, 0, s, capturing);
+  cudaError_t e = h->ops->atom(a, h->mf, h->w0.data(), h->b0.data(), h->w1.data(), h->b1, 0, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "nep_atom kernel");
+  ev_record(h, SLOT_ATOM, 1, s, capturing);
+  ev_record(h, SLOT_GATHER, 0, s, capturing);
+  e = h->ops->gather(a, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "nep_gather kernel");
+  ev_record(h, SLOT_GATHER, 1, s, capturing);
+  return NEP_OK;
+}
+
+bool valid_handle(const nep_handle *h) { return h && h->ops; }
+
+}  // namespace
+
+// ======================================================================== C ABI
+extern "C" {
+
+int nep_supported(int *shapes, int max) {
+  const int n = shape_count();
+  for (int i = 0; i < n && i < max && shapes; ++i) {
+    const ShapeOps *o = shape_at(i);
+    int *r = shapes + 8 * i;
+    r[0] = o->nR; r[1] = o->KR; r[2] = o->nA; r[3] = o->KA; r[4] = o->H; r[5] = o->L3; r[6] = o->L4; r[7] = o->L5;
+  }
+  return n;
+}
+
+int nep_create(const nep_params *p, nep_handle **out) {
+  if (!out) return fail(nullptr, NEP_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (!p) return fail(nullptr, NEP_ERR_ARG, "params is null");
+  if (p->version != 3) return fail(nullptr, NEP_ERR_ARG, "version must be 3");
+  if (p->n_types < 1 || p->n_types > NEP_MAX_TYPES) return fail(nullptr, NEP_ERR_ARG, "n_types out of range");
+  if (!(p->rc_radial > 0) || !(p->rc_angular > 0) || p->rc_angular > p->rc_radial || !std::isfinite(p->rc_radial))
+    return fail(nullptr, NEP_ERR_ARG, "need 0 < rc_angular <= rc_radial");
+  if (p->n_max_radial < 0 || p->n_max_angular < 0 || p->basis_radial < 0 || p->basis_angular < 0 || p->n_neuron < 1)
+    return fail(nullptr, NEP_ERR_ARG, "negative size");
+  if (p->l_max_3b < 1 || p->l_max_3b > 4 || !(p->l_max_4b == 0 || p->l_max_4b == 2) ||
+      !(p->l_max_5b == 0 || p->l_max_5b == 1))
+    return fail(nullptr, NEP_ERR_ARG, "need l_max_3b in 1..4, l_max_4b in {0,2}, l_max_5b in {0,1}");
+  if (!p->c_radial || !p->c_angular || !p->w0 || !p->b0 || !p->w1)
+    return fail(nullptr, NEP_ERR_ARG, "null weight pointer");
+  const ShapeOps *ops = nullptr;
+  for (int i = 0; i < shape_count(); ++i) {
+    const ShapeOps *o = shape_at(i);
+    if (o->nR == p->n_max_radial && o->KR == p->basis_radial && o->nA == p->n_max_angular &&
+        o->KA == p->basis_angular && o->H == p->n_neuron && o->L3 == p->l_max_3b && o->L4 == p->l_max_4b &&
+        o->L5 == p->l_max_5b)
+      ops = o;
+  }
+  if (!ops) return fail(nullptr, NEP_ERR_UNSUPPORTED, "no kernel compiled for these hyper-parameters");
+  nep_handle *h = new nep_handle();
+  h->ops = ops;
+  h->T = p->n_types; h->nR = p->n_max_radial; h->nA = p->n_max_angular; h->KR = p->basis_radial;
+  h->KA = p->basis_angular; h->L3 = p->l_max_3b; h->L4 = p->l_max_4b; h->L5 = p->l_max_5b; h->H = p->n_neuron;
+  h->n_des = ops->n_des;
+  h->rcR = p->rc_radial;
+  h->rcA = p->rc_angular;
+  h->skin = p->skin > 0 ? p->skin : 1.0;
+  const int T = h->T;
+  auto copyf = [](const double *src, size_t n, std::vector<float> &dst) {
+    dst.resize(n);
+    for (size_t k = 0; k < n; ++k) dst[k] = (float)src[k];
+  };
+  copyf(p->c_radial, (size_t)T * T * (h->nR + 1) * (h->KR + 1), h->cR);
+  copyf(p->c_angular, (size_t)T * T * (h->nA + 1) * (h->KA + 1), h->cA);
+  copyf(p->w0, (size_t)h->H * h->n_des, h->w0);
+  copyf(p->b0, h->H, h->b0);
+  copyf(p->w1, h->H, h->w1);
+  h->b1 = (float)p->b1;
+  for (float v : h->w0) if (!std::isfinite(v)) { delete h; return fail(nullptr, NEP_ERR_ARG, "non-finite weight"); }
+  if (p->mass) {
+    h->mass.assign(p->mass, p->mass + T);
+    for (double m : h->mass)
+      if (!(m > 0) || !std::isfinite(m)) { delete h; return fail(nullptr, NEP_ERR_ARG, "mass must be positive"); }
+  }
+  model_constants(h->mf);
+  cudaGetDevice(&h->device);
+  cudaError_t e = cudaMallocHost(&h->h_status, sizeof(BuildStatus));
+  if (e != cudaSuccess) { delete h; return fail(nullptr, NEP_ERR_CUDA, "pinned alloc failed"); }
+  std::memset(h->h_status, 0, sizeof(BuildStatus));
+  if (h->d_cR.ensure(h->cR.size()) != cudaSuccess || h->d_cA.ensure(h->cA.size()) != cudaSuccess ||
+      h->d_inv_mk.ensure(T) != cudaSuccess || h->d_mk_half.ensure(T) != cudaSuccess) {
+    nep_destroy(h);
+    return fail(nullptr, NEP_ERR_OOM, "device alloc failed");
+  }
+  std::vector<double> imk(T, 0.0), mkh(T, 0.0);
+  for (int t = 0; t < T && !h->mass.empty(); ++t) {
+    imk[t] = 1.0 / (h->mass[t] * kKappa);
+    mkh[t] = 0.5 * h->mass[t] * kKappa;
+  }
+  cudaMemcpy(h->d_cR.p, h->cR.data(), h->cR.size() * sizeof(float), cudaMemcpyHostToDevice);
+  cudaMemcpy(h->d_cA.p, h->cA.data(), h->cA.size() * sizeof(float), cudaMemcpyHostToDevice);
+  cudaMemcpy(h->d_inv_mk.p, imk.data(), T * sizeof(double), cudaMemcpyHostToDevice);
+  e = cudaMemcpy(h->d_mk_half.p, mkh.data(), T * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { nep_destroy(h); return fail(nullptr, NEP_ERR_CUDA, cudaGetErrorString(e)); }
+  for (int sl = 0; sl < N_SLOTS; ++sl)
+    for (int w = 0; w < 2; ++w) cudaEventCreate(&h->ev[sl][w]);
+  cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+  *out = h;
+  return NEP_OK;
+}
+
+int nep_destroy(nep_handle *h) {
+  if (!h) return NEP_OK;
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (int sl = 0; sl < N_SLOTS; ++sl)
+    for (int w = 0; w < 2; ++w)
+      if (h->ev[sl][w]) cudaEventDestroy(h->ev[sl][w]);
+  if (h->h_status) cudaFreeHost(h->h_status);
+  h->d_cR.release(); h->d_cA.release(); h->d_inv_mk.release(); h->d_mk_half.release();
+  h->x.release(); h->v.release(); h->F.release(); h->x_ref.release(); h->origin.release();
+  h->partial_atom.release(); h->partial_gather.release(); h->thermo_stage.release();
+  h->types.release(); h->cell_of.release(); h->cell_count.release(); h->cell_cursor.release();
+  h->cell_start.release(); h->cell_atoms.release(); h->nn_r.release(); h->nn_a.release(); h->rev_a.release();
+  h->thermo_ctl.release(); h->nl_r.release(); h->nl_a.release(); h->pos4.release(); h->dtab.release();
+  h->p_ang.release(); h->e_rad.release(); h->status.release();
+  delete h;
+  return NEP_OK;
+}
+
+const char *nep_last_error(const nep_handle *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int nep_n_des(const nep_handle *h) { return valid_handle(h) ? h->n_des : NEP_ERR_ARG; }
+
+int nep_compute(nep_handle *h, int n_atoms, const double *pos, const int *types, const double *box, double *energy,
+                double *energy_total, double *force, double *virial, double *virial_total, nep_stream_t stream) {
+  if (!valid_handle(h)) return NEP_ERR_ARG;
+  h->err.clear();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_atoms < 0 || !box) return fail(h, NEP_ERR_ARG, "n_atoms < 0 or box is null");
+  if (n_atoms > 0 && (!pos || !types || !force)) return fail(h, NEP_ERR_ARG, "pos, types and force are required");
+  h->md_ready = false;
+  for (int sl = 0; sl < N_SLOTS; ++sl) h->slot_ran[sl] = false;
+  if (n_atoms == 0) {
+    if (energy_total) CK(cudaMemsetAsync(energy_total, 0, sizeof(double), s), "memset");
+    if (virial_total) CK(cudaMemsetAsync(virial_total, 0, 9 * sizeof(double), s), "memset");
+    return NEP_OK;
+  }
+  ev_record(h, SLOT_REBUILD, 0, s, false);
+  int rc = load_structure(h, n_atoms, pos, types, box, s);
+  if (rc) return rc;
+  ev_record(h, SLOT_REBUILD, 1, s, false);
+  rc = run_forces(h, n_atoms, energy, force, virial, 0, 0.0, s, false);
+  if (rc) return rc;
+  ev_record(h, SLOT_FINAL, 0, s, false);
+  launch_finalize(h->ops->atom_blocks(n_atoms), h->partial_atom.p, h->ops->gather_blocks(n_atoms),
+                  h->partial_gather.p, energy_total, virial_total, nullptr, nullptr, n_atoms, h->volume, s);
+  ev_record(h, SLOT_FINAL, 1, s, false);
+  CK(cudaGetLastError(), "finalize");
+  return NEP_OK;
+}
+
+int nep_descriptors(nep_handle *h, int n_atoms, const double *pos, const int *types, const double *box, double *q,
+                    nep_stream_t stream) {
+  if (!valid_handle(h)) return NEP_ERR_ARG;
+  h->err.clear();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_atoms < 0 || !box) return fail(h, NEP_ERR_ARG, "n_atoms < 0 or box is null");
+  if (n_atoms == 0) return NEP_OK;
+  if (!pos || !types || !q) return fail(h, NEP_ERR_ARG, "null pointer");
+  h->md_ready = false;
+  int rc = load_structure(h, n_atoms, pos, types, box, s);
+  if (rc) return rc;
+  AtomArgs a = make_args(h, n_atoms);
+  a.q_out = q;
+  cudaError_t e = h->ops->atom(a, h->mf, h->w0.data(), h->b0.data(), h->w1.data(), h->b1, 1, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "descriptor kernel");
+  return NEP_OK;
+}
+
+int nep_compute_host(nep_handle *h, int n_atoms, const double *pos, const int *types, const double *box, double *energy,
+                     double *energy_total, double *force, double *virial, double *virial_total) {
+  if (!valid_handle(h)) return NEP_ERR_ARG;
+  if (n_atoms < 0 || !box || (n_atoms > 0 && (!pos || !types || !force)))
+    return fail(h, NEP_ERR_ARG, "invalid arguments");
+  const size_t N = (size_t)std::max(n_atoms, 1);
+  double *dpos = nullptr, *dE = nullptr, *dF = nullptr, *dW = nullptr, *dtot = nullptr;
+  int *dT = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto al = [&](void **p, size_t b) { if (e == cudaSuccess) e = cudaMalloc(p, b); };
+  al((void **)&dpos, 3 * N * sizeof(double));
+  al((void **)&dT, N * sizeof(int));
+  al((void **)&dF, 3 * N * sizeof(double));
+  al((void **)&dtot, 10 * sizeof(double));
+  if (energy) al((void **)&dE, N * sizeof(double));
+  if (virial) al((void **)&dW, 9 * N * sizeof(double));
+  int rc = NEP_OK;
+  if (e != cudaSuccess) rc = cuda_fail(h, e, "nep_compute_host alloc");
+  if (!rc && n_atoms > 0) {
+    cudaMemcpy(dpos, pos, 3 * N * sizeof(double), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(dT, types, N * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) rc = cuda_fail(h, e, "copy in");
+  }
+  if (!rc) rc = nep_compute(h, n_atoms, dpos, dT, box, dE, dtot, dF, dW, dtot + 1, nullptr);
+  if (!rc) {
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) rc = cuda_fail(h, e, "nep_compute_host");
+  }
+  if (!rc) {
+    double tot[10];
+    cudaMemcpy(tot, dtot, sizeof(tot), cudaMemcpyDeviceToHost);
+    if (energy_total) *energy_total = tot[0];
+    if (virial_total) std::memcpy(virial_total, tot + 1, 9 * sizeof(double));
+    if (n_atoms > 0) {
+      cudaMemcpy(force, dF, 3 * N * sizeof(double), cudaMemcpyDeviceToHost);
+      if (energy) cudaMemcpy(energy, dE, N * sizeof(double), cudaMemcpyDeviceToHost);
+      if (virial) cudaMemcpy(virial, dW, 9 * N * sizeof(double), cudaMemcpyDeviceToHost);
+    }
+  }
+  cudaFree(dpos); cudaFree(dT); cudaFree(dF); cudaFree(dtot);
+  if (dE) cudaFree(dE);
+  if (dW) cudaFree(dW);
+  return rc;
+}
+
+int md_init(nep_handle *h, int n_atoms, const double *pos, const int *types, const double *box, const double *vel,
+            nep_stream_t stream) {
+  if (!valid_handle(h)) return NEP_ERR_ARG;
+  h->err.clear();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (h->mass.empty()) return fail(h, NEP_ERR_ARG, "md_init needs params->mass");
+  if (n_atoms < 1 || !pos || !types || !box) return fail(h, NEP_ERR_ARG, "md_init needs atoms, types and a box");
+  h->md_ready = false;
+  int rc = load_structure(h, n_atoms, pos, types, box, s);
+  if (rc) return rc;
+  if (vel) CK(cudaMemcpyAsync(h->v.p, vel, sizeof(double) * 3 * n_atoms, cudaMemcpyDeviceToDevice, s), "copy vel");
+  else CK(cudaMemsetAsync(h->v.p, 0, sizeof(double) * 3 * n_atoms, s), "memset vel");
+  rc = run_forces(h, n_atoms, nullptr, h->F.p, nullptr, 0, 0.0, s, false);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(s), "md_init");
+  h->h_status->n_rebuilds = 0;
+  h->h_status->md_steps = 0;
+  h->h_status->rebuild = 0;
+  CK(cudaMemcpy(h->status.p, h->h_status, sizeof(BuildStatus), cudaMemcpyHostToDevice), "status");
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  h->md_ready = true;
+  return NEP_OK;
+}
+
+int md_init_host(nep_handle *h, int n_atoms, const double *pos, const int *types, const double *box,
+                 const double *vel) {
+  if (!valid_handle(h)) return NEP_ERR_ARG;
+  if (n_atoms < 1 || !pos || !types || !box) return fail(h, NEP_ERR_ARG, "md_init needs atoms, types and a box");
+  double *dp = nullptr, *dv = nullptr;
+  int *dt = nullptr;
+  cudaError_t e = cudaMalloc(&dp, 3 * (size_t)n_atoms * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&dt, (size_t)n_atoms * sizeof(int));
+  if (e == cudaSuccess && vel) e = cudaMalloc(&dv, 3 * (size_t)n_atoms * sizeof(double));
+  int rc = NEP_OK;
+  if (e == cudaSuccess) {
+    cudaMemcpy(dp, pos, 3 * (size_t)n_atoms * sizeof(double), cudaMemcpyHostToDevice);
+    if (vel) cudaMemcpy(dv, vel, 3 * (size_t)n_atoms * sizeof(double), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(dt, types, (size_t)n_atoms * sizeof(int), cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) rc = cuda_fail(h, e, "md_init_host");
+  if (!rc) rc = md_init(h, n_atoms, dp, dt, box, dv, nullptr);
+  if (!rc) {
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) rc = cuda_fail(h, e, "md_init_host");
+  }
+  cudaFree(dp);
+  cudaFree(dt);
+  if (dv) cudaFree(dv);
+  return rc;
+}
+
+namespace {
+// Launch one MD step on stream s (used both for capture and, if needed, directly).
+int md_step_launch(nep_handle *h, double dt, cudaStream_t s, bool capturing) {
+  const int N = h->N;
+  const double half_skin2 = 0.25 * h->skin * h->skin;
+  ev_record(h, SLOT_DRIFT, 0, s, capturing);
+  launch_drift(N, h->x.p, h->v.p, h->F.p, h->pos4.p, h->x_ref.p, h->origin.p, h->d_inv_mk.p, dt, half_skin2,
+               h->status.p, s);
+  ev_record(h, SLOT_DRIFT, 1, s, capturing);
+  ev_record(h, SLOT_REBUILD, 0, s, capturing);
+  const float rlR = (float)(h->rcR + h->skin), rlA = (float)(h->rcA + h->skin);
+  launch_rebuild(N, h->T, h->grid, h->dtab.p, rlR * rlR, rlA * rlA, h->cap_r, h->cap_a, 0, h->x.p, h->x_ref.p,
+                 h->origin.p, h->types.p, h->pos4.p, h->cell_of.p, h->cell_count.p, h->cell_cursor.p,
+                 h->cell_start.p, h->cell_atoms.p, h->nl_r.p, h->nn_r.p, h->nl_a.p, h->nn_a.p, h->rev_a.p,
+                 h->status.p, s);
+  ev_record(h, SLOT_REBUILD, 1, s, capturing);
+  int rc = run_forces(h, N, nullptr, h->F.p, nullptr, 1, 0.5 * dt, s, capturing);
+  if (rc) return rc;
+  ev_record(h, SLOT_FINAL, 0, s, capturing);
+  launch_finalize(h->ops->atom_blocks(N), h->partial_atom.p, h->ops->gather_blocks(N), h->partial_gather.p, nullptr,
+                  nullptr, h->thermo_stage.p, h->thermo_ctl.p, N, h->volume, s);
+  ev_record(h, SLOT_FINAL, 1, s, capturing);
+  CK(cudaGetLastError(), "md step launch");
+  return NEP_OK;
+}
+}  // namespace
+
+int md_run(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *thermo, nep_stream_t stream) {
+  if (!valid_handle(h)) return NEP_ERR_ARG;
+  h->err.clear();
+  if (!h->md_ready) return fail(h, NEP_ERR_STATE, "md_run before md_init");
+  if (n_steps < 0 || !(dt_fs > 0) || !std::isfinite(dt_fs) || thermo_every < 1)
+    return fail(h, NEP_ERR_ARG, "need n_steps >= 0, dt > 0, thermo_every >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_steps == 0) return NEP_OK;
+  const int rows = thermo ? n_steps / thermo_every : 0;
+  CK(h->thermo_stage.ensure((size_t)4 * (rows + 1)), "alloc thermo");
+  int ctl[4] = {0, 0, thermo ? thermo_every : (n_steps + 1), 0};
+  CK(cudaMemcpyAsync(h->thermo_ctl.p, ctl, sizeof(ctl), cudaMemcpyHostToDevice, s), "thermo ctl");
+  // (re)capture the one-step graph when the step size or the profiling mode changed
+  if (!h->graph || h->graph_dt != dt_fs || h->graph_prof != h->prof || h->graph_thermo != h->thermo_stage.p) {
+    if (h->graph) {
+      cudaGraphExecDestroy(h->graph);
+      h->graph = nullptr;
+    }
+    CK(cudaStreamSynchronize(s), "sync");
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "capture");
+    int rc = md_step_launch(h, dt_fs, h->cap_stream, true);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
+    e = cudaGraphInstantiate(&h->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
+    h->graph_dt = dt_fs;
+    h->graph_prof = h->prof;
+    h->graph_thermo = h->thermo_stage.p;
+  }
+  for (int st = 0; st < n_steps; ++st) CK(cudaGraphLaunch(h->graph, s), "graph launch");
+  if (thermo && rows > 0)
+    CK(cudaMemcpyAsync(thermo, h->thermo_stage.p, sizeof(double) * 4 * rows, cudaMemcpyDeviceToDevice, s), "thermo");
+  int rc = read_status(h, s);
+  if (rc) return rc;
+  if (h->h_status->overflow || h->h_status->rev_missing) {
+    h->md_ready = false;
+    return fail(h, NEP_ERR_NEIGHBOR_OVERFLOW, "neighbour list overflow during md_run; call md_init again");
+  }
+  return NEP_OK;
+}
+
+int md_get_state(nep_handle *h, double *pos, double *vel, double *force, nep_stream_t stream) {
+  if (!valid_handle(h)) return NEP_ERR_ARG;
+  if (!h->md_ready) return fail(h, NEP_ERR_STATE, "no MD state");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t b = sizeof(double) * 3 * (size_t)h->N;
+  if (pos) {
+    launch_wrap(h->N, h->x.p, h->grid, pos, s);
+    CK(cudaGetLastError(), "wrap");
+  }
+  if (vel) CK(cudaMemcpyAsync(vel, h->v.p, b, cudaMemcpyDeviceToDevice, s), "copy");
+  if (force) CK(cudaMemcpyAsync(force, h->F.p, b, cudaMemcpyDeviceToDevice, s), "copy");
+  return NEP_OK;
+}
+
+int md_get_state_host(nep_handle *h, double *pos, double *vel, double *force) {
+  if (!valid_handle(h)) return NEP_ERR_ARG;
+  if (!h->md_ready) return fail(h, NEP_ERR_STATE, "no MD state");
+  const size_t b = sizeof(double) * 3 * (size_t)h->N;
+  if (pos) {
+    CK(cudaMemcpy(pos, h->x.p, b, cudaMemcpyDeviceToHost), "copy");
+    const Grid &g = h->grid;
+    for (int i = 0; i < h->N; ++i) {
+      double sf[3];
+      for (int c = 0; c < 3; ++c)
+        sf[c] = pos[3 * i] * g.Hinv[0][c] + pos[3 * i + 1] * g.Hinv[1][c] + pos[3 * i + 2] * g.Hinv[2][c];
+      for (int c = 0; c < 3; ++c) sf[c] -= std::floor(sf[c]);
+      for (int c = 0; c < 3; ++c) pos[3 * i + c] = sf[0] * g.H[0][c] + sf[1] * g.H[1][c] + sf[2] * g.H[2][c];
+    }
+  }
+  if (vel) CK(cudaMemcpy(vel, h->v.p, b, cudaMemcpyDeviceToHost), "copy");
+  if (force) CK(cudaMemcpy(force, h->F.p, b, cudaMemcpyDeviceToHost), "copy");
+  return NEP_OK;
+}
+
+int nep_get_stats(nep_handle *h, nep_stats *out) {
+  if (!valid_handle(h) || !out) return NEP_ERR_ARG;
+  nep_stats s = h->stats_cache;
+  s.cap_radial = h->cap_r;
+  s.cap_angular = h->cap_a;
+  if (h->status.p) {
+    cudaMemcpy(h->h_status, h->status.p, sizeof(BuildStatus), cudaMemcpyDeviceToHost);
+    s.n_rebuilds = h->h_status->n_rebuilds;
+    s.md_steps = h->h_status->md_steps;
+    s.max_radial = h->h_status->max_r;
+    s.max_angular = h->h_status->max_a;
+    if (h->N > 0) {
+      s.mean_radial = (double)h->h_status->sum_r / h->N;
+      s.mean_angular = (double)h->h_status->sum_a / h->N;
+    }
+  }
+  *out = s;
+  return NEP_OK;
+}
+
+int nep_set_profiling(nep_handle *h, int enable) {
+  if (!valid_handle(h)) return NEP_ERR_ARG;
+  h->prof = enable != 0;
+  return NEP_OK;
+}
+
+int nep_kernel_slots(void) { return N_SLOTS; }
+
+const char *nep_kernel_name(int slot) { return (slot >= 0 && slot < N_SLOTS) ? kSlotNames[slot] : ""; }
+
+int nep_kernel_times(nep_handle *h, float *ms_out, int n_slots) {
+  if (!valid_handle(h) || !ms_out) return NEP_ERR_ARG;
+  for (int sl = 0; sl < n_slots && sl < N_SLOTS; ++sl) {
+    ms_out[sl] = 0.f;
+    if (!h->prof || !h->slot_ran[sl]) continue;
+    if (cudaEventSynchronize(h->ev[sl][1]) != cudaSuccess) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev[sl][0], h->ev[sl][1]) == cudaSuccess) ms_out[sl] = ms;
+  }
+  return NEP_OK;
+}
+
+}  // extern "C"

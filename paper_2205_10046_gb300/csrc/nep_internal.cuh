@@ -1,0 +1,109 @@
+// Internal declarations of libnep (GB300 / sm_103a). Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nep {
+
+constexpr int kMaxTypes = 8;
+constexpr int kListBuf = 160;   // per-atom candidate buffer of the list builder
+constexpr int kMaxImage = 3;    // largest cell/image offset searched per axis
+constexpr int kAtomBlock = 128; // threads per block of the per-atom kernel
+constexpr int kGatherBlock = 128;
+constexpr int kReduceSlots = 12; // per-block partial sums: U, KE, W[9], spare
+
+// Geometry of one neighbour build: the cell grid, the packing of list entries and the
+// table of pair shift vectors indexed by the packed image code.
+struct Grid {
+  int nc[3];          // cells per axis
+  int R[3];           // cell offsets searched per axis (1 for large cells)
+  int ncell;
+  int jbits;          // bits of the atom index in a list entry
+  unsigned jmask;
+  int obits;          // bits of one offset component in the code (2 or 3)
+  int ncode;          // entries of the shift table (2^(3 obits))
+  double H[3][3];     // cell rows
+  double Hinv[3][3];  // s = r . Hinv
+  double Hc[3][3];    // rows of one grid cell: H[a] / nc[a]
+};
+
+// Device-visible status written by the builders.
+struct BuildStatus {
+  int overflow;        // any atom exceeded a list capacity
+  int max_r, max_a;    // largest radial/angular list length
+  int rev_missing;     // angular pairs without their reverse pair (must stay 0)
+  unsigned long long sum_r, sum_a;  // total list entries
+  int rebuild;         // a rebuild is pending (set by the drift kernel or the host)
+  int bad_input;       // bit 0: type out of range, bit 1: non-finite position
+  long long n_rebuilds;
+  long long md_steps;
+};
+
+// Pair vector d = r_j - r_i from cell-local FP32 coordinates and the shift of the image
+// code. The explicitly rounded operations make d_ji the exact negation of d_ij, so both
+// atoms of a pair take the same inclusion decision in every kernel.
+__device__ __forceinline__ float3 pair_vector(const float4 &pi, const float4 &pj, const float4 &D) {
+  return make_float3(__fadd_rn(__fsub_rn(pj.x, pi.x), D.x), __fadd_rn(__fsub_rn(pj.y, pi.y), D.y),
+                     __fadd_rn(__fsub_rn(pj.z, pi.z), D.z));
+}
+__device__ __forceinline__ float norm2(const float3 &d) {
+  return __fmaf_rn(d.z, d.z, __fmaf_rn(d.y, d.y, __fmul_rn(d.x, d.x)));
+}
+__device__ __forceinline__ int type_of(const float4 &p) { return __float_as_int(p.w); }
+
+// Arguments of the per-atom and gather kernels (everything except the model weights).
+struct AtomArgs {
+  int N, T;
+  int jbits;
+  unsigned jmask;
+  int ncode;
+  float rcR, rcA;
+  const float4 *pos4;      // [N] cell-local xyz + type bits
+  const float4 *dtab;      // [ncode] pair shift vectors
+  const unsigned *nl_r;    // [cap_r][N] packed entries, grouped by neighbour type
+  const int *nn_r;         // [T][N] radial entries per neighbour type
+  const unsigned *nl_a;    // [cap_a][N]
+  const int *nn_a;         // [N]
+  const int *rev_a;        // [cap_a][N] flat index of the reverse angular pair
+  const float *c_r;        // [T][T][nR+1][KR+1] FP32 copy
+  const float *c_a;        // [T][T][nA+1][KA+1]
+  float *e_rad;            // [N][T][est] radial force coefficients
+  int est;
+  float4 *p_ang;           // [cap_a][N] angular partial forces
+  double *energy;          // [N] or null
+  double *q_out;           // [N][N_des] descriptor output (descriptor mode) or null
+  double *partial_atom;    // [gridDim] block sums of U
+  // gather outputs
+  double *force;           // [N][3] or null (md keeps FP64 forces here)
+  double *virial;          // [N][9] or null
+  double *partial_gather;  // [gridDim][kReduceSlots]
+  // md kick in the gather epilogue
+  int md_kick;
+  double half_dt;          // dt/2 in fs
+  const double *inv_mass_kappa;  // [T] 1 / (m * 103.64...) for a = F * that
+  const double *mass_kappa_half; // [T] m * 103.64... / 2 for kinetic energy
+  double *vel;             // [N][3]
+};
+
+// Model constants of one handle, FP32.
+struct ModelF {
+  float c3b[24];
+  float c4b[5];
+  float c5b[3];
+};
+
+// Per-shape launchers (one instantiation per compiled hyper-parameter shape).
+struct ShapeOps {
+  int nR, KR, nA, KA, H, L3, L4, L5;
+  int n_des;
+  cudaError_t (*atom)(const AtomArgs &, const ModelF &, const float *w0, const float *b0, const float *w1,
+                      float b1, int descriptor_only, cudaStream_t s);
+  cudaError_t (*gather)(const AtomArgs &, cudaStream_t s);
+  int (*atom_blocks)(int N);
+  int (*gather_blocks)(int N);
+};
+
+int shape_count();
+const ShapeOps *shape_at(int i);
+
+}  // namespace nep

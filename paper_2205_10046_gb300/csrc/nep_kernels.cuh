@@ -1,0 +1,683 @@
+// NEP3 per-atom kernels for GB300 (sm_103a), templated on the model shape.
+//
+// Two kernels replace the four of the paper's Appendix B:
+//   atom_kernel   one thread per atom: radial descriptor (Eq. qin), angular sums S_nk
+//                 (Eq. S_nk) and the explicit 3/4/5-body components (Sec. II D), the
+//                 network U_i and dU_i/dq (Eq. Ui), then the per-type radial force
+//                 coefficients and the angular partial forces dU_i/dr_ij (the angular terms
+//                 of Eq. partial_force), stored per angular pair (Algorithms 1 and 3 fused).
+//   gather_kernel one thread per atom: F_i = sum_j [dU_i/dr_ij - dU_j/dr_ji] (Eqs. F_ij,
+//                 F_i) and W_i = sum_j r_ij (x) dU_j/dr_ji (Eq. virial) for the radial
+//                 part from both atoms' force coefficients and for the angular part from
+//                 the stored partial forces of both atoms, with no atomics (Algorithms 2, 4).
+//
+// Differences from the paper's GPU design, for GB300:
+//   * the radial descriptor accumulates the Chebyshev sums per neighbour type,
+//     F^t_k = sum_{j of type t} f_k(r_ij), and contracts with c^{t_i t}_{nk} once per atom
+//     (the radial list is grouped by neighbour type), so a pair costs O(K) instead of
+//     O(n K); the radial partial forces likewise use e^t_k = sum_n dU/dq_n c^{t_i t}_{nk};
+//   * S_nk are evaluated from the homogeneous polynomials b_k(d) scaled by r^-l, and the
+//     angular gradient uses the tangential projection of grad b_k (no unit-vector round-off);
+//   * pair vectors come from cell-local FP32 coordinates plus an image shift table, so no
+//     FP64 arithmetic (slow on GB300) runs in the pair loops;
+//   * S_nk wait in shared memory while the network runs, to bound register pressure.
+#pragma once
+#include "nep_internal.cuh"
+
+namespace nep {
+
+template <int NR_, int KR_, int NA_, int KA_, int H_, int L3_, int L4_, int L5_>
+struct Shape {
+  static constexpr int NR = NR_, KR = KR_, NA = NA_, KA = KA_, H = H_, L3 = L3_, L4 = L4_, L5 = L5_;
+  static constexpr int NB = L3 + (L4 >= 2 ? 1 : 0) + (L5 >= 1 ? 1 : 0);
+  static constexpr int NDES = (NR + 1) + (NA + 1) * NB;
+  static constexpr int KEND3 = L3 == 1 ? 3 : L3 == 2 ? 8 : L3 == 3 ? 15 : 24;
+  static constexpr int NK = KEND3 > 8 ? KEND3 : (L4 >= 2 ? 8 : KEND3);
+  static constexpr int EST = ((KR + 2) + 3) / 4 * 4;  // KR+1 coefficients and their sum
+  static constexpr int OFF4 = (NR + 1) + (NA + 1) * L3;
+  static constexpr int OFF5 = OFF4 + (L4 >= 2 ? NA + 1 : 0);
+};
+
+template <class S>
+struct AnnConst {
+  float w0[S::H * S::NDES];
+  float b0[S::H];
+  float w1[S::H];
+  float b1;
+  ModelF m;
+};
+
+// l of polynomial k (blocks 0-2, 3-7, 8-14, 15-23)
+__host__ __device__ constexpr int l_of_k(int k) { return k < 3 ? 1 : k < 8 ? 2 : k < 15 ? 3 : 4; }
+
+// b_k(d) of Sec. II D as homogeneous polynomials of the pair vector (s = |d|^2).
+template <int k>
+__device__ __forceinline__ float poly_b(float x, float y, float z, float s) {
+  if constexpr (k == 0) return z;
+  else if constexpr (k == 1) return x;
+  else if constexpr (k == 2) return y;
+  else if constexpr (k == 3) return 3.f * z * z - s;
+  else if constexpr (k == 4) return x * z;
+  else if constexpr (k == 5) return y * z;
+  else if constexpr (k == 6) return x * x - y * y;
+  else if constexpr (k == 7) return 2.f * x * y;
+  else if constexpr (k == 8) return (5.f * z * z - 3.f * s) * z;
+  else if constexpr (k == 9) return (5.f * z * z - s) * x;
+  else if constexpr (k == 10) return (5.f * z * z - s) * y;
+  else if constexpr (k == 11) return (x * x - y * y) * z;
+  else if constexpr (k == 12) return 2.f * x * y * z;
+  else if constexpr (k == 13) return (x * x - 3.f * y * y) * x;
+  else if constexpr (k == 14) return (3.f * x * x - y * y) * y;
+  else if constexpr (k == 15) return (35.f * z * z - 30.f * s) * z * z + 3.f * s * s;
+  else if constexpr (k == 16) return (7.f * z * z - 3.f * s) * x * z;
+  else if constexpr (k == 17) return (7.f * z * z - 3.f * s) * y * z;
+  else if constexpr (k == 18) return (7.f * z * z - s) * (x * x - y * y);
+  else if constexpr (k == 19) return (7.f * z * z - s) * 2.f * x * y;
+  else if constexpr (k == 20) return (x * x - 3.f * y * y) * x * z;
+  else if constexpr (k == 21) return (3.f * x * x - y * y) * y * z;
+  else if constexpr (k == 22) return (x * x - y * y) * (x * x - y * y) - 4.f * x * x * y * y;
+  else return 4.f * (x * x - y * y) * x * y;
+}
+
+// Gradient of b_k(d) with s = |d|^2 held fixed. Only its component tangential to d is
+// used: grad |d|^2 = 2d is radial, so the tangential part equals that of the full gradient.
+template <int k>
+__device__ __forceinline__ float3 poly_grad(float x, float y, float z, float s) {
+  if constexpr (k == 0) return make_float3(0.f, 0.f, 1.f);
+  else if constexpr (k == 1) return make_float3(1.f, 0.f, 0.f);
+  else if constexpr (k == 2) return make_float3(0.f, 1.f, 0.f);
+  else if constexpr (k == 3) return make_float3(0.f, 0.f, 6.f * z);
+  else if constexpr (k == 4) return make_float3(z, 0.f, x);
+  else if constexpr (k == 5) return make_float3(0.f, z, y);
+  else if constexpr (k == 6) return make_float3(2.f * x, -2.f * y, 0.f);
+  else if constexpr (k == 7) return make_float3(2.f * y, 2.f * x, 0.f);
+  else if constexpr (k == 8) return make_float3(0.f, 0.f, 15.f * z * z - 3.f * s);
+  else if constexpr (k == 9) return make_float3(5.f * z * z - s, 0.f, 10.f * x * z);
+  else if constexpr (k == 10) return make_float3(0.f, 5.f * z * z - s, 10.f * y * z);
+  else if constexpr (k == 11) return make_float3(2.f * x * z, -2.f * y * z, x * x - y * y);
+  else if constexpr (k == 12) return make_float3(2.f * y * z, 2.f * x * z, 2.f * x * y);
+  else if constexpr (k == 13) return make_float3(3.f * (x * x - y * y), -6.f * x * y, 0.f);
+  else if constexpr (k == 14) return make_float3(6.f * x * y, 3.f * (x * x - y * y), 0.f);
+  else if constexpr (k == 15) return make_float3(0.f, 0.f, (140.f * z * z - 60.f * s) * z);
+  else if constexpr (k == 16) return make_float3((7.f * z * z - 3.f * s) * z, 0.f, (21.f * z * z - 3.f * s) * x);
+  else if constexpr (k == 17) return make_float3(0.f, (7.f * z * z - 3.f * s) * z, (21.f * z * z - 3.f * s) * y);
+  else if constexpr (k == 18)
+    return make_float3(2.f * x * (7.f * z * z - s), -2.f * y * (7.f * z * z - s), 14.f * z * (x * x - y * y));
+  else if constexpr (k == 19)
+    return make_float3(2.f * y * (7.f * z * z - s), 2.f * x * (7.f * z * z - s), 28.f * x * y * z);
+  else if constexpr (k == 20)
+    return make_float3(3.f * (x * x - y * y) * z, -6.f * x * y * z, (x * x - 3.f * y * y) * x);
+  else if constexpr (k == 21)
+    return make_float3(6.f * x * y * z, 3.f * (x * x - y * y) * z, (3.f * x * x - y * y) * y);
+  else if constexpr (k == 22)
+    return make_float3(4.f * x * (x * x - 3.f * y * y), 4.f * y * (y * y - 3.f * x * x), 0.f);
+  else return make_float3(4.f * y * (3.f * x * x - y * y), 4.f * x * (x * x - 3.f * y * y), 0.f);
+}
+
+// Unrolled compile-time loop helper.
+template <int I, int N, class F>
+__device__ __forceinline__ void static_for(F &&f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    static_for<I + 1, N>(f);
+  }
+}
+
+// f_k(r) = (T_k(x) + 1) fc/2 with fc = (1 + cos(pi r/rc))/2 and x = 2(r/rc - 1)^2 - 1
+// (Eq. f_n and the cosine cutoff); fills f[0..K].
+template <int K>
+__device__ __forceinline__ void cheb_basis(float r, float inv_rc, float *f) {
+  const float u = r * inv_rc;
+  const float hfc = 0.25f * (1.f + __cosf(3.14159265358979f * u));
+  const float t1 = u - 1.f;
+  const float x = 2.f * t1 * t1 - 1.f;
+  const float x2 = 2.f * x;
+  float tkm1 = 1.f, tk = x;
+  f[0] = 2.f * hfc;
+  if constexpr (K >= 1) f[1] = __fmaf_rn(x, hfc, hfc);
+#pragma unroll
+  for (int k = 2; k <= K; ++k) {
+    const float tn = __fmaf_rn(x2, tk, -tkm1);
+    tkm1 = tk;
+    tk = tn;
+    f[k] = __fmaf_rn(tn, hfc, hfc);
+  }
+}
+
+// f_k(r) and f_k'(r) for k = 0..K.
+template <int K>
+__device__ __forceinline__ void cheb_basis_d(float r, float inv_rc, float *f, float *fp) {
+  const float u = r * inv_rc;
+  float sn, cs;
+  __sincosf(3.14159265358979f * u, &sn, &cs);
+  const float hfc = 0.25f * (1.f + cs);                       // fc/2
+  const float hfcp = -0.25f * 3.14159265358979f * inv_rc * sn; // fc'/2
+  const float t1 = u - 1.f;
+  const float x = 2.f * t1 * t1 - 1.f;
+  const float xp = 4.f * t1 * inv_rc;  // dx/dr
+  const float x2 = 2.f * x;
+  const float a = xp * hfc;            // T_k' coefficient
+  float tkm1 = 1.f, tk = x, dkm1 = 0.f, dk = 1.f;
+  f[0] = 2.f * hfc;
+  fp[0] = 2.f * hfcp;
+  if constexpr (K >= 1) {
+    f[1] = __fmaf_rn(x, hfc, hfc);
+    fp[1] = __fmaf_rn(a, 1.f, (x + 1.f) * hfcp);
+  }
+#pragma unroll
+  for (int k = 2; k <= K; ++k) {
+    const float tn = __fmaf_rn(x2, tk, -tkm1);
+    const float dn = __fmaf_rn(x2, dk, __fmaf_rn(2.f, tk, -dkm1));
+    tkm1 = tk;
+    tk = tn;
+    dkm1 = dk;
+    dk = dn;
+    f[k] = __fmaf_rn(tn, hfc, hfc);
+    fp[k] = __fmaf_rn(a, dn, (tn + 1.f) * hfcp);
+  }
+}
+
+// ------------------------------------------------------------------------ per-atom kernel
+template <class S, bool DESC_ONLY>
+__global__ void __launch_bounds__(kAtomBlock, 1)
+    atom_kernel(const AtomArgs a, const __grid_constant__ AnnConst<S> w) {
+  constexpr int NR = S::NR, KR = S::KR, NA = S::NA, KA = S::KA, NK = S::NK, NDES = S::NDES;
+  extern __shared__ float4 smem4[];
+  const int T = a.T;
+  float4 *dtab_s = smem4;                                        // [ncode]
+  float *cR_s = reinterpret_cast<float *>(smem4 + a.ncode);      // [T][T][NR+1][KR+1]
+  float *cA_s = cR_s + T * T * (NR + 1) * (KR + 1);              // [T][T][NA+1][KA+1]
+  float *S_s = cA_s + T * T * (NA + 1) * (KA + 1);               // [NA+1][NK][block]
+  for (int v = threadIdx.x; v < a.ncode; v += blockDim.x) dtab_s[v] = a.dtab[v];
+  for (int v = threadIdx.x; v < T * T * (NR + 1) * (KR + 1); v += blockDim.x) cR_s[v] = a.c_r[v];
+  for (int v = threadIdx.x; v < T * T * (NA + 1) * (KA + 1); v += blockDim.x) cA_s[v] = a.c_a[v];
+  __syncthreads();
+
+  const int N = a.N;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double Ublock = 0.0;
+  if (i < N) {
+    const float4 pi = a.pos4[i];
+    const int ti = type_of(pi);
+    const float inv_rcR = 1.f / a.rcR, inv_rcA = 1.f / a.rcA;
+    const float rcR2 = a.rcR * a.rcR, rcA2 = a.rcA * a.rcA;
+
+    float q[NDES];
+#pragma unroll
+    for (int v = 0; v < NDES; ++v) q[v] = 0.f;
+
+    // ---- radial descriptor, Eq. qin: per neighbour type, F^t_k = sum_j f_k(r_ij)
+    int base = 0;
+    for (int t = 0; t < T; ++t) {
+      const int cnt = a.nn_r[t * N + i];
+      float Fk[KR + 1];
+#pragma unroll
+      for (int k = 0; k <= KR; ++k) Fk[k] = 0.f;
+      for (int m = 0; m < cnt; ++m) {
+        const unsigned e = a.nl_r[(size_t)(base + m) * N + i];
+        const float4 pj = a.pos4[e & a.jmask];
+        const float3 d = pair_vector(pi, pj, dtab_s[e >> a.jbits]);
+        const float r2 = norm2(d);
+        if (r2 < rcR2) {
+          float f[KR + 1];
+          cheb_basis<KR>(r2 * rsqrtf(r2), inv_rcR, f);
+#pragma unroll
+          for (int k = 0; k <= KR; ++k) Fk[k] += f[k];
+        }
+      }
+      const float *c = cR_s + (ti * T + t) * (NR + 1) * (KR + 1);
+#pragma unroll
+      for (int n = 0; n <= NR; ++n) {
+        float acc = q[n];
+#pragma unroll
+        for (int k = 0; k <= KR; ++k) acc = __fmaf_rn(c[n * (KR + 1) + k], Fk[k], acc);
+        q[n] = acc;
+      }
+      base += cnt;
+    }
+
+    // ---- angular sums S_nk, Eq. S_nk, with b_k(d) r^-l
+    float Sv[NA + 1][NK];
+#pragma unroll
+    for (int n = 0; n <= NA; ++n)
+#pragma unroll
+      for (int k = 0; k < NK; ++k) Sv[n][k] = 0.f;
+    const int na = a.nn_a[i];
+    for (int m = 0; m < na; ++m) {
+      const unsigned e = a.nl_a[(size_t)m * N + i];
+      const float4 pj = a.pos4[e & a.jmask];
+      const float3 d = pair_vector(pi, pj, dtab_s[e >> a.jbits]);
+      const float r2 = norm2(d);
+      if (r2 < rcA2) {
+        const int tj = type_of(pj);
+        const float rinv = rsqrtf(r2);
+        float f[KA + 1];
+        cheb_basis<KA>(r2 * rinv, inv_rcA, f);
+        const float *c = cA_s + (ti * T + tj) * (NA + 1) * (KA + 1);
+        float g[NA + 1];
+#pragma unroll
+        for (int n = 0; n <= NA; ++n) {
+          float acc = 0.f;
+#pragma unroll
+          for (int k = 0; k <= KA; ++k) acc = __fmaf_rn(c[n * (KA + 1) + k], f[k], acc);
+          g[n] = acc;
+        }
+        const float rl[5] = {1.f, rinv, rinv * rinv, rinv * rinv * rinv, (rinv * rinv) * (rinv * rinv)};
+        static_for<0, NK>([&](auto kc) {
+          constexpr int k = decltype(kc)::value;
+          const float b = poly_b<k>(d.x, d.y, d.z, r2) * rl[l_of_k(k)];
+#pragma unroll
+          for (int n = 0; n <= NA; ++n) Sv[n][k] = __fmaf_rn(g[n], b, Sv[n][k]);
+        });
+      }
+    }
+
+    // ---- angular descriptor components (Sec. II D)
+#pragma unroll
+    for (int n = 0; n <= NA; ++n) {
+      static_for<0, S::L3>([&](auto lc) {
+        constexpr int l = decltype(lc)::value + 1;
+        constexpr int k0 = l == 1 ? 0 : l == 2 ? 3 : l == 3 ? 8 : 15;
+        constexpr int k1 = l == 1 ? 3 : l == 2 ? 8 : l == 3 ? 15 : 24;
+        float acc = 0.f;
+#pragma unroll
+        for (int k = k0; k < k1; ++k) acc = __fmaf_rn(w.m.c3b[k] * Sv[n][k], Sv[n][k], acc);
+        q[(NR + 1) + (l - 1) * (NA + 1) + n] = acc;
+      });
+      if constexpr (S::L4 >= 2) {
+        const float s3 = Sv[n][3], s4 = Sv[n][4], s5 = Sv[n][5], s6 = Sv[n][6], s7 = Sv[n][7];
+        q[S::OFF4 + n] = w.m.c4b[0] * s3 * s3 * s3 + w.m.c4b[1] * s3 * (s4 * s4 + s5 * s5) +
+                         w.m.c4b[2] * s3 * (s6 * s6 + s7 * s7) + w.m.c4b[3] * s6 * (s5 * s5 - s4 * s4) +
+                         w.m.c4b[4] * s4 * s5 * s7;
+      }
+      if constexpr (S::L5 >= 1) {
+        const float s0 = Sv[n][0], s12 = Sv[n][1] * Sv[n][1] + Sv[n][2] * Sv[n][2];
+        q[S::OFF5 + n] = w.m.c5b[0] * s0 * s0 * s0 * s0 + w.m.c5b[1] * s0 * s0 * s12 + w.m.c5b[2] * s12 * s12;
+      }
+    }
+
+    if constexpr (DESC_ONLY) {
+#pragma unroll
+      for (int v = 0; v < NDES; ++v) a.q_out[(size_t)i * NDES + v] = (double)q[v];
+    } else {
+      // park S in shared memory while the network runs ([n][k][thread]: conflict-free)
+      float *Sme = S_s + threadIdx.x;
+#pragma unroll
+      for (int n = 0; n <= NA; ++n)
+#pragma unroll
+        for (int k = 0; k < NK; ++k) Sme[(n * NK + k) * kAtomBlock] = Sv[n][k];
+
+      // ---- network, Eq. Ui, and dU/dq
+      float U = 0.f;
+      float dq[NDES];
+#pragma unroll
+      for (int v = 0; v < NDES; ++v) dq[v] = 0.f;
+#pragma unroll
+      for (int mu = 0; mu < S::H; ++mu) {
+        float z = -w.b0[mu];
+#pragma unroll
+        for (int v = 0; v < NDES; ++v) z = __fmaf_rn(w.w0[mu * NDES + v], q[v], z);
+        const float h = tanhf(z);
+        U = __fmaf_rn(w.w1[mu], h, U);
+        const float beta = w.w1[mu] * (1.f - h * h);
+#pragma unroll
+        for (int v = 0; v < NDES; ++v) dq[v] = __fmaf_rn(beta, w.w0[mu * NDES + v], dq[v]);
+      }
+      U -= w.b1;
+      if (a.energy) a.energy[i] = (double)U;
+      Ublock = (double)U;
+
+      // ---- radial force coefficients e^t_k = sum_n dU/dq_n c^{t_i t}_{nk} and their sum
+      for (int t = 0; t < T; ++t) {
+        const float *c = cR_s + (ti * T + t) * (NR + 1) * (KR + 1);
+        float ev[S::EST];
+        float tot = 0.f;
+#pragma unroll
+        for (int k = 0; k <= KR; ++k) {
+          float acc = 0.f;
+#pragma unroll
+          for (int n = 0; n <= NR; ++n) acc = __fmaf_rn(dq[n], c[n * (KR + 1) + k], acc);
+          ev[k] = acc;
+          tot += acc;
+        }
+        ev[KR + 1] = tot;
+#pragma unroll
+        for (int k = KR + 2; k < S::EST; ++k) ev[k] = 0.f;
+        float4 *dst = reinterpret_cast<float4 *>(a.e_rad + ((size_t)i * T + t) * S::EST);
+#pragma unroll
+        for (int k4 = 0; k4 < S::EST / 4; ++k4)
+          dst[k4] = make_float4(ev[4 * k4], ev[4 * k4 + 1], ev[4 * k4 + 2], ev[4 * k4 + 3]);
+      }
+
+      // ---- dU/dS_nk from the explicit 3/4/5-body forms
+      float dS[NA + 1][NK];
+#pragma unroll
+      for (int n = 0; n <= NA; ++n) {
+        float s[NK];
+#pragma unroll
+        for (int k = 0; k < NK; ++k) s[k] = Sme[(n * NK + k) * kAtomBlock];
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+          if (k < S::KEND3) {
+            const float d3 = dq[(NR + 1) + (l_of_k(k) - 1) * (NA + 1) + n];
+            dS[n][k] = 2.f * w.m.c3b[k] * s[k] * d3;
+          } else {
+            dS[n][k] = 0.f;
+          }
+        }
+        if constexpr (S::L4 >= 2) {
+          const float d4 = dq[S::OFF4 + n];
+          const float *C = w.m.c4b;
+          dS[n][3] += d4 * (3.f * C[0] * s[3] * s[3] + C[1] * (s[4] * s[4] + s[5] * s[5]) + C[2] * (s[6] * s[6] + s[7] * s[7]));
+          dS[n][4] += d4 * (2.f * C[1] * s[3] * s[4] - 2.f * C[3] * s[6] * s[4] + C[4] * s[5] * s[7]);
+          dS[n][5] += d4 * (2.f * C[1] * s[3] * s[5] + 2.f * C[3] * s[6] * s[5] + C[4] * s[4] * s[7]);
+          dS[n][6] += d4 * (2.f * C[2] * s[3] * s[6] + C[3] * (s[5] * s[5] - s[4] * s[4]));
+          dS[n][7] += d4 * (2.f * C[2] * s[3] * s[7] + C[4] * s[4] * s[5]);
+        }
+        if constexpr (S::L5 >= 1) {
+          const float d5 = dq[S::OFF5 + n];
+          const float *C = w.m.c5b;
+          const float s12 = s[1] * s[1] + s[2] * s[2];
+          dS[n][0] += d5 * (4.f * C[0] * s[0] * s[0] * s[0] + 2.f * C[1] * s[0] * s12);
+          const float common = 2.f * C[1] * s[0] * s[0] + 4.f * C[2] * s12;
+          dS[n][1] += d5 * common * s[1];
+          dS[n][2] += d5 * common * s[2];
+        }
+      }
+
+      // ---- angular partial forces dU_i/dr_ij (angular terms of Eq. partial_force)
+      for (int m = 0; m < na; ++m) {
+        const unsigned e = a.nl_a[(size_t)m * N + i];
+        const float4 pj = a.pos4[e & a.jmask];
+        const float3 d = pair_vector(pi, pj, dtab_s[e >> a.jbits]);
+        const float r2 = norm2(d);
+        if (r2 < rcA2) {
+          const int tj = type_of(pj);
+          const float rinv = rsqrtf(r2);
+          float f[KA + 1], fp[KA + 1];
+          cheb_basis_d<KA>(r2 * rinv, inv_rcA, f, fp);
+          const float *c = cA_s + (ti * T + tj) * (NA + 1) * (KA + 1);
+          float g[NA + 1], gp[NA + 1];
+#pragma unroll
+          for (int n = 0; n <= NA; ++n) {
+            float acc = 0.f, accp = 0.f;
+#pragma unroll
+            for (int k = 0; k <= KA; ++k) {
+              const float cc = c[n * (KA + 1) + k];
+              acc = __fmaf_rn(cc, f[k], acc);
+              accp = __fmaf_rn(cc, fp[k], accp);
+            }
+            g[n] = acc;
+            gp[n] = accp;
+          }
+          float Gx[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, Gy[5] = {0.f, 0.f, 0.f, 0.f, 0.f},
+                Gz[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, Y[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+          static_for<0, NK>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            constexpr int l = l_of_k(k);
+            float ak = 0.f, ck = 0.f;
+#pragma unroll
+            for (int n = 0; n <= NA; ++n) {
+              ak = __fmaf_rn(dS[n][k], g[n], ak);
+              ck = __fmaf_rn(dS[n][k], gp[n], ck);
+            }
+            const float3 gb = poly_grad<k>(d.x, d.y, d.z, r2);
+            Gx[l] = __fmaf_rn(ak, gb.x, Gx[l]);
+            Gy[l] = __fmaf_rn(ak, gb.y, Gy[l]);
+            Gz[l] = __fmaf_rn(ak, gb.z, Gz[l]);
+            Y[l] = __fmaf_rn(ck, poly_b<k>(d.x, d.y, d.z, r2), Y[l]);
+          });
+          const float r1 = rinv, r2i = rinv * rinv, r3 = r2i * rinv, r4 = r2i * r2i;
+          const float gx = Gx[1] * r1 + Gx[2] * r2i + Gx[3] * r3 + Gx[4] * r4;
+          const float gy = Gy[1] * r1 + Gy[2] * r2i + Gy[3] * r3 + Gy[4] * r4;
+          const float gz = Gz[1] * r1 + Gz[2] * r2i + Gz[3] * r3 + Gz[4] * r4;
+          const float yy = Y[1] * r1 + Y[2] * r2i + Y[3] * r3 + Y[4] * r4;
+          const float ux = d.x * rinv, uy = d.y * rinv, uz = d.z * rinv;
+          const float gu = gx * ux + gy * uy + gz * uz;
+          const float px = (gx - gu * ux) + yy * ux;
+          const float py = (gy - gu * uy) + yy * uy;
+          const float pz = (gz - gu * uz) + yy * uz;
+          a.p_ang[(size_t)m * N + i] = make_float4(px, py, pz, 0.f);
+        }
+      }
+    }
+  }
+  if constexpr (!DESC_ONLY) {
+    // deterministic block sum of U (fixed shuffle tree, then fixed warp order)
+    __shared__ double red[kAtomBlock / 32];
+    double v = Ublock;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int wv = 0; wv < kAtomBlock / 32; ++wv) s += red[wv];
+      a.partial_atom[blockIdx.x] = s;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------ gather kernel
+template <class S>
+__global__ void __launch_bounds__(kGatherBlock)
+    gather_kernel(const AtomArgs a) {
+  constexpr int KR = S::KR, EST = S::EST;
+  extern __shared__ float4 smem4[];
+  float4 *dtab_s = smem4;
+  for (int v = threadIdx.x; v < a.ncode; v += blockDim.x) dtab_s[v] = a.dtab[v];
+  __syncthreads();
+  const int N = a.N, T = a.T;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double part[kReduceSlots];
+#pragma unroll
+  for (int s = 0; s < kReduceSlots; ++s) part[s] = 0.0;
+  if (i < N) {
+    const float4 pi = a.pos4[i];
+    const int ti = type_of(pi);
+    const float inv_rcR = 1.f / a.rcR;
+    const float rcR2 = a.rcR * a.rcR, rcA2 = a.rcA * a.rcA;
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    float w[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) w[c] = 0.f;
+    // ---- radial part (Algorithm 2): s_i from own e^{t_j}, s_j from neighbour's e^{t_i}
+    int base = 0;
+    for (int t = 0; t < T; ++t) {
+      const int cnt = a.nn_r[t * N + i];
+      float eo[EST];
+      const float4 *src = reinterpret_cast<const float4 *>(a.e_rad + ((size_t)i * T + t) * EST);
+#pragma unroll
+      for (int k4 = 0; k4 < EST / 4; ++k4) {
+        const float4 v = src[k4];
+        eo[4 * k4] = v.x; eo[4 * k4 + 1] = v.y; eo[4 * k4 + 2] = v.z; eo[4 * k4 + 3] = v.w;
+      }
+      for (int m = 0; m < cnt; ++m) {
+        const unsigned e = a.nl_r[(size_t)(base + m) * N + i];
+        const int j = e & a.jmask;
+        const float4 pj = a.pos4[j];
+        const float3 d = pair_vector(pi, pj, dtab_s[e >> a.jbits]);
+        const float r2 = norm2(d);
+        if (r2 < rcR2) {
+          const float rinv = rsqrtf(r2);
+          const float r = r2 * rinv;
+          float ej[EST];
+          const float4 *srcj = reinterpret_cast<const float4 *>(a.e_rad + ((size_t)j * T + ti) * EST);
+#pragma unroll
+          for (int k4 = 0; k4 < EST / 4; ++k4) {
+            const float4 v = __ldg(srcj + k4);
+            ej[4 * k4] = v.x; ej[4 * k4 + 1] = v.y; ej[4 * k4 + 2] = v.z; ej[4 * k4 + 3] = v.w;
+          }
+          // sum_k e_k f_k'(r) = (x' fc/2) sum_k e_k T_k'(x) + (fc'/2) (sum_k e_k T_k(x) + sum_k e_k)
+          const float u = r * inv_rcR;
+          float sn, cs;
+          __sincosf(3.14159265358979f * u, &sn, &cs);
+          const float hfc = 0.25f * (1.f + cs);
+          const float hfcp = -0.25f * 3.14159265358979f * inv_rcR * sn;
+          const float t1 = u - 1.f;
+          const float x = 2.f * t1 * t1 - 1.f;
+          const float xp = 4.f * t1 * inv_rcR;
+          const float x2 = 2.f * x;
+          float tkm1 = 1.f, tk = x, dkm1 = 0.f, dk = 1.f;
+          float oT = eo[0], oD = 0.f, jT = ej[0], jD = 0.f;
+          if (KR >= 1) {
+            oT = __fmaf_rn(eo[1], x, oT);
+            jT = __fmaf_rn(ej[1], x, jT);
+            oD = eo[1];
+            jD = ej[1];
+          }
+#pragma unroll
+          for (int k = 2; k <= KR; ++k) {
+            const float tn = __fmaf_rn(x2, tk, -tkm1);
+            const float dn = __fmaf_rn(x2, dk, __fmaf_rn(2.f, tk, -dkm1));
+            tkm1 = tk; tk = tn; dkm1 = dk; dk = dn;
+            oT = __fmaf_rn(eo[k], tn, oT);
+            jT = __fmaf_rn(ej[k], tn, jT);
+            oD = __fmaf_rn(eo[k], dn, oD);
+            jD = __fmaf_rn(ej[k], dn, jD);
+          }
+          const float a1 = xp * hfc;
+          const float si = __fmaf_rn(a1, oD, hfcp * (oT + eo[KR + 1]));
+          const float sj = __fmaf_rn(a1, jD, hfcp * (jT + ej[KR + 1]));
+          const float fs = (si + sj) * rinv;
+          fx = __fmaf_rn(fs, d.x, fx);
+          fy = __fmaf_rn(fs, d.y, fy);
+          fz = __fmaf_rn(fs, d.z, fz);
+          // W_i += r_ij (x) dU_j/dr_ji with dU_j/dr_ji = -s_j d / r
+          const float ws = -sj * rinv;
+          const float px = ws * d.x, py = ws * d.y, pz = ws * d.z;
+          w[0] = __fmaf_rn(d.x, px, w[0]);
+          w[1] = __fmaf_rn(d.y, py, w[1]);
+          w[2] = __fmaf_rn(d.z, pz, w[2]);
+          w[3] = __fmaf_rn(d.x, py, w[3]);
+          w[4] = __fmaf_rn(d.x, pz, w[4]);
+          w[5] = __fmaf_rn(d.y, pz, w[5]);
+          w[6] = __fmaf_rn(d.y, px, w[6]);
+          w[7] = __fmaf_rn(d.z, px, w[7]);
+          w[8] = __fmaf_rn(d.z, py, w[8]);
+        }
+      }
+      base += cnt;
+    }
+    // ---- angular part (Algorithm 4): F_i += P_ij - P_ji, W_i += r_ij (x) P_ji
+    const int na = a.nn_a[i];
+    for (int m = 0; m < na; ++m) {
+      const size_t slot = (size_t)m * N + i;
+      const unsigned e = a.nl_a[slot];
+      const float4 pj = a.pos4[e & a.jmask];
+      const float3 d = pair_vector(pi, pj, dtab_s[e >> a.jbits]);
+      const float r2 = norm2(d);
+      if (r2 < rcA2) {
+        const float4 pij = a.p_ang[slot];
+        const float4 pji = a.p_ang[a.rev_a[slot]];
+        fx += pij.x - pji.x;
+        fy += pij.y - pji.y;
+        fz += pij.z - pji.z;
+        w[0] = __fmaf_rn(d.x, pji.x, w[0]);
+        w[1] = __fmaf_rn(d.y, pji.y, w[1]);
+        w[2] = __fmaf_rn(d.z, pji.z, w[2]);
+        w[3] = __fmaf_rn(d.x, pji.y, w[3]);
+        w[4] = __fmaf_rn(d.x, pji.z, w[4]);
+        w[5] = __fmaf_rn(d.y, pji.z, w[5]);
+        w[6] = __fmaf_rn(d.y, pji.x, w[6]);
+        w[7] = __fmaf_rn(d.z, pji.x, w[7]);
+        w[8] = __fmaf_rn(d.z, pji.y, w[8]);
+      }
+    }
+    const double Fx = fx, Fy = fy, Fz = fz;
+    if (a.force) {
+      a.force[3 * (size_t)i] = Fx;
+      a.force[3 * (size_t)i + 1] = Fy;
+      a.force[3 * (size_t)i + 2] = Fz;
+    }
+    if (a.virial) {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) a.virial[9 * (size_t)i + c] = (double)w[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 9; ++c) part[2 + c] = (double)w[c];
+    if (a.md_kick) {  // second half-kick of velocity Verlet, and kinetic energy
+      double *v = a.vel + 3 * (size_t)i;
+      const double s = a.half_dt * a.inv_mass_kappa[ti];
+      const double vx = v[0] + s * Fx, vy = v[1] + s * Fy, vz = v[2] + s * Fz;
+      v[0] = vx; v[1] = vy; v[2] = vz;
+      part[1] = a.mass_kappa_half[ti] * (vx * vx + vy * vy + vz * vz);
+    }
+  }
+  // deterministic block sums of (spare, KE, W[9])
+  __shared__ double red[kGatherBlock / 32][kReduceSlots];
+#pragma unroll
+  for (int s = 1; s < 11; ++s) {
+    double v = part[s];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][s] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 11 && threadIdx.x >= 1) {
+    double s = 0.0;
+    for (int wv = 0; wv < kGatherBlock / 32; ++wv) s += red[wv][threadIdx.x];
+    a.partial_gather[(size_t)blockIdx.x * kReduceSlots + threadIdx.x] = s;
+  }
+}
+
+// ------------------------------------------------------------------------ launchers
+template <class S>
+size_t atom_smem_bytes(int T, int ncode) {
+  return sizeof(float4) * ncode +
+         sizeof(float) * (T * T * (S::NR + 1) * (S::KR + 1) + T * T * (S::NA + 1) * (S::KA + 1) +
+                          (S::NA + 1) * S::NK * kAtomBlock);
+}
+
+template <class S>
+cudaError_t launch_atom(const AtomArgs &a, const ModelF &mf, const float *w0, const float *b0, const float *w1,
+                        float b1, int descriptor_only, cudaStream_t st) {
+  if (a.N <= 0) return cudaSuccess;
+  AnnConst<S> w;  // host staging; copied into the launch by value
+  for (int v = 0; v < S::H * S::NDES; ++v) w.w0[v] = w0[v];
+  for (int v = 0; v < S::H; ++v) {
+    w.b0[v] = b0[v];
+    w.w1[v] = w1[v];
+  }
+  w.b1 = b1;
+  w.m = mf;
+  const int blocks = (a.N + kAtomBlock - 1) / kAtomBlock;
+  const size_t smem = atom_smem_bytes<S>(a.T, a.ncode);
+  if (descriptor_only) {
+    auto k = atom_kernel<S, true>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<blocks, kAtomBlock, smem, st>>>(a, w);
+  } else {
+    auto k = atom_kernel<S, false>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<blocks, kAtomBlock, smem, st>>>(a, w);
+  }
+  return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t launch_gather(const AtomArgs &a, cudaStream_t st) {
+  if (a.N <= 0) return cudaSuccess;
+  const int blocks = (a.N + kGatherBlock - 1) / kGatherBlock;
+  gather_kernel<S><<<blocks, kGatherBlock, sizeof(float4) * a.ncode, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <class S> int atom_blocks(int N) { return (N + kAtomBlock - 1) / kAtomBlock; }
+template <class S> int gather_blocks(int N) { return (N + kGatherBlock - 1) / kGatherBlock; }
+
+template <class S>
+ShapeOps make_ops() {
+  ShapeOps o;
+  o.nR = S::NR; o.KR = S::KR; o.nA = S::NA; o.KA = S::KA; o.H = S::H;
+  o.L3 = S::L3; o.L4 = S::L4; o.L5 = S::L5; o.n_des = S::NDES;
+  o.atom = &launch_atom<S>;
+  o.gather = &launch_gather<S>;
+  o.atom_blocks = &atom_blocks<S>;
+  o.gather_blocks = &gather_blocks<S>;
+  return o;
+}
+
+}  // namespace nep

@@ -1,0 +1,285 @@
+"""Thin ctypes binding of libnep (include/nep.h).
+
+Argument marshalling only: every step of the NEP evaluation runs in the library's CUDA
+kernels. Functions keep the C names (nep_create, nep_compute, md_init, md_run, ...);
+device arrays are torch CUDA tensors, passed by data pointer on torch's current stream.
+There is no CPU fallback: if libnep.so is missing or cannot load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnep.so")
+
+NEP_OK = 0
+ERRORS = {-1: "NEP_ERR_ARG", -2: "NEP_ERR_OOM", -3: "NEP_ERR_CUDA", -4: "NEP_ERR_NEIGHBOR_OVERFLOW",
+          -5: "NEP_ERR_NONFINITE", -6: "NEP_ERR_UNSUPPORTED", -7: "NEP_ERR_STATE"}
+
+
+class NepError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class nep_params(C.Structure):
+    _fields_ = [("version", C.c_int), ("n_types", C.c_int), ("rc_radial", C.c_double),
+                ("rc_angular", C.c_double), ("n_max_radial", C.c_int), ("n_max_angular", C.c_int),
+                ("basis_radial", C.c_int), ("basis_angular", C.c_int), ("l_max_3b", C.c_int),
+                ("l_max_4b", C.c_int), ("l_max_5b", C.c_int), ("n_neuron", C.c_int),
+                ("c_radial", C.c_void_p), ("c_angular", C.c_void_p), ("w0", C.c_void_p),
+                ("b0", C.c_void_p), ("w1", C.c_void_p), ("b1", C.c_double), ("mass", C.c_void_p),
+                ("skin", C.c_double)]
+
+
+class nep_stats(C.Structure):
+    _fields_ = [("n_atoms", C.c_int), ("cap_radial", C.c_int), ("cap_angular", C.c_int),
+                ("max_radial", C.c_int), ("max_angular", C.c_int), ("mean_radial", C.c_double),
+                ("mean_angular", C.c_double), ("mean_radial_in_rc", C.c_double),
+                ("mean_angular_in_rc", C.c_double), ("n_rebuilds", C.c_longlong),
+                ("md_steps", C.c_longlong), ("cells", C.c_int * 3)]
+
+
+_lib = None
+
+# exported symbol -> (restype, argtypes)
+_P = C.c_void_p
+_SIGS = {
+    "nep_create": (C.c_int, [C.POINTER(nep_params), C.POINTER(_P)]),
+    "nep_destroy": (C.c_int, [_P]),
+    "nep_last_error": (C.c_char_p, [_P]),
+    "nep_compute": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "nep_compute_host": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "nep_descriptors": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P]),
+    "nep_n_des": (C.c_int, [_P]),
+    "md_init": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P]),
+    "md_init_host": (C.c_int, [_P, C.c_int, _P, _P, _P, _P]),
+    "md_run": (C.c_int, [_P, C.c_int, C.c_double, C.c_int, _P, _P]),
+    "md_get_state": (C.c_int, [_P, _P, _P, _P, _P]),
+    "md_get_state_host": (C.c_int, [_P, _P, _P, _P]),
+    "nep_get_stats": (C.c_int, [_P, C.POINTER(nep_stats)]),
+    "nep_set_profiling": (C.c_int, [_P, C.c_int]),
+    "nep_kernel_slots": (C.c_int, []),
+    "nep_kernel_name": (C.c_char_p, [C.c_int]),
+    "nep_kernel_times": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int]),
+    "nep_supported": (C.c_int, [C.POINTER(C.c_int), C.c_int]),
+}
+EXPORTED = tuple(_SIGS)
+
+
+def load(path: str | None = None) -> C.CDLL:
+    """Load libnep.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    if _lib is None:
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libnep.so not built ({p}); run __graft_entry__.build()")
+        lib = C.CDLL(p)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(rc: int, h=None):
+    if rc != NEP_OK:
+        msg = load().nep_last_error(h)
+        raise NepError(rc, msg.decode() if msg else "")
+
+
+def _stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _dev(t, dtype, shape=None, name="array"):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.data_ptr()
+
+
+def _box(box) -> np.ndarray:
+    b = np.ascontiguousarray(np.asarray(box, dtype=np.float64).reshape(3, 3))
+    return b
+
+
+def nep_supported():
+    lib = load()
+    n = lib.nep_supported(None, 0)
+    buf = (C.c_int * (8 * n))()
+    lib.nep_supported(buf, n)
+    return [tuple(buf[8 * i:8 * i + 8]) for i in range(n)]
+
+
+def nep_create(model, skin: float = 1.0):
+    """Handle for a workloads.NepModel (weights are copied into the library)."""
+    lib = load()
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in
+            (model.c_radial, model.c_angular, model.w0, model.b0, model.w1)]
+    mass = None if model.mass is None else np.ascontiguousarray(model.mass, dtype=np.float64)
+    p = nep_params(3, model.n_types, model.rc_radial, model.rc_angular, model.n_max_radial,
+                   model.n_max_angular, model.basis_radial, model.basis_angular, model.l_max_3b,
+                   model.l_max_4b, model.l_max_5b, model.n_neuron,
+                   *[a.ctypes.data for a in arrs], float(model.b1),
+                   None if mass is None else mass.ctypes.data, float(skin))
+    h = C.c_void_p()
+    rc = lib.nep_create(C.byref(p), C.byref(h))
+    _check(rc, None)
+    return h
+
+
+def nep_destroy(h):
+    if h:
+        load().nep_destroy(h)
+
+
+def nep_n_des(h) -> int:
+    return int(load().nep_n_des(h))
+
+
+def nep_compute(h, pos, types, box, energy=None, energy_total=None, force=None, virial=None,
+                virial_total=None):
+    """Device evaluation; pos [N,3] f64, types [N] i32, outputs preallocated CUDA f64 tensors."""
+    import torch
+    n = int(pos.shape[0])
+    b = _box(box)
+    rc = load().nep_compute(h, n, _dev(pos, torch.float64, (n, 3), "pos"), _dev(types, torch.int32, (n,), "types"),
+                            b.ctypes.data, _dev(energy, torch.float64, (n,), "energy"),
+                            _dev(energy_total, torch.float64, (1,), "energy_total"),
+                            _dev(force, torch.float64, (n, 3), "force"), _dev(virial, torch.float64, (n, 9), "virial"),
+                            _dev(virial_total, torch.float64, (9,), "virial_total"), _stream())
+    _check(rc, h)
+
+
+def nep_compute_host(h, pos, types, box):
+    """Host-array evaluation: returns (U [N], E, F [N,3], W [N,9], W_total [9])."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    types = np.ascontiguousarray(types, dtype=np.int32)
+    n = pos.shape[0]
+    U = np.zeros(n)
+    F = np.zeros((n, 3))
+    Wv = np.zeros((n, 9))
+    Wt = np.zeros(9)
+    E = C.c_double(0.0)
+    b = _box(box)
+    rc = load().nep_compute_host(h, n, pos.ctypes.data, types.ctypes.data, b.ctypes.data, U.ctypes.data,
+                                 C.addressof(E), F.ctypes.data, Wv.ctypes.data, Wt.ctypes.data)
+    _check(rc, h)
+    return U, float(E.value), F, Wv, Wt
+
+
+def nep_descriptors(h, pos, types, box, q):
+    import torch
+    n = int(pos.shape[0])
+    b = _box(box)
+    rc = load().nep_descriptors(h, n, _dev(pos, torch.float64, (n, 3), "pos"), _dev(types, torch.int32, (n,), "types"),
+                                b.ctypes.data, _dev(q, torch.float64, None, "q"), _stream())
+    _check(rc, h)
+
+
+def md_init(h, pos, types, box, vel=None):
+    import torch
+    n = int(pos.shape[0])
+    b = _box(box)
+    rc = load().md_init(h, n, _dev(pos, torch.float64, (n, 3), "pos"), _dev(types, torch.int32, (n,), "types"),
+                        b.ctypes.data, _dev(vel, torch.float64, (n, 3), "vel"), _stream())
+    _check(rc, h)
+
+
+def md_init_host(h, pos, types, box, vel=None):
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    types = np.ascontiguousarray(types, dtype=np.int32)
+    v = None if vel is None else np.ascontiguousarray(vel, dtype=np.float64).reshape(-1, 3)
+    b = _box(box)
+    rc = load().md_init_host(h, pos.shape[0], pos.ctypes.data, types.ctypes.data, b.ctypes.data,
+                             None if v is None else v.ctypes.data)
+    _check(rc, h)
+
+
+def md_run(h, n_steps: int, dt_fs: float, thermo_every: int = 1, thermo=None):
+    import torch
+    rc = load().md_run(h, int(n_steps), float(dt_fs), int(thermo_every), _dev(thermo, torch.float64, None, "thermo"),
+                       _stream())
+    _check(rc, h)
+
+
+def md_get_state(h, pos=None, vel=None, force=None):
+    import torch
+    rc = load().md_get_state(h, _dev(pos, torch.float64, None, "pos"), _dev(vel, torch.float64, None, "vel"),
+                             _dev(force, torch.float64, None, "force"), _stream())
+    _check(rc, h)
+
+
+def md_get_state_host(h, n: int):
+    pos = np.zeros((n, 3))
+    vel = np.zeros((n, 3))
+    F = np.zeros((n, 3))
+    rc = load().md_get_state_host(h, pos.ctypes.data, vel.ctypes.data, F.ctypes.data)
+    _check(rc, h)
+    return pos, vel, F
+
+
+def nep_get_stats(h) -> dict:
+    s = nep_stats()
+    _check(load().nep_get_stats(h, C.byref(s)), h)
+    d = {f: getattr(s, f) for f, _ in nep_stats._fields_}
+    d["cells"] = tuple(s.cells)
+    return d
+
+
+def nep_set_profiling(h, enable: bool):
+    _check(load().nep_set_profiling(h, 1 if enable else 0), h)
+
+
+def nep_kernel_times(h) -> dict:
+    lib = load()
+    n = lib.nep_kernel_slots()
+    buf = (C.c_float * n)()
+    _check(lib.nep_kernel_times(h, buf, n), h)
+    return {lib.nep_kernel_name(i).decode(): float(buf[i]) for i in range(n)}
+
+
+class NEP:
+    """Convenience owner of one handle (destroyed with the object)."""
+
+    def __init__(self, model, skin: float = 1.0):
+        self.model = model
+        self.h = nep_create(model, skin)
+
+    def close(self):
+        if self.h:
+            nep_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def compute(self, pos, types, box, per_atom_virial: bool = False):
+        """pos/types as CUDA tensors; returns dict of CUDA tensors (U, E, F, W?, W_total)."""
+        import torch
+        n = int(pos.shape[0])
+        dev = pos.device
+        out = dict(U=torch.empty(n, dtype=torch.float64, device=dev),
+                   E=torch.empty(1, dtype=torch.float64, device=dev),
+                   F=torch.empty((n, 3), dtype=torch.float64, device=dev),
+                   W_total=torch.empty(9, dtype=torch.float64, device=dev))
+        if per_atom_virial:
+            out["W"] = torch.empty((n, 9), dtype=torch.float64, device=dev)
+        nep_compute(self.h, pos, types, box, out["U"], out["E"], out["F"], out.get("W"), out["W_total"])
+        return out
