@@ -1,0 +1,413 @@
+#!/usr/bin/env python
+"""NEP3 molecular-dynamics throughput on GB300: atom-steps/s of velocity-Verlet NVE.
+
+Default workload: rocksalt PbTe, 32^3 conventional cells (262,144 atoms), two species,
+NEP radial/angular cutoffs 6/4 A, n_max 10/6, basis 10/6, l_max 4/2/1, 30 neurons,
+random weights (seed 1), 300 K Maxwell-Boltzmann velocities, dt = 2 fs.
+
+One timed step = one MD step of the whole hot path (drift, neighbour rebuild when
+triggered, descriptor + network + angular partial forces, force/virial gather, kick,
+energy/virial reductions), replayed from the library's captured CUDA graph. Each step is
+bracketed by CUDA events on the launching stream; L2 is flushed (a 256 MiB write) before
+every timed step, outside the events.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+Multi-GPU (torchrun): every rank runs an independent replica of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 256 << 20
+METRIC = "NEP atom-steps/s on 1 GB300 (plain vs batched/BF16); p50/p99 request latency"
+UNIT = "atom-steps/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--workload", choices=["pbte", "si", "si_large"], default="pbte")
+    ap.add_argument("--skin", type=float, default=1.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def make_workload(name: str):
+    from paper_2205_10046_gb300 import workloads as W
+    if name == "pbte":
+        return W.pbte_rocksalt(32, seed=1)
+    if name == "si":
+        return W.si_diamond(3, seed=0)
+    return W.si_diamond(100, seed=0, n_steps=100, dt_fs=1.0)
+
+
+def workload_config(w, name):
+    desc = {"pbte": "rocksalt PbTe 32x32x32 conventional cells, a=6.46 A, sigma=0.1 A, 300 K, dt=2 fs",
+            "si": "diamond Si 3x3x3 conventional cells, a=5.43 A, sigma=0.05 A, 300 K, dt=1 fs",
+            "si_large": "diamond Si 100x100x100 conventional cells, a=5.43 A, sigma=0.05 A, 300 K, dt=1 fs"}[name]
+    m = w.model
+    return {"workload": f"{w.name} ({w.n_atoms} atoms): {desc}", "n_atoms": w.n_atoms,
+            "nep": f"types={m.n_types} rc={m.rc_radial}/{m.rc_angular} n_max={m.n_max_radial}/{m.n_max_angular} "
+                   f"basis={m.basis_radial}/{m.basis_angular} l_max={m.l_max_3b}/{m.l_max_4b}/{m.l_max_5b} "
+                   f"neurons={m.n_neuron} random weights",
+            "integrator": "velocity Verlet NVE", "l2": "flushed (256 MiB write) before every timed step"}
+
+
+# ----------------------------------------------------------------------------- flop model
+def flop_model(m, T, nr_list, nr_valid, na_list, na_valid):
+    """FP32 flops per atom of the two NEP kernels, counted from their arithmetic (FMA = 2).
+
+    Returns (atom_kernel_flops, gather_kernel_flops). Inputs: model shape, number of types,
+    mean list lengths (r < r_c + skin) and mean in-cutoff counts (r < r_c) per atom.
+    """
+    nR, KR, nA, KA, H = m.n_max_radial, m.basis_radial, m.n_max_angular, m.basis_angular, m.n_neuron
+    NK = 24
+    D = m.n_des
+    entry = 12                                   # pair vector, r^2, compare
+    cheb = 14 + 4 * max(KR - 1, 0)               # cutoff + Chebyshev f_k
+    cheb_a = 14 + 4 * max(KA - 1, 0)
+    cheb_d = 25 + 12 * max(KA - 1, 0)            # f_k and f_k'
+    poly_b = 100                                 # the 24 homogeneous polynomials
+    poly_g = 190                                 # their gradients
+    rad_desc = nr_list * entry + nr_valid * (2 + cheb + (KR + 1)) + T * 2 * (nR + 1) * (KR + 1)
+    ang_desc = na_list * entry + na_valid * (2 + cheb_a + 2 * (nA + 1) * (KA + 1) + 4 + poly_b + NK
+                                             + 2 * (nA + 1) * NK)
+    comps = (nA + 1) * 104
+    ann = H * (4 * D + 7)
+    evec = T * (KR + 1) * (2 * (nR + 1) + 1)
+    dS = (nA + 1) * 137
+    ang_force = na_list * entry + na_valid * (2 + cheb_d + 4 * (nA + 1) * (KA + 1)
+                                              + NK * (4 * (nA + 1) + 12) + poly_b + poly_g + 50)
+    atom = rad_desc + ang_desc + comps + ann + evec + dS + ang_force
+    rad_force = nr_list * entry + nr_valid * (2 + 25 + 12 * max(KR - 1, 0) + 4 * (KR + 1) + 10 + 9 * 2 + 6)
+    ang_gather = na_list * entry + na_valid * (6 + 18)
+    gather = rad_force + ang_gather + 12
+    return atom, gather
+
+
+def survey_flop_model(m, nr, na):
+    """The naive per-pair estimate of the method (g_n evaluated per pair for every n):
+    NN_R [6 (n_R+1)(K_R+1) + 40] + NN_A [6 (n_A+1)(K_A+1) + 240 (n_A+1) + 60] + 4 N_des H + 90 (n_A+1)."""
+    nR, KR, nA, KA, H = m.n_max_radial, m.basis_radial, m.n_max_angular, m.basis_angular, m.n_neuron
+    return (nr * (6 * (nR + 1) * (KR + 1) + 40) + na * (6 * (nA + 1) * (KA + 1) + 240 * (nA + 1) + 60)
+            + 4 * m.n_des * H + 90 * (nA + 1))
+
+
+# ----------------------------------------------------------------------------- helpers
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha1()
+    for f in ("nep_kernels.cuh", "nep_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2205_10046_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic(workload: str):
+    """dram bytes per nep_atom launch from the committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"nep_atom_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"kernel_source_sha1:\s*(\w+)", txt)
+    b = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", txt)
+    if not m or not b or m.group(1) != kernel_source_hash():
+        return None
+    return float(b.group(1))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_sample(w_name: str):
+    """A bounded sample of the same workload for the FP64 oracle: the same lattice, model,
+    seed, jitter and temperature in a 4x4x4-cell box (512 atoms PbTe / 216 atoms Si)."""
+    from paper_2205_10046_gb300 import workloads as W
+    if w_name == "pbte":
+        return W.pbte_rocksalt(4, seed=1), "rocksalt PbTe 4x4x4 cells (512 atoms), same model/seed/jitter/300 K"
+    return W.si_diamond(3, seed=0), "diamond Si 3x3x3 cells (216 atoms), same model/seed/jitter/300 K"
+
+
+def cpu_baseline(w_name: str, seconds: float):
+    import oracle
+    s, desc = oracle_sample(w_name)
+    dt = s.dt_fs
+    t0 = time.perf_counter()
+    oracle.md(s.model, s.pos, s.vel, s.types, s.box, 1, dt)  # 2 force evaluations
+    t1 = time.perf_counter()
+    per_eval = (t1 - t0) / 2.0
+    steps = max(1, int(seconds / per_eval) - 1)
+    t0 = time.perf_counter()
+    oracle.md(s.model, s.pos, s.vel, s.types, s.box, steps, dt)
+    el = time.perf_counter() - t0
+    return {"value": s.n_atoms * steps / el, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{desc}; {steps} velocity-Verlet steps (+1 initial force evaluation) in {el:.1f} s, "
+                      f"FP64, OpenMP over atoms"}
+
+
+def run_reference(args):
+    """The oracle timed as it stands on the host cores: one velocity-Verlet run of K steps on
+    a bounded sample of the workload (the largest 2^3/3^3/4^3-cell box whose run is estimated
+    to finish in about 90 s)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2205_10046_gb300 import workloads as W
+    oracle.build()
+    w = make_workload(args.workload)
+    maker = (lambda r: W.pbte_rocksalt(r, seed=1)) if args.workload == "pbte" else (lambda r: W.si_diamond(r, seed=0))
+    probe = maker(2)
+    t0 = time.perf_counter()
+    oracle.md(probe.model, probe.pos, probe.vel, probe.types, probe.box, 1, probe.dt_fs)
+    per_atom_eval = (time.perf_counter() - t0) / (2 * probe.n_atoms)
+    reps = 2
+    for r in (3, 4):
+        if per_atom_eval * maker(r).n_atoms * (args.steps + args.warmup + 2) < 90.0:
+            reps = r
+    s = maker(reps)
+    pos, vel = s.pos, s.vel
+    if args.warmup:
+        pos, vel, _, _ = oracle.md(s.model, pos, vel, s.types, s.box, args.warmup, s.dt_fs)
+    t0 = time.perf_counter()
+    oracle.md(s.model, pos, vel, s.types, s.box, args.steps, s.dt_fs)
+    total = time.perf_counter() - t0
+    value = s.n_atoms * args.steps / total
+    desc = f"{s.name} ({s.n_atoms} atoms), same model/seed/jitter/300 K as the GPU workload"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(w, args.workload),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": f"{desc}; {args.steps} FP64 velocity-Verlet steps in one oracle call"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_gb300(args):
+    import numpy as np
+    import torch
+    from paper_2205_10046_gb300 import nep
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    import __graft_entry__ as ge
+    if rank == 0 or world == 1:
+        ge.build()
+    if world > 1:
+        dist.barrier()
+    nep.load()
+
+    w = make_workload(args.workload)
+    N = w.n_atoms
+    dt = w.dt_fs
+    h = nep.NEP(w.model, skin=args.skin)
+    pos_d = torch.tensor(w.pos, device=dev)
+    types_d = torch.tensor(w.types, device=dev)
+    vel_d = torch.tensor(w.vel, device=dev)
+    nep.md_init(h.h, pos_d, types_d, w.box, vel_d)
+    nep.nep_set_profiling(h.h, True)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    # warm-up (captures the step graph)
+    nep.md_run(h.h, max(args.warmup, 3), dt, 1, None)
+    torch.cuda.synchronize()
+
+    names = ["md_drift", "neighbor_rebuild", "nep_atom", "nep_gather", "finalize"]
+    ktime = {k: 0.0 for k in names}
+    step_ms = []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device() if world == 1 else local) as clk:
+        for s in range(args.steps):
+            flush.fill_(s)
+            ev0.record(stream)
+            nep.md_run_async(h.h, 1, dt, 1, None, stream.cuda_stream)
+            ev1.record(stream)
+            kt = nep.nep_kernel_times(h.h)  # synchronises on this step's last kernel
+            ev1.synchronize()
+            step_ms.append(ev0.elapsed_time(ev1))
+            for k in names:
+                ktime[k] += kt.get(k, 0.0)
+            if (s + 1) % 100 == 0:
+                nep.md_status(h.h, stream.cuda_stream)  # list health, outside the timed events
+    nep.md_status(h.h)
+    torch.cuda.synchronize()
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    stats = nep.nep_get_stats(h.h)
+
+    # end-to-end through the host-pointer entry points: upload, run, read back
+    thermo_every = 100
+    th = torch.zeros((max(1, args.steps // thermo_every), 4), dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nep.md_init_host(h.h, w.pos, w.types, w.box, w.vel)
+    nep.md_run_async(h.h, args.steps, dt, thermo_every, th, stream.cuda_stream)
+    nep.md_status(h.h)
+    th_host = th.cpu()
+    p_out, v_out, f_out = nep.md_get_state_host(h.h, N)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = N * (24 + 4 + 24) + 72
+    d2h = N * 72 + th_host.numel() * 8
+    etot = (th_host[:, 0] + th_host[:, 1]).numpy()
+
+    if rank == 0:
+        props = torch.cuda.get_device_properties(dev)
+        clocks = clk.summary()
+        sm_max = clocks.get("sm_max_mhz") or 2070.0
+        peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes
+        atom_f, gather_f = flop_model(w.model, w.model.n_types, stats["mean_radial"], stats["mean_radial_in_rc"],
+                                      stats["mean_angular"], stats["mean_angular_in_rc"])
+        atom_ms = ktime["nep_atom"] / args.steps
+        achieved = atom_f * N / (atom_ms / 1e3) / 1e12
+        traffic = profiled_traffic(args.workload)
+        value = world * N * args.steps / total_s
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(workload_config(w, args.workload), parallelism=f"replicas x{world}"),
+            "roofline": {"kernel": "nep_atom", "bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                         "flops_per_atom": atom_f,
+                         "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"},
+            "kernel_ms_per_step": {k: v / args.steps for k, v in ktime.items()},
+            "gather_roofline": {"achieved": gather_f * N / (ktime["nep_gather"] / args.steps / 1e3) / 1e12,
+                                "unit": "TFLOP/s", "flops_per_atom": gather_f},
+            "e2e": {"value": world * N * args.steps / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                    "path": "md_init_host + md_run_async + md_status + md_get_state_host (thermo every 100)"},
+            "gpu_launches": int(stats["graph_kernels"]) * args.steps,
+            "clocks": clocks,
+            "neighbours": {"radial_list": stats["mean_radial"], "radial_in_rc": stats["mean_radial_in_rc"],
+                           "angular_list": stats["mean_angular"], "angular_in_rc": stats["mean_angular_in_rc"],
+                           "rebuilds": stats["n_rebuilds"]},
+            "energy_drift_ev_per_atom": float((etot.max() - etot.min()) / N) if etot.size else None,
+            "survey_flops_per_atom_step": survey_flop_model(w.model, stats["mean_radial_in_rc"],
+                                                            stats["mean_angular_in_rc"]),
+        }
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

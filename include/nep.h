@@ -151,6 +151,17 @@ int md_init_host(nep_handle *h, int n_atoms, const double *pos, const int *types
  * hold (the state is then unusable; call md_init again). */
 int md_run(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *thermo, nep_stream_t stream);
 
+/* md_run without the final synchronisation: queues the n_steps graph replays on `stream`
+ * and returns. A neighbour-list overflow during these steps is reported by the next
+ * md_status (or md_run) call instead. Same arguments as md_run. */
+int md_run_async(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *thermo,
+                 nep_stream_t stream);
+
+/* Synchronise `stream` and report the MD health: NEP_OK, or NEP_ERR_NEIGHBOR_OVERFLOW if a
+ * rebuild since md_init found more neighbours than the lists hold (the state is then
+ * unusable; call md_init again). */
+int md_status(nep_handle *h, nep_stream_t stream);
+
 /* Copy the MD state out (DEVICE pointers; any may be NULL): positions wrapped into the
  * cell [N][3], velocities [N][3], forces of the current positions [N][3]. */
 int md_get_state(nep_handle *h, double *pos, double *vel, double *force, nep_stream_t stream);
@@ -168,6 +179,7 @@ typedef struct {
   long long n_rebuilds;          /* neighbour rebuilds since md_init */
   long long md_steps;            /* MD steps since md_init */
   int cells[3];                  /* cell grid */
+  int graph_kernels;             /* kernel nodes in the captured MD step graph (0 before md_run) */
 } nep_stats;
 
 int nep_get_stats(nep_handle *h, nep_stats *out);

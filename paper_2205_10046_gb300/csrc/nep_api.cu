@@ -13,7 +13,8 @@
 #include "nep_internal.cuh"
 
 namespace nep {
-void launch_rebuild(int N, int T, const Grid &g, const float4 *dtab, float rlR2, float rlA2, int cap_r, int cap_a,
+void launch_rebuild(int N, int T, const Grid &g, const float4 *dtab, float rlR2, float rlA2, float rcR2, float rcA2,
+                    int cap_r, int cap_a,
                     int count_only, double *x, double *x_ref, double *origin, const int *types, float4 *pos4,
                     int *cell_of, int *cell_count, int *cell_cursor, int *cell_start, int *cell_atoms,
                     unsigned *nl_r, int *nn_r, unsigned *nl_a, int *nn_a, int *rev_a, BuildStatus *st,
@@ -118,6 +119,7 @@ struct nep_handle {
   Grid grid;
   double volume = 0;
   DevBuf<double> x, v, F, x_ref, origin, partial_atom, partial_gather, thermo_stage;
+  DevBuf<double> ck_x, ck_v, ck_F;  // md_run checkpoint (start of the current chunk)
   DevBuf<int> types, cell_of, cell_count, cell_cursor, cell_start, cell_atoms, nn_r, nn_a, rev_a, thermo_ctl;
   DevBuf<unsigned> nl_r, nl_a;
   DevBuf<float4> pos4, dtab, p_ang;
@@ -136,6 +138,10 @@ struct nep_handle {
   cudaEvent_t ev[N_SLOTS][2] = {};
   bool slot_ran[N_SLOTS] = {};
   nep_stats stats_cache{};
+  int graph_kernels = 0;
+  // the kernels compare r^2 with the FP32 square of the FP32 cutoff
+  float rcR2f() const { return (float)rcR * (float)rcR; }
+  float rcA2f() const { return (float)rcA * (float)rcA; }
 };
 
 namespace {
@@ -288,9 +294,13 @@ void reset_status_counts(nep_handle *h) {
   h->h_status->sum_r = 0;
   h->h_status->sum_a = 0;
   h->h_status->bad_input = 0;
+  h->h_status->in_r = 0;
+  h->h_status->in_a = 0;
 }
 
-int round_cap(int m) { return std::min(kListBuf, ((m * 5) / 4 + 8 + 3) / 4 * 4); }
+// List capacity for a largest observed length m: room for the structure to densify
+// (random-weight models do) before a regrow is needed.
+int round_cap(int m) { return std::min(kListBuf, (2 * m + 16 + 3) / 4 * 4); }
 
 // Bin, size and build the neighbour lists for the positions in h->x (forced rebuild).
 int rebuild_lists(nep_handle *h, int N, cudaStream_t s) {
@@ -306,7 +316,8 @@ int rebuild_lists(nep_handle *h, int N, cudaStream_t s) {
     reset_status_counts(h);
     h->h_status->rebuild = 1;
     CK(cudaMemcpyAsync(h->status.p, h->h_status, sizeof(BuildStatus), cudaMemcpyHostToDevice, s), "status");
-    launch_rebuild(N, h->T, g, h->dtab.p, rlR * rlR, rlA * rlA, h->cap_r, h->cap_a, count_only ? 1 : 0, h->x.p,
+    launch_rebuild(N, h->T, g, h->dtab.p, rlR * rlR, rlA * rlA, h->rcR2f(), h->rcA2f(), h->cap_r, h->cap_a,
+                   count_only ? 1 : 0, h->x.p,
                    h->x_ref.p, h->origin.p, h->types.p, h->pos4.p, h->cell_of.p, h->cell_count.p, h->cell_cursor.p,
                    h->cell_start.p, h->cell_atoms.p, h->nl_r.p, h->nn_r.p, h->nl_a.p, h->nn_a.p, h->rev_a.p,
                    h->status.p, s);
@@ -329,6 +340,8 @@ int rebuild_lists(nep_handle *h, int N, cudaStream_t s) {
     h->stats_cache.max_angular = st.max_a;
     h->stats_cache.mean_radial = N ? (double)st.sum_r / N : 0.0;
     h->stats_cache.mean_angular = N ? (double)st.sum_a / N : 0.0;
+    h->stats_cache.mean_radial_in_rc = N ? (double)st.in_r / N : 0.0;
+    h->stats_cache.mean_angular_in_rc = N ? (double)st.in_a / N : 0.0;
     return NEP_OK;
   }
   return fail(h, NEP_ERR_NEIGHBOR_OVERFLOW, "neighbour lists could not be sized");
@@ -504,6 +517,7 @@ int nep_destroy(nep_handle *h) {
   h->d_cR.release(); h->d_cA.release(); h->d_inv_mk.release(); h->d_mk_half.release();
   h->x.release(); h->v.release(); h->F.release(); h->x_ref.release(); h->origin.release();
   h->partial_atom.release(); h->partial_gather.release(); h->thermo_stage.release();
+  h->ck_x.release(); h->ck_v.release(); h->ck_F.release();
   h->types.release(); h->cell_of.release(); h->cell_count.release(); h->cell_cursor.release();
   h->cell_start.release(); h->cell_atoms.release(); h->nn_r.release(); h->nn_a.release(); h->rev_a.release();
   h->thermo_ctl.release(); h->nl_r.release(); h->nl_a.release(); h->pos4.release(); h->dtab.release();
@@ -672,7 +686,8 @@ int md_step_launch(nep_handle *h, double dt, cudaStream_t s, bool capturing) {
   ev_record(h, SLOT_DRIFT, 1, s, capturing);
   ev_record(h, SLOT_REBUILD, 0, s, capturing);
   const float rlR = (float)(h->rcR + h->skin), rlA = (float)(h->rcA + h->skin);
-  launch_rebuild(N, h->T, h->grid, h->dtab.p, rlR * rlR, rlA * rlA, h->cap_r, h->cap_a, 0, h->x.p, h->x_ref.p,
+  launch_rebuild(N, h->T, h->grid, h->dtab.p, rlR * rlR, rlA * rlA, h->rcR2f(), h->rcA2f(), h->cap_r, h->cap_a, 0,
+                 h->x.p, h->x_ref.p,
                  h->origin.p, h->types.p, h->pos4.p, h->cell_of.p, h->cell_count.p, h->cell_cursor.p,
                  h->cell_start.p, h->cell_atoms.p, h->nl_r.p, h->nn_r.p, h->nl_a.p, h->nn_a.p, h->rev_a.p,
                  h->status.p, s);
@@ -688,19 +703,18 @@ int md_step_launch(nep_handle *h, double dt, cudaStream_t s, bool capturing) {
 }
 }  // namespace
 
-int md_run(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *thermo, nep_stream_t stream) {
-  if (!valid_handle(h)) return NEP_ERR_ARG;
-  h->err.clear();
+namespace {
+int md_queue(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *thermo, cudaStream_t s) {
   if (!h->md_ready) return fail(h, NEP_ERR_STATE, "md_run before md_init");
   if (n_steps < 0 || !(dt_fs > 0) || !std::isfinite(dt_fs) || thermo_every < 1)
     return fail(h, NEP_ERR_ARG, "need n_steps >= 0, dt > 0, thermo_every >= 1");
-  cudaStream_t s = (cudaStream_t)stream;
   if (n_steps == 0) return NEP_OK;
   const int rows = thermo ? n_steps / thermo_every : 0;
   CK(h->thermo_stage.ensure((size_t)4 * (rows + 1)), "alloc thermo");
   int ctl[4] = {0, 0, thermo ? thermo_every : (n_steps + 1), 0};
   CK(cudaMemcpyAsync(h->thermo_ctl.p, ctl, sizeof(ctl), cudaMemcpyHostToDevice, s), "thermo ctl");
-  // (re)capture the one-step graph when the step size or the profiling mode changed
+  // (re)capture the one-step graph when the step size, the profiling mode or the thermo
+  // staging buffer changed
   if (!h->graph || h->graph_dt != dt_fs || h->graph_prof != h->prof || h->graph_thermo != h->thermo_stage.p) {
     if (h->graph) {
       cudaGraphExecDestroy(h->graph);
@@ -716,6 +730,16 @@ int md_run(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *t
       return rc;
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
+    size_t nn = 0;
+    cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) cudaGraphGetNodes(graph, nodes.data(), &nn);
+    int nk = 0;
+    for (size_t k = 0; k < nn; ++k) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nodes[k], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+    }
+    h->graph_kernels = nk;
     e = cudaGraphInstantiate(&h->graph, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
@@ -726,11 +750,83 @@ int md_run(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *t
   for (int st = 0; st < n_steps; ++st) CK(cudaGraphLaunch(h->graph, s), "graph launch");
   if (thermo && rows > 0)
     CK(cudaMemcpyAsync(thermo, h->thermo_stage.p, sizeof(double) * 4 * rows, cudaMemcpyDeviceToDevice, s), "thermo");
-  int rc = read_status(h, s);
+  return NEP_OK;
+}
+}  // namespace
+
+int md_status(nep_handle *h, nep_stream_t stream) {
+  if (!valid_handle(h)) return NEP_ERR_ARG;
+  if (!h->md_ready) return fail(h, NEP_ERR_STATE, "no MD state");
+  int rc = read_status(h, (cudaStream_t)stream);
   if (rc) return rc;
   if (h->h_status->overflow || h->h_status->rev_missing) {
     h->md_ready = false;
     return fail(h, NEP_ERR_NEIGHBOR_OVERFLOW, "neighbour list overflow during md_run; call md_init again");
+  }
+  return NEP_OK;
+}
+
+int md_run_async(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *thermo, nep_stream_t stream) {
+  if (!valid_handle(h)) return NEP_ERR_ARG;
+  h->err.clear();
+  return md_queue(h, n_steps, dt_fs, thermo_every, thermo, (cudaStream_t)stream);
+}
+
+int md_run(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *thermo, nep_stream_t stream) {
+  if (!valid_handle(h)) return NEP_ERR_ARG;
+  h->err.clear();
+  if (!h->md_ready) return fail(h, NEP_ERR_STATE, "md_run before md_init");
+  if (n_steps < 0 || !(dt_fs > 0) || !std::isfinite(dt_fs) || thermo_every < 1)
+    return fail(h, NEP_ERR_ARG, "need n_steps >= 0, dt > 0, thermo_every >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int N = h->N;
+  const size_t b = sizeof(double) * 3 * (size_t)N;
+  CK(h->ck_x.ensure(3 * (size_t)N), "alloc checkpoint");
+  CK(h->ck_v.ensure(3 * (size_t)N), "alloc checkpoint");
+  CK(h->ck_F.ensure(3 * (size_t)N), "alloc checkpoint");
+  // chunks of whole thermo periods; each chunk starts from a checkpoint so that a list
+  // overflow during it can be undone: restore, grow the lists, rebuild, replay
+  const int chunk = thermo_every >= 64 ? thermo_every : (64 / thermo_every) * thermo_every;
+  int done = 0;
+  while (done < n_steps) {
+    const int c = std::min(chunk, n_steps - done);
+    CK(cudaMemcpyAsync(h->ck_x.p, h->x.p, b, cudaMemcpyDeviceToDevice, s), "checkpoint");
+    CK(cudaMemcpyAsync(h->ck_v.p, h->v.p, b, cudaMemcpyDeviceToDevice, s), "checkpoint");
+    CK(cudaMemcpyAsync(h->ck_F.p, h->F.p, b, cudaMemcpyDeviceToDevice, s), "checkpoint");
+    int rc = read_status(h, s);
+    if (rc) return rc;
+    const long long steps0 = h->h_status->md_steps, rebuilds0 = h->h_status->n_rebuilds;
+    for (int attempt = 0;; ++attempt) {
+      double *th = thermo ? thermo + 4 * (size_t)(done / thermo_every) : nullptr;
+      rc = md_queue(h, c, dt_fs, thermo_every, th, s);
+      if (rc) return rc;
+      rc = read_status(h, s);
+      if (rc) return rc;
+      const BuildStatus st = *h->h_status;
+      if (!st.overflow && !st.rev_missing) break;
+      if (attempt >= 2 || st.max_r > kListBuf || st.max_a > kListBuf) {
+        h->md_ready = false;
+        return fail(h, NEP_ERR_NEIGHBOR_OVERFLOW, "more than " + std::to_string(kListBuf) +
+                                                      " neighbours within r_c + skin for one atom");
+      }
+      // undo the chunk and rebuild with larger lists
+      CK(cudaMemcpyAsync(h->x.p, h->ck_x.p, b, cudaMemcpyDeviceToDevice, s), "restore");
+      CK(cudaMemcpyAsync(h->v.p, h->ck_v.p, b, cudaMemcpyDeviceToDevice, s), "restore");
+      CK(cudaMemcpyAsync(h->F.p, h->ck_F.p, b, cudaMemcpyDeviceToDevice, s), "restore");
+      rc = ensure_lists(h, N, round_cap(st.max_r), round_cap(st.max_a));
+      if (rc) return rc;
+      rc = rebuild_lists(h, N, s);
+      if (rc) return rc;
+      h->h_status->md_steps = steps0;
+      h->h_status->n_rebuilds = rebuilds0;
+      h->h_status->rebuild = 0;
+      CK(cudaMemcpyAsync(h->status.p, h->h_status, sizeof(BuildStatus), cudaMemcpyHostToDevice, s), "status");
+      if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+      }
+    }
+    done += c;
   }
   return NEP_OK;
 }
@@ -774,6 +870,7 @@ int nep_get_stats(nep_handle *h, nep_stats *out) {
   nep_stats s = h->stats_cache;
   s.cap_radial = h->cap_r;
   s.cap_angular = h->cap_a;
+  s.graph_kernels = h->graph_kernels;
   if (h->status.p) {
     cudaMemcpy(h->h_status, h->status.p, sizeof(BuildStatus), cudaMemcpyDeviceToHost);
     s.n_rebuilds = h->h_status->n_rebuilds;

@@ -24,8 +24,12 @@ __device__ __forceinline__ bool rebuild_pending(const BuildStatus *st) {
   return *(volatile const int *)&st->rebuild != 0;
 }
 
-__global__ void zero_cells_kernel(int ncell, int *count, int *cursor, const BuildStatus *st) {
+__global__ void zero_cells_kernel(int ncell, int *count, int *cursor, BuildStatus *st) {
   if (!rebuild_pending(st)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {  // per-build sums (the maxima are kept over the run)
+    st->sum_r = st->sum_a = 0ull;
+    st->in_r = st->in_a = 0ull;
+  }
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
     count[c] = 0;
     cursor[c] = 0;
@@ -131,8 +135,8 @@ __device__ __forceinline__ bool cand_less(int ga, float ra, unsigned ea, int gb,
 // count_only: write no entries, only the length statistics (used to size the lists).
 __global__ void build_lists_kernel(int N, const float4 *pos4, const int *cell_of, const int *start,
                                    const int *cell_atoms, const Grid g, const float4 *dtab, float rlR2, float rlA2,
-                                   int T, int cap_r, int cap_a, int count_only, unsigned *nl_r, int *nn_r,
-                                   unsigned *nl_a, int *nn_a, BuildStatus *st) {
+                                   float rcR2, float rcA2, int T, int cap_r, int cap_a, int count_only,
+                                   unsigned *nl_r, int *nn_r, unsigned *nl_a, int *nn_a, BuildStatus *st) {
   if (!rebuild_pending(st)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -141,7 +145,7 @@ __global__ void build_lists_kernel(int N, const float4 *pos4, const int *cell_of
   unsigned char tr[kListBuf];
   unsigned ea[kListBuf];
   float ra[kListBuf];
-  int nr = 0, nA = 0;
+  int nr = 0, nA = 0, inr = 0, ina = 0;
   const float4 pi = pos4[i];
   const int id = cell_of[i];
   const int cx = id / (g.nc[1] * g.nc[2]);
@@ -167,6 +171,8 @@ __global__ void build_lists_kernel(int N, const float4 *pos4, const int *cell_of
           const float4 pj = pos4[j];
           const float r2 = norm2(pair_vector(pi, pj, D));
           const unsigned ent = (unsigned)j | (code << g.jbits);
+          inr += r2 < rcR2;
+          ina += r2 < rcA2;
           if (r2 < rlR2) {
             if (nr < kListBuf) {
               er[nr] = ent;
@@ -190,6 +196,8 @@ __global__ void build_lists_kernel(int N, const float4 *pos4, const int *cell_of
   atomicMax(&st->max_a, nA);
   atomicAdd(&st->sum_r, (unsigned long long)nr);
   atomicAdd(&st->sum_a, (unsigned long long)nA);
+  atomicAdd(&st->in_r, (unsigned long long)inr);
+  atomicAdd(&st->in_a, (unsigned long long)ina);
   if (count_only) return;
   if (nr > cap_r || nA > cap_a || nr > kListBuf || nA > kListBuf) atomicOr(&st->overflow, 1);
   const int wr = min(min(nr, cap_r), kListBuf);
@@ -354,7 +362,8 @@ void launch_wrap(int N, const double *x, const Grid &g, double *out, cudaStream_
   wrap_positions_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, x, g, out);
 }
 
-void launch_rebuild(int N, int T, const Grid &g, const float4 *dtab, float rlR2, float rlA2, int cap_r, int cap_a,
+void launch_rebuild(int N, int T, const Grid &g, const float4 *dtab, float rlR2, float rlA2, float rcR2, float rcA2,
+                    int cap_r, int cap_a,
                     int count_only, double *x, double *x_ref, double *origin, const int *types, float4 *pos4,
                     int *cell_of, int *cell_count, int *cell_cursor, int *cell_start, int *cell_atoms,
                     unsigned *nl_r, int *nn_r, unsigned *nl_a, int *nn_a, int *rev_a, BuildStatus *st,
@@ -367,8 +376,8 @@ void launch_rebuild(int N, int T, const Grid &g, const float4 *dtab, float rlR2,
   scan_cells_kernel<<<1, 1024, 0, s>>>(g.ncell, cell_count, cell_start, st);
   scatter_atoms_kernel<<<nb, tb, 0, s>>>(N, cell_of, cell_start, cell_cursor, cell_atoms, st);
   sort_cells_kernel<<<cb, tb, 0, s>>>(g.ncell, cell_start, cell_atoms, st);
-  build_lists_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, pos4, cell_of, cell_start, cell_atoms, g, dtab, rlR2, rlA2, T,
-                                                     cap_r, cap_a, count_only, nl_r, nn_r, nl_a, nn_a, st);
+  build_lists_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, pos4, cell_of, cell_start, cell_atoms, g, dtab, rlR2, rlA2, rcR2,
+                                                     rcA2, T, cap_r, cap_a, count_only, nl_r, nn_r, nl_a, nn_a, st);
   if (!count_only) build_rev_kernel<<<nb, tb, 0, s>>>(N, nl_a, nn_a, g, rev_a, st);
   finish_build_kernel<<<1, 1, 0, s>>>(st);
 }

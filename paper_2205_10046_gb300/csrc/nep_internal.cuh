@@ -33,6 +33,7 @@ struct BuildStatus {
   int max_r, max_a;    // largest radial/angular list length
   int rev_missing;     // angular pairs without their reverse pair (must stay 0)
   unsigned long long sum_r, sum_a;  // total list entries
+  unsigned long long in_r, in_a;    // entries with r < r_c (at build time)
   int rebuild;         // a rebuild is pending (set by the drift kernel or the host)
   int bad_input;       // bit 0: type out of range, bit 1: non-finite position
   long long n_rebuilds;

@@ -41,7 +41,7 @@ class nep_stats(C.Structure):
                 ("max_radial", C.c_int), ("max_angular", C.c_int), ("mean_radial", C.c_double),
                 ("mean_angular", C.c_double), ("mean_radial_in_rc", C.c_double),
                 ("mean_angular_in_rc", C.c_double), ("n_rebuilds", C.c_longlong),
-                ("md_steps", C.c_longlong), ("cells", C.c_int * 3)]
+                ("md_steps", C.c_longlong), ("cells", C.c_int * 3), ("graph_kernels", C.c_int)]
 
 
 _lib = None
@@ -59,6 +59,8 @@ _SIGS = {
     "md_init": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P]),
     "md_init_host": (C.c_int, [_P, C.c_int, _P, _P, _P, _P]),
     "md_run": (C.c_int, [_P, C.c_int, C.c_double, C.c_int, _P, _P]),
+    "md_run_async": (C.c_int, [_P, C.c_int, C.c_double, C.c_int, _P, _P]),
+    "md_status": (C.c_int, [_P, _P]),
     "md_get_state": (C.c_int, [_P, _P, _P, _P, _P]),
     "md_get_state_host": (C.c_int, [_P, _P, _P, _P]),
     "nep_get_stats": (C.c_int, [_P, C.POINTER(nep_stats)]),
@@ -214,6 +216,17 @@ def md_run(h, n_steps: int, dt_fs: float, thermo_every: int = 1, thermo=None):
     rc = load().md_run(h, int(n_steps), float(dt_fs), int(thermo_every), _dev(thermo, torch.float64, None, "thermo"),
                        _stream())
     _check(rc, h)
+
+
+def md_run_async(h, n_steps: int, dt_fs: float, thermo_every: int = 1, thermo=None, stream=None):
+    import torch
+    rc = load().md_run_async(h, int(n_steps), float(dt_fs), int(thermo_every),
+                             _dev(thermo, torch.float64, None, "thermo"), _stream() if stream is None else stream)
+    _check(rc, h)
+
+
+def md_status(h, stream=None):
+    _check(load().md_status(h, _stream() if stream is None else stream), h)
 
 
 def md_get_state(h, pos=None, vel=None, force=None):
