@@ -180,6 +180,7 @@ typedef struct {
   long long md_steps;            /* MD steps since md_init */
   int cells[3];                  /* cell grid */
   int graph_kernels;             /* kernel nodes in the captured MD step graph (0 before md_run) */
+  int rebuild_kernels;           /* kernels of one neighbour rebuild (run only on rebuild steps) */
 } nep_stats;
 
 int nep_get_stats(nep_handle *h, nep_stats *out);

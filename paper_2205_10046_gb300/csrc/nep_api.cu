@@ -13,16 +13,15 @@
 #include "nep_internal.cuh"
 
 namespace nep {
-void launch_rebuild(int N, int T, const Grid &g, const float4 *dtab, float rlR2, float rlA2, float rcR2, float rcA2,
-                    int cap_r, int cap_a,
-                    int count_only, double *x, double *x_ref, double *origin, const int *types, float4 *pos4,
-                    int *cell_of, int *cell_count, int *cell_cursor, int *cell_start, int *cell_atoms,
-                    unsigned *nl_r, int *nn_r, unsigned *nl_a, int *nn_a, int *rev_a, BuildStatus *st,
-                    cudaStream_t s);
-void launch_drift(int N, double *x, double *v, const double *F, float4 *pos4, const double *x_ref,
-                  const double *origin, const double *inv_mass_kappa, double dt, double half_skin2, BuildStatus *st,
-                  cudaStream_t s);
-void launch_wrap(int N, const double *x, const Grid &g, double *out, cudaStream_t s);
+cudaError_t launch_rebuild(int N, int T, const Grid &g, const float4 *dtab, float rlR2, float rlA2, float rcR2,
+                           float rcA2, const AtomState &a, const ListBufs &L, int count_only, BuildStatus *st,
+                           cudaStream_t s);
+void launch_iota(int N, int *perm, cudaStream_t s);
+void launch_rebuild_condition(cudaGraphConditionalHandle hc, const BuildStatus *st, cudaStream_t s);
+void launch_drift(int N, const AtomState &a, const double *inv_mass_kappa, double dt, double half_skin2,
+                  BuildStatus *st, cudaStream_t s);
+void launch_export(int N, const AtomState &a, const Grid &g, double *pos, double *vel, double *force,
+                   cudaStream_t s);
 void launch_finalize(int nb_atom, const double *partial_atom, int nb_gather, const double *partial_gather,
                      double *energy_total, double *virial_total, double *thermo_stage, int *thermo_ctl, int N,
                      double volume, cudaStream_t s);
@@ -120,6 +119,9 @@ struct nep_handle {
   double volume = 0;
   DevBuf<double> x, v, F, x_ref, origin, partial_atom, partial_gather, thermo_stage;
   DevBuf<double> ck_x, ck_v, ck_F;  // md_run checkpoint (start of the current chunk)
+  DevBuf<int> ck_types, ck_perm;
+  DevBuf<double> x2, v2, F2;        // reorder scratch
+  DevBuf<int> types2, perm2, cell2, perm;
   DevBuf<int> types, cell_of, cell_count, cell_cursor, cell_start, cell_atoms, nn_r, nn_a, rev_a, thermo_ctl;
   DevBuf<unsigned> nl_r, nl_a;
   DevBuf<float4> pos4, dtab, p_ang;
@@ -132,7 +134,8 @@ struct nep_handle {
   double graph_dt = 0;
   bool graph_prof = false;
   const double *graph_thermo = nullptr;
-  cudaStream_t cap_stream = nullptr;
+  cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
+  int rebuild_kernels = 0;  // kernels in the conditional rebuild body of the step graph
   // profiling
   bool prof = false;
   cudaEvent_t ev[N_SLOTS][2] = {};
@@ -259,6 +262,13 @@ int ensure_atoms(nep_handle *h, int N) {
   CK(h->cell_of.ensure(n), "alloc");
   CK(h->cell_atoms.ensure(n), "alloc");
   CK(h->pos4.ensure(n), "alloc");
+  CK(h->x2.ensure(3 * n), "alloc");
+  CK(h->v2.ensure(3 * n), "alloc");
+  CK(h->F2.ensure(3 * n), "alloc");
+  CK(h->types2.ensure(n), "alloc");
+  CK(h->perm2.ensure(n), "alloc");
+  CK(h->cell2.ensure(n), "alloc");
+  CK(h->perm.ensure(n), "alloc");
   CK(h->nn_r.ensure(n * h->T), "alloc");
   CK(h->nn_a.ensure(n), "alloc");
   CK(h->e_rad.ensure(n * h->T * (size_t)(((h->KR + 2) + 3) / 4 * 4)), "alloc");
@@ -298,6 +308,23 @@ void reset_status_counts(nep_handle *h) {
   h->h_status->in_a = 0;
 }
 
+AtomState atom_state(nep_handle *h) {
+  AtomState a;
+  a.x = h->x.p; a.v = h->v.p; a.F = h->F.p; a.x_ref = h->x_ref.p; a.origin = h->origin.p;
+  a.types = h->types.p; a.perm = h->perm.p; a.cell_of = h->cell_of.p; a.pos4 = h->pos4.p;
+  a.x2 = h->x2.p; a.v2 = h->v2.p; a.F2 = h->F2.p; a.types2 = h->types2.p; a.perm2 = h->perm2.p;
+  a.cell2 = h->cell2.p;
+  return a;
+}
+
+ListBufs list_bufs(nep_handle *h) {
+  ListBufs L;
+  L.cell_count = h->cell_count.p; L.cell_cursor = h->cell_cursor.p; L.cell_start = h->cell_start.p;
+  L.cell_atoms = h->cell_atoms.p; L.nl_r = h->nl_r.p; L.nn_r = h->nn_r.p; L.nl_a = h->nl_a.p; L.nn_a = h->nn_a.p;
+  L.rev_a = h->rev_a.p; L.cap_r = h->cap_r; L.cap_a = h->cap_a;
+  return L;
+}
+
 // List capacity for a largest observed length m: room for the structure to densify
 // (random-weight models do) before a regrow is needed.
 int round_cap(int m) { return std::min(kListBuf, (2 * m + 16 + 3) / 4 * 4); }
@@ -316,11 +343,9 @@ int rebuild_lists(nep_handle *h, int N, cudaStream_t s) {
     reset_status_counts(h);
     h->h_status->rebuild = 1;
     CK(cudaMemcpyAsync(h->status.p, h->h_status, sizeof(BuildStatus), cudaMemcpyHostToDevice, s), "status");
-    launch_rebuild(N, h->T, g, h->dtab.p, rlR * rlR, rlA * rlA, h->rcR2f(), h->rcA2f(), h->cap_r, h->cap_a,
-                   count_only ? 1 : 0, h->x.p,
-                   h->x_ref.p, h->origin.p, h->types.p, h->pos4.p, h->cell_of.p, h->cell_count.p, h->cell_cursor.p,
-                   h->cell_start.p, h->cell_atoms.p, h->nl_r.p, h->nn_r.p, h->nl_a.p, h->nn_a.p, h->rev_a.p,
-                   h->status.p, s);
+    CK(launch_rebuild(N, h->T, g, h->dtab.p, rlR * rlR, rlA * rlA, h->rcR2f(), h->rcA2f(), atom_state(h),
+                      list_bufs(h), count_only ? 1 : 0, h->status.p, s),
+       "launch rebuild");
     CK(cudaGetLastError(), "launch rebuild");
     int rc = read_status(h, s);
     if (rc) return rc;
@@ -374,6 +399,7 @@ AtomArgs make_args(nep_handle *h, int N) {
   a.inv_mass_kappa = h->d_inv_mk.p;
   a.mass_kappa_half = h->d_mk_half.p;
   a.vel = h->v.p;
+  a.perm = h->perm.p;
   return a;
 }
 
@@ -388,15 +414,19 @@ int load_structure(nep_handle *h, int N, const double *pos, const int *types, co
   CK(cudaMemcpyAsync(h->dtab.p, dtab.data(), dtab.size() * sizeof(float4), cudaMemcpyHostToDevice, s), "copy");
   CK(cudaMemcpyAsync(h->x.p, pos, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s), "copy pos");
   CK(cudaMemcpyAsync(h->types.p, types, sizeof(int) * N, cudaMemcpyDeviceToDevice, s), "copy types");
+  launch_iota(N, h->perm.p, s);
   h->N = N;
   h->stats_cache.n_atoms = N;
   for (int a = 0; a < 3; ++a) h->stats_cache.cells[a] = h->grid.nc[a];
   return rebuild_lists(h, N, s);
 }
 
+// Outputs for the caller (nep_compute) are scattered to the caller's atom order; the MD
+// forces (force == h->F) stay in the internal order.
 int run_forces(nep_handle *h, int N, double *energy, double *force, double *virial, int md_kick, double half_dt,
                cudaStream_t s, bool capturing) {
   AtomArgs a = make_args(h, N);
+  if (force == h->F.p) a.perm = nullptr;
   a.energy = energy;
   a.force = force;
   a.virial = virial;
@@ -502,6 +532,7 @@ int nep_create(const nep_params *p, nep_handle **out) {
   for (int sl = 0; sl < N_SLOTS; ++sl)
     for (int w = 0; w < 2; ++w) cudaEventCreate(&h->ev[sl][w]);
   cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+  cudaStreamCreateWithFlags(&h->cap_stream2, cudaStreamNonBlocking);
   *out = h;
   return NEP_OK;
 }
@@ -510,6 +541,7 @@ int nep_destroy(nep_handle *h) {
   if (!h) return NEP_OK;
   if (h->graph) cudaGraphExecDestroy(h->graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
   for (int sl = 0; sl < N_SLOTS; ++sl)
     for (int w = 0; w < 2; ++w)
       if (h->ev[sl][w]) cudaEventDestroy(h->ev[sl][w]);
@@ -517,7 +549,9 @@ int nep_destroy(nep_handle *h) {
   h->d_cR.release(); h->d_cA.release(); h->d_inv_mk.release(); h->d_mk_half.release();
   h->x.release(); h->v.release(); h->F.release(); h->x_ref.release(); h->origin.release();
   h->partial_atom.release(); h->partial_gather.release(); h->thermo_stage.release();
-  h->ck_x.release(); h->ck_v.release(); h->ck_F.release();
+  h->ck_x.release(); h->ck_v.release(); h->ck_F.release(); h->ck_types.release(); h->ck_perm.release();
+  h->x2.release(); h->v2.release(); h->F2.release(); h->types2.release(); h->perm2.release(); h->cell2.release();
+  h->perm.release();
   h->types.release(); h->cell_of.release(); h->cell_count.release(); h->cell_cursor.release();
   h->cell_start.release(); h->cell_atoms.release(); h->nn_r.release(); h->nn_a.release(); h->rev_a.release();
   h->thermo_ctl.release(); h->nl_r.release(); h->nl_a.release(); h->pos4.release(); h->dtab.release();
@@ -629,10 +663,14 @@ int md_init(nep_handle *h, int n_atoms, const double *pos, const int *types, con
   if (h->mass.empty()) return fail(h, NEP_ERR_ARG, "md_init needs params->mass");
   if (n_atoms < 1 || !pos || !types || !box) return fail(h, NEP_ERR_ARG, "md_init needs atoms, types and a box");
   h->md_ready = false;
-  int rc = load_structure(h, n_atoms, pos, types, box, s);
+  // velocities enter in the caller's order; the neighbour build below moves them into the
+  // internal (cell) order together with positions, types and perm
+  int rc = ensure_atoms(h, n_atoms);
   if (rc) return rc;
   if (vel) CK(cudaMemcpyAsync(h->v.p, vel, sizeof(double) * 3 * n_atoms, cudaMemcpyDeviceToDevice, s), "copy vel");
   else CK(cudaMemsetAsync(h->v.p, 0, sizeof(double) * 3 * n_atoms, s), "memset vel");
+  rc = load_structure(h, n_atoms, pos, types, box, s);
+  if (rc) return rc;
   rc = run_forces(h, n_atoms, nullptr, h->F.p, nullptr, 0, 0.0, s, false);
   if (rc) return rc;
   CK(cudaStreamSynchronize(s), "md_init");
@@ -681,16 +719,49 @@ int md_step_launch(nep_handle *h, double dt, cudaStream_t s, bool capturing) {
   const int N = h->N;
   const double half_skin2 = 0.25 * h->skin * h->skin;
   ev_record(h, SLOT_DRIFT, 0, s, capturing);
-  launch_drift(N, h->x.p, h->v.p, h->F.p, h->pos4.p, h->x_ref.p, h->origin.p, h->d_inv_mk.p, dt, half_skin2,
-               h->status.p, s);
+  launch_drift(N, atom_state(h), h->d_inv_mk.p, dt, half_skin2, h->status.p, s);
   ev_record(h, SLOT_DRIFT, 1, s, capturing);
   ev_record(h, SLOT_REBUILD, 0, s, capturing);
   const float rlR = (float)(h->rcR + h->skin), rlA = (float)(h->rcA + h->skin);
-  launch_rebuild(N, h->T, h->grid, h->dtab.p, rlR * rlR, rlA * rlA, h->rcR2f(), h->rcA2f(), h->cap_r, h->cap_a, 0,
-                 h->x.p, h->x_ref.p,
-                 h->origin.p, h->types.p, h->pos4.p, h->cell_of.p, h->cell_count.p, h->cell_cursor.p,
-                 h->cell_start.p, h->cell_atoms.p, h->nl_r.p, h->nn_r.p, h->nl_a.p, h->nn_a.p, h->rev_a.p,
-                 h->status.p, s);
+  if (capturing) {
+    // the rebuild kernels sit in the body of a conditional (IF) node; a one-thread kernel sets
+    // its condition from the drift kernel's request, so steps without a rebuild launch none
+    cudaStreamCaptureStatus cs;
+    unsigned long long id = 0;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edges = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(s, &cs, &id, &g, &deps, &edges, &nd), "capture info");
+    cudaGraphConditionalHandle hc;
+    CK(cudaGraphConditionalHandleCreate(&hc, g, 0, 0), "conditional handle");
+    launch_rebuild_condition(hc, h->status.p, s);
+    CK(cudaGetLastError(), "condition kernel");
+    CK(cudaStreamGetCaptureInfo(s, &cs, &id, &g, &deps, &edges, &nd), "capture info");
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = hc;
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    CK(cudaGraphAddNode(&cnode, g, deps, edges, nd, &np), "conditional node");
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies), "capture deps");
+    CK(cudaStreamBeginCaptureToGraph(h->cap_stream2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed),
+       "capture body");
+    cudaError_t e = launch_rebuild(N, h->T, h->grid, h->dtab.p, rlR * rlR, rlA * rlA, h->rcR2f(), h->rcA2f(),
+                                   atom_state(h), list_bufs(h), 0, h->status.p, h->cap_stream2);
+    cudaGraph_t out = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(h->cap_stream2, &out);
+    if (e != cudaSuccess) return cuda_fail(h, e, "launch rebuild");
+    if (e2 != cudaSuccess) return cuda_fail(h, e2, "end body capture");
+    size_t nn = 0;
+    cudaGraphGetNodes(body, nullptr, &nn);
+    h->rebuild_kernels = (int)nn;
+  } else {
+    CK(launch_rebuild(N, h->T, h->grid, h->dtab.p, rlR * rlR, rlA * rlA, h->rcR2f(), h->rcA2f(), atom_state(h),
+                      list_bufs(h), 0, h->status.p, s),
+       "launch rebuild");
+  }
   ev_record(h, SLOT_REBUILD, 1, s, capturing);
   int rc = run_forces(h, N, nullptr, h->F.p, nullptr, 1, 0.5 * dt, s, capturing);
   if (rc) return rc;
@@ -784,6 +855,9 @@ int md_run(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *t
   CK(h->ck_x.ensure(3 * (size_t)N), "alloc checkpoint");
   CK(h->ck_v.ensure(3 * (size_t)N), "alloc checkpoint");
   CK(h->ck_F.ensure(3 * (size_t)N), "alloc checkpoint");
+  CK(h->ck_types.ensure((size_t)N), "alloc checkpoint");
+  CK(h->ck_perm.ensure((size_t)N), "alloc checkpoint");
+  const size_t bi = sizeof(int) * (size_t)N;
   // chunks of whole thermo periods; each chunk starts from a checkpoint so that a list
   // overflow during it can be undone: restore, grow the lists, rebuild, replay
   const int chunk = thermo_every >= 64 ? thermo_every : (64 / thermo_every) * thermo_every;
@@ -793,6 +867,8 @@ int md_run(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *t
     CK(cudaMemcpyAsync(h->ck_x.p, h->x.p, b, cudaMemcpyDeviceToDevice, s), "checkpoint");
     CK(cudaMemcpyAsync(h->ck_v.p, h->v.p, b, cudaMemcpyDeviceToDevice, s), "checkpoint");
     CK(cudaMemcpyAsync(h->ck_F.p, h->F.p, b, cudaMemcpyDeviceToDevice, s), "checkpoint");
+    CK(cudaMemcpyAsync(h->ck_types.p, h->types.p, bi, cudaMemcpyDeviceToDevice, s), "checkpoint");
+    CK(cudaMemcpyAsync(h->ck_perm.p, h->perm.p, bi, cudaMemcpyDeviceToDevice, s), "checkpoint");
     int rc = read_status(h, s);
     if (rc) return rc;
     const long long steps0 = h->h_status->md_steps, rebuilds0 = h->h_status->n_rebuilds;
@@ -813,6 +889,8 @@ int md_run(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *t
       CK(cudaMemcpyAsync(h->x.p, h->ck_x.p, b, cudaMemcpyDeviceToDevice, s), "restore");
       CK(cudaMemcpyAsync(h->v.p, h->ck_v.p, b, cudaMemcpyDeviceToDevice, s), "restore");
       CK(cudaMemcpyAsync(h->F.p, h->ck_F.p, b, cudaMemcpyDeviceToDevice, s), "restore");
+      CK(cudaMemcpyAsync(h->types.p, h->ck_types.p, bi, cudaMemcpyDeviceToDevice, s), "restore");
+      CK(cudaMemcpyAsync(h->perm.p, h->ck_perm.p, bi, cudaMemcpyDeviceToDevice, s), "restore");
       rc = ensure_lists(h, N, round_cap(st.max_r), round_cap(st.max_a));
       if (rc) return rc;
       rc = rebuild_lists(h, N, s);
@@ -835,13 +913,8 @@ int md_get_state(nep_handle *h, double *pos, double *vel, double *force, nep_str
   if (!valid_handle(h)) return NEP_ERR_ARG;
   if (!h->md_ready) return fail(h, NEP_ERR_STATE, "no MD state");
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t b = sizeof(double) * 3 * (size_t)h->N;
-  if (pos) {
-    launch_wrap(h->N, h->x.p, h->grid, pos, s);
-    CK(cudaGetLastError(), "wrap");
-  }
-  if (vel) CK(cudaMemcpyAsync(vel, h->v.p, b, cudaMemcpyDeviceToDevice, s), "copy");
-  if (force) CK(cudaMemcpyAsync(force, h->F.p, b, cudaMemcpyDeviceToDevice, s), "copy");
+  launch_export(h->N, atom_state(h), h->grid, pos, vel, force, s);
+  CK(cudaGetLastError(), "export");
   return NEP_OK;
 }
 
@@ -849,19 +922,17 @@ int md_get_state_host(nep_handle *h, double *pos, double *vel, double *force) {
   if (!valid_handle(h)) return NEP_ERR_ARG;
   if (!h->md_ready) return fail(h, NEP_ERR_STATE, "no MD state");
   const size_t b = sizeof(double) * 3 * (size_t)h->N;
-  if (pos) {
-    CK(cudaMemcpy(pos, h->x.p, b, cudaMemcpyDeviceToHost), "copy");
-    const Grid &g = h->grid;
-    for (int i = 0; i < h->N; ++i) {
-      double sf[3];
-      for (int c = 0; c < 3; ++c)
-        sf[c] = pos[3 * i] * g.Hinv[0][c] + pos[3 * i + 1] * g.Hinv[1][c] + pos[3 * i + 2] * g.Hinv[2][c];
-      for (int c = 0; c < 3; ++c) sf[c] -= std::floor(sf[c]);
-      for (int c = 0; c < 3; ++c) pos[3 * i + c] = sf[0] * g.H[0][c] + sf[1] * g.H[1][c] + sf[2] * g.H[2][c];
-    }
-  }
-  if (vel) CK(cudaMemcpy(vel, h->v.p, b, cudaMemcpyDeviceToHost), "copy");
-  if (force) CK(cudaMemcpy(force, h->F.p, b, cudaMemcpyDeviceToHost), "copy");
+  double *d = nullptr;
+  CK(cudaMalloc(&d, 3 * b), "alloc");
+  int rc = md_get_state(h, pos ? d : nullptr, vel ? d + 3 * (size_t)h->N : nullptr,
+                        force ? d + 6 * (size_t)h->N : nullptr, nullptr);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (!rc && e == cudaSuccess && pos) e = cudaMemcpy(pos, d, b, cudaMemcpyDeviceToHost);
+  if (!rc && e == cudaSuccess && vel) e = cudaMemcpy(vel, d + 3 * (size_t)h->N, b, cudaMemcpyDeviceToHost);
+  if (!rc && e == cudaSuccess && force) e = cudaMemcpy(force, d + 6 * (size_t)h->N, b, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_fail(h, e, "md_get_state_host");
   return NEP_OK;
 }
 
@@ -871,6 +942,7 @@ int nep_get_stats(nep_handle *h, nep_stats *out) {
   s.cap_radial = h->cap_r;
   s.cap_angular = h->cap_a;
   s.graph_kernels = h->graph_kernels;
+  s.rebuild_kernels = h->rebuild_kernels;
   if (h->status.p) {
     cudaMemcpy(h->h_status, h->status.p, sizeof(BuildStatus), cudaMemcpyDeviceToHost);
     s.n_rebuilds = h->h_status->n_rebuilds;

@@ -1,21 +1,23 @@
-// Neighbour-list construction, velocity-Verlet drift and reductions for libnep.
+// Neighbour-list construction, atom reordering, velocity-Verlet drift and reductions.
 //
 // The paper takes its neighbour lists as given (Appendix B lists NN_i^R, NN_i^A, NL_im^R,
-// NL_im^A); here they are built on the GPU from a cell list:
-//   bin_atoms     wrap positions into the cell (FP64), assign each atom to a grid cell,
-//                 write cell-local FP32 coordinates, count atoms per cell;
-//   scan_cells    exclusive prefix sum of the cell counts (one block, deterministic);
-//   scatter_atoms place atoms into their cells; sort_cells orders each cell by atom index
-//                 so the lists do not depend on atomic ordering;
-//   build_lists   per atom: scan the (2R+1)^3 neighbouring cells (all periodic images when
-//                 the cell is thin), keep pairs within r_c + skin, group the radial list by
-//                 neighbour type and sort every list by distance (valid pairs first, which
-//                 keeps warps convergent when the pair loops skip r >= r_c);
-//   build_rev     for every angular pair (i, j, image), the slot of (j, i, -image) in the
-//                 list of j, so forces are gathered without atomics (Algorithm 4's "index
-//                 manipulations").
-// Every builder returns early unless a rebuild is pending, so the whole sequence can sit
-// in the captured MD step graph and only run when an atom moved more than skin/2.
+// NL_im^A); here they are built on the GPU from a cell list at every rebuild:
+//   bin_atoms      validate, wrap positions into the cell (FP64), cell index, cell counts;
+//   scan_cells     exclusive prefix sum of the counts (one block, deterministic);
+//   scatter/sort   atoms into their cells, each cell ordered by atom index (deterministic);
+//   reorder        move every per-atom array into cell order (the internal order), so a
+//                  warp's atoms are spatial neighbours and their neighbour data is shared in
+//                  L1; perm keeps the caller's index of each internal atom;
+//   commit         cell-local FP32 coordinates, cell origins, reference positions;
+//   build_lists    per atom: scan the (2R+1)^3 neighbouring cells (all periodic images when
+//                  the cell is thin), keep pairs within r_c + skin, group the radial list by
+//                  neighbour type and put the pairs inside r_c before the skin pairs (which
+//                  keeps warps convergent in the pair loops); two passes, count then write;
+//   build_rev      for every angular pair (i, j, image), the slot of (j, i, -image) in the list
+//                  of j, so forces are gathered without atomics (Algorithm 4's "index
+//                  manipulations").
+// Every builder returns early unless a rebuild is pending, so the whole sequence sits in the
+// captured MD step graph and only works when an atom moved more than skin/2.
 #include "nep_internal.cuh"
 
 namespace nep {
@@ -36,16 +38,16 @@ __global__ void zero_cells_kernel(int ncell, int *count, int *cursor, BuildStatu
   }
 }
 
-__global__ void bin_atoms_kernel(int N, int T, double *x, double *x_ref, double *origin, const int *types,
-                                 float4 *pos4, int *cell_of, int *count, const Grid g, BuildStatus *st) {
+__global__ void bin_atoms_kernel(int N, int T, AtomState a, int *count, const Grid g, BuildStatus *st) {
   if (!rebuild_pending(st)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  double r[3] = {x[3 * (size_t)i], x[3 * (size_t)i + 1], x[3 * (size_t)i + 2]};
-  int ti = types[i];
+  double *x = a.x + 3 * (size_t)i;
+  double r[3] = {x[0], x[1], x[2]};
+  const int ti = a.types[i];
   if (ti < 0 || ti >= T) {
     atomicOr(&st->bad_input, 1);
-    ti = 0;
+    a.types[i] = 0;
   }
   if (!isfinite(r[0]) || !isfinite(r[1]) || !isfinite(r[2])) {
     atomicOr(&st->bad_input, 2);
@@ -56,22 +58,12 @@ __global__ void bin_atoms_kernel(int N, int T, double *x, double *x_ref, double 
   for (int b = 0; b < 3; ++b) {
     s[b] = r[0] * g.Hinv[0][b] + r[1] * g.Hinv[1][b] + r[2] * g.Hinv[2][b];
     s[b] -= floor(s[b]);
-    int cb = (int)(s[b] * g.nc[b]);
+    const int cb = (int)(s[b] * g.nc[b]);
     c[b] = cb < 0 ? 0 : (cb >= g.nc[b] ? g.nc[b] - 1 : cb);
   }
-  double o[3];
-  for (int b = 0; b < 3; ++b) {
-    r[b] = s[0] * g.H[0][b] + s[1] * g.H[1][b] + s[2] * g.H[2][b];
-    o[b] = c[0] * g.Hc[0][b] + c[1] * g.Hc[1][b] + c[2] * g.Hc[2][b];
-  }
-  for (int b = 0; b < 3; ++b) {
-    x[3 * (size_t)i + b] = r[b];
-    x_ref[3 * (size_t)i + b] = r[b];
-    origin[3 * (size_t)i + b] = o[b];
-  }
-  pos4[i] = make_float4((float)(r[0] - o[0]), (float)(r[1] - o[1]), (float)(r[2] - o[2]), __int_as_float(ti));
+  for (int b = 0; b < 3; ++b) x[b] = s[0] * g.H[0][b] + s[1] * g.H[1][b] + s[2] * g.H[2][b];
   const int id = (c[0] * g.nc[1] + c[1]) * g.nc[2] + c[2];
-  cell_of[i] = id;
+  a.cell_of[i] = id;
   atomicAdd(count + id, 1);
 }
 
@@ -87,7 +79,7 @@ __global__ void scan_cells_kernel(int ncell, const int *count, int *start, const
   part[threadIdx.x] = s;
   __syncthreads();
   for (int off = 1; off < blockDim.x; off <<= 1) {
-    int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    const int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
     __syncthreads();
     part[threadIdx.x] += v;
     __syncthreads();
@@ -125,29 +117,51 @@ __global__ void sort_cells_kernel(int ncell, const int *start, int *cell_atoms, 
   }
 }
 
-// Sort key for list candidates: (group, squared distance, packed entry), ascending.
-__device__ __forceinline__ bool cand_less(int ga, float ra, unsigned ea, int gb, float rb, unsigned eb) {
-  if (ga != gb) return ga < gb;
-  if (ra != rb) return ra < rb;
-  return ea < eb;
+// Internal atom p takes the data of atom cell_atoms[p] (into the scratch arrays).
+__global__ void reorder_gather_kernel(int N, const int *cell_atoms, AtomState a, const BuildStatus *st) {
+  if (!rebuild_pending(st)) return;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  const int o = cell_atoms[p];
+  for (int b = 0; b < 3; ++b) {
+    a.x2[3 * (size_t)p + b] = a.x[3 * (size_t)o + b];
+    a.v2[3 * (size_t)p + b] = a.v[3 * (size_t)o + b];
+    a.F2[3 * (size_t)p + b] = a.F[3 * (size_t)o + b];
+  }
+  a.types2[p] = a.types[o];
+  a.perm2[p] = a.perm[o];
+  a.cell2[p] = a.cell_of[o];
 }
 
-// count_only: write no entries, only the length statistics (used to size the lists).
-__global__ void build_lists_kernel(int N, const float4 *pos4, const int *cell_of, const int *start,
-                                   const int *cell_atoms, const Grid g, const float4 *dtab, float rlR2, float rlA2,
-                                   float rcR2, float rcA2, int T, int cap_r, int cap_a, int count_only,
-                                   unsigned *nl_r, int *nn_r, unsigned *nl_a, int *nn_a, BuildStatus *st) {
+// Copy the reordered data back and derive the cell-local coordinates.
+__global__ void reorder_commit_kernel(int N, AtomState a, const Grid g, const BuildStatus *st) {
   if (!rebuild_pending(st)) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  unsigned er[kListBuf];
-  float rr[kListBuf];
-  unsigned char tr[kListBuf];
-  unsigned ea[kListBuf];
-  float ra[kListBuf];
-  int nr = 0, nA = 0, inr = 0, ina = 0;
-  const float4 pi = pos4[i];
-  const int id = cell_of[i];
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  const int id = a.cell2[p];
+  const int c0 = id / (g.nc[1] * g.nc[2]), c1 = (id / g.nc[2]) % g.nc[1], c2 = id % g.nc[2];
+  double r[3], o[3];
+  for (int b = 0; b < 3; ++b) {
+    r[b] = a.x2[3 * (size_t)p + b];
+    o[b] = c0 * g.Hc[0][b] + c1 * g.Hc[1][b] + c2 * g.Hc[2][b];
+    a.x[3 * (size_t)p + b] = r[b];
+    a.x_ref[3 * (size_t)p + b] = r[b];
+    a.origin[3 * (size_t)p + b] = o[b];
+    a.v[3 * (size_t)p + b] = a.v2[3 * (size_t)p + b];
+    a.F[3 * (size_t)p + b] = a.F2[3 * (size_t)p + b];
+  }
+  const int t = a.types2[p];
+  a.types[p] = t;
+  a.perm[p] = a.perm2[p];
+  a.cell_of[p] = id;
+  a.pos4[p] = make_float4((float)(r[0] - o[0]), (float)(r[1] - o[1]), (float)(r[2] - o[2]), __int_as_float(t));
+}
+
+// Visit every neighbour candidate (j, image) of atom i: f(j, entry, r2, type_j). Atoms are
+// in cell order, so the atoms of cell c are j in [start[c], start[c+1]).
+template <class F>
+__device__ __forceinline__ void for_candidates(int i, const float4 &pi, int id, const Grid &g, const float4 *dtab,
+                                               const int *start, const float4 *pos4, F &&f) {
   const int cx = id / (g.nc[1] * g.nc[2]);
   const int cy = (id / g.nc[2]) % g.nc[1];
   const int cz = id % g.nc[2];
@@ -165,107 +179,123 @@ __global__ void build_lists_kernel(int N, const float4 *pos4, const int *cell_of
         const float4 D = dtab[code];
         const int cell = (x * g.nc[1] + y) * g.nc[2] + z;
         const bool self_image = (ox == 0 && oy == 0 && oz == 0);
-        for (int p = start[cell]; p < start[cell + 1]; ++p) {
-          const int j = cell_atoms[p];
+        const int pe = start[cell + 1];
+        for (int j = start[cell]; j < pe; ++j) {
           if (self_image && j == i) continue;
           const float4 pj = pos4[j];
-          const float r2 = norm2(pair_vector(pi, pj, D));
-          const unsigned ent = (unsigned)j | (code << g.jbits);
-          inr += r2 < rcR2;
-          ina += r2 < rcA2;
-          if (r2 < rlR2) {
-            if (nr < kListBuf) {
-              er[nr] = ent;
-              rr[nr] = r2;
-              tr[nr] = (unsigned char)type_of(pj);
-            }
-            ++nr;
-          }
-          if (r2 < rlA2) {
-            if (nA < kListBuf) {
-              ea[nA] = ent;
-              ra[nA] = r2;
-            }
-            ++nA;
-          }
+          f(j, (unsigned)j | (code << g.jbits), norm2(pair_vector(pi, pj, D)), type_of(pj));
         }
       }
     }
   }
+}
+
+// Two passes over the candidates: count, then write. The radial list is grouped by
+// neighbour type; inside every group (and in the angular list) the pairs already inside
+// r_c come before the skin pairs, so the warps of the pair loops stay convergent.
+// count_only: record only the length statistics (used to size the lists).
+__global__ void build_lists_kernel(int N, int T, const float4 *pos4, const int *cell_of, const int *start,
+                                   const Grid g, const float4 *dtab, float rlR2, float rlA2, float rcR2, float rcA2,
+                                   ListBufs L, int count_only, BuildStatus *st) {
+  if (!rebuild_pending(st)) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const float4 pi = pos4[i];
+  const int id = cell_of[i];
+  // per-type counters stay in registers: every update is unrolled over the types
+  int cr0[kMaxTypes], cr1[kMaxTypes];
+#pragma unroll
+  for (int t = 0; t < kMaxTypes; ++t) cr0[t] = cr1[t] = 0;
+  int ca0 = 0, ca1 = 0;
+  for_candidates(i, pi, id, g, dtab, start, pos4, [&](int, unsigned, float r2, int tj) {
+    if (r2 < rlR2) {
+      const bool core = r2 < rcR2;
+#pragma unroll
+      for (int t = 0; t < kMaxTypes; ++t) {
+        cr0[t] += (tj == t && core) ? 1 : 0;
+        cr1[t] += (tj == t && !core) ? 1 : 0;
+      }
+    }
+    if (r2 < rlA2) {
+      if (r2 < rcA2) ++ca0;
+      else ++ca1;
+    }
+  });
+  int nr = 0, inr = 0;
+#pragma unroll
+  for (int t = 0; t < kMaxTypes; ++t) {
+    nr += cr0[t] + cr1[t];
+    inr += cr0[t];
+  }
+  const int nA = ca0 + ca1;
   atomicMax(&st->max_r, nr);
   atomicMax(&st->max_a, nA);
   atomicAdd(&st->sum_r, (unsigned long long)nr);
   atomicAdd(&st->sum_a, (unsigned long long)nA);
   atomicAdd(&st->in_r, (unsigned long long)inr);
-  atomicAdd(&st->in_a, (unsigned long long)ina);
+  atomicAdd(&st->in_a, (unsigned long long)ca0);
   if (count_only) return;
-  if (nr > cap_r || nA > cap_a || nr > kListBuf || nA > kListBuf) atomicOr(&st->overflow, 1);
-  const int wr = min(min(nr, cap_r), kListBuf);
-  const int wa = min(min(nA, cap_a), kListBuf);
-  // insertion sorts: radial by (type, r2, entry), angular by (r2, entry)
-  for (int p = 1; p < wr; ++p) {
-    const unsigned e = er[p];
-    const float r = rr[p];
-    const unsigned char t = tr[p];
-    int q = p - 1;
-    while (q >= 0 && cand_less(t, r, e, tr[q], rr[q], er[q])) {
-      er[q + 1] = er[q];
-      rr[q + 1] = rr[q];
-      tr[q + 1] = tr[q];
-      --q;
+  if (nr > L.cap_r || nA > L.cap_a) {  // leave the lists empty; the host grows them and rebuilds
+    atomicOr(&st->overflow, 1);
+    for (int t = 0; t < T; ++t) L.nn_r[t * N + i] = 0;
+    L.nn_a[i] = 0;
+    return;
+  }
+  int cur0[kMaxTypes], cur1[kMaxTypes];
+  int off = 0;
+#pragma unroll
+  for (int t = 0; t < kMaxTypes; ++t) {
+    cur0[t] = off;
+    cur1[t] = off + cr0[t];
+    off += cr0[t] + cr1[t];
+    if (t < T) L.nn_r[t * N + i] = cr0[t] + cr1[t];
+  }
+  int ka0 = 0, ka1 = ca0;
+  for_candidates(i, pi, id, g, dtab, start, pos4, [&](int, unsigned ent, float r2, int tj) {
+    if (r2 < rlR2) {
+      const bool core = r2 < rcR2;
+      int slot = 0;
+#pragma unroll
+      for (int t = 0; t < kMaxTypes; ++t) {
+        if (tj == t) {
+          slot = core ? cur0[t] : cur1[t];
+          cur0[t] += core ? 1 : 0;
+          cur1[t] += core ? 0 : 1;
+        }
+      }
+      L.nl_r[(size_t)slot * N + i] = ent;
     }
-    er[q + 1] = e;
-    rr[q + 1] = r;
-    tr[q + 1] = t;
-  }
-  for (int p = 1; p < wa; ++p) {
-    const unsigned e = ea[p];
-    const float r = ra[p];
-    int q = p - 1;
-    while (q >= 0 && cand_less(0, r, e, 0, ra[q], ea[q])) {
-      ea[q + 1] = ea[q];
-      ra[q + 1] = ra[q];
-      --q;
-    }
-    ea[q + 1] = e;
-    ra[q + 1] = r;
-  }
-  for (int t = 0; t < T; ++t) nn_r[t * N + i] = 0;
-  for (int p = 0; p < wr; ++p) {
-    nl_r[(size_t)p * N + i] = er[p];
-    nn_r[tr[p] * N + i] += 1;
-  }
-  for (int p = 0; p < wa; ++p) nl_a[(size_t)p * N + i] = ea[p];
-  nn_a[i] = wa;
+    if (r2 < rlA2) L.nl_a[(size_t)(r2 < rcA2 ? ka0++ : ka1++) * N + i] = ent;
+  });
+  L.nn_a[i] = nA;
 }
 
-__global__ void build_rev_kernel(int N, const unsigned *nl_a, const int *nn_a, const Grid g, int *rev_a,
-                                 BuildStatus *st) {
+__global__ void build_rev_kernel(int N, const ListBufs L, const Grid g, BuildStatus *st) {
   if (!rebuild_pending(st)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const unsigned om = (1u << g.obits) - 1u;
-  const int na = nn_a[i];
+  const int na = L.nn_a[i];
   for (int m = 0; m < na; ++m) {
     const size_t slot = (size_t)m * N + i;
-    const unsigned e = nl_a[slot];
+    const unsigned e = L.nl_a[slot];
     const int j = e & g.jmask;
     const unsigned code = e >> g.jbits;
     const unsigned cx = code & om, cy = (code >> g.obits) & om, cz = (code >> (2 * g.obits)) & om;
     const unsigned rc = (2u * g.R[0] - cx) | ((2u * g.R[1] - cy) << g.obits) | ((2u * g.R[2] - cz) << (2 * g.obits));
     const unsigned target = (unsigned)i | (rc << g.jbits);
-    const int nj = nn_a[j];
+    const int nj = L.nn_a[j];
     int found = -1;
     for (int q = 0; q < nj; ++q)
-      if (nl_a[(size_t)q * N + j] == target) {
+      if (L.nl_a[(size_t)q * N + j] == target) {
         found = q;
         break;
       }
     if (found < 0) {
       atomicAdd(&st->rev_missing, 1);
-      rev_a[slot] = (int)slot;  // points at a finite entry; the status reports the error
+      L.rev_a[slot] = (int)slot;  // a finite entry; the status reports the error
     } else {
-      rev_a[slot] = (int)((size_t)found * N + j);
+      L.rev_a[slot] = (int)((size_t)found * N + j);
     }
   }
 }
@@ -277,40 +307,80 @@ __global__ void finish_build_kernel(BuildStatus *st) {
   }
 }
 
+// Sets the condition of the graph's rebuild node from the drift kernel's request.
+__global__ void rebuild_condition_kernel(cudaGraphConditionalHandle hc, const BuildStatus *st) {
+  cudaGraphSetConditional(hc, *(volatile const int *)&st->rebuild != 0 ? 1u : 0u);
+}
+
+__global__ void iota_kernel(int N, int *perm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) perm[i] = i;
+}
+
 // Velocity Verlet, first half: v += dt/2 F/m; x += dt v; refresh cell-local coordinates;
 // request a rebuild when an atom moved more than skin/2 since the last build.
-__global__ void md_drift_kernel(int N, double *x, double *v, const double *F, float4 *pos4, const double *x_ref,
-                                const double *origin, const double *inv_mass_kappa, double dt, double half_skin2,
+__global__ void md_drift_kernel(int N, AtomState a, const double *inv_mass_kappa, double dt, double half_skin2,
                                 BuildStatus *st) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) st->md_steps += 1;
   if (i >= N) return;
-  float4 p = pos4[i];
+  float4 p = a.pos4[i];
   const double s = 0.5 * dt * inv_mass_kappa[type_of(p)];
   double r[3], d2 = 0.0;
   for (int b = 0; b < 3; ++b) {
     const size_t k = 3 * (size_t)i + b;
-    const double vb = v[k] + s * F[k];
-    v[k] = vb;
-    r[b] = x[k] + dt * vb;
-    x[k] = r[b];
-    const double dd = r[b] - x_ref[k];
+    const double vb = a.v[k] + s * a.F[k];
+    a.v[k] = vb;
+    r[b] = a.x[k] + dt * vb;
+    a.x[k] = r[b];
+    const double dd = r[b] - a.x_ref[k];
     d2 += dd * dd;
   }
-  p.x = (float)(r[0] - origin[3 * (size_t)i]);
-  p.y = (float)(r[1] - origin[3 * (size_t)i + 1]);
-  p.z = (float)(r[2] - origin[3 * (size_t)i + 2]);
-  pos4[i] = p;
+  p.x = (float)(r[0] - a.origin[3 * (size_t)i]);
+  p.y = (float)(r[1] - a.origin[3 * (size_t)i + 1]);
+  p.z = (float)(r[2] - a.origin[3 * (size_t)i + 2]);
+  a.pos4[i] = p;
   if (d2 > half_skin2) st->rebuild = 1;
 }
 
+// Caller-order copies of the MD state: positions wrapped into the cell, velocities, forces.
+__global__ void export_state_kernel(int N, const AtomState a, const Grid g, double *pos, double *vel, double *force) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const size_t u = 3 * (size_t)a.perm[i];
+  if (pos) {
+    const double r[3] = {a.x[3 * (size_t)i], a.x[3 * (size_t)i + 1], a.x[3 * (size_t)i + 2]};
+    double s[3];
+    for (int b = 0; b < 3; ++b) {
+      s[b] = r[0] * g.Hinv[0][b] + r[1] * g.Hinv[1][b] + r[2] * g.Hinv[2][b];
+      s[b] -= floor(s[b]);
+    }
+    for (int b = 0; b < 3; ++b) pos[u + b] = s[0] * g.H[0][b] + s[1] * g.H[1][b] + s[2] * g.H[2][b];
+  }
+  for (int b = 0; b < 3; ++b) {
+    if (vel) vel[u + b] = a.v[3 * (size_t)i + b];
+    if (force) force[u + b] = a.F[3 * (size_t)i + b];
+  }
+}
+
 // Deterministic totals: E = sum U_i, W = sum W_i, kinetic energy; optional thermo row.
-// One block; every thread sums a fixed strided subset, then a fixed tree.
+// One block; every thread sums a fixed strided subset, then a fixed tree. In MD mode
+// (thermo_ctl set) steps without a thermo row only advance the step counter.
 __global__ void finalize_kernel(int nb_atom, const double *partial_atom, int nb_gather, const double *partial_gather,
                                 double *energy_total, double *virial_total, double *thermo_stage,
                                 int *thermo_ctl /* [0] step-in-call, [1] rows written, [2] every */, int N,
                                 double volume) {
   __shared__ double red[256][kReduceSlots];
+  __shared__ int emit;
+  if (threadIdx.x == 0) {
+    emit = 1;
+    if (thermo_ctl) {
+      const int step = ++thermo_ctl[0];
+      emit = (step % thermo_ctl[2] == 0);
+    }
+  }
+  __syncthreads();
+  if (!emit) return;
   double acc[kReduceSlots];
   for (int s = 0; s < kReduceSlots; ++s) acc[s] = 0.0;
   for (int b = threadIdx.x; b < nb_atom; b += blockDim.x) acc[0] += partial_atom[b];
@@ -328,64 +398,54 @@ __global__ void finalize_kernel(int nb_atom, const double *partial_atom, int nb_
     if (virial_total)
       for (int c = 0; c < 9; ++c) virial_total[c] = red[0][2 + c];
     if (thermo_ctl) {
-      const int step = ++thermo_ctl[0];
-      if (step % thermo_ctl[2] == 0) {
-        const int row = thermo_ctl[1]++;
-        const double kb = 8.617333262e-5;
-        const double ke = red[0][1];
-        const double tr = red[0][2] + red[0][3] + red[0][4];
-        double *o = thermo_stage + 4 * (size_t)row;
-        o[0] = red[0][0];
-        o[1] = ke;
-        o[2] = N > 1 ? 2.0 * ke / ((3.0 * N - 3.0) * kb) : 0.0;
-        o[3] = (2.0 * ke + tr) / (3.0 * volume) * 160.21766208;  // eV/A^3 -> GPa
-      }
+      const int row = thermo_ctl[1]++;
+      const double kb = 8.617333262e-5;
+      const double ke = red[0][1];
+      const double tr = red[0][2] + red[0][3] + red[0][4];
+      double *o = thermo_stage + 4 * (size_t)row;
+      o[0] = red[0][0];
+      o[1] = ke;
+      o[2] = N > 1 ? 2.0 * ke / ((3.0 * N - 3.0) * kb) : 0.0;
+      o[3] = (2.0 * ke + tr) / (3.0 * volume) * 160.21766208;  // eV/A^3 -> GPa
     }
   }
 }
 
-// Positions wrapped into the cell (fractional coordinates in [0, 1)).
-__global__ void wrap_positions_kernel(int N, const double *x, const Grid g, double *out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const double r[3] = {x[3 * (size_t)i], x[3 * (size_t)i + 1], x[3 * (size_t)i + 2]};
-  double s[3];
-  for (int b = 0; b < 3; ++b) {
-    s[b] = r[0] * g.Hinv[0][b] + r[1] * g.Hinv[1][b] + r[2] * g.Hinv[2][b];
-    s[b] -= floor(s[b]);
-  }
-  for (int b = 0; b < 3; ++b) out[3 * (size_t)i + b] = s[0] * g.H[0][b] + s[1] * g.H[1][b] + s[2] * g.H[2][b];
-}
-
 // ------------------------------------------------------------------ host launchers
-void launch_wrap(int N, const double *x, const Grid &g, double *out, cudaStream_t s) {
-  wrap_positions_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, x, g, out);
-}
-
-void launch_rebuild(int N, int T, const Grid &g, const float4 *dtab, float rlR2, float rlA2, float rcR2, float rcA2,
-                    int cap_r, int cap_a,
-                    int count_only, double *x, double *x_ref, double *origin, const int *types, float4 *pos4,
-                    int *cell_of, int *cell_count, int *cell_cursor, int *cell_start, int *cell_atoms,
-                    unsigned *nl_r, int *nn_r, unsigned *nl_a, int *nn_a, int *rev_a, BuildStatus *st,
-                    cudaStream_t s) {
+cudaError_t launch_rebuild(int N, int T, const Grid &g, const float4 *dtab, float rlR2, float rlA2, float rcR2,
+                           float rcA2, const AtomState &a, const ListBufs &L, int count_only, BuildStatus *st,
+                           cudaStream_t s) {
   const int tb = 256;
   const int nb = (N + tb - 1) / tb;
   const int cb = (g.ncell + tb - 1) / tb;
-  zero_cells_kernel<<<cb < 1024 ? cb : 1024, tb, 0, s>>>(g.ncell, cell_count, cell_cursor, st);
-  bin_atoms_kernel<<<nb, tb, 0, s>>>(N, T, x, x_ref, origin, types, pos4, cell_of, cell_count, g, st);
-  scan_cells_kernel<<<1, 1024, 0, s>>>(g.ncell, cell_count, cell_start, st);
-  scatter_atoms_kernel<<<nb, tb, 0, s>>>(N, cell_of, cell_start, cell_cursor, cell_atoms, st);
-  sort_cells_kernel<<<cb, tb, 0, s>>>(g.ncell, cell_start, cell_atoms, st);
-  build_lists_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, pos4, cell_of, cell_start, cell_atoms, g, dtab, rlR2, rlA2, rcR2,
-                                                     rcA2, T, cap_r, cap_a, count_only, nl_r, nn_r, nl_a, nn_a, st);
-  if (!count_only) build_rev_kernel<<<nb, tb, 0, s>>>(N, nl_a, nn_a, g, rev_a, st);
+  zero_cells_kernel<<<cb < 1024 ? cb : 1024, tb, 0, s>>>(g.ncell, L.cell_count, L.cell_cursor, st);
+  bin_atoms_kernel<<<nb, tb, 0, s>>>(N, T, a, L.cell_count, g, st);
+  scan_cells_kernel<<<1, 1024, 0, s>>>(g.ncell, L.cell_count, L.cell_start, st);
+  scatter_atoms_kernel<<<nb, tb, 0, s>>>(N, a.cell_of, L.cell_start, L.cell_cursor, L.cell_atoms, st);
+  sort_cells_kernel<<<cb, tb, 0, s>>>(g.ncell, L.cell_start, L.cell_atoms, st);
+  reorder_gather_kernel<<<nb, tb, 0, s>>>(N, L.cell_atoms, a, st);
+  reorder_commit_kernel<<<nb, tb, 0, s>>>(N, a, g, st);
+  build_lists_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, T, a.pos4, a.cell_of, L.cell_start, g, dtab, rlR2, rlA2,
+                                                     rcR2, rcA2, L, count_only, st);
+  if (!count_only) build_rev_kernel<<<nb, tb, 0, s>>>(N, L, g, st);
   finish_build_kernel<<<1, 1, 0, s>>>(st);
+  return cudaGetLastError();
 }
 
-void launch_drift(int N, double *x, double *v, const double *F, float4 *pos4, const double *x_ref,
-                  const double *origin, const double *inv_mass_kappa, double dt, double half_skin2, BuildStatus *st,
-                  cudaStream_t s) {
-  md_drift_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, x, v, F, pos4, x_ref, origin, inv_mass_kappa, dt, half_skin2, st);
+void launch_rebuild_condition(cudaGraphConditionalHandle hc, const BuildStatus *st, cudaStream_t s) {
+  rebuild_condition_kernel<<<1, 1, 0, s>>>(hc, st);
+}
+
+void launch_iota(int N, int *perm, cudaStream_t s) { iota_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, perm); }
+
+void launch_drift(int N, const AtomState &a, const double *inv_mass_kappa, double dt, double half_skin2,
+                  BuildStatus *st, cudaStream_t s) {
+  md_drift_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, a, inv_mass_kappa, dt, half_skin2, st);
+}
+
+void launch_export(int N, const AtomState &a, const Grid &g, double *pos, double *vel, double *force,
+                   cudaStream_t s) {
+  export_state_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, a, g, pos, vel, force);
 }
 
 void launch_finalize(int nb_atom, const double *partial_atom, int nb_gather, const double *partial_gather,

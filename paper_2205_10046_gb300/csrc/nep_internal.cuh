@@ -6,7 +6,7 @@
 namespace nep {
 
 constexpr int kMaxTypes = 8;
-constexpr int kListBuf = 160;   // per-atom candidate buffer of the list builder
+constexpr int kListBuf = 512;   // largest neighbour-list capacity per atom
 constexpr int kMaxImage = 3;    // largest cell/image offset searched per axis
 constexpr int kAtomBlock = 128; // threads per block of the per-atom kernel
 constexpr int kGatherBlock = 128;
@@ -25,6 +25,27 @@ struct Grid {
   double H[3][3];     // cell rows
   double Hinv[3][3];  // s = r . Hinv
   double Hc[3][3];    // rows of one grid cell: H[a] / nc[a]
+};
+
+// Per-atom device arrays. Internally atoms are kept in cell order (re-sorted at every
+// neighbour rebuild); perm[i] is the caller's index of internal atom i.
+struct AtomState {
+  double *x, *v, *F, *x_ref, *origin;  // [N][3]
+  int *types, *perm, *cell_of;         // [N]
+  float4 *pos4;                        // [N] cell-local FP32 coordinates + type bits
+  double *x2, *v2, *F2;                // reorder scratch [N][3]
+  int *types2, *perm2, *cell2;         // reorder scratch [N]
+};
+
+// Cell list and neighbour lists.
+struct ListBufs {
+  int *cell_count, *cell_cursor, *cell_start, *cell_atoms;
+  unsigned *nl_r;  // [cap_r][N]
+  int *nn_r;       // [T][N]
+  unsigned *nl_a;  // [cap_a][N]
+  int *nn_a;       // [N]
+  int *rev_a;      // [cap_a][N]
+  int cap_r, cap_a;
 };
 
 // Device-visible status written by the builders.
@@ -71,6 +92,7 @@ struct AtomArgs {
   float *e_rad;            // [N][T][est] radial force coefficients
   int est;
   float4 *p_ang;           // [cap_a][N] angular partial forces
+  const int *perm;         // [N] caller index of each internal atom (outputs are scattered)
   double *energy;          // [N] or null
   double *q_out;           // [N][N_des] descriptor output (descriptor mode) or null
   double *partial_atom;    // [gridDim] block sums of U

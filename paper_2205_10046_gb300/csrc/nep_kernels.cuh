@@ -36,6 +36,11 @@ struct Shape {
   static constexpr int EST = ((KR + 2) + 3) / 4 * 4;  // KR+1 coefficients and their sum
   static constexpr int OFF4 = (NR + 1) + (NA + 1) * L3;
   static constexpr int OFF5 = OFF4 + (L4 >= 2 ? NA + 1 : 0);
+  static constexpr int NDP = (NDES + 3) / 4 * 4;  // padded w0 row in shared memory
+  // S_nk is accumulated in NPASS passes over the angular neighbours, NCH values of n per
+  // pass, so that at most ~4 x 24 accumulators are live at once
+  static constexpr int NPASS = ((NA + 1) * NK > 144) ? ((NA + 1) + 3) / 4 : 1;
+  static constexpr int NCH = ((NA + 1) + NPASS - 1) / NPASS;
 };
 
 template <class S>
@@ -177,6 +182,62 @@ __device__ __forceinline__ void cheb_basis_d(float r, float inv_rc, float *f, fl
   }
 }
 
+// Loop over the cnt list entries of atom i starting at slot `slot0` (slot-major lists),
+// software-pipelined: the list entry is fetched two iterations ahead and the neighbour's
+// position one iteration ahead, so the gathers overlap the arithmetic of earlier pairs.
+template <class Body>
+__device__ __forceinline__ void for_pairs(const unsigned *__restrict__ nl, int slot0, int cnt, int N, int i,
+                                          const float4 *__restrict__ pos4, unsigned jmask, Body &&body) {
+  if (cnt <= 0) return;
+  const unsigned *col = nl + (size_t)slot0 * N + i;
+  unsigned e0 = __ldg(col);
+  unsigned e1 = cnt > 1 ? __ldg(col + N) : 0u;
+  float4 p0 = __ldg(pos4 + (e0 & jmask));
+  for (int m = 0; m < cnt; ++m) {
+    const unsigned e = e0;
+    const float4 pj = p0;
+    if (m + 1 < cnt) p0 = __ldg(pos4 + (e1 & jmask));
+    e0 = e1;
+    if (m + 2 < cnt) e1 = __ldg(col + (size_t)(m + 2) * N);
+    body(m, e, pj);
+  }
+}
+
+// Batched variant for short pair bodies: the positions of D pairs are requested together and
+// the list entries of the next D pairs one batch ahead.
+template <int D, class Body>
+__device__ __forceinline__ void for_pairs_batch(const unsigned *__restrict__ nl, int slot0, int cnt, int N, int i,
+                                                const float4 *__restrict__ pos4, unsigned jmask, Body &&body) {
+  if (cnt <= 0) return;
+  const unsigned *col = nl + (size_t)slot0 * N + i;
+  unsigned e[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) e[d] = d < cnt ? __ldg(col + (size_t)d * N) : 0u;
+  for (int m0 = 0; m0 < cnt; m0 += D) {
+    float4 p[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) p[d] = __ldg(pos4 + (e[d] & jmask));
+    unsigned en[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) en[d] = (m0 + D + d < cnt) ? __ldg(col + (size_t)(m0 + D + d) * N) : 0u;
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+      if (m0 + d < cnt) body(m0 + d, e[d], p[d]);
+#pragma unroll
+    for (int d = 0; d < D; ++d) e[d] = en[d];
+  }
+}
+
+// Plain loop over list entries (for pair bodies long enough to hide the gather themselves).
+template <class Body>
+__device__ __forceinline__ void for_pairs_plain(const unsigned *__restrict__ nl, int cnt, int N, int i,
+                                                const float4 *__restrict__ pos4, unsigned jmask, Body &&body) {
+  for (int m = 0; m < cnt; ++m) {
+    const unsigned e = __ldg(nl + (size_t)m * N + i);
+    body(m, e, __ldg(pos4 + (e & jmask)));
+  }
+}
+
 // ------------------------------------------------------------------------ per-atom kernel
 template <class S, bool DESC_ONLY>
 __global__ void __launch_bounds__(kAtomBlock, 1)
@@ -184,11 +245,23 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
   constexpr int NR = S::NR, KR = S::KR, NA = S::NA, KA = S::KA, NK = S::NK, NDES = S::NDES;
   extern __shared__ float4 smem4[];
   const int T = a.T;
+  constexpr int NDP = S::NDP;
   float4 *dtab_s = smem4;                                        // [ncode]
-  float *cR_s = reinterpret_cast<float *>(smem4 + a.ncode);      // [T][T][NR+1][KR+1]
+  float *w0_s = reinterpret_cast<float *>(smem4 + a.ncode);      // [H][NDP]
+  float *b0_s = w0_s + S::H * NDP;                               // [H]
+  float *w1_s = b0_s + S::H;                                     // [H]
+  float *cR_s = w1_s + S::H;                                     // [T][T][NR+1][KR+1]
   float *cA_s = cR_s + T * T * (NR + 1) * (KR + 1);              // [T][T][NA+1][KA+1]
   float *S_s = cA_s + T * T * (NA + 1) * (KA + 1);               // [NA+1][NK][block]
   for (int v = threadIdx.x; v < a.ncode; v += blockDim.x) dtab_s[v] = a.dtab[v];
+  for (int v = threadIdx.x; v < S::H * NDP; v += blockDim.x) {
+    const int mu = v / NDP, c = v - mu * NDP;
+    w0_s[v] = c < NDES ? w.w0[mu * NDES + c] : 0.f;
+  }
+  for (int v = threadIdx.x; v < S::H; v += blockDim.x) {
+    b0_s[v] = w.b0[v];
+    w1_s[v] = w.w1[v];
+  }
   for (int v = threadIdx.x; v < T * T * (NR + 1) * (KR + 1); v += blockDim.x) cR_s[v] = a.c_r[v];
   for (int v = threadIdx.x; v < T * T * (NA + 1) * (KA + 1); v += blockDim.x) cA_s[v] = a.c_a[v];
   __syncthreads();
@@ -213,9 +286,7 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
       float Fk[KR + 1];
 #pragma unroll
       for (int k = 0; k <= KR; ++k) Fk[k] = 0.f;
-      for (int m = 0; m < cnt; ++m) {
-        const unsigned e = a.nl_r[(size_t)(base + m) * N + i];
-        const float4 pj = a.pos4[e & a.jmask];
+      for_pairs_batch<4>(a.nl_r, base, cnt, N, i, a.pos4, a.jmask, [&](int, unsigned e, const float4 &pj) {
         const float3 d = pair_vector(pi, pj, dtab_s[e >> a.jbits]);
         const float r2 = norm2(d);
         if (r2 < rcR2) {
@@ -224,7 +295,7 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
 #pragma unroll
           for (int k = 0; k <= KR; ++k) Fk[k] += f[k];
         }
-      }
+      });
       const float *c = cR_s + (ti * T + t) * (NR + 1) * (KR + 1);
 #pragma unroll
       for (int n = 0; n <= NR; ++n) {
@@ -236,95 +307,113 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
       base += cnt;
     }
 
-    // ---- angular sums S_nk, Eq. S_nk, with b_k(d) r^-l
-    float Sv[NA + 1][NK];
-#pragma unroll
-    for (int n = 0; n <= NA; ++n)
-#pragma unroll
-      for (int k = 0; k < NK; ++k) Sv[n][k] = 0.f;
+    // ---- angular sums S_nk (Eq. S_nk, b_k(d) r^-l) and the angular descriptor components
+    // (Sec. II D), one chunk of n per pass over the angular neighbours
     const int na = a.nn_a[i];
-    for (int m = 0; m < na; ++m) {
-      const unsigned e = a.nl_a[(size_t)m * N + i];
-      const float4 pj = a.pos4[e & a.jmask];
-      const float3 d = pair_vector(pi, pj, dtab_s[e >> a.jbits]);
-      const float r2 = norm2(d);
-      if (r2 < rcA2) {
-        const int tj = type_of(pj);
-        const float rinv = rsqrtf(r2);
-        float f[KA + 1];
-        cheb_basis<KA>(r2 * rinv, inv_rcA, f);
-        const float *c = cA_s + (ti * T + tj) * (NA + 1) * (KA + 1);
-        float g[NA + 1];
+    static_for<0, S::NPASS>([&](auto pc) {
+      constexpr int n0 = decltype(pc)::value * S::NCH;
+      constexpr int n1 = (n0 + S::NCH < NA + 1) ? n0 + S::NCH : NA + 1;
+      constexpr int NC = n1 - n0;
+      float Sv[NC][NK];
 #pragma unroll
-        for (int n = 0; n <= NA; ++n) {
+      for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int k = 0; k < NK; ++k) Sv[c][k] = 0.f;
+      for_pairs(a.nl_a, 0, na, N, i, a.pos4, a.jmask, [&](int, unsigned e, const float4 &pj) {
+        const float3 d = pair_vector(pi, pj, dtab_s[e >> a.jbits]);
+        const float r2 = norm2(d);
+        if (r2 < rcA2) {
+          const int tj = type_of(pj);
+          const float rinv = rsqrtf(r2);
+          float f[KA + 1];
+          cheb_basis<KA>(r2 * rinv, inv_rcA, f);
+          const float *cc = cA_s + ((ti * T + tj) * (NA + 1) + n0) * (KA + 1);
+          float g[NC];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k <= KA; ++k) acc = __fmaf_rn(cc[c * (KA + 1) + k], f[k], acc);
+            g[c] = acc;
+          }
+          const float rl[5] = {1.f, rinv, rinv * rinv, rinv * rinv * rinv, (rinv * rinv) * (rinv * rinv)};
+          static_for<0, NK>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            const float b = poly_b<k>(d.x, d.y, d.z, r2) * rl[l_of_k(k)];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) Sv[c][k] = __fmaf_rn(g[c], b, Sv[c][k]);
+          });
+        }
+      });
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int n = n0 + c;
+        static_for<0, S::L3>([&](auto lc) {
+          constexpr int l = decltype(lc)::value + 1;
+          constexpr int k0 = l == 1 ? 0 : l == 2 ? 3 : l == 3 ? 8 : 15;
+          constexpr int k1 = l == 1 ? 3 : l == 2 ? 8 : l == 3 ? 15 : 24;
           float acc = 0.f;
 #pragma unroll
-          for (int k = 0; k <= KA; ++k) acc = __fmaf_rn(c[n * (KA + 1) + k], f[k], acc);
-          g[n] = acc;
-        }
-        const float rl[5] = {1.f, rinv, rinv * rinv, rinv * rinv * rinv, (rinv * rinv) * (rinv * rinv)};
-        static_for<0, NK>([&](auto kc) {
-          constexpr int k = decltype(kc)::value;
-          const float b = poly_b<k>(d.x, d.y, d.z, r2) * rl[l_of_k(k)];
-#pragma unroll
-          for (int n = 0; n <= NA; ++n) Sv[n][k] = __fmaf_rn(g[n], b, Sv[n][k]);
+          for (int k = k0; k < k1; ++k) acc = __fmaf_rn(w.m.c3b[k] * Sv[c][k], Sv[c][k], acc);
+          q[(NR + 1) + (l - 1) * (NA + 1) + n] = acc;
         });
-      }
-    }
-
-    // ---- angular descriptor components (Sec. II D)
+        if constexpr (S::L4 >= 2) {
+          const float s3 = Sv[c][3], s4 = Sv[c][4], s5 = Sv[c][5], s6 = Sv[c][6], s7 = Sv[c][7];
+          q[S::OFF4 + n] = w.m.c4b[0] * s3 * s3 * s3 + w.m.c4b[1] * s3 * (s4 * s4 + s5 * s5) +
+                           w.m.c4b[2] * s3 * (s6 * s6 + s7 * s7) + w.m.c4b[3] * s6 * (s5 * s5 - s4 * s4) +
+                           w.m.c4b[4] * s4 * s5 * s7;
+        }
+        if constexpr (S::L5 >= 1) {
+          const float s0 = Sv[c][0], s12 = Sv[c][1] * Sv[c][1] + Sv[c][2] * Sv[c][2];
+          q[S::OFF5 + n] = w.m.c5b[0] * s0 * s0 * s0 * s0 + w.m.c5b[1] * s0 * s0 * s12 + w.m.c5b[2] * s12 * s12;
+        }
+        if constexpr (!DESC_ONLY) {
+          // park S_n in shared memory while the network runs ([n][k][thread]: conflict-free)
 #pragma unroll
-    for (int n = 0; n <= NA; ++n) {
-      static_for<0, S::L3>([&](auto lc) {
-        constexpr int l = decltype(lc)::value + 1;
-        constexpr int k0 = l == 1 ? 0 : l == 2 ? 3 : l == 3 ? 8 : 15;
-        constexpr int k1 = l == 1 ? 3 : l == 2 ? 8 : l == 3 ? 15 : 24;
-        float acc = 0.f;
-#pragma unroll
-        for (int k = k0; k < k1; ++k) acc = __fmaf_rn(w.m.c3b[k] * Sv[n][k], Sv[n][k], acc);
-        q[(NR + 1) + (l - 1) * (NA + 1) + n] = acc;
-      });
-      if constexpr (S::L4 >= 2) {
-        const float s3 = Sv[n][3], s4 = Sv[n][4], s5 = Sv[n][5], s6 = Sv[n][6], s7 = Sv[n][7];
-        q[S::OFF4 + n] = w.m.c4b[0] * s3 * s3 * s3 + w.m.c4b[1] * s3 * (s4 * s4 + s5 * s5) +
-                         w.m.c4b[2] * s3 * (s6 * s6 + s7 * s7) + w.m.c4b[3] * s6 * (s5 * s5 - s4 * s4) +
-                         w.m.c4b[4] * s4 * s5 * s7;
+          for (int k = 0; k < NK; ++k) S_s[(n * NK + k) * kAtomBlock + threadIdx.x] = Sv[c][k];
+        }
       }
-      if constexpr (S::L5 >= 1) {
-        const float s0 = Sv[n][0], s12 = Sv[n][1] * Sv[n][1] + Sv[n][2] * Sv[n][2];
-        q[S::OFF5 + n] = w.m.c5b[0] * s0 * s0 * s0 * s0 + w.m.c5b[1] * s0 * s0 * s12 + w.m.c5b[2] * s12 * s12;
-      }
-    }
+    });
 
     if constexpr (DESC_ONLY) {
+      const size_t io = a.perm ? (size_t)a.perm[i] : (size_t)i;
 #pragma unroll
-      for (int v = 0; v < NDES; ++v) a.q_out[(size_t)i * NDES + v] = (double)q[v];
+      for (int v = 0; v < NDES; ++v) a.q_out[io * NDES + v] = (double)q[v];
     } else {
-      // park S in shared memory while the network runs ([n][k][thread]: conflict-free)
       float *Sme = S_s + threadIdx.x;
-#pragma unroll
-      for (int n = 0; n <= NA; ++n)
-#pragma unroll
-        for (int k = 0; k < NK; ++k) Sme[(n * NK + k) * kAtomBlock] = Sv[n][k];
 
-      // ---- network, Eq. Ui, and dU/dq
+      // ---- network, Eq. Ui, and dU/dq (weights broadcast from shared memory)
       float U = 0.f;
       float dq[NDES];
 #pragma unroll
       for (int v = 0; v < NDES; ++v) dq[v] = 0.f;
-#pragma unroll
+#pragma unroll 1
       for (int mu = 0; mu < S::H; ++mu) {
-        float z = -w.b0[mu];
+        const float4 *row = reinterpret_cast<const float4 *>(w0_s + mu * NDP);
+        float zp[4] = {-b0_s[mu], 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int v = 0; v < NDES; ++v) z = __fmaf_rn(w.w0[mu * NDES + v], q[v], z);
-        const float h = tanhf(z);
-        U = __fmaf_rn(w.w1[mu], h, U);
-        const float beta = w.w1[mu] * (1.f - h * h);
+        for (int v4 = 0; v4 < NDP / 4; ++v4) {
+          const float4 wv = row[v4];
+          const float wc[4] = {wv.x, wv.y, wv.z, wv.w};
 #pragma unroll
-        for (int v = 0; v < NDES; ++v) dq[v] = __fmaf_rn(beta, w.w0[mu * NDES + v], dq[v]);
+          for (int c = 0; c < 4; ++c)
+            if (4 * v4 + c < NDES) zp[c] = __fmaf_rn(wc[c], q[4 * v4 + c], zp[c]);
+        }
+        const float h = tanhf((zp[0] + zp[1]) + (zp[2] + zp[3]));
+        const float w1m = w1_s[mu];
+        U = __fmaf_rn(w1m, h, U);
+        const float beta = w1m * (1.f - h * h);
+#pragma unroll
+        for (int v4 = 0; v4 < NDP / 4; ++v4) {
+          const float4 wv = row[v4];
+          const float wc[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (4 * v4 + c < NDES) dq[4 * v4 + c] = __fmaf_rn(beta, wc[c], dq[4 * v4 + c]);
+        }
       }
       U -= w.b1;
-      if (a.energy) a.energy[i] = (double)U;
+      if (a.energy) a.energy[a.perm ? a.perm[i] : i] = (double)U;
       Ublock = (double)U;
 
       // ---- radial force coefficients e^t_k = sum_n dU/dq_n c^{t_i t}_{nk} and their sum
@@ -349,46 +438,45 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
           dst[k4] = make_float4(ev[4 * k4], ev[4 * k4 + 1], ev[4 * k4 + 2], ev[4 * k4 + 3]);
       }
 
-      // ---- dU/dS_nk from the explicit 3/4/5-body forms
-      float dS[NA + 1][NK];
+      // ---- dU/dS_nk from the explicit 3/4/5-body forms, written over S in shared memory
 #pragma unroll
       for (int n = 0; n <= NA; ++n) {
-        float s[NK];
+        float s[NK], dS[NK];
 #pragma unroll
         for (int k = 0; k < NK; ++k) s[k] = Sme[(n * NK + k) * kAtomBlock];
 #pragma unroll
         for (int k = 0; k < NK; ++k) {
           if (k < S::KEND3) {
             const float d3 = dq[(NR + 1) + (l_of_k(k) - 1) * (NA + 1) + n];
-            dS[n][k] = 2.f * w.m.c3b[k] * s[k] * d3;
+            dS[k] = 2.f * w.m.c3b[k] * s[k] * d3;
           } else {
-            dS[n][k] = 0.f;
+            dS[k] = 0.f;
           }
         }
         if constexpr (S::L4 >= 2) {
           const float d4 = dq[S::OFF4 + n];
           const float *C = w.m.c4b;
-          dS[n][3] += d4 * (3.f * C[0] * s[3] * s[3] + C[1] * (s[4] * s[4] + s[5] * s[5]) + C[2] * (s[6] * s[6] + s[7] * s[7]));
-          dS[n][4] += d4 * (2.f * C[1] * s[3] * s[4] - 2.f * C[3] * s[6] * s[4] + C[4] * s[5] * s[7]);
-          dS[n][5] += d4 * (2.f * C[1] * s[3] * s[5] + 2.f * C[3] * s[6] * s[5] + C[4] * s[4] * s[7]);
-          dS[n][6] += d4 * (2.f * C[2] * s[3] * s[6] + C[3] * (s[5] * s[5] - s[4] * s[4]));
-          dS[n][7] += d4 * (2.f * C[2] * s[3] * s[7] + C[4] * s[4] * s[5]);
+          dS[3] += d4 * (3.f * C[0] * s[3] * s[3] + C[1] * (s[4] * s[4] + s[5] * s[5]) + C[2] * (s[6] * s[6] + s[7] * s[7]));
+          dS[4] += d4 * (2.f * C[1] * s[3] * s[4] - 2.f * C[3] * s[6] * s[4] + C[4] * s[5] * s[7]);
+          dS[5] += d4 * (2.f * C[1] * s[3] * s[5] + 2.f * C[3] * s[6] * s[5] + C[4] * s[4] * s[7]);
+          dS[6] += d4 * (2.f * C[2] * s[3] * s[6] + C[3] * (s[5] * s[5] - s[4] * s[4]));
+          dS[7] += d4 * (2.f * C[2] * s[3] * s[7] + C[4] * s[4] * s[5]);
         }
         if constexpr (S::L5 >= 1) {
           const float d5 = dq[S::OFF5 + n];
           const float *C = w.m.c5b;
           const float s12 = s[1] * s[1] + s[2] * s[2];
-          dS[n][0] += d5 * (4.f * C[0] * s[0] * s[0] * s[0] + 2.f * C[1] * s[0] * s12);
+          dS[0] += d5 * (4.f * C[0] * s[0] * s[0] * s[0] + 2.f * C[1] * s[0] * s12);
           const float common = 2.f * C[1] * s[0] * s[0] + 4.f * C[2] * s12;
-          dS[n][1] += d5 * common * s[1];
-          dS[n][2] += d5 * common * s[2];
+          dS[1] += d5 * common * s[1];
+          dS[2] += d5 * common * s[2];
         }
+#pragma unroll
+        for (int k = 0; k < NK; ++k) Sme[(n * NK + k) * kAtomBlock] = dS[k];
       }
 
       // ---- angular partial forces dU_i/dr_ij (angular terms of Eq. partial_force)
-      for (int m = 0; m < na; ++m) {
-        const unsigned e = a.nl_a[(size_t)m * N + i];
-        const float4 pj = a.pos4[e & a.jmask];
+      for_pairs(a.nl_a, 0, na, N, i, a.pos4, a.jmask, [&](int m, unsigned e, const float4 &pj) {
         const float3 d = pair_vector(pi, pj, dtab_s[e >> a.jbits]);
         const float r2 = norm2(d);
         if (r2 < rcA2) {
@@ -410,28 +498,26 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
             g[n] = acc;
             gp[n] = accp;
           }
-          float Gx[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, Gy[5] = {0.f, 0.f, 0.f, 0.f, 0.f},
-                Gz[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, Y[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+          // G = sum_k a_k r^-l grad b_k (tangential part used), Y = sum_k c_k r^-l b_k
+          const float rl[5] = {1.f, rinv, rinv * rinv, rinv * rinv * rinv, (rinv * rinv) * (rinv * rinv)};
+          float gx = 0.f, gy = 0.f, gz = 0.f, yy = 0.f;
           static_for<0, NK>([&](auto kc) {
             constexpr int k = decltype(kc)::value;
-            constexpr int l = l_of_k(k);
             float ak = 0.f, ck = 0.f;
 #pragma unroll
             for (int n = 0; n <= NA; ++n) {
-              ak = __fmaf_rn(dS[n][k], g[n], ak);
-              ck = __fmaf_rn(dS[n][k], gp[n], ck);
+              const float ds = Sme[(n * NK + k) * kAtomBlock];
+              ak = __fmaf_rn(ds, g[n], ak);
+              ck = __fmaf_rn(ds, gp[n], ck);
             }
+            ak *= rl[l_of_k(k)];
+            ck *= rl[l_of_k(k)];
             const float3 gb = poly_grad<k>(d.x, d.y, d.z, r2);
-            Gx[l] = __fmaf_rn(ak, gb.x, Gx[l]);
-            Gy[l] = __fmaf_rn(ak, gb.y, Gy[l]);
-            Gz[l] = __fmaf_rn(ak, gb.z, Gz[l]);
-            Y[l] = __fmaf_rn(ck, poly_b<k>(d.x, d.y, d.z, r2), Y[l]);
+            gx = __fmaf_rn(ak, gb.x, gx);
+            gy = __fmaf_rn(ak, gb.y, gy);
+            gz = __fmaf_rn(ak, gb.z, gz);
+            yy = __fmaf_rn(ck, poly_b<k>(d.x, d.y, d.z, r2), yy);
           });
-          const float r1 = rinv, r2i = rinv * rinv, r3 = r2i * rinv, r4 = r2i * r2i;
-          const float gx = Gx[1] * r1 + Gx[2] * r2i + Gx[3] * r3 + Gx[4] * r4;
-          const float gy = Gy[1] * r1 + Gy[2] * r2i + Gy[3] * r3 + Gy[4] * r4;
-          const float gz = Gz[1] * r1 + Gz[2] * r2i + Gz[3] * r3 + Gz[4] * r4;
-          const float yy = Y[1] * r1 + Y[2] * r2i + Y[3] * r3 + Y[4] * r4;
           const float ux = d.x * rinv, uy = d.y * rinv, uz = d.z * rinv;
           const float gu = gx * ux + gy * uy + gz * uz;
           const float px = (gx - gu * ux) + yy * ux;
@@ -439,7 +525,7 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
           const float pz = (gz - gu * uz) + yy * uz;
           a.p_ang[(size_t)m * N + i] = make_float4(px, py, pz, 0.f);
         }
-      }
+      });
     }
   }
   if constexpr (!DESC_ONLY) {
@@ -492,10 +578,8 @@ __global__ void __launch_bounds__(kGatherBlock)
         const float4 v = src[k4];
         eo[4 * k4] = v.x; eo[4 * k4 + 1] = v.y; eo[4 * k4 + 2] = v.z; eo[4 * k4 + 3] = v.w;
       }
-      for (int m = 0; m < cnt; ++m) {
-        const unsigned e = a.nl_r[(size_t)(base + m) * N + i];
+      for_pairs_batch<4>(a.nl_r, base, cnt, N, i, a.pos4, a.jmask, [&](int, unsigned e, const float4 &pj) {
         const int j = e & a.jmask;
-        const float4 pj = a.pos4[j];
         const float3 d = pair_vector(pi, pj, dtab_s[e >> a.jbits]);
         const float r2 = norm2(d);
         if (r2 < rcR2) {
@@ -556,15 +640,13 @@ __global__ void __launch_bounds__(kGatherBlock)
           w[7] = __fmaf_rn(d.z, px, w[7]);
           w[8] = __fmaf_rn(d.z, py, w[8]);
         }
-      }
+      });
       base += cnt;
     }
     // ---- angular part (Algorithm 4): F_i += P_ij - P_ji, W_i += r_ij (x) P_ji
     const int na = a.nn_a[i];
-    for (int m = 0; m < na; ++m) {
+    for_pairs(a.nl_a, 0, na, N, i, a.pos4, a.jmask, [&](int m, unsigned e, const float4 &pj) {
       const size_t slot = (size_t)m * N + i;
-      const unsigned e = a.nl_a[slot];
-      const float4 pj = a.pos4[e & a.jmask];
       const float3 d = pair_vector(pi, pj, dtab_s[e >> a.jbits]);
       const float r2 = norm2(d);
       if (r2 < rcA2) {
@@ -583,16 +665,17 @@ __global__ void __launch_bounds__(kGatherBlock)
         w[7] = __fmaf_rn(d.z, pji.x, w[7]);
         w[8] = __fmaf_rn(d.z, pji.y, w[8]);
       }
-    }
+    });
     const double Fx = fx, Fy = fy, Fz = fz;
+    const size_t io = a.perm ? (size_t)a.perm[i] : (size_t)i;
     if (a.force) {
-      a.force[3 * (size_t)i] = Fx;
-      a.force[3 * (size_t)i + 1] = Fy;
-      a.force[3 * (size_t)i + 2] = Fz;
+      a.force[3 * io] = Fx;
+      a.force[3 * io + 1] = Fy;
+      a.force[3 * io + 2] = Fz;
     }
     if (a.virial) {
 #pragma unroll
-      for (int c = 0; c < 9; ++c) a.virial[9 * (size_t)i + c] = (double)w[c];
+      for (int c = 0; c < 9; ++c) a.virial[9 * io + c] = (double)w[c];
     }
 #pragma unroll
     for (int c = 0; c < 9; ++c) part[2 + c] = (double)w[c];
@@ -625,8 +708,8 @@ __global__ void __launch_bounds__(kGatherBlock)
 template <class S>
 size_t atom_smem_bytes(int T, int ncode) {
   return sizeof(float4) * ncode +
-         sizeof(float) * (T * T * (S::NR + 1) * (S::KR + 1) + T * T * (S::NA + 1) * (S::KA + 1) +
-                          (S::NA + 1) * S::NK * kAtomBlock);
+         sizeof(float) * (S::H * S::NDP + 2 * S::H + T * T * (S::NR + 1) * (S::KR + 1) +
+                          T * T * (S::NA + 1) * (S::KA + 1) + (S::NA + 1) * S::NK * kAtomBlock);
 }
 
 template <class S>

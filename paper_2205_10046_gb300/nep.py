@@ -41,7 +41,8 @@ class nep_stats(C.Structure):
                 ("max_radial", C.c_int), ("max_angular", C.c_int), ("mean_radial", C.c_double),
                 ("mean_angular", C.c_double), ("mean_radial_in_rc", C.c_double),
                 ("mean_angular_in_rc", C.c_double), ("n_rebuilds", C.c_longlong),
-                ("md_steps", C.c_longlong), ("cells", C.c_int * 3), ("graph_kernels", C.c_int)]
+                ("md_steps", C.c_longlong), ("cells", C.c_int * 3), ("graph_kernels", C.c_int),
+                ("rebuild_kernels", C.c_int)]
 
 
 _lib = None
