@@ -194,6 +194,28 @@ int nep_kernel_slots(void);
 const char *nep_kernel_name(int slot);
 int nep_kernel_times(nep_handle *h, float *ms_out, int n_slots);
 
+/* Descriptor evaluation for callers that cannot allocate device memory (for example a
+ * host program whose device memory is planned up front, or code where cudaMalloc must not
+ * be called). Same arguments and results as nep_descriptors, but the model is passed
+ * directly (no handle, which would allocate) and every scratch array comes from one fixed
+ * device array inside the library: NEP_STATIC_SCRATCH_BYTES on every GPU that loads the
+ * library, held until the process exits. No cudaMalloc, cudaFree or other allocating call
+ * is made.
+ *   - n_atoms above NEP_STATIC_MAX_ATOMS, or neighbour lists that do not fit the scratch,
+ *     are rejected with NEP_ERR_ARG; nep_last_error(NULL) gives the message.
+ *   - The first call on a device looks up the scratch address on that device (with the
+ *     device current); make that first call before any stream capture.
+ *   - All calls share the one scratch array, which keeps the previous call's contents (each
+ *     call rewrites what it reads). Calls that overlap on the GPU race with each other:
+ *     serialise them (one stream, or synchronise between calls).
+ *   - The call synchronises `stream` twice (to size the neighbour lists) and returns with
+ *     the descriptor kernel queued on `stream`.
+ * The paper has no counterpart: this is a deployment variant of nep_descriptors. */
+#define NEP_STATIC_MAX_ATOMS 4096
+#define NEP_STATIC_SCRATCH_BYTES (16u << 20)
+int nep_descriptors_static(const nep_params *params, int n_atoms, const double *pos, const int *types,
+                           const double *box, double *q, nep_stream_t stream);
+
 /* Compiled hyper-parameter shapes: writes up to `max` rows of 8 ints
  * (n_max^R, N_bas^R, n_max^A, N_bas^A, N_neu, l_max^3b, l_max^4b, l_max^5b) and
  * returns the number of shapes. */

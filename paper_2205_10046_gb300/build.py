@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libnep.so")
 BUILD = os.path.join(ROOT, "_build", "libnep")
 
-SOURCES = ["nep_api.cu", "nep_build.cu", "nep_shape_si.cu", "nep_shape_pbte.cu", "nep_shape_mixed.cu"]
+SOURCES = ["nep_api.cu", "nep_build.cu", "nep_static.cu", "nep_shape_si.cu", "nep_shape_pbte.cu",
+           "nep_shape_mixed.cu"]
 HEADERS = ["nep_internal.cuh", "nep_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -42,6 +42,145 @@ const ShapeOps *shape_at(int i) {
 
 using namespace nep;
 
+namespace nep {
+
+// The paper's 3-body (C3b), 4-body (C4b) and 5-body (C5b) coefficients (Sec. II D),
+// evaluated here from the printed expressions.
+void model_constants(ModelF &m) {
+  const double p = 3.14159265358979323846;
+  const double c3[24] = {3.0 / (4 * p), 3.0 / (4 * p), 3.0 / (4 * p),
+                         5.0 / (16 * p), 15.0 / (4 * p), 15.0 / (4 * p), 15.0 / (16 * p), 15.0 / (16 * p),
+                         7.0 / (16 * p), 21.0 / (32 * p), 21.0 / (32 * p), 105.0 / (16 * p), 105.0 / (16 * p),
+                         35.0 / (32 * p), 35.0 / (32 * p),
+                         9.0 / (256 * p), 45.0 / (32 * p), 45.0 / (32 * p), 45.0 / (64 * p), 45.0 / (64 * p),
+                         315.0 / (32 * p), 315.0 / (32 * p), 315.0 / (256 * p), 315.0 / (256 * p)};
+  for (int k = 0; k < 24; ++k) m.c3b[k] = (float)c3[k];
+  const double y20 = 0.25 * std::sqrt(5.0 / p), y21 = 0.5 * std::sqrt(7.5 / p), y22 = 0.25 * std::sqrt(7.5 / p);
+  m.c4b[0] = (float)(-std::sqrt(2.0 / 35.0) * y20 * y20 * y20);
+  m.c4b[1] = (float)(-6.0 * std::sqrt(1.0 / 70.0) * y20 * y21 * y21);
+  m.c4b[2] = (float)(6.0 * std::sqrt(2.0 / 35.0) * y20 * y22 * y22);
+  m.c4b[3] = (float)(6.0 * std::sqrt(3.0 / 35.0) * y21 * y21 * y22);
+  m.c4b[4] = (float)(-12.0 * std::sqrt(3.0 / 35.0) * y21 * y21 * y22);
+  m.c5b[0] = (float)(21.0 / (80.0 * p * p));
+  m.c5b[1] = (float)(21.0 / (40.0 * p * p));
+  m.c5b[2] = (float)(21.0 / (80.0 * p * p));
+}
+
+// Cell grid, image range and shift table (dtab[0..ncode), at most 512 entries) for the cell
+// rows `box` and the list radius rl. Returns NEP_OK or an error code with *err set.
+int build_grid(const double *box, double rl, int N, Grid &g, float4 *dtab, double *volume, const char **err) {
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) g.H[a][b] = box[3 * a + b];
+  double cof[3][3];
+  const double(*H)[3] = g.H;
+  cof[0][0] = H[1][1] * H[2][2] - H[1][2] * H[2][1];
+  cof[0][1] = H[1][2] * H[2][0] - H[1][0] * H[2][2];
+  cof[0][2] = H[1][0] * H[2][1] - H[1][1] * H[2][0];
+  cof[1][0] = H[2][1] * H[0][2] - H[2][2] * H[0][1];
+  cof[1][1] = H[2][2] * H[0][0] - H[2][0] * H[0][2];
+  cof[1][2] = H[2][0] * H[0][1] - H[2][1] * H[0][0];
+  cof[2][0] = H[0][1] * H[1][2] - H[0][2] * H[1][1];
+  cof[2][1] = H[0][2] * H[1][0] - H[0][0] * H[1][2];
+  cof[2][2] = H[0][0] * H[1][1] - H[0][1] * H[1][0];
+  const double det = H[0][0] * cof[0][0] + H[0][1] * cof[0][1] + H[0][2] * cof[0][2];
+  if (!(std::fabs(det) > 1e-12) || !std::isfinite(det)) {
+    *err = "box is singular or non-finite";
+    return NEP_ERR_ARG;
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) g.Hinv[a][b] = cof[b][a] / det;
+  *volume = std::fabs(det);
+  double th[3];
+  for (int a = 0; a < 3; ++a) {
+    // face distance along axis a: |det| / |row b x row c| = 1 / |column a of Hinv|
+    const double n = std::sqrt(g.Hinv[0][a] * g.Hinv[0][a] + g.Hinv[1][a] * g.Hinv[1][a] + g.Hinv[2][a] * g.Hinv[2][a]);
+    th[a] = 1.0 / n;
+    g.nc[a] = std::max(1, (int)std::floor(th[a] / rl));
+  }
+  // keep the grid no larger than about 4 cells per atom (coarser cells stay valid)
+  const long long limit = std::max<long long>(64, 4LL * N);
+  while ((long long)g.nc[0] * g.nc[1] * g.nc[2] > limit) {
+    int a = 0;
+    for (int b = 1; b < 3; ++b)
+      if (g.nc[b] > g.nc[a]) a = b;
+    g.nc[a] = std::max(1, g.nc[a] / 2);
+  }
+  int rmax = 0;
+  for (int a = 0; a < 3; ++a) {
+    g.R[a] = (int)std::ceil(rl * g.nc[a] / th[a] - 1e-12);
+    if (g.R[a] < 1) g.R[a] = 1;
+    rmax = std::max(rmax, g.R[a]);
+  }
+  if (rmax > kMaxImage) {
+    *err = "cell thinner than a third of r_c^R + skin; replicate the cell before calling";
+    return NEP_ERR_UNSUPPORTED;
+  }
+  g.ncell = g.nc[0] * g.nc[1] * g.nc[2];
+  g.obits = rmax <= 1 ? 2 : 3;
+  int jb = 1;
+  while ((1LL << jb) < (long long)std::max(N, 2)) ++jb;
+  if (jb + 3 * g.obits > 32) {
+    *err = "too many atoms for the packed neighbour entries";
+    return NEP_ERR_UNSUPPORTED;
+  }
+  g.jbits = jb;
+  g.jmask = (jb >= 32) ? 0xffffffffu : ((1u << jb) - 1u);
+  g.ncode = 1 << (3 * g.obits);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) g.Hc[a][b] = g.H[a][b] / g.nc[a];
+  for (int c = 0; c < g.ncode; ++c) dtab[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int ox = -g.R[0]; ox <= g.R[0]; ++ox)
+    for (int oy = -g.R[1]; oy <= g.R[1]; ++oy)
+      for (int oz = -g.R[2]; oz <= g.R[2]; ++oz) {
+        const unsigned code = (unsigned)(ox + g.R[0]) | ((unsigned)(oy + g.R[1]) << g.obits) |
+                              ((unsigned)(oz + g.R[2]) << (2 * g.obits));
+        double D[3];
+        for (int b = 0; b < 3; ++b) D[b] = ox * g.Hc[0][b] + oy * g.Hc[1][b] + oz * g.Hc[2][b];
+        dtab[code] = make_float4((float)D[0], (float)D[1], (float)D[2], 0.f);
+      }
+  return NEP_OK;
+}
+
+// Validates the model parameters and finds the compiled kernel shape.
+int check_params(const nep_params *p, const ShapeOps **ops_out, const char **err) {
+  *ops_out = nullptr;
+  if (!p) { *err = "params is null"; return NEP_ERR_ARG; }
+  if (p->version != 3) { *err = "version must be 3"; return NEP_ERR_ARG; }
+  if (p->n_types < 1 || p->n_types > NEP_MAX_TYPES) { *err = "n_types out of range"; return NEP_ERR_ARG; }
+  if (!(p->rc_radial > 0) || !(p->rc_angular > 0) || p->rc_angular > p->rc_radial || !std::isfinite(p->rc_radial)) {
+    *err = "need 0 < rc_angular <= rc_radial";
+    return NEP_ERR_ARG;
+  }
+  if (p->n_max_radial < 0 || p->n_max_angular < 0 || p->basis_radial < 0 || p->basis_angular < 0 ||
+      p->n_neuron < 1) {
+    *err = "negative size";
+    return NEP_ERR_ARG;
+  }
+  if (p->l_max_3b < 1 || p->l_max_3b > 4 || !(p->l_max_4b == 0 || p->l_max_4b == 2) ||
+      !(p->l_max_5b == 0 || p->l_max_5b == 1)) {
+    *err = "need l_max_3b in 1..4, l_max_4b in {0,2}, l_max_5b in {0,1}";
+    return NEP_ERR_ARG;
+  }
+  if (!p->c_radial || !p->c_angular || !p->w0 || !p->b0 || !p->w1) {
+    *err = "null weight pointer";
+    return NEP_ERR_ARG;
+  }
+  for (int i = 0; i < shape_count(); ++i) {
+    const ShapeOps *o = shape_at(i);
+    if (o->nR == p->n_max_radial && o->KR == p->basis_radial && o->nA == p->n_max_angular &&
+        o->KA == p->basis_angular && o->H == p->n_neuron && o->L3 == p->l_max_3b && o->L4 == p->l_max_4b &&
+        o->L5 == p->l_max_5b)
+      *ops_out = o;
+  }
+  if (!*ops_out) {
+    *err = "no kernel compiled for these hyper-parameters";
+    return NEP_ERR_UNSUPPORTED;
+  }
+  return NEP_OK;
+}
+
+}  // namespace nep
+
 namespace {
 
 const double kPi = 3.14159265358979323846;
@@ -74,29 +213,11 @@ struct DevBuf {
   }
 };
 
-// The paper's 3-body (C3b), 4-body (C4b) and 5-body (C5b) coefficients (Sec. II D),
-// evaluated here from the printed expressions.
-void model_constants(ModelF &m) {
-  const double p = kPi;
-  const double c3[24] = {3.0 / (4 * p), 3.0 / (4 * p), 3.0 / (4 * p),
-                         5.0 / (16 * p), 15.0 / (4 * p), 15.0 / (4 * p), 15.0 / (16 * p), 15.0 / (16 * p),
-                         7.0 / (16 * p), 21.0 / (32 * p), 21.0 / (32 * p), 105.0 / (16 * p), 105.0 / (16 * p),
-                         35.0 / (32 * p), 35.0 / (32 * p),
-                         9.0 / (256 * p), 45.0 / (32 * p), 45.0 / (32 * p), 45.0 / (64 * p), 45.0 / (64 * p),
-                         315.0 / (32 * p), 315.0 / (32 * p), 315.0 / (256 * p), 315.0 / (256 * p)};
-  for (int k = 0; k < 24; ++k) m.c3b[k] = (float)c3[k];
-  const double y20 = 0.25 * std::sqrt(5.0 / p), y21 = 0.5 * std::sqrt(7.5 / p), y22 = 0.25 * std::sqrt(7.5 / p);
-  m.c4b[0] = (float)(-std::sqrt(2.0 / 35.0) * y20 * y20 * y20);
-  m.c4b[1] = (float)(-6.0 * std::sqrt(1.0 / 70.0) * y20 * y21 * y21);
-  m.c4b[2] = (float)(6.0 * std::sqrt(2.0 / 35.0) * y20 * y22 * y22);
-  m.c4b[3] = (float)(6.0 * std::sqrt(3.0 / 35.0) * y21 * y21 * y22);
-  m.c4b[4] = (float)(-12.0 * std::sqrt(3.0 / 35.0) * y21 * y21 * y22);
-  m.c5b[0] = (float)(21.0 / (80.0 * p * p));
-  m.c5b[1] = (float)(21.0 / (40.0 * p * p));
-  m.c5b[2] = (float)(21.0 / (80.0 * p * p));
-}
-
 }  // namespace
+
+namespace nep {
+void set_create_error(const char *msg) { g_create_error = msg ? msg : ""; }
+}  // namespace nep
 
 struct nep_handle {
   // model
@@ -176,78 +297,12 @@ void ev_record(nep_handle *h, int slot, int which, cudaStream_t s, bool capturin
   if (which == 1) h->slot_ran[slot] = true;
 }
 
-bool mat_inverse(const double H[3][3], double Hinv[3][3], double *det_out) {
-  double cof[3][3];
-  cof[0][0] = H[1][1] * H[2][2] - H[1][2] * H[2][1];
-  cof[0][1] = H[1][2] * H[2][0] - H[1][0] * H[2][2];
-  cof[0][2] = H[1][0] * H[2][1] - H[1][1] * H[2][0];
-  cof[1][0] = H[2][1] * H[0][2] - H[2][2] * H[0][1];
-  cof[1][1] = H[2][2] * H[0][0] - H[2][0] * H[0][2];
-  cof[1][2] = H[2][0] * H[0][1] - H[2][1] * H[0][0];
-  cof[2][0] = H[0][1] * H[1][2] - H[0][2] * H[1][1];
-  cof[2][1] = H[0][2] * H[1][0] - H[0][0] * H[1][2];
-  cof[2][2] = H[0][0] * H[1][1] - H[0][1] * H[1][0];
-  const double det = H[0][0] * cof[0][0] + H[0][1] * cof[0][1] + H[0][2] * cof[0][2];
-  if (!(std::fabs(det) > 1e-12) || !std::isfinite(det)) return false;
-  for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b) Hinv[a][b] = cof[b][a] / det;
-  *det_out = det;
-  return true;
-}
-
-// Cell grid, image range and shift table for a cell `box` and list radius rc_list.
 int setup_grid(nep_handle *h, int N, const double *box, std::vector<float4> &dtab) {
-  Grid &g = h->grid;
-  for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b) g.H[a][b] = box[3 * a + b];
-  double det;
-  if (!mat_inverse(g.H, g.Hinv, &det)) return fail(h, NEP_ERR_ARG, "box is singular or non-finite");
-  h->volume = std::fabs(det);
-  const double rl = h->rcR + h->skin;
-  double th[3];
-  for (int a = 0; a < 3; ++a) {
-    // face distance along axis a: |det| / |row b x row c| = 1 / |column a of Hinv|
-    const double n = std::sqrt(g.Hinv[0][a] * g.Hinv[0][a] + g.Hinv[1][a] * g.Hinv[1][a] + g.Hinv[2][a] * g.Hinv[2][a]);
-    th[a] = 1.0 / n;
-    g.nc[a] = std::max(1, (int)std::floor(th[a] / rl));
-  }
-  // keep the grid no larger than about 4 cells per atom (coarser cells stay valid)
-  const long long limit = std::max<long long>(64, 4LL * N);
-  while ((long long)g.nc[0] * g.nc[1] * g.nc[2] > limit) {
-    int a = 0;
-    for (int b = 1; b < 3; ++b)
-      if (g.nc[b] > g.nc[a]) a = b;
-    g.nc[a] = std::max(1, g.nc[a] / 2);
-  }
-  int rmax = 0;
-  for (int a = 0; a < 3; ++a) {
-    g.R[a] = (int)std::ceil(rl * g.nc[a] / th[a] - 1e-12);
-    if (g.R[a] < 1) g.R[a] = 1;
-    rmax = std::max(rmax, g.R[a]);
-  }
-  if (rmax > kMaxImage)
-    return fail(h, NEP_ERR_UNSUPPORTED,
-                "cell thinner than a third of r_c^R + skin; replicate the cell before calling");
-  g.ncell = g.nc[0] * g.nc[1] * g.nc[2];
-  g.obits = rmax <= 1 ? 2 : 3;
-  int jb = 1;
-  while ((1LL << jb) < (long long)std::max(N, 2)) ++jb;
-  if (jb + 3 * g.obits > 32) return fail(h, NEP_ERR_UNSUPPORTED, "too many atoms for the packed neighbour entries");
-  g.jbits = jb;
-  g.jmask = (jb >= 32) ? 0xffffffffu : ((1u << jb) - 1u);
-  g.ncode = 1 << (3 * g.obits);
-  for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b) g.Hc[a][b] = g.H[a][b] / g.nc[a];
-  dtab.assign(g.ncode, make_float4(0.f, 0.f, 0.f, 0.f));
-  for (int ox = -g.R[0]; ox <= g.R[0]; ++ox)
-    for (int oy = -g.R[1]; oy <= g.R[1]; ++oy)
-      for (int oz = -g.R[2]; oz <= g.R[2]; ++oz) {
-        const unsigned code = (unsigned)(ox + g.R[0]) | ((unsigned)(oy + g.R[1]) << g.obits) |
-                              ((unsigned)(oz + g.R[2]) << (2 * g.obits));
-        double D[3];
-        for (int b = 0; b < 3; ++b) D[b] = ox * g.Hc[0][b] + oy * g.Hc[1][b] + oz * g.Hc[2][b];
-        dtab[code] = make_float4((float)D[0], (float)D[1], (float)D[2], 0.f);
-      }
+  dtab.assign(1 << (3 * 3), make_float4(0.f, 0.f, 0.f, 0.f));
+  const char *err = nullptr;
+  const int rc = nep::build_grid(box, h->rcR + h->skin, N, h->grid, dtab.data(), &h->volume, &err);
+  if (rc) return fail(h, rc, err);
+  dtab.resize(h->grid.ncode);
   return NEP_OK;
 }
 
@@ -463,27 +518,10 @@ int nep_supported(int *shapes, int max) {
 int nep_create(const nep_params *p, nep_handle **out) {
   if (!out) return fail(nullptr, NEP_ERR_ARG, "out is null");
   *out = nullptr;
-  if (!p) return fail(nullptr, NEP_ERR_ARG, "params is null");
-  if (p->version != 3) return fail(nullptr, NEP_ERR_ARG, "version must be 3");
-  if (p->n_types < 1 || p->n_types > NEP_MAX_TYPES) return fail(nullptr, NEP_ERR_ARG, "n_types out of range");
-  if (!(p->rc_radial > 0) || !(p->rc_angular > 0) || p->rc_angular > p->rc_radial || !std::isfinite(p->rc_radial))
-    return fail(nullptr, NEP_ERR_ARG, "need 0 < rc_angular <= rc_radial");
-  if (p->n_max_radial < 0 || p->n_max_angular < 0 || p->basis_radial < 0 || p->basis_angular < 0 || p->n_neuron < 1)
-    return fail(nullptr, NEP_ERR_ARG, "negative size");
-  if (p->l_max_3b < 1 || p->l_max_3b > 4 || !(p->l_max_4b == 0 || p->l_max_4b == 2) ||
-      !(p->l_max_5b == 0 || p->l_max_5b == 1))
-    return fail(nullptr, NEP_ERR_ARG, "need l_max_3b in 1..4, l_max_4b in {0,2}, l_max_5b in {0,1}");
-  if (!p->c_radial || !p->c_angular || !p->w0 || !p->b0 || !p->w1)
-    return fail(nullptr, NEP_ERR_ARG, "null weight pointer");
   const ShapeOps *ops = nullptr;
-  for (int i = 0; i < shape_count(); ++i) {
-    const ShapeOps *o = shape_at(i);
-    if (o->nR == p->n_max_radial && o->KR == p->basis_radial && o->nA == p->n_max_angular &&
-        o->KA == p->basis_angular && o->H == p->n_neuron && o->L3 == p->l_max_3b && o->L4 == p->l_max_4b &&
-        o->L5 == p->l_max_5b)
-      ops = o;
-  }
-  if (!ops) return fail(nullptr, NEP_ERR_UNSUPPORTED, "no kernel compiled for these hyper-parameters");
+  const char *perr = nullptr;
+  const int prc = check_params(p, &ops, &perr);
+  if (prc) return fail(nullptr, prc, perr);
   nep_handle *h = new nep_handle();
   h->ops = ops;
   h->T = p->n_types; h->nR = p->n_max_radial; h->nA = p->n_max_angular; h->KR = p->basis_radial;

@@ -129,4 +129,13 @@ struct ShapeOps {
 int shape_count();
 const ShapeOps *shape_at(int i);
 
+// Host helpers shared by the handle-based and the static-scratch entry points.
+struct Grid;
+void model_constants(ModelF &m);
+int build_grid(const double *box, double rl, int N, Grid &g, float4 *dtab, double *volume, const char **err);
+cudaError_t launch_rebuild(int N, int T, const Grid &g, const float4 *dtab, float rlR2, float rlA2, float rcR2,
+                           float rcA2, const AtomState &a, const ListBufs &L, int count_only, BuildStatus *st,
+                           cudaStream_t s);
+void launch_iota(int N, int *perm, cudaStream_t s);
+
 }  // namespace nep

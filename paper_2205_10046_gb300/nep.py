@@ -70,6 +70,7 @@ _SIGS = {
     "nep_kernel_name": (C.c_char_p, [C.c_int]),
     "nep_kernel_times": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int]),
     "nep_supported": (C.c_int, [C.POINTER(C.c_int), C.c_int]),
+    "nep_descriptors_static": (C.c_int, [C.POINTER(nep_params), C.c_int, _P, _P, _P, _P, _P]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -127,9 +128,8 @@ def nep_supported():
     return [tuple(buf[8 * i:8 * i + 8]) for i in range(n)]
 
 
-def nep_create(model, skin: float = 1.0):
-    """Handle for a workloads.NepModel (weights are copied into the library)."""
-    lib = load()
+def _params(model, skin: float):
+    """nep_params for a workloads.NepModel; returns (struct, arrays kept alive by the caller)."""
     arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in
             (model.c_radial, model.c_angular, model.w0, model.b0, model.w1)]
     mass = None if model.mass is None else np.ascontiguousarray(model.mass, dtype=np.float64)
@@ -138,6 +138,13 @@ def nep_create(model, skin: float = 1.0):
                    model.l_max_4b, model.l_max_5b, model.n_neuron,
                    *[a.ctypes.data for a in arrs], float(model.b1),
                    None if mass is None else mass.ctypes.data, float(skin))
+    return p, (arrs, mass)
+
+
+def nep_create(model, skin: float = 1.0):
+    """Handle for a workloads.NepModel (weights are copied into the library)."""
+    lib = load()
+    p, _keep = _params(model, skin)
     h = C.c_void_p()
     rc = lib.nep_create(C.byref(p), C.byref(h))
     _check(rc, None)
@@ -191,6 +198,18 @@ def nep_descriptors(h, pos, types, box, q):
     rc = load().nep_descriptors(h, n, _dev(pos, torch.float64, (n, 3), "pos"), _dev(types, torch.int32, (n,), "types"),
                                 b.ctypes.data, _dev(q, torch.float64, None, "q"), _stream())
     _check(rc, h)
+
+
+def nep_descriptors_static(model, pos, types, box, q, skin: float = 1.0):
+    """Descriptors without any device allocation (library-internal fixed scratch)."""
+    import torch
+    n = int(pos.shape[0])
+    b = _box(box)
+    p, _keep = _params(model, skin)
+    rc = load().nep_descriptors_static(C.byref(p), n, _dev(pos, torch.float64, (n, 3), "pos"),
+                                       _dev(types, torch.int32, (n,), "types"), b.ctypes.data,
+                                       _dev(q, torch.float64, None, "q"), _stream())
+    _check(rc, None)
 
 
 def md_init(h, pos, types, box, vel=None):
