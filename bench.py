@@ -46,6 +46,8 @@ def parse_args():
     ap.add_argument("--skin", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--plain-graph", action="store_true",
+                    help="capture the rebuild as ordinary kernel nodes (for kernel-level profilers)")
     return ap.parse_args()
 
 
@@ -302,6 +304,7 @@ def run_gb300(args):
     vel_d = torch.tensor(w.vel, device=dev)
     nep.md_init(h.h, pos_d, types_d, w.box, vel_d)
     nep.nep_set_profiling(h.h, True)
+    nep.nep_set_graph_conditional(h.h, not args.plain_graph)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 

@@ -190,6 +190,12 @@ int nep_get_stats(nep_handle *h, nep_stats *out);
  * for the most recent call, the device time in ms of each kernel slot (names via
  * nep_kernel_name; slots that did not run report 0). */
 int nep_set_profiling(nep_handle *h, int enable);
+
+/* How md_run captures the neighbour rebuild in its step graph: 1 (default) = inside a
+ * conditional graph node that runs only when a rebuild is due; 0 = as ordinary kernel
+ * nodes that return at once when no rebuild is due (for profilers that cannot look inside
+ * graphs with conditional nodes). Results are identical. */
+int nep_set_graph_conditional(nep_handle *h, int enable);
 int nep_kernel_slots(void);
 const char *nep_kernel_name(int slot);
 int nep_kernel_times(nep_handle *h, float *ms_out, int n_slots);

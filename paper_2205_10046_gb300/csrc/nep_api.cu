@@ -257,6 +257,8 @@ struct nep_handle {
   const double *graph_thermo = nullptr;
   cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
   int rebuild_kernels = 0;  // kernels in the conditional rebuild body of the step graph
+  bool graph_cond = true;   // rebuild inside a conditional node (else early-exit kernel nodes)
+  bool graph_cond_used = true;
   // profiling
   bool prof = false;
   cudaEvent_t ev[N_SLOTS][2] = {};
@@ -761,7 +763,7 @@ int md_step_launch(nep_handle *h, double dt, cudaStream_t s, bool capturing) {
   ev_record(h, SLOT_DRIFT, 1, s, capturing);
   ev_record(h, SLOT_REBUILD, 0, s, capturing);
   const float rlR = (float)(h->rcR + h->skin), rlA = (float)(h->rcA + h->skin);
-  if (capturing) {
+  if (capturing && h->graph_cond) {
     // the rebuild kernels sit in the body of a conditional (IF) node; a one-thread kernel sets
     // its condition from the drift kernel's request, so steps without a rebuild launch none
     cudaStreamCaptureStatus cs;
@@ -799,6 +801,7 @@ int md_step_launch(nep_handle *h, double dt, cudaStream_t s, bool capturing) {
     CK(launch_rebuild(N, h->T, h->grid, h->dtab.p, rlR * rlR, rlA * rlA, h->rcR2f(), h->rcA2f(), atom_state(h),
                       list_bufs(h), 0, h->status.p, s),
        "launch rebuild");
+    h->rebuild_kernels = 0;
   }
   ev_record(h, SLOT_REBUILD, 1, s, capturing);
   int rc = run_forces(h, N, nullptr, h->F.p, nullptr, 1, 0.5 * dt, s, capturing);
@@ -824,7 +827,8 @@ int md_queue(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double 
   CK(cudaMemcpyAsync(h->thermo_ctl.p, ctl, sizeof(ctl), cudaMemcpyHostToDevice, s), "thermo ctl");
   // (re)capture the one-step graph when the step size, the profiling mode or the thermo
   // staging buffer changed
-  if (!h->graph || h->graph_dt != dt_fs || h->graph_prof != h->prof || h->graph_thermo != h->thermo_stage.p) {
+  if (!h->graph || h->graph_dt != dt_fs || h->graph_prof != h->prof || h->graph_thermo != h->thermo_stage.p ||
+      h->graph_cond_used != h->graph_cond) {
     if (h->graph) {
       cudaGraphExecDestroy(h->graph);
       h->graph = nullptr;
@@ -855,6 +859,7 @@ int md_queue(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double 
     h->graph_dt = dt_fs;
     h->graph_prof = h->prof;
     h->graph_thermo = h->thermo_stage.p;
+    h->graph_cond_used = h->graph_cond;
   }
   for (int st = 0; st < n_steps; ++st) CK(cudaGraphLaunch(h->graph, s), "graph launch");
   if (thermo && rows > 0)
@@ -999,6 +1004,12 @@ int nep_get_stats(nep_handle *h, nep_stats *out) {
 int nep_set_profiling(nep_handle *h, int enable) {
   if (!valid_handle(h)) return NEP_ERR_ARG;
   h->prof = enable != 0;
+  return NEP_OK;
+}
+
+int nep_set_graph_conditional(nep_handle *h, int enable) {
+  if (!valid_handle(h)) return NEP_ERR_ARG;
+  h->graph_cond = enable != 0;
   return NEP_OK;
 }
 

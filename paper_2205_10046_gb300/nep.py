@@ -66,6 +66,7 @@ _SIGS = {
     "md_get_state_host": (C.c_int, [_P, _P, _P, _P]),
     "nep_get_stats": (C.c_int, [_P, C.POINTER(nep_stats)]),
     "nep_set_profiling": (C.c_int, [_P, C.c_int]),
+    "nep_set_graph_conditional": (C.c_int, [_P, C.c_int]),
     "nep_kernel_slots": (C.c_int, []),
     "nep_kernel_name": (C.c_char_p, [C.c_int]),
     "nep_kernel_times": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int]),
@@ -275,6 +276,10 @@ def nep_get_stats(h) -> dict:
 
 def nep_set_profiling(h, enable: bool):
     _check(load().nep_set_profiling(h, 1 if enable else 0), h)
+
+
+def nep_set_graph_conditional(h, enable: bool):
+    _check(load().nep_set_graph_conditional(h, 1 if enable else 0), h)
 
 
 def nep_kernel_times(h) -> dict:
