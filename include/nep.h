@@ -56,6 +56,7 @@ extern "C" {
 #define NEP_ERR_UNSUPPORTED (-6)       /* hyper-parameters without a compiled kernel, or a cell
                                           thinner than a third of the list radius */
 #define NEP_ERR_STATE (-7)             /* call out of order (e.g. md_run before md_init) */
+#define NEP_ERR_TIMEOUT (-8)           /* a device-side wait ran out (tensor-core completion) */
 
 #define NEP_MAX_TYPES 8
 
@@ -190,6 +191,14 @@ int nep_get_stats(nep_handle *h, nep_stats *out);
  * for the most recent call, the device time in ms of each kernel slot (names via
  * nep_kernel_name; slots that did not run report 0). */
 int nep_set_profiling(nep_handle *h, int enable);
+
+/* Arithmetic of the network (Eq. Ui) and its gradient dU/dq:
+ *   0 (default) FP32 on the FMA pipes;
+ *   1 BF16 operands on the tensor cores (tcgen05.mma, FP32 accumulation in tensor memory):
+ *     descriptor -> hidden and hidden -> dU/dq as two GEMMs per 128-atom tile. Descriptors,
+ *     partial forces and all accumulations stay FP32; integration and totals FP64.
+ * Applies to nep_compute and md_run (nep_descriptors has no network). */
+int nep_set_precision(nep_handle *h, int mode);
 
 /* How md_run captures the neighbour rebuild in its step graph: 1 (default) = inside a
  * conditional graph node that runs only when a rebuild is due; 0 = as ordinary kernel

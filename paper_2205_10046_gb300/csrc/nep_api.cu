@@ -258,6 +258,9 @@ struct nep_handle {
   cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
   int rebuild_kernels = 0;  // kernels in the conditional rebuild body of the step graph
   bool graph_cond = true;   // rebuild inside a conditional node (else early-exit kernel nodes)
+  int precision = 0;        // network arithmetic: 0 FP32 SIMT, 1 BF16 tensor cores
+  int graph_prec = 0;
+  DevBuf<uint4> d_tc;       // BF16 W0 operand tiles for the tensor-core network
   bool graph_cond_used = true;
   // profiling
   bool prof = false;
@@ -457,6 +460,10 @@ AtomArgs make_args(nep_handle *h, int N) {
   a.mass_kappa_half = h->d_mk_half.p;
   a.vel = h->v.p;
   a.perm = h->perm.p;
+  a.precision = h->precision;
+  a.tc_b1 = h->d_tc.p;
+  a.tc_b2 = h->d_tc.p ? h->d_tc.p + (size_t)h->ops->np1 * h->ops->kp1 * 2 / 16 : nullptr;
+  a.tc_err = h->status.p ? &h->status.p->tc_timeout : nullptr;
   return a;
 }
 
@@ -595,7 +602,7 @@ int nep_destroy(nep_handle *h) {
   h->types.release(); h->cell_of.release(); h->cell_count.release(); h->cell_cursor.release();
   h->cell_start.release(); h->cell_atoms.release(); h->nn_r.release(); h->nn_a.release(); h->rev_a.release();
   h->thermo_ctl.release(); h->nl_r.release(); h->nl_a.release(); h->pos4.release(); h->dtab.release();
-  h->p_ang.release(); h->e_rad.release(); h->status.release();
+  h->p_ang.release(); h->e_rad.release(); h->status.release(); h->d_tc.release();
   delete h;
   return NEP_OK;
 }
@@ -828,7 +835,7 @@ int md_queue(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double 
   // (re)capture the one-step graph when the step size, the profiling mode or the thermo
   // staging buffer changed
   if (!h->graph || h->graph_dt != dt_fs || h->graph_prof != h->prof || h->graph_thermo != h->thermo_stage.p ||
-      h->graph_cond_used != h->graph_cond) {
+      h->graph_cond_used != h->graph_cond || h->graph_prec != h->precision) {
     if (h->graph) {
       cudaGraphExecDestroy(h->graph);
       h->graph = nullptr;
@@ -860,6 +867,7 @@ int md_queue(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double 
     h->graph_prof = h->prof;
     h->graph_thermo = h->thermo_stage.p;
     h->graph_cond_used = h->graph_cond;
+    h->graph_prec = h->precision;
   }
   for (int st = 0; st < n_steps; ++st) CK(cudaGraphLaunch(h->graph, s), "graph launch");
   if (thermo && rows > 0)
@@ -873,6 +881,7 @@ int md_status(nep_handle *h, nep_stream_t stream) {
   if (!h->md_ready) return fail(h, NEP_ERR_STATE, "no MD state");
   int rc = read_status(h, (cudaStream_t)stream);
   if (rc) return rc;
+  if (h->h_status->tc_timeout) return fail(h, NEP_ERR_TIMEOUT, "a tensor-core completion wait ran out");
   if (h->h_status->overflow || h->h_status->rev_missing) {
     h->md_ready = false;
     return fail(h, NEP_ERR_NEIGHBOR_OVERFLOW, "neighbour list overflow during md_run; call md_init again");
@@ -1004,6 +1013,37 @@ int nep_get_stats(nep_handle *h, nep_stats *out) {
 int nep_set_profiling(nep_handle *h, int enable) {
   if (!valid_handle(h)) return NEP_ERR_ARG;
   h->prof = enable != 0;
+  return NEP_OK;
+}
+
+// BF16 (round to nearest even) of a float, as raw bits.
+static uint16_t to_bf16(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+int nep_set_precision(nep_handle *h, int mode) {
+  if (!valid_handle(h)) return NEP_ERR_ARG;
+  if (mode != 0 && mode != 1) return fail(h, NEP_ERR_ARG, "precision must be 0 (FP32) or 1 (BF16 tensor cores)");
+  if (mode == 1 && !h->d_tc.p) {
+    // W0 as the two GEMM operands, K-major no-swizzle UMMA layout, zero padded:
+    //   B1 [NP1 x KP1]: (mu, nu) -> w0[mu][nu];  B2 [KP1 x NP1]: (nu, mu) -> w0[mu][nu]
+    const int KP1 = h->ops->kp1, NP1 = h->ops->np1, D = h->n_des, H = h->H;
+    std::vector<uint16_t> t(2 * (size_t)NP1 * KP1, 0);
+    auto off = [](int r, int k, int KC) { return ((r / 8) * KC + k / 8) * 64 + (r % 8) * 8 + (k % 8); };
+    uint16_t *b1 = t.data(), *b2 = t.data() + (size_t)NP1 * KP1;
+    for (int mu = 0; mu < H; ++mu)
+      for (int nu = 0; nu < D; ++nu) {
+        const uint16_t v = to_bf16(h->w0[(size_t)mu * D + nu]);
+        b1[off(mu, nu, KP1 / 8)] = v;
+        b2[off(nu, mu, NP1 / 8)] = v;
+      }
+    CK(h->d_tc.ensure(t.size() * 2 / 16), "alloc tiles");
+    CK(cudaMemcpy(h->d_tc.p, t.data(), t.size() * 2, cudaMemcpyHostToDevice), "copy tiles");
+  }
+  h->precision = mode;
   return NEP_OK;
 }
 

@@ -57,6 +57,7 @@ struct BuildStatus {
   unsigned long long in_r, in_a;    // entries with r < r_c (at build time)
   int rebuild;         // a rebuild is pending (set by the drift kernel or the host)
   int bad_input;       // bit 0: type out of range, bit 1: non-finite position
+  int tc_timeout;      // a tensor-core completion wait ran out (results invalid)
   long long n_rebuilds;
   long long md_steps;
 };
@@ -106,6 +107,11 @@ struct AtomArgs {
   const double *inv_mass_kappa;  // [T] 1 / (m * 103.64...) for a = F * that
   const double *mass_kappa_half; // [T] m * 103.64... / 2 for kinetic energy
   double *vel;             // [N][3]
+  // tensor-core network (precision 1): W0 operand tiles in the UMMA layout, error flag
+  int precision;           // 0: FP32 network on the FMA pipes; 1: BF16 tensor-core network
+  const uint4 *tc_b1;      // GEMM1 operand W0 [NP1 x KP1] (bf16)
+  const uint4 *tc_b2;      // GEMM2 operand W0^T [NP2 x KP2] (bf16)
+  int *tc_err;             // set when a tensor-core wait ran out
 };
 
 // Model constants of one handle, FP32.
@@ -119,6 +125,7 @@ struct ModelF {
 struct ShapeOps {
   int nR, KR, nA, KA, H, L3, L4, L5;
   int n_des;
+  int kp1, np1;  // tensor-core network tile shapes (K of GEMM1, N of GEMM1)
   cudaError_t (*atom)(const AtomArgs &, const ModelF &, const float *w0, const float *b0, const float *w1,
                       float b1, int descriptor_only, cudaStream_t s);
   cudaError_t (*gather)(const AtomArgs &, cudaStream_t s);

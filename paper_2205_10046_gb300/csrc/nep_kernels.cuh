@@ -22,6 +22,8 @@
 //     FP64 arithmetic (slow on GB300) runs in the pair loops;
 //   * S_nk wait in shared memory while the network runs, to bound register pressure.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "nep_internal.cuh"
 
 namespace nep {
@@ -41,6 +43,18 @@ struct Shape {
   // pass, so that at most ~4 x 24 accumulators are live at once
   static constexpr int NPASS = ((NA + 1) * NK > 144) ? ((NA + 1) + 3) / 4 : 1;
   static constexpr int NCH = ((NA + 1) + NPASS - 1) / NPASS;
+  // tensor-core network (BF16 operands, FP32 accumulation in TMEM), one 128-atom tile:
+  //   GEMM1 z[128 x NP1] = q[128 x KP1] . W0[NP1 x KP1]^T,  GEMM2 dq[128 x NP2] = beta[128 x KP2] . W0^T
+  static constexpr int KP1 = (NDES + 15) / 16 * 16;
+  static constexpr int NP1 = (H + 15) / 16 * 16;
+  static constexpr int KP2 = NP1, NP2 = KP1;
+  static constexpr int NS = (NA + 1) * NK;               // TMEM columns holding S_nk
+  static constexpr int DCOL = (NS + 15) / 16 * 16;       // TMEM column of the GEMM results
+  static constexpr int TMEM_COLS = 256;
+  static constexpr int TILE_A = kAtomBlock * (KP1 > KP2 ? KP1 : KP2) * 2;  // bytes
+  static constexpr int TILE_B = NP1 * KP1 * 2;                             // each of B1, B2
+  static_assert(DCOL + (NP1 > NP2 ? NP1 : NP2) <= TMEM_COLS, "S and the network results must fit 256 TMEM columns");
+  static_assert(NP1 <= 256 && NP2 <= 256, "UMMA N limit");
 };
 
 template <class S>
@@ -126,6 +140,76 @@ __device__ __forceinline__ void static_for(F &&f) {
     f(std::integral_constant<int, I>{});
     static_for<I + 1, N>(f);
   }
+}
+
+// ------------------------------------------------------------------ tcgen05 / mbarrier
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor, no swizzle: start address, LBO (next 8x16-byte core matrix
+// along K), SBO (next core matrix along M/N), version bit.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M x N.
+template <int M, int N>
+__host__ __device__ constexpr uint32_t umma_idesc_bf16() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(mbar))
+               : "memory");
+}
+
+// Wait for an mbarrier phase with an iteration limit; returns false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 24) && !done; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(smem_addr(mbar)), "r"(parity)
+        : "memory");
+  }
+  return done != 0;
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float *v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+               "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+               "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+               "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+               : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t *>(&b);
+}
+
+// Byte offset of element (row r, k) in a K-major no-swizzle operand tile with KC = K/8
+// 16-byte chunks per row group: core matrix (r/8, k/8) at ((r/8) KC + k/8) * 128.
+__host__ __device__ constexpr int umma_off(int r, int k, int KC) {
+  return ((r / 8) * KC + k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2;
 }
 
 // f_k(r) = (T_k(x) + 1) fc/2 with fc = (1 + cos(pi r/rc))/2 and x = 2(r/rc - 1)^2 - 1
@@ -239,24 +323,29 @@ __device__ __forceinline__ void for_pairs_plain(const unsigned *__restrict__ nl,
 }
 
 // ------------------------------------------------------------------------ per-atom kernel
-template <class S, bool DESC_ONLY>
+template <class S, bool DESC_ONLY, int PREC>
 __global__ void __launch_bounds__(kAtomBlock, 1)
     atom_kernel(const AtomArgs a, const __grid_constant__ AnnConst<S> w) {
+  static_assert(PREC == 0 || !DESC_ONLY, "the descriptor-only kernel has no network");
   constexpr int NR = S::NR, KR = S::KR, NA = S::NA, KA = S::KA, NK = S::NK, NDES = S::NDES;
   extern __shared__ float4 smem4[];
   const int T = a.T;
   constexpr int NDP = S::NDP;
   float4 *dtab_s = smem4;                                        // [ncode]
-  float *w0_s = reinterpret_cast<float *>(smem4 + a.ncode);      // [H][NDP]
-  float *b0_s = w0_s + S::H * NDP;                               // [H]
+  float *w0_s = reinterpret_cast<float *>(smem4 + a.ncode);      // [H][NDP] (FP32 network only)
+  float *b0_s = w0_s + (PREC == 0 ? S::H * NDP : 0);             // [H]
   float *w1_s = b0_s + S::H;                                     // [H]
   float *cR_s = w1_s + S::H;                                     // [T][T][NR+1][KR+1]
   float *cA_s = cR_s + T * T * (NR + 1) * (KR + 1);              // [T][T][NA+1][KA+1]
-  float *S_s = cA_s + T * T * (NA + 1) * (KA + 1);               // [NA+1][NK][block]
+  // [NA+1][NK][block]: S_nk while the FP32 network runs, then dU/dS_nk. For the tensor-core
+  // network S_nk waits in TMEM instead and this region first holds the BF16 operand tiles.
+  float *S_s = cA_s + T * T * (NA + 1) * (KA + 1);
   for (int v = threadIdx.x; v < a.ncode; v += blockDim.x) dtab_s[v] = a.dtab[v];
-  for (int v = threadIdx.x; v < S::H * NDP; v += blockDim.x) {
-    const int mu = v / NDP, c = v - mu * NDP;
-    w0_s[v] = c < NDES ? w.w0[mu * NDES + c] : 0.f;
+  if constexpr (PREC == 0) {
+    for (int v = threadIdx.x; v < S::H * NDP; v += blockDim.x) {
+      const int mu = v / NDP, c = v - mu * NDP;
+      w0_s[v] = c < NDES ? w.w0[mu * NDES + c] : 0.f;
+    }
   }
   for (int v = threadIdx.x; v < S::H; v += blockDim.x) {
     b0_s[v] = w.b0[v];
@@ -264,13 +353,46 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
   }
   for (int v = threadIdx.x; v < T * T * (NR + 1) * (KR + 1); v += blockDim.x) cR_s[v] = a.c_r[v];
   for (int v = threadIdx.x; v < T * T * (NA + 1) * (KA + 1); v += blockDim.x) cA_s[v] = a.c_a[v];
+  // tensor-core network: operand tiles (128-byte aligned) and TMEM for S_nk and the results
+  __shared__ __align__(8) uint64_t tc_mbar;
+  __shared__ uint32_t tc_tmem;
+  unsigned char *tileA = nullptr, *tileB1 = nullptr, *tileB2 = nullptr;
+  if constexpr (PREC == 1) {
+    unsigned char *base = reinterpret_cast<unsigned char *>(S_s);
+    base += (128u - (smem_addr(base) & 127u)) & 127u;
+    tileA = base;
+    tileB1 = tileA + S::TILE_A;
+    tileB2 = tileB1 + S::TILE_B;
+    for (int v = threadIdx.x; v < S::TILE_B / 16; v += blockDim.x) {
+      reinterpret_cast<uint4 *>(tileB1)[v] = a.tc_b1[v];
+      reinterpret_cast<uint4 *>(tileB2)[v] = a.tc_b2[v];
+    }
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&tc_mbar)));
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x < 32) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tc_tmem)),
+                   "r"(S::TMEM_COLS));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
   __syncthreads();
+  uint32_t tmem_row = 0;  // TMEM address of this warp's 32 lanes, column 0
+  if constexpr (PREC == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tmem_row = tc_tmem + ((uint32_t)((threadIdx.x >> 5) * 32) << 16);
+  }
 
   const int N = a.N;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // Threads past the last atom run the same code with no neighbours (the tensor-core steps
+  // are block- and warp-collective); they write nothing.
+  const bool active = i < N;
   double Ublock = 0.0;
-  if (i < N) {
-    const float4 pi = a.pos4[i];
+  {
+    const float4 pi = active ? a.pos4[i] : make_float4(0.f, 0.f, 0.f, __int_as_float(0));
     const int ti = type_of(pi);
     const float inv_rcR = 1.f / a.rcR, inv_rcA = 1.f / a.rcA;
     const float rcR2 = a.rcR * a.rcR, rcA2 = a.rcA * a.rcA;
@@ -282,7 +404,7 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
     // ---- radial descriptor, Eq. qin: per neighbour type, F^t_k = sum_j f_k(r_ij)
     int base = 0;
     for (int t = 0; t < T; ++t) {
-      const int cnt = a.nn_r[t * N + i];
+      const int cnt = active ? a.nn_r[t * N + i] : 0;
       float Fk[KR + 1];
 #pragma unroll
       for (int k = 0; k <= KR; ++k) Fk[k] = 0.f;
@@ -309,7 +431,7 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
 
     // ---- angular sums S_nk (Eq. S_nk, b_k(d) r^-l) and the angular descriptor components
     // (Sec. II D), one chunk of n per pass over the angular neighbours
-    const int na = a.nn_a[i];
+    const int na = active ? a.nn_a[i] : 0;
     static_for<0, S::NPASS>([&](auto pc) {
       constexpr int n0 = decltype(pc)::value * S::NCH;
       constexpr int n1 = (n0 + S::NCH < NA + 1) ? n0 + S::NCH : NA + 1;
@@ -367,54 +489,141 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
           const float s0 = Sv[c][0], s12 = Sv[c][1] * Sv[c][1] + Sv[c][2] * Sv[c][2];
           q[S::OFF5 + n] = w.m.c5b[0] * s0 * s0 * s0 * s0 + w.m.c5b[1] * s0 * s0 * s12 + w.m.c5b[2] * s12 * s12;
         }
-        if constexpr (!DESC_ONLY) {
+        if constexpr (!DESC_ONLY && PREC == 0) {
           // park S_n in shared memory while the network runs ([n][k][thread]: conflict-free)
 #pragma unroll
           for (int k = 0; k < NK; ++k) S_s[(n * NK + k) * kAtomBlock + threadIdx.x] = Sv[c][k];
+        }
+        if constexpr (PREC == 1) {
+          // park S_n in this thread's TMEM lane, columns n NK .. n NK + NK - 1
+          __syncwarp();
+#pragma unroll
+          for (int k8 = 0; k8 < NK / 8; ++k8) tmem_st8(tmem_row + n * NK + 8 * k8, &Sv[c][8 * k8]);
         }
       }
     });
 
     if constexpr (DESC_ONLY) {
-      const size_t io = a.perm ? (size_t)a.perm[i] : (size_t)i;
+      if (active) {
+        const size_t io = a.perm ? (size_t)a.perm[i] : (size_t)i;
 #pragma unroll
-      for (int v = 0; v < NDES; ++v) a.q_out[io * NDES + v] = (double)q[v];
+        for (int v = 0; v < NDES; ++v) a.q_out[io * NDES + v] = (double)q[v];
+      }
     } else {
       float *Sme = S_s + threadIdx.x;
 
-      // ---- network, Eq. Ui, and dU/dq (weights broadcast from shared memory)
+      // ---- network, Eq. Ui, and dU/dq
       float U = 0.f;
       float dq[NDES];
 #pragma unroll
       for (int v = 0; v < NDES; ++v) dq[v] = 0.f;
-#pragma unroll 1
-      for (int mu = 0; mu < S::H; ++mu) {
-        const float4 *row = reinterpret_cast<const float4 *>(w0_s + mu * NDP);
-        float zp[4] = {-b0_s[mu], 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int v4 = 0; v4 < NDP / 4; ++v4) {
-          const float4 wv = row[v4];
-          const float wc[4] = {wv.x, wv.y, wv.z, wv.w};
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-            if (4 * v4 + c < NDES) zp[c] = __fmaf_rn(wc[c], q[4 * v4 + c], zp[c]);
+      if constexpr (PREC == 0) {
+        // FP32 on the FMA pipes, weights broadcast from shared memory
+  #pragma unroll 1
+        for (int mu = 0; mu < S::H; ++mu) {
+          const float4 *row = reinterpret_cast<const float4 *>(w0_s + mu * NDP);
+          float zp[4] = {-b0_s[mu], 0.f, 0.f, 0.f};
+  #pragma unroll
+          for (int v4 = 0; v4 < NDP / 4; ++v4) {
+            const float4 wv = row[v4];
+            const float wc[4] = {wv.x, wv.y, wv.z, wv.w};
+  #pragma unroll
+            for (int c = 0; c < 4; ++c)
+              if (4 * v4 + c < NDES) zp[c] = __fmaf_rn(wc[c], q[4 * v4 + c], zp[c]);
+          }
+          const float h = tanhf((zp[0] + zp[1]) + (zp[2] + zp[3]));
+          const float w1m = w1_s[mu];
+          U = __fmaf_rn(w1m, h, U);
+          const float beta = w1m * (1.f - h * h);
+  #pragma unroll
+          for (int v4 = 0; v4 < NDP / 4; ++v4) {
+            const float4 wv = row[v4];
+            const float wc[4] = {wv.x, wv.y, wv.z, wv.w};
+  #pragma unroll
+            for (int c = 0; c < 4; ++c)
+              if (4 * v4 + c < NDES) dq[4 * v4 + c] = __fmaf_rn(beta, wc[c], dq[4 * v4 + c]);
+          }
         }
-        const float h = tanhf((zp[0] + zp[1]) + (zp[2] + zp[3]));
-        const float w1m = w1_s[mu];
-        U = __fmaf_rn(w1m, h, U);
-        const float beta = w1m * (1.f - h * h);
+      } else {
+        // BF16 tensor cores (tcgen05), FP32 accumulation in TMEM, one 128-atom tile per block
+        static_assert(NK % 8 == 0, "S_nk is moved in groups of 8 TMEM columns");
+        constexpr int KC1 = S::KP1 / 8, KC2 = S::KP2 / 8;
+        const int r = threadIdx.x;
+        // q row -> operand tile A (bf16, K-major)
 #pragma unroll
-        for (int v4 = 0; v4 < NDP / 4; ++v4) {
-          const float4 wv = row[v4];
-          const float wc[4] = {wv.x, wv.y, wv.z, wv.w};
+        for (int kc = 0; kc < KC1; ++kc) {
+          uint32_t pk[4];
 #pragma unroll
-          for (int c = 0; c < 4; ++c)
-            if (4 * v4 + c < NDES) dq[4 * v4 + c] = __fmaf_rn(beta, wc[c], dq[4 * v4 + c]);
+          for (int h2 = 0; h2 < 4; ++h2) {
+            const int k0 = 8 * kc + 2 * h2;
+            pk[h2] = pack_bf16x2(k0 < NDES ? q[k0] : 0.f, k0 + 1 < NDES ? q[k0 + 1] : 0.f);
+          }
+          *reinterpret_cast<uint4 *>(tileA + umma_off(r, 8 * kc, KC1)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (threadIdx.x == 0) {  // GEMM1: z = q . W0^T into TMEM columns DCOL ..
+          constexpr uint32_t idesc = umma_idesc_bf16<kAtomBlock, S::NP1>();
+#pragma unroll
+          for (int st = 0; st < S::KP1 / 16; ++st)
+            umma_bf16(tc_tmem + S::DCOL, umma_desc(smem_addr(tileA) + 256 * st, 128, KC1 * 128),
+                      umma_desc(smem_addr(tileB1) + 256 * st, 128, KC1 * 128), idesc, st > 0 ? 1u : 0u);
+          umma_commit(&tc_mbar);
+        }
+        __syncwarp();
+        if (!mbar_wait(&tc_mbar, 0)) atomicOr(a.tc_err, 1);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // tanh layer from this row of z; beta = w1 (1 - h^2) -> operand tile A (reused)
+#pragma unroll
+        for (int c8 = 0; c8 < S::NP1 / 8; ++c8) {
+          float z[8];
+          tmem_ld8(tmem_row + S::DCOL + 8 * c8, z);
+          float bt[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int mu = 8 * c8 + j;
+            bt[j] = 0.f;
+            if (mu < S::H) {
+              const float h = tanhf(z[j] - b0_s[mu]);
+              U = __fmaf_rn(w1_s[mu], h, U);
+              bt[j] = w1_s[mu] * (1.f - h * h);
+            }
+          }
+          *reinterpret_cast<uint4 *>(tileA + umma_off(r, 8 * c8, KC2)) =
+              make_uint4(pack_bf16x2(bt[0], bt[1]), pack_bf16x2(bt[2], bt[3]), pack_bf16x2(bt[4], bt[5]),
+                         pack_bf16x2(bt[6], bt[7]));
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (threadIdx.x == 0) {  // GEMM2: dq = beta . W0 into the same TMEM columns
+          constexpr uint32_t idesc = umma_idesc_bf16<kAtomBlock, S::NP2>();
+#pragma unroll
+          for (int st = 0; st < S::KP2 / 16; ++st)
+            umma_bf16(tc_tmem + S::DCOL, umma_desc(smem_addr(tileA) + 256 * st, 128, KC2 * 128),
+                      umma_desc(smem_addr(tileB2) + 256 * st, 128, KC2 * 128), idesc, st > 0 ? 1u : 0u);
+          umma_commit(&tc_mbar);
+        }
+        __syncwarp();
+        if (!mbar_wait(&tc_mbar, 1)) atomicOr(a.tc_err, 1);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int c8 = 0; c8 < S::NP2 / 8; ++c8) {
+          float v[8];
+          tmem_ld8(tmem_row + S::DCOL + 8 * c8, v);
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (8 * c8 + j < NDES) dq[8 * c8 + j] = v[j];
         }
       }
       U -= w.b1;
-      if (a.energy) a.energy[a.perm ? a.perm[i] : i] = (double)U;
-      Ublock = (double)U;
+      if (active) {
+        if (a.energy) a.energy[a.perm ? a.perm[i] : i] = (double)U;
+        Ublock = (double)U;
+      }
 
       // ---- radial force coefficients e^t_k = sum_n dU/dq_n c^{t_i t}_{nk} and their sum
       for (int t = 0; t < T; ++t) {
@@ -432,18 +641,26 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
         ev[KR + 1] = tot;
 #pragma unroll
         for (int k = KR + 2; k < S::EST; ++k) ev[k] = 0.f;
-        float4 *dst = reinterpret_cast<float4 *>(a.e_rad + ((size_t)i * T + t) * S::EST);
+        if (active) {
+          float4 *dst = reinterpret_cast<float4 *>(a.e_rad + ((size_t)i * T + t) * S::EST);
 #pragma unroll
-        for (int k4 = 0; k4 < S::EST / 4; ++k4)
-          dst[k4] = make_float4(ev[4 * k4], ev[4 * k4 + 1], ev[4 * k4 + 2], ev[4 * k4 + 3]);
+          for (int k4 = 0; k4 < S::EST / 4; ++k4)
+            dst[k4] = make_float4(ev[4 * k4], ev[4 * k4 + 1], ev[4 * k4 + 2], ev[4 * k4 + 3]);
+        }
       }
 
       // ---- dU/dS_nk from the explicit 3/4/5-body forms, written over S in shared memory
 #pragma unroll
       for (int n = 0; n <= NA; ++n) {
         float s[NK], dS[NK];
+        if constexpr (PREC == 0) {
 #pragma unroll
-        for (int k = 0; k < NK; ++k) s[k] = Sme[(n * NK + k) * kAtomBlock];
+          for (int k = 0; k < NK; ++k) s[k] = Sme[(n * NK + k) * kAtomBlock];
+        } else {
+          __syncwarp();
+#pragma unroll
+          for (int k8 = 0; k8 < NK / 8; ++k8) tmem_ld8(tmem_row + n * NK + 8 * k8, &s[8 * k8]);
+        }
 #pragma unroll
         for (int k = 0; k < NK; ++k) {
           if (k < S::KEND3) {
@@ -540,6 +757,14 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
       double s = 0.0;
       for (int wv = 0; wv < kAtomBlock / 32; ++wv) s += red[wv];
       a.partial_atom[blockIdx.x] = s;
+    }
+  }
+  if constexpr (PREC == 1) {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc_tmem), "r"(S::TMEM_COLS));
     }
   }
 }
@@ -706,10 +931,17 @@ __global__ void __launch_bounds__(kGatherBlock)
 
 // ------------------------------------------------------------------------ launchers
 template <class S>
-size_t atom_smem_bytes(int T, int ncode) {
-  return sizeof(float4) * ncode +
-         sizeof(float) * (S::H * S::NDP + 2 * S::H + T * T * (S::NR + 1) * (S::KR + 1) +
-                          T * T * (S::NA + 1) * (S::KA + 1) + (S::NA + 1) * S::NK * kAtomBlock);
+size_t atom_smem_bytes(int T, int ncode, int prec) {
+  static_assert((size_t)(S::NA + 1) * S::NK * kAtomBlock * 4 >= (size_t)S::TILE_A + 2 * S::TILE_B + 128,
+                "the S region must hold the tensor-core operand tiles");
+  size_t b = sizeof(float4) * ncode +
+             sizeof(float) * ((prec == 0 ? S::H * S::NDP : 0) + 2 * S::H + T * T * (S::NR + 1) * (S::KR + 1) +
+                              T * T * (S::NA + 1) * (S::KA + 1) + (S::NA + 1) * S::NK * kAtomBlock);
+  // the tensor-core kernel holds 256 of the SM's 512 TMEM columns: keep at most two blocks
+  // per SM (a third would wait in tcgen05.alloc) by asking for more than a third of the
+  // 228 KB of shared memory
+  if (prec == 1 && b < 80 * 1024) b = 80 * 1024;
+  return b;
 }
 
 template <class S>
@@ -725,19 +957,16 @@ cudaError_t launch_atom(const AtomArgs &a, const ModelF &mf, const float *w0, co
   w.b1 = b1;
   w.m = mf;
   const int blocks = (a.N + kAtomBlock - 1) / kAtomBlock;
-  const size_t smem = atom_smem_bytes<S>(a.T, a.ncode);
-  if (descriptor_only) {
-    auto k = atom_kernel<S, true>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = atom_smem_bytes<S>(a.T, a.ncode, descriptor_only ? 0 : a.precision);
+  auto go = [&](auto kern) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<blocks, kAtomBlock, smem, st>>>(a, w);
-  } else {
-    auto k = atom_kernel<S, false>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k<<<blocks, kAtomBlock, smem, st>>>(a, w);
-  }
-  return cudaGetLastError();
+    kern<<<blocks, kAtomBlock, smem, st>>>(a, w);
+    return cudaGetLastError();
+  };
+  if (descriptor_only) return go(atom_kernel<S, true, 0>);
+  if (a.precision == 1) return go(atom_kernel<S, false, 1>);
+  return go(atom_kernel<S, false, 0>);
 }
 
 template <class S>
@@ -756,6 +985,7 @@ ShapeOps make_ops() {
   ShapeOps o;
   o.nR = S::NR; o.KR = S::KR; o.nA = S::NA; o.KA = S::KA; o.H = S::H;
   o.L3 = S::L3; o.L4 = S::L4; o.L5 = S::L5; o.n_des = S::NDES;
+  o.kp1 = S::KP1; o.np1 = S::NP1;
   o.atom = &launch_atom<S>;
   o.gather = &launch_gather<S>;
   o.atom_blocks = &atom_blocks<S>;

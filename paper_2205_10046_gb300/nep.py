@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libnep.so")
 
 NEP_OK = 0
 ERRORS = {-1: "NEP_ERR_ARG", -2: "NEP_ERR_OOM", -3: "NEP_ERR_CUDA", -4: "NEP_ERR_NEIGHBOR_OVERFLOW",
-          -5: "NEP_ERR_NONFINITE", -6: "NEP_ERR_UNSUPPORTED", -7: "NEP_ERR_STATE"}
+          -5: "NEP_ERR_NONFINITE", -6: "NEP_ERR_UNSUPPORTED", -7: "NEP_ERR_STATE", -8: "NEP_ERR_TIMEOUT"}
 
 
 class NepError(RuntimeError):
@@ -67,6 +67,7 @@ _SIGS = {
     "nep_get_stats": (C.c_int, [_P, C.POINTER(nep_stats)]),
     "nep_set_profiling": (C.c_int, [_P, C.c_int]),
     "nep_set_graph_conditional": (C.c_int, [_P, C.c_int]),
+    "nep_set_precision": (C.c_int, [_P, C.c_int]),
     "nep_kernel_slots": (C.c_int, []),
     "nep_kernel_name": (C.c_char_p, [C.c_int]),
     "nep_kernel_times": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int]),
@@ -278,6 +279,11 @@ def nep_set_profiling(h, enable: bool):
     _check(load().nep_set_profiling(h, 1 if enable else 0), h)
 
 
+def nep_set_precision(h, mode: int):
+    """0: FP32 network on the FMA pipes; 1: BF16 tensor-core network (tcgen05)."""
+    _check(load().nep_set_precision(h, int(mode)), h)
+
+
 def nep_set_graph_conditional(h, enable: bool):
     _check(load().nep_set_graph_conditional(h, 1 if enable else 0), h)
 
@@ -293,9 +299,11 @@ def nep_kernel_times(h) -> dict:
 class NEP:
     """Convenience owner of one handle (destroyed with the object)."""
 
-    def __init__(self, model, skin: float = 1.0):
+    def __init__(self, model, skin: float = 1.0, precision: int = 0):
         self.model = model
         self.h = nep_create(model, skin)
+        if precision:
+            nep_set_precision(self.h, precision)
 
     def close(self):
         if self.h:
