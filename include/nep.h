@@ -124,6 +124,22 @@ int nep_compute_host(nep_handle *h, int n_atoms, const double *pos, const int *t
                      double *energy, double *energy_total, double *force, double *virial,
                      double *virial_total);
 
+/* Many independent periodic structures in one evaluation (batched form of nep_compute; the
+ * training set of Sec. III is such a batch, evaluated for every candidate of Eq. loss).
+ * Structure s owns atoms [offsets[s], offsets[s+1]) of the concatenated arrays and the cell
+ * rows boxes[s][3][3]; thin cells are handled with all their periodic images (up to 3 cell
+ * lengths per axis: an image range above that returns NEP_ERR_UNSUPPORTED naming the
+ * structure). offsets [n_struct+1] (offsets[0] = 0, non-decreasing) and boxes [n_struct][9]
+ * are HOST pointers; the rest are DEVICE pointers, N = offsets[n_struct]: pos [N][3],
+ * types [N]; outputs energy [N] (or NULL), energy_struct [n_struct] (or NULL: E_s = sum of
+ * U_i over the structure), force [N][3] (required), virial [N][9] (or NULL), virial_struct
+ * [n_struct][9] (or NULL: sum of W_i). Empty structures are allowed (zero sums). The grids of
+ * the last layout (offsets and boxes) are kept and reused while it repeats. Synchronises
+ * `stream` to size the neighbour lists, like nep_compute; errors as nep_compute. */
+int nep_compute_batch(nep_handle *h, int n_struct, const int *offsets, const double *pos, const int *types,
+                      const double *boxes, double *energy, double *energy_struct, double *force,
+                      double *virial, double *virial_struct, nep_stream_t stream);
+
 /* Descriptor vectors q^i (Eqs. qin and S_nk with the explicit components of Sec. II D)
  * into q [N][N_des] FP64 (DEVICE pointers, as nep_compute). */
 int nep_descriptors(nep_handle *h, int n_atoms, const double *pos, const int *types, const double *box,

@@ -17,10 +17,13 @@ OUT = os.path.join(HERE, "libnep.so")
 BUILD = os.path.join(ROOT, "_build", "libnep")
 
 SOURCES = ["nep_api.cu", "nep_build.cu", "nep_static.cu", "nep_shape_si.cu", "nep_shape_pbte.cu",
-           "nep_shape_mixed.cu"]
+           "nep_shape_mixed.cu", "nep_batch_si.cu", "nep_batch_pbte.cu", "nep_batch_mixed.cu"]
 HEADERS = ["nep_internal.cuh", "nep_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+# host code is compiled without FMA contraction, so host-side geometry (image shift tables)
+# rounds the same on x86-64 and aarch64 hosts and equals the device's explicitly rounded form
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+         "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]
 
 

@@ -13,15 +13,9 @@
 #include "nep_internal.cuh"
 
 namespace nep {
-cudaError_t launch_rebuild(int N, int T, const Grid &g, const float4 *dtab, float rlR2, float rlA2, float rcR2,
-                           float rcA2, const AtomState &a, const ListBufs &L, int count_only, BuildStatus *st,
-                           cudaStream_t s);
-void launch_iota(int N, int *perm, cudaStream_t s);
 void launch_rebuild_condition(cudaGraphConditionalHandle hc, const BuildStatus *st, cudaStream_t s);
 void launch_drift(int N, const AtomState &a, const double *inv_mass_kappa, double dt, double half_skin2,
                   BuildStatus *st, cudaStream_t s);
-void launch_export(int N, const AtomState &a, const Grid &g, double *pos, double *vel, double *force,
-                   cudaStream_t s);
 void launch_finalize(int nb_atom, const double *partial_atom, int nb_gather, const double *partial_gather,
                      double *energy_total, double *virial_total, double *thermo_stage, int *thermo_ctl, int N,
                      double volume, cudaStream_t s);
@@ -66,9 +60,12 @@ void model_constants(ModelF &m) {
   m.c5b[2] = (float)(21.0 / (80.0 * p * p));
 }
 
-// Cell grid, image range and shift table (dtab[0..ncode), at most 512 entries) for the cell
-// rows `box` and the list radius rl. Returns NEP_OK or an error code with *err set.
+// Cell grid, image range and shift table (dtab[0..ncode), at most 512 entries; skipped when
+// dtab is null) for the cell rows `box` and the list radius rl. Returns NEP_OK or an error
+// code with *err set.
 int build_grid(const double *box, double rl, int N, Grid &g, float4 *dtab, double *volume, const char **err) {
+  g.cell_off = 0;
+  g.dtab_off = 0;
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) g.H[a][b] = box[3 * a + b];
   double cof[3][3];
@@ -128,6 +125,7 @@ int build_grid(const double *box, double rl, int N, Grid &g, float4 *dtab, doubl
   g.ncode = 1 << (3 * g.obits);
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) g.Hc[a][b] = g.H[a][b] / g.nc[a];
+  if (!dtab) return NEP_OK;
   for (int c = 0; c < g.ncode; ++c) dtab[c] = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int ox = -g.R[0]; ox <= g.R[0]; ++ox)
     for (int oy = -g.R[1]; oy <= g.R[1]; ++oy)
@@ -262,6 +260,14 @@ struct nep_handle {
   int graph_prec = 0;
   DevBuf<uint4> d_tc;       // BF16 W0 operand tiles for the tensor-core network
   bool graph_cond_used = true;
+  // batches of structures: layout of the last batch (reused while unchanged)
+  int nb_struct = 0;
+  std::vector<int> b_offsets;
+  std::vector<double> b_boxes;
+  std::vector<Grid> b_grids;
+  DevBuf<Grid> d_grids;
+  DevBuf<int> d_sid, d_offsets;
+  DevBuf<double> b_e, b_w;  // caller-order per-atom energies and virials when the caller keeps none
   // profiling
   bool prof = false;
   cudaEvent_t ev[N_SLOTS][2] = {};
@@ -390,7 +396,7 @@ ListBufs list_bufs(nep_handle *h) {
 int round_cap(int m) { return std::min(kListBuf, (2 * m + 16 + 3) / 4 * 4); }
 
 // Bin, size and build the neighbour lists for the positions in h->x (forced rebuild).
-int rebuild_lists(nep_handle *h, int N, cudaStream_t s) {
+int rebuild_lists(nep_handle *h, int N, cudaStream_t s, const Batch &B = Batch{nullptr, nullptr, 0}) {
   Grid &g = h->grid;
   CK(h->cell_count.ensure(g.ncell + 1), "alloc cells");
   CK(h->cell_cursor.ensure(g.ncell + 1), "alloc cells");
@@ -403,7 +409,7 @@ int rebuild_lists(nep_handle *h, int N, cudaStream_t s) {
     reset_status_counts(h);
     h->h_status->rebuild = 1;
     CK(cudaMemcpyAsync(h->status.p, h->h_status, sizeof(BuildStatus), cudaMemcpyHostToDevice, s), "status");
-    CK(launch_rebuild(N, h->T, g, h->dtab.p, rlR * rlR, rlA * rlA, h->rcR2f(), h->rcA2f(), atom_state(h),
+    CK(launch_rebuild(N, h->T, g, B, h->dtab.p, rlR * rlR, rlA * rlA, h->rcR2f(), h->rcA2f(), atom_state(h),
                       list_bufs(h), count_only ? 1 : 0, h->status.p, s),
        "launch rebuild");
     CK(cudaGetLastError(), "launch rebuild");
@@ -509,6 +515,85 @@ int run_forces(nep_handle *h, int N, double *energy, double *force, double *viri
 
 bool valid_handle(const nep_handle *h) { return h && h->ops; }
 
+// Grids of all structures of a batch: each structure has its own cell grid and image
+// range; the cells are numbered structure by structure, the shift tables share one code
+// width (the largest), and list entries one atom-index width (for the whole batch).
+int setup_batch(nep_handle *h, int n_struct, const int *offsets, const double *boxes, int N, cudaStream_t s) {
+  int rc = ensure_atoms(h, N);
+  if (rc) return rc;
+  const bool same = n_struct == h->nb_struct && (int)h->b_offsets.size() == n_struct + 1 &&
+                    std::equal(offsets, offsets + n_struct + 1, h->b_offsets.begin()) &&
+                    std::equal(boxes, boxes + 9 * (size_t)n_struct, h->b_boxes.begin());
+  if (!same) {
+    h->nb_struct = 0;
+    std::vector<Grid> &G = h->b_grids;
+    G.assign(n_struct, Grid{});
+    int obits = 2;
+    for (int k = 0; k < n_struct; ++k) {
+      const char *err = nullptr;
+      double vol = 0;
+      rc = nep::build_grid(boxes + 9 * (size_t)k, h->rcR + h->skin, std::max(offsets[k + 1] - offsets[k], 1), G[k],
+                           nullptr, &vol, &err);
+      if (rc) return fail(h, rc, "structure " + std::to_string(k) + ": " + err);
+      obits = std::max(obits, G[k].obits);
+    }
+    int jb = 1;
+    while ((1LL << jb) < (long long)std::max(N, 2)) ++jb;
+    if (jb + 3 * obits > 32) return fail(h, NEP_ERR_UNSUPPORTED, "too many atoms for the packed neighbour entries");
+    if (n_struct > (1 << 23)) return fail(h, NEP_ERR_UNSUPPORTED, "more than 2^23 structures");
+    const int ncode = 1 << (3 * obits);
+    long long ncell = 0;
+    for (int k = 0; k < n_struct; ++k) {
+      Grid &g = G[k];
+      g.obits = obits;
+      g.ncode = ncode;
+      g.jbits = jb;
+      g.jmask = (jb >= 32) ? 0xffffffffu : ((1u << jb) - 1u);
+      g.cell_off = (int)ncell;
+      g.dtab_off = k * ncode;
+      ncell += g.ncell;
+      if (ncell > (1LL << 30)) return fail(h, NEP_ERR_UNSUPPORTED, "too many cells in the batch");
+    }
+    Grid gg = G[0];  // batch-wide fields: cell count, entry packing
+    gg.ncell = (int)ncell;
+    gg.cell_off = 0;
+    gg.dtab_off = 0;
+    h->grid = gg;
+    CK(h->d_grids.ensure(n_struct), "alloc batch");
+    CK(h->d_offsets.ensure(n_struct + 1), "alloc batch");
+    CK(h->dtab.ensure((size_t)n_struct * ncode), "alloc batch");
+    CK(cudaMemcpyAsync(h->d_grids.p, G.data(), sizeof(Grid) * n_struct, cudaMemcpyHostToDevice, s), "copy grids");
+    CK(cudaMemcpyAsync(h->d_offsets.p, offsets, sizeof(int) * (n_struct + 1), cudaMemcpyHostToDevice, s),
+       "copy offsets");
+    launch_shift_tables(n_struct, h->d_grids.p, ncode, obits, h->dtab.p, s);
+    // the copies above read pageable host memory that changes on the next call
+    CK(cudaStreamSynchronize(s), "batch setup");
+    h->b_offsets.assign(offsets, offsets + n_struct + 1);
+    h->b_boxes.assign(boxes, boxes + 9 * (size_t)n_struct);
+    h->nb_struct = n_struct;
+  }
+  CK(h->d_sid.ensure(std::max(N, 1)), "alloc batch");
+  launch_struct_ids(n_struct, h->d_offsets.p, h->d_sid.p, s);
+  CK(cudaGetLastError(), "batch setup");
+  return NEP_OK;
+}
+
+Batch batch_of(nep_handle *h) {
+  Batch B;
+  B.grids = h->d_grids.p;
+  B.sid = h->d_sid.p;
+  B.n = h->nb_struct;
+  return B;
+}
+
+int check_offsets(nep_handle *h, int n_struct, const int *offsets) {
+  if (n_struct < 0 || !offsets) return fail(h, NEP_ERR_ARG, "n_struct < 0 or offsets is null");
+  if (offsets[0] != 0) return fail(h, NEP_ERR_ARG, "offsets[0] must be 0");
+  for (int k = 0; k < n_struct; ++k)
+    if (offsets[k + 1] < offsets[k]) return fail(h, NEP_ERR_ARG, "offsets must be non-decreasing");
+  return NEP_OK;
+}
+
 }  // namespace
 
 // ======================================================================== C ABI
@@ -603,6 +688,7 @@ int nep_destroy(nep_handle *h) {
   h->cell_start.release(); h->cell_atoms.release(); h->nn_r.release(); h->nn_a.release(); h->rev_a.release();
   h->thermo_ctl.release(); h->nl_r.release(); h->nl_a.release(); h->pos4.release(); h->dtab.release();
   h->p_ang.release(); h->e_rad.release(); h->status.release(); h->d_tc.release();
+  h->d_grids.release(); h->d_sid.release(); h->d_offsets.release(); h->b_e.release(); h->b_w.release();
   delete h;
   return NEP_OK;
 }
@@ -636,6 +722,68 @@ int nep_compute(nep_handle *h, int n_atoms, const double *pos, const int *types,
                   h->partial_gather.p, energy_total, virial_total, nullptr, nullptr, n_atoms, h->volume, s);
   ev_record(h, SLOT_FINAL, 1, s, false);
   CK(cudaGetLastError(), "finalize");
+  return NEP_OK;
+}
+
+int nep_compute_batch(nep_handle *h, int n_struct, const int *offsets, const double *pos, const int *types,
+                      const double *boxes, double *energy, double *energy_struct, double *force, double *virial,
+                      double *virial_struct, nep_stream_t stream) {
+  if (!valid_handle(h)) return NEP_ERR_ARG;
+  h->err.clear();
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = check_offsets(h, n_struct, offsets);
+  if (rc) return rc;
+  if (n_struct > 0 && !boxes) return fail(h, NEP_ERR_ARG, "boxes is null");
+  const int N = n_struct > 0 ? offsets[n_struct] : 0;
+  if (N > 0 && (!pos || !types || !force)) return fail(h, NEP_ERR_ARG, "pos, types and force are required");
+  h->md_ready = false;
+  for (int sl = 0; sl < N_SLOTS; ++sl) h->slot_ran[sl] = false;
+  if (N == 0) {
+    if (energy_struct && n_struct) CK(cudaMemsetAsync(energy_struct, 0, sizeof(double) * n_struct, s), "memset");
+    if (virial_struct && n_struct) CK(cudaMemsetAsync(virial_struct, 0, 9 * sizeof(double) * n_struct, s), "memset");
+    return NEP_OK;
+  }
+  ev_record(h, SLOT_REBUILD, 0, s, false);
+  rc = setup_batch(h, n_struct, offsets, boxes, N, s);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(h->x.p, pos, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s), "copy pos");
+  CK(cudaMemcpyAsync(h->types.p, types, sizeof(int) * N, cudaMemcpyDeviceToDevice, s), "copy types");
+  launch_iota(N, h->perm.p, s);
+  h->N = N;
+  h->stats_cache.n_atoms = N;
+  for (int a = 0; a < 3; ++a) h->stats_cache.cells[a] = 0;
+  const Batch B = batch_of(h);
+  rc = rebuild_lists(h, N, s, B);
+  if (rc) return rc;
+  ev_record(h, SLOT_REBUILD, 1, s, false);
+  double *e_atom = energy, *w_atom = virial;
+  if (!e_atom && energy_struct) {
+    CK(h->b_e.ensure(N), "alloc");
+    e_atom = h->b_e.p;
+  }
+  if (!w_atom && virial_struct) {
+    CK(h->b_w.ensure(9 * (size_t)N), "alloc");
+    w_atom = h->b_w.p;
+  }
+  AtomArgs a = make_args(h, N);
+  a.energy = e_atom;
+  a.force = force;
+  a.virial = w_atom;
+  a.s_out = N;
+  ev_record(h, SLOT_ATOM, 0, s, false);
+  cudaError_t e = h->ops->atom_batch(a, h->mf, h->w0.data(), h->b0.data(), h->w1.data(), h->b1, 1, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "nep_atom kernel (batch)");
+  ev_record(h, SLOT_ATOM, 1, s, false);
+  ev_record(h, SLOT_GATHER, 0, s, false);
+  e = h->ops->gather_batch(a, 1, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "nep_gather kernel (batch)");
+  ev_record(h, SLOT_GATHER, 1, s, false);
+  ev_record(h, SLOT_FINAL, 0, s, false);
+  if (energy_struct || virial_struct)
+    launch_struct_sums(n_struct, 1, h->d_offsets.p, N, energy_struct ? e_atom : nullptr,
+                       virial_struct ? w_atom : nullptr, energy_struct, virial_struct, s);
+  ev_record(h, SLOT_FINAL, 1, s, false);
+  CK(cudaGetLastError(), "structure sums");
   return NEP_OK;
 }
 
@@ -795,7 +943,7 @@ int md_step_launch(nep_handle *h, double dt, cudaStream_t s, bool capturing) {
     CK(cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies), "capture deps");
     CK(cudaStreamBeginCaptureToGraph(h->cap_stream2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed),
        "capture body");
-    cudaError_t e = launch_rebuild(N, h->T, h->grid, h->dtab.p, rlR * rlR, rlA * rlA, h->rcR2f(), h->rcA2f(),
+    cudaError_t e = launch_rebuild(N, h->T, h->grid, Batch{}, h->dtab.p, rlR * rlR, rlA * rlA, h->rcR2f(), h->rcA2f(),
                                    atom_state(h), list_bufs(h), 0, h->status.p, h->cap_stream2);
     cudaGraph_t out = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(h->cap_stream2, &out);
@@ -805,7 +953,7 @@ int md_step_launch(nep_handle *h, double dt, cudaStream_t s, bool capturing) {
     cudaGraphGetNodes(body, nullptr, &nn);
     h->rebuild_kernels = (int)nn;
   } else {
-    CK(launch_rebuild(N, h->T, h->grid, h->dtab.p, rlR * rlR, rlA * rlA, h->rcR2f(), h->rcA2f(), atom_state(h),
+    CK(launch_rebuild(N, h->T, h->grid, Batch{}, h->dtab.p, rlR * rlR, rlA * rlA, h->rcR2f(), h->rcA2f(), atom_state(h),
                       list_bufs(h), 0, h->status.p, s),
        "launch rebuild");
     h->rebuild_kernels = 0;
@@ -965,7 +1113,7 @@ int md_get_state(nep_handle *h, double *pos, double *vel, double *force, nep_str
   if (!valid_handle(h)) return NEP_ERR_ARG;
   if (!h->md_ready) return fail(h, NEP_ERR_STATE, "no MD state");
   cudaStream_t s = (cudaStream_t)stream;
-  launch_export(h->N, atom_state(h), h->grid, pos, vel, force, s);
+  launch_export(h->N, atom_state(h), h->grid, Batch{}, pos, vel, force, s);
   CK(cudaGetLastError(), "export");
   return NEP_OK;
 }

@@ -22,6 +22,11 @@
 
 namespace nep {
 
+// Grid of the structure that atom i belongs to.
+__device__ __forceinline__ const Grid &grid_of(const Batch &B, const Grid &g, int i) {
+  return B.grids ? B.grids[B.sid[i]] : g;
+}
+
 __device__ __forceinline__ bool rebuild_pending(const BuildStatus *st) {
   return *(volatile const int *)&st->rebuild != 0;
 }
@@ -38,10 +43,12 @@ __global__ void zero_cells_kernel(int ncell, int *count, int *cursor, BuildStatu
   }
 }
 
-__global__ void bin_atoms_kernel(int N, int T, AtomState a, int *count, const Grid g, BuildStatus *st) {
+__global__ void bin_atoms_kernel(int N, int T, AtomState a, int *count, const Grid g0, const Batch B,
+                                 BuildStatus *st) {
   if (!rebuild_pending(st)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  const Grid &g = grid_of(B, g0, i);
   double *x = a.x + 3 * (size_t)i;
   double r[3] = {x[0], x[1], x[2]};
   const int ti = a.types[i];
@@ -62,7 +69,7 @@ __global__ void bin_atoms_kernel(int N, int T, AtomState a, int *count, const Gr
     c[b] = cb < 0 ? 0 : (cb >= g.nc[b] ? g.nc[b] - 1 : cb);
   }
   for (int b = 0; b < 3; ++b) x[b] = s[0] * g.H[0][b] + s[1] * g.H[1][b] + s[2] * g.H[2][b];
-  const int id = (c[0] * g.nc[1] + c[1]) * g.nc[2] + c[2];
+  const int id = g.cell_off + (c[0] * g.nc[1] + c[1]) * g.nc[2] + c[2];
   a.cell_of[i] = id;
   atomicAdd(count + id, 1);
 }
@@ -134,11 +141,14 @@ __global__ void reorder_gather_kernel(int N, const int *cell_atoms, AtomState a,
 }
 
 // Copy the reordered data back and derive the cell-local coordinates.
-__global__ void reorder_commit_kernel(int N, AtomState a, const Grid g, const BuildStatus *st) {
+__global__ void reorder_commit_kernel(int N, AtomState a, const Grid g0, const Batch B, const BuildStatus *st) {
   if (!rebuild_pending(st)) return;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
-  const int id = a.cell2[p];
+  // cells are numbered structure by structure, so atom p stays inside its structure's range
+  const Grid &g = grid_of(B, g0, p);
+  const int gid = a.cell2[p];
+  const int id = gid - g.cell_off;
   const int c0 = id / (g.nc[1] * g.nc[2]), c1 = (id / g.nc[2]) % g.nc[1], c2 = id % g.nc[2];
   double r[3], o[3];
   for (int b = 0; b < 3; ++b) {
@@ -153,15 +163,19 @@ __global__ void reorder_commit_kernel(int N, AtomState a, const Grid g, const Bu
   const int t = a.types2[p];
   a.types[p] = t;
   a.perm[p] = a.perm2[p];
-  a.cell_of[p] = id;
-  a.pos4[p] = make_float4((float)(r[0] - o[0]), (float)(r[1] - o[1]), (float)(r[2] - o[2]), __int_as_float(t));
+  a.cell_of[p] = gid;
+  const int sidp = B.grids ? B.sid[p] : 0;
+  a.pos4[p] = make_float4((float)(r[0] - o[0]), (float)(r[1] - o[1]), (float)(r[2] - o[2]),
+                          __int_as_float(t | (sidp << 8)));
 }
 
 // Visit every neighbour candidate (j, image) of atom i: f(j, entry, r2, type_j). Atoms are
 // in cell order, so the atoms of cell c are j in [start[c], start[c+1]).
 template <class F>
-__device__ __forceinline__ void for_candidates(int i, const float4 &pi, int id, const Grid &g, const float4 *dtab,
+__device__ __forceinline__ void for_candidates(int i, const float4 &pi, int gid, const Grid &g, const float4 *dtab0,
                                                const int *start, const float4 *pos4, F &&f) {
+  const int id = gid - g.cell_off;
+  const float4 *dtab = dtab0 + g.dtab_off;
   const int cx = id / (g.nc[1] * g.nc[2]);
   const int cy = (id / g.nc[2]) % g.nc[1];
   const int cz = id % g.nc[2];
@@ -177,7 +191,7 @@ __device__ __forceinline__ void for_candidates(int i, const float4 &pi, int id, 
         const unsigned code = (unsigned)(ox + g.R[0]) | ((unsigned)(oy + g.R[1]) << g.obits) |
                               ((unsigned)(oz + g.R[2]) << (2 * g.obits));
         const float4 D = dtab[code];
-        const int cell = (x * g.nc[1] + y) * g.nc[2] + z;
+        const int cell = g.cell_off + (x * g.nc[1] + y) * g.nc[2] + z;
         const bool self_image = (ox == 0 && oy == 0 && oz == 0);
         const int pe = start[cell + 1];
         for (int j = start[cell]; j < pe; ++j) {
@@ -195,11 +209,12 @@ __device__ __forceinline__ void for_candidates(int i, const float4 &pi, int id, 
 // r_c come before the skin pairs, so the warps of the pair loops stay convergent.
 // count_only: record only the length statistics (used to size the lists).
 __global__ void build_lists_kernel(int N, int T, const float4 *pos4, const int *cell_of, const int *start,
-                                   const Grid g, const float4 *dtab, float rlR2, float rlA2, float rcR2, float rcA2,
-                                   ListBufs L, int count_only, BuildStatus *st) {
+                                   const Grid g0, const Batch B, const float4 *dtab, float rlR2, float rlA2,
+                                   float rcR2, float rcA2, ListBufs L, int count_only, BuildStatus *st) {
   if (!rebuild_pending(st)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  const Grid &g = grid_of(B, g0, i);
   const float4 pi = pos4[i];
   const int id = cell_of[i];
   // per-type counters stay in registers: every update is unrolled over the types
@@ -270,10 +285,11 @@ __global__ void build_lists_kernel(int N, int T, const float4 *pos4, const int *
   L.nn_a[i] = nA;
 }
 
-__global__ void build_rev_kernel(int N, const ListBufs L, const Grid g, BuildStatus *st) {
+__global__ void build_rev_kernel(int N, const ListBufs L, const Grid g0, const Batch B, BuildStatus *st) {
   if (!rebuild_pending(st)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  const Grid &g = grid_of(B, g0, i);
   const unsigned om = (1u << g.obits) - 1u;
   const int na = L.nn_a[i];
   for (int m = 0; m < na; ++m) {
@@ -344,9 +360,11 @@ __global__ void md_drift_kernel(int N, AtomState a, const double *inv_mass_kappa
 }
 
 // Caller-order copies of the MD state: positions wrapped into the cell, velocities, forces.
-__global__ void export_state_kernel(int N, const AtomState a, const Grid g, double *pos, double *vel, double *force) {
+__global__ void export_state_kernel(int N, const AtomState a, const Grid g0, const Batch B, double *pos, double *vel,
+                                    double *force) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  const Grid &g = grid_of(B, g0, i);
   const size_t u = 3 * (size_t)a.perm[i];
   if (pos) {
     const double r[3] = {a.x[3 * (size_t)i], a.x[3 * (size_t)i + 1], a.x[3 * (size_t)i + 2]};
@@ -411,23 +429,92 @@ __global__ void finalize_kernel(int nb_atom, const double *partial_atom, int nb_
   }
 }
 
+// ------------------------------------------------------------------ batches
+// Structure s owns the atoms [offsets[s], offsets[s+1]) in the caller's order, and (the
+// cells being numbered structure by structure) the same range in the internal order.
+__global__ void struct_ids_kernel(int n_struct, const int *offsets, int *sid) {
+  const int s = blockIdx.x;
+  if (s >= n_struct) return;
+  for (int i = offsets[s] + threadIdx.x; i < offsets[s + 1]; i += blockDim.x) sid[i] = s;
+}
+
+// Shift vector of every image code of every structure (zero for codes outside the range).
+__global__ void shift_tables_kernel(int n_struct, const Grid *grids, int ncode, int obits, float4 *dtab) {
+  const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= (long long)n_struct * ncode) return;
+  const int s = (int)(v / ncode), code = (int)(v % ncode);
+  const Grid &g = grids[s];
+  const int om = (1 << obits) - 1;
+  const int o[3] = {(code & om) - g.R[0], ((code >> obits) & om) - g.R[1], ((code >> (2 * obits)) & om) - g.R[2]};
+  float4 D = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (abs(o[0]) <= g.R[0] && abs(o[1]) <= g.R[1] && abs(o[2]) <= g.R[2]) {
+    double d[3];
+    for (int b = 0; b < 3; ++b)
+      d[b] = __dadd_rn(__dadd_rn(__dmul_rn(o[0], g.Hc[0][b]), __dmul_rn(o[1], g.Hc[1][b])), __dmul_rn(o[2], g.Hc[2][b]));
+    D = make_float4((float)d[0], (float)d[1], (float)d[2], 0.f);
+  }
+  dtab[g.dtab_off + code] = D;
+}
+
+// Per-structure sums E_s = sum U_i and W_s = sum W_i (FP64, fixed order): one warp per
+// (structure, member); lanes take a fixed strided subset, then a fixed shuffle tree.
+__global__ void struct_sums_kernel(int n_struct, int members, const int *offsets, int N, const double *e_atom,
+                                   const double *w_atom, double *e_struct, double *w_struct) {
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= (long long)n_struct * members) return;
+  const int m = (int)(wid / n_struct), s = (int)(wid % n_struct);
+  const size_t base = (size_t)m * N;
+  double acc[10];
+  for (int c = 0; c < 10; ++c) acc[c] = 0.0;
+  for (int i = offsets[s] + lane; i < offsets[s + 1]; i += 32) {
+    if (e_atom) acc[0] += e_atom[base + i];
+    if (w_atom)
+      for (int c = 0; c < 9; ++c) acc[1 + c] += w_atom[9 * (base + i) + c];
+  }
+  for (int c = 0; c < 10; ++c)
+    for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], o);
+  if (lane == 0) {
+    if (e_struct) e_struct[(size_t)m * n_struct + s] = acc[0];
+    if (w_struct)
+      for (int c = 0; c < 9; ++c) w_struct[9 * ((size_t)m * n_struct + s) + c] = acc[1 + c];
+  }
+}
+
+void launch_struct_ids(int n_struct, const int *offsets, int *sid, cudaStream_t s) {
+  if (n_struct > 0) struct_ids_kernel<<<n_struct, 128, 0, s>>>(n_struct, offsets, sid);
+}
+
+void launch_shift_tables(int n_struct, const Grid *grids, int ncode, int obits, float4 *dtab, cudaStream_t s) {
+  const long long n = (long long)n_struct * ncode;
+  if (n > 0) shift_tables_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n_struct, grids, ncode, obits, dtab);
+}
+
+void launch_struct_sums(int n_struct, int members, const int *offsets, int N, const double *e_atom,
+                        const double *w_atom, double *e_struct, double *w_struct, cudaStream_t s) {
+  const long long warps = (long long)n_struct * members;
+  if (warps > 0)
+    struct_sums_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(n_struct, members, offsets, N, e_atom,
+                                                                             w_atom, e_struct, w_struct);
+}
+
 // ------------------------------------------------------------------ host launchers
-cudaError_t launch_rebuild(int N, int T, const Grid &g, const float4 *dtab, float rlR2, float rlA2, float rcR2,
-                           float rcA2, const AtomState &a, const ListBufs &L, int count_only, BuildStatus *st,
-                           cudaStream_t s) {
+cudaError_t launch_rebuild(int N, int T, const Grid &g, const Batch &B, const float4 *dtab, float rlR2, float rlA2,
+                           float rcR2, float rcA2, const AtomState &a, const ListBufs &L, int count_only,
+                           BuildStatus *st, cudaStream_t s) {
   const int tb = 256;
   const int nb = (N + tb - 1) / tb;
   const int cb = (g.ncell + tb - 1) / tb;
   zero_cells_kernel<<<cb < 1024 ? cb : 1024, tb, 0, s>>>(g.ncell, L.cell_count, L.cell_cursor, st);
-  bin_atoms_kernel<<<nb, tb, 0, s>>>(N, T, a, L.cell_count, g, st);
+  bin_atoms_kernel<<<nb, tb, 0, s>>>(N, T, a, L.cell_count, g, B, st);
   scan_cells_kernel<<<1, 1024, 0, s>>>(g.ncell, L.cell_count, L.cell_start, st);
   scatter_atoms_kernel<<<nb, tb, 0, s>>>(N, a.cell_of, L.cell_start, L.cell_cursor, L.cell_atoms, st);
   sort_cells_kernel<<<cb, tb, 0, s>>>(g.ncell, L.cell_start, L.cell_atoms, st);
   reorder_gather_kernel<<<nb, tb, 0, s>>>(N, L.cell_atoms, a, st);
-  reorder_commit_kernel<<<nb, tb, 0, s>>>(N, a, g, st);
-  build_lists_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, T, a.pos4, a.cell_of, L.cell_start, g, dtab, rlR2, rlA2,
-                                                     rcR2, rcA2, L, count_only, st);
-  if (!count_only) build_rev_kernel<<<nb, tb, 0, s>>>(N, L, g, st);
+  reorder_commit_kernel<<<nb, tb, 0, s>>>(N, a, g, B, st);
+  build_lists_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, T, a.pos4, a.cell_of, L.cell_start, g, B, dtab, rlR2,
+                                                     rlA2, rcR2, rcA2, L, count_only, st);
+  if (!count_only) build_rev_kernel<<<nb, tb, 0, s>>>(N, L, g, B, st);
   finish_build_kernel<<<1, 1, 0, s>>>(st);
   return cudaGetLastError();
 }
@@ -443,9 +530,9 @@ void launch_drift(int N, const AtomState &a, const double *inv_mass_kappa, doubl
   md_drift_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, a, inv_mass_kappa, dt, half_skin2, st);
 }
 
-void launch_export(int N, const AtomState &a, const Grid &g, double *pos, double *vel, double *force,
+void launch_export(int N, const AtomState &a, const Grid &g, const Batch &B, double *pos, double *vel, double *force,
                    cudaStream_t s) {
-  export_state_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, a, g, pos, vel, force);
+  export_state_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, a, g, B, pos, vel, force);
 }
 
 void launch_finalize(int nb_atom, const double *partial_atom, int nb_gather, const double *partial_gather,

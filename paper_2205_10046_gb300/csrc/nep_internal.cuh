@@ -25,6 +25,16 @@ struct Grid {
   double H[3][3];     // cell rows
   double Hinv[3][3];  // s = r . Hinv
   double Hc[3][3];    // rows of one grid cell: H[a] / nc[a]
+  int cell_off;       // first global cell of this structure (batches; 0 for one structure)
+  int dtab_off;       // first shift-table entry of this structure (batches; 0 for one structure)
+};
+
+// Structures of a batch: grid of every structure and the structure of every atom (internal
+// order). A single structure uses grids == nullptr and the grid passed by value.
+struct Batch {
+  const Grid *grids;
+  const int *sid;
+  int n;
 };
 
 // Per-atom device arrays. Internally atoms are kept in cell order (re-sorted at every
@@ -72,7 +82,9 @@ __device__ __forceinline__ float3 pair_vector(const float4 &pi, const float4 &pj
 __device__ __forceinline__ float norm2(const float3 &d) {
   return __fmaf_rn(d.z, d.z, __fmaf_rn(d.y, d.y, __fmul_rn(d.x, d.x)));
 }
-__device__ __forceinline__ int type_of(const float4 &p) { return __float_as_int(p.w); }
+// pos4.w holds the atom type in bits 0-7 and its structure (batches) in bits 8-31.
+__device__ __forceinline__ int type_of(const float4 &p) { return __float_as_int(p.w) & 0xFF; }
+__device__ __forceinline__ int struct_of(const float4 &p) { return __float_as_int(p.w) >> 8; }
 
 // Arguments of the per-atom and gather kernels (everything except the model weights).
 struct AtomArgs {
@@ -112,6 +124,15 @@ struct AtomArgs {
   const uint4 *tc_b1;      // GEMM1 operand W0 [NP1 x KP1] (bf16)
   const uint4 *tc_b2;      // GEMM2 operand W0^T [NP2 x KP2] (bf16)
   int *tc_err;             // set when a tensor-core wait ran out
+  // Batched kernels only. dtab then holds ncode shift vectors per structure (the structure
+  // index sits in pos4.w above the type bits), and blockIdx.y selects the member of a
+  // population whose coefficients and network the block uses; every per-member array is
+  // offset by member x its stride (in elements).
+  const float *pop_ann;    // [P][H*N_des + 2H + 1]: w0, b0, w1, b1 per member, or null
+  const uint4 *pop_tc;     // [P][2 tiles] BF16 operand tiles per member (precision 1), or null
+  long long s_cr, s_ca, s_ann, s_tc;  // strides of c_r, c_a, pop_ann, pop_tc
+  long long s_erad, s_pang;           // strides of e_rad, p_ang
+  long long s_out;                    // atoms per member in energy (x1), force (x3), virial (x9)
 };
 
 // Model constants of one handle, FP32.
@@ -129,6 +150,10 @@ struct ShapeOps {
   cudaError_t (*atom)(const AtomArgs &, const ModelF &, const float *w0, const float *b0, const float *w1,
                       float b1, int descriptor_only, cudaStream_t s);
   cudaError_t (*gather)(const AtomArgs &, cudaStream_t s);
+  // batched kernels (per-structure shift tables; `members` population members along y)
+  cudaError_t (*atom_batch)(const AtomArgs &, const ModelF &, const float *w0, const float *b0, const float *w1,
+                            float b1, int members, cudaStream_t s);
+  cudaError_t (*gather_batch)(const AtomArgs &, int members, cudaStream_t s);
   int (*atom_blocks)(int N);
   int (*gather_blocks)(int N);
 };
@@ -140,9 +165,17 @@ const ShapeOps *shape_at(int i);
 struct Grid;
 void model_constants(ModelF &m);
 int build_grid(const double *box, double rl, int N, Grid &g, float4 *dtab, double *volume, const char **err);
-cudaError_t launch_rebuild(int N, int T, const Grid &g, const float4 *dtab, float rlR2, float rlA2, float rcR2,
-                           float rcA2, const AtomState &a, const ListBufs &L, int count_only, BuildStatus *st,
-                           cudaStream_t s);
+cudaError_t launch_rebuild(int N, int T, const Grid &g, const Batch &B, const float4 *dtab, float rlR2, float rlA2,
+                           float rcR2, float rcA2, const AtomState &a, const ListBufs &L, int count_only,
+                           BuildStatus *st, cudaStream_t s);
 void launch_iota(int N, int *perm, cudaStream_t s);
+void launch_export(int N, const AtomState &a, const Grid &g, const Batch &B, double *pos, double *vel, double *force,
+                   cudaStream_t s);
+// batches: structure index of every atom, the shift tables of all structures, and the
+// per-structure sums of per-atom energies and virials (caller order, per member)
+void launch_struct_ids(int n_struct, const int *offsets, int *sid, cudaStream_t s);
+void launch_shift_tables(int n_struct, const Grid *grids, int ncode, int obits, float4 *dtab, cudaStream_t s);
+void launch_struct_sums(int n_struct, int members, const int *offsets, int N, const double *e_atom,
+                        const double *w_atom, double *e_struct, double *w_struct, cudaStream_t s);
 
 }  // namespace nep

@@ -323,7 +323,7 @@ __device__ __forceinline__ void for_pairs_plain(const unsigned *__restrict__ nl,
 }
 
 // ------------------------------------------------------------------------ per-atom kernel
-template <class S, bool DESC_ONLY, int PREC>
+template <class S, bool DESC_ONLY, int PREC, bool BATCH = false>
 __global__ void __launch_bounds__(kAtomBlock, 1)
     atom_kernel(const AtomArgs a, const __grid_constant__ AnnConst<S> w) {
   static_assert(PREC == 0 || !DESC_ONLY, "the descriptor-only kernel has no network");
@@ -331,8 +331,12 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
   extern __shared__ float4 smem4[];
   const int T = a.T;
   constexpr int NDP = S::NDP;
-  float4 *dtab_s = smem4;                                        // [ncode]
-  float *w0_s = reinterpret_cast<float *>(smem4 + a.ncode);      // [H][NDP] (FP32 network only)
+  // batches: the shift tables stay in global memory, one per structure, and blockIdx.y is
+  // the population member whose coefficients and network this block evaluates
+  const int mem = BATCH ? (int)blockIdx.y : 0;
+  const float *pw = (BATCH && a.pop_ann) ? a.pop_ann + mem * a.s_ann : nullptr;
+  float4 *dtab_s = smem4;                                        // [ncode] (one structure)
+  float *w0_s = reinterpret_cast<float *>(smem4 + (BATCH ? 0 : a.ncode));  // [H][NDP] (FP32 network)
   float *b0_s = w0_s + (PREC == 0 ? S::H * NDP : 0);             // [H]
   float *w1_s = b0_s + S::H;                                     // [H]
   float *cR_s = w1_s + S::H;                                     // [T][T][NR+1][KR+1]
@@ -340,19 +344,23 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
   // [NA+1][NK][block]: S_nk while the FP32 network runs, then dU/dS_nk. For the tensor-core
   // network S_nk waits in TMEM instead and this region first holds the BF16 operand tiles.
   float *S_s = cA_s + T * T * (NA + 1) * (KA + 1);
-  for (int v = threadIdx.x; v < a.ncode; v += blockDim.x) dtab_s[v] = a.dtab[v];
+  if constexpr (!BATCH)
+    for (int v = threadIdx.x; v < a.ncode; v += blockDim.x) dtab_s[v] = a.dtab[v];
   if constexpr (PREC == 0) {
     for (int v = threadIdx.x; v < S::H * NDP; v += blockDim.x) {
       const int mu = v / NDP, c = v - mu * NDP;
-      w0_s[v] = c < NDES ? w.w0[mu * NDES + c] : 0.f;
+      w0_s[v] = c < NDES ? (pw ? pw[mu * NDES + c] : w.w0[mu * NDES + c]) : 0.f;
     }
   }
   for (int v = threadIdx.x; v < S::H; v += blockDim.x) {
-    b0_s[v] = w.b0[v];
-    w1_s[v] = w.w1[v];
+    b0_s[v] = pw ? pw[S::H * NDES + v] : w.b0[v];
+    w1_s[v] = pw ? pw[S::H * NDES + S::H + v] : w.w1[v];
   }
-  for (int v = threadIdx.x; v < T * T * (NR + 1) * (KR + 1); v += blockDim.x) cR_s[v] = a.c_r[v];
-  for (int v = threadIdx.x; v < T * T * (NA + 1) * (KA + 1); v += blockDim.x) cA_s[v] = a.c_a[v];
+  __shared__ float b1_s;
+  if (threadIdx.x == 0) b1_s = pw ? pw[S::H * NDES + 2 * S::H] : w.b1;
+  const float *c_r = a.c_r + mem * a.s_cr, *c_a = a.c_a + mem * a.s_ca;
+  for (int v = threadIdx.x; v < T * T * (NR + 1) * (KR + 1); v += blockDim.x) cR_s[v] = c_r[v];
+  for (int v = threadIdx.x; v < T * T * (NA + 1) * (KA + 1); v += blockDim.x) cA_s[v] = c_a[v];
   // tensor-core network: operand tiles (128-byte aligned) and TMEM for S_nk and the results
   __shared__ __align__(8) uint64_t tc_mbar;
   __shared__ uint32_t tc_tmem;
@@ -363,9 +371,14 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
     tileA = base;
     tileB1 = tileA + S::TILE_A;
     tileB2 = tileB1 + S::TILE_B;
+    const uint4 *b1t = a.tc_b1, *b2t = a.tc_b2;
+    if (BATCH && a.pop_tc) {
+      b1t = a.pop_tc + mem * a.s_tc;
+      b2t = b1t + S::TILE_B / 16;
+    }
     for (int v = threadIdx.x; v < S::TILE_B / 16; v += blockDim.x) {
-      reinterpret_cast<uint4 *>(tileB1)[v] = a.tc_b1[v];
-      reinterpret_cast<uint4 *>(tileB2)[v] = a.tc_b2[v];
+      reinterpret_cast<uint4 *>(tileB1)[v] = b1t[v];
+      reinterpret_cast<uint4 *>(tileB2)[v] = b2t[v];
     }
     if (threadIdx.x == 0) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&tc_mbar)));
@@ -396,6 +409,12 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
     const int ti = type_of(pi);
     const float inv_rcR = 1.f / a.rcR, inv_rcA = 1.f / a.rcA;
     const float rcR2 = a.rcR * a.rcR, rcA2 = a.rcA * a.rcA;
+    // shift vector of a list entry: from shared memory, or from the structure's own table
+    const float4 *dtab_b = BATCH ? a.dtab + (size_t)struct_of(pi) * a.ncode : dtab_s;
+    auto shift = [&](unsigned e) -> float4 {
+      if constexpr (BATCH) return __ldg(dtab_b + (e >> a.jbits));
+      else return dtab_s[e >> a.jbits];
+    };
 
     float q[NDES];
 #pragma unroll
@@ -409,7 +428,7 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
 #pragma unroll
       for (int k = 0; k <= KR; ++k) Fk[k] = 0.f;
       for_pairs_batch<4>(a.nl_r, base, cnt, N, i, a.pos4, a.jmask, [&](int, unsigned e, const float4 &pj) {
-        const float3 d = pair_vector(pi, pj, dtab_s[e >> a.jbits]);
+        const float3 d = pair_vector(pi, pj, shift(e));
         const float r2 = norm2(d);
         if (r2 < rcR2) {
           float f[KR + 1];
@@ -442,7 +461,7 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
 #pragma unroll
         for (int k = 0; k < NK; ++k) Sv[c][k] = 0.f;
       for_pairs(a.nl_a, 0, na, N, i, a.pos4, a.jmask, [&](int, unsigned e, const float4 &pj) {
-        const float3 d = pair_vector(pi, pj, dtab_s[e >> a.jbits]);
+        const float3 d = pair_vector(pi, pj, shift(e));
         const float r2 = norm2(d);
         if (r2 < rcA2) {
           const int tj = type_of(pj);
@@ -619,9 +638,10 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
             if (8 * c8 + j < NDES) dq[8 * c8 + j] = v[j];
         }
       }
-      U -= w.b1;
+      if constexpr (BATCH) U -= b1_s;
+      else U -= w.b1;
       if (active) {
-        if (a.energy) a.energy[a.perm ? a.perm[i] : i] = (double)U;
+        if (a.energy) a.energy[mem * a.s_out + (a.perm ? a.perm[i] : i)] = (double)U;
         Ublock = (double)U;
       }
 
@@ -642,7 +662,7 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
 #pragma unroll
         for (int k = KR + 2; k < S::EST; ++k) ev[k] = 0.f;
         if (active) {
-          float4 *dst = reinterpret_cast<float4 *>(a.e_rad + ((size_t)i * T + t) * S::EST);
+          float4 *dst = reinterpret_cast<float4 *>(a.e_rad + mem * a.s_erad + ((size_t)i * T + t) * S::EST);
 #pragma unroll
           for (int k4 = 0; k4 < S::EST / 4; ++k4)
             dst[k4] = make_float4(ev[4 * k4], ev[4 * k4 + 1], ev[4 * k4 + 2], ev[4 * k4 + 3]);
@@ -694,7 +714,7 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
 
       // ---- angular partial forces dU_i/dr_ij (angular terms of Eq. partial_force)
       for_pairs(a.nl_a, 0, na, N, i, a.pos4, a.jmask, [&](int m, unsigned e, const float4 &pj) {
-        const float3 d = pair_vector(pi, pj, dtab_s[e >> a.jbits]);
+        const float3 d = pair_vector(pi, pj, shift(e));
         const float r2 = norm2(d);
         if (r2 < rcA2) {
           const int tj = type_of(pj);
@@ -740,7 +760,7 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
           const float px = (gx - gu * ux) + yy * ux;
           const float py = (gy - gu * uy) + yy * uy;
           const float pz = (gz - gu * uz) + yy * uz;
-          a.p_ang[(size_t)m * N + i] = make_float4(px, py, pz, 0.f);
+          a.p_ang[mem * a.s_pang + (size_t)m * N + i] = make_float4(px, py, pz, 0.f);
         }
       });
     }
@@ -756,7 +776,7 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
     if (threadIdx.x == 0) {
       double s = 0.0;
       for (int wv = 0; wv < kAtomBlock / 32; ++wv) s += red[wv];
-      a.partial_atom[blockIdx.x] = s;
+      a.partial_atom[(size_t)mem * gridDim.x + blockIdx.x] = s;
     }
   }
   if constexpr (PREC == 1) {
@@ -770,14 +790,19 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
 }
 
 // ------------------------------------------------------------------------ gather kernel
-template <class S>
+template <class S, bool BATCH = false>
 __global__ void __launch_bounds__(kGatherBlock)
     gather_kernel(const AtomArgs a) {
   constexpr int KR = S::KR, EST = S::EST;
   extern __shared__ float4 smem4[];
   float4 *dtab_s = smem4;
-  for (int v = threadIdx.x; v < a.ncode; v += blockDim.x) dtab_s[v] = a.dtab[v];
-  __syncthreads();
+  const int mem = BATCH ? (int)blockIdx.y : 0;
+  if constexpr (!BATCH) {
+    for (int v = threadIdx.x; v < a.ncode; v += blockDim.x) dtab_s[v] = a.dtab[v];
+    __syncthreads();
+  }
+  const float *e_rad = a.e_rad + mem * a.s_erad;
+  const float4 *p_ang = a.p_ang + mem * a.s_pang;
   const int N = a.N, T = a.T;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double part[kReduceSlots];
@@ -786,6 +811,11 @@ __global__ void __launch_bounds__(kGatherBlock)
   if (i < N) {
     const float4 pi = a.pos4[i];
     const int ti = type_of(pi);
+    const float4 *dtab_b = BATCH ? a.dtab + (size_t)struct_of(pi) * a.ncode : dtab_s;
+    auto shift = [&](unsigned e) -> float4 {
+      if constexpr (BATCH) return __ldg(dtab_b + (e >> a.jbits));
+      else return dtab_s[e >> a.jbits];
+    };
     const float inv_rcR = 1.f / a.rcR;
     const float rcR2 = a.rcR * a.rcR, rcA2 = a.rcA * a.rcA;
     float fx = 0.f, fy = 0.f, fz = 0.f;
@@ -797,7 +827,7 @@ __global__ void __launch_bounds__(kGatherBlock)
     for (int t = 0; t < T; ++t) {
       const int cnt = a.nn_r[t * N + i];
       float eo[EST];
-      const float4 *src = reinterpret_cast<const float4 *>(a.e_rad + ((size_t)i * T + t) * EST);
+      const float4 *src = reinterpret_cast<const float4 *>(e_rad + ((size_t)i * T + t) * EST);
 #pragma unroll
       for (int k4 = 0; k4 < EST / 4; ++k4) {
         const float4 v = src[k4];
@@ -805,13 +835,13 @@ __global__ void __launch_bounds__(kGatherBlock)
       }
       for_pairs_batch<4>(a.nl_r, base, cnt, N, i, a.pos4, a.jmask, [&](int, unsigned e, const float4 &pj) {
         const int j = e & a.jmask;
-        const float3 d = pair_vector(pi, pj, dtab_s[e >> a.jbits]);
+        const float3 d = pair_vector(pi, pj, shift(e));
         const float r2 = norm2(d);
         if (r2 < rcR2) {
           const float rinv = rsqrtf(r2);
           const float r = r2 * rinv;
           float ej[EST];
-          const float4 *srcj = reinterpret_cast<const float4 *>(a.e_rad + ((size_t)j * T + ti) * EST);
+          const float4 *srcj = reinterpret_cast<const float4 *>(e_rad + ((size_t)j * T + ti) * EST);
 #pragma unroll
           for (int k4 = 0; k4 < EST / 4; ++k4) {
             const float4 v = __ldg(srcj + k4);
@@ -872,11 +902,11 @@ __global__ void __launch_bounds__(kGatherBlock)
     const int na = a.nn_a[i];
     for_pairs(a.nl_a, 0, na, N, i, a.pos4, a.jmask, [&](int m, unsigned e, const float4 &pj) {
       const size_t slot = (size_t)m * N + i;
-      const float3 d = pair_vector(pi, pj, dtab_s[e >> a.jbits]);
+      const float3 d = pair_vector(pi, pj, shift(e));
       const float r2 = norm2(d);
       if (r2 < rcA2) {
-        const float4 pij = a.p_ang[slot];
-        const float4 pji = a.p_ang[a.rev_a[slot]];
+        const float4 pij = p_ang[slot];
+        const float4 pji = p_ang[a.rev_a[slot]];
         fx += pij.x - pji.x;
         fy += pij.y - pji.y;
         fz += pij.z - pji.z;
@@ -892,7 +922,7 @@ __global__ void __launch_bounds__(kGatherBlock)
       }
     });
     const double Fx = fx, Fy = fy, Fz = fz;
-    const size_t io = a.perm ? (size_t)a.perm[i] : (size_t)i;
+    const size_t io = mem * a.s_out + (a.perm ? (size_t)a.perm[i] : (size_t)i);
     if (a.force) {
       a.force[3 * io] = Fx;
       a.force[3 * io + 1] = Fy;
@@ -925,7 +955,7 @@ __global__ void __launch_bounds__(kGatherBlock)
   if (threadIdx.x < 11 && threadIdx.x >= 1) {
     double s = 0.0;
     for (int wv = 0; wv < kGatherBlock / 32; ++wv) s += red[wv][threadIdx.x];
-    a.partial_gather[(size_t)blockIdx.x * kReduceSlots + threadIdx.x] = s;
+    a.partial_gather[((size_t)mem * gridDim.x + blockIdx.x) * kReduceSlots + threadIdx.x] = s;
   }
 }
 
@@ -977,6 +1007,56 @@ cudaError_t launch_gather(const AtomArgs &a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Batched launches (grid.y = population members); instantiated in the nep_batch_*.cu units.
+template <class S>
+cudaError_t launch_atom_batch(const AtomArgs &a, const ModelF &mf, const float *w0, const float *b0,
+                              const float *w1, float b1, int members, cudaStream_t st);
+template <class S>
+cudaError_t launch_gather_batch(const AtomArgs &a, int members, cudaStream_t st);
+
+#ifdef NEP_BATCH_KERNELS
+template <class S>
+cudaError_t launch_atom_batch(const AtomArgs &a, const ModelF &mf, const float *w0, const float *b0,
+                              const float *w1, float b1, int members, cudaStream_t st) {
+  if (a.N <= 0 || members <= 0) return cudaSuccess;
+  AnnConst<S> w;
+  for (int v = 0; v < S::H * S::NDES; ++v) w.w0[v] = w0 ? w0[v] : 0.f;
+  for (int v = 0; v < S::H; ++v) {
+    w.b0[v] = b0 ? b0[v] : 0.f;
+    w.w1[v] = w1 ? w1[v] : 0.f;
+  }
+  w.b1 = b1;
+  w.m = mf;
+  const dim3 grid((a.N + kAtomBlock - 1) / kAtomBlock, members);
+  const size_t smem = atom_smem_bytes<S>(a.T, 0, a.precision);
+  auto go = [&](auto kern) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kAtomBlock, smem, st>>>(a, w);
+    return cudaGetLastError();
+  };
+  if (a.precision == 1) return go(atom_kernel<S, false, 1, true>);
+  return go(atom_kernel<S, false, 0, true>);
+}
+
+template <class S>
+cudaError_t launch_gather_batch(const AtomArgs &a, int members, cudaStream_t st) {
+  if (a.N <= 0 || members <= 0) return cudaSuccess;
+  const dim3 grid((a.N + kGatherBlock - 1) / kGatherBlock, members);
+  gather_kernel<S, true><<<grid, kGatherBlock, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <class S>
+void attach_batch(ShapeOps &o) {
+  o.atom_batch = &launch_atom_batch<S>;
+  o.gather_batch = &launch_gather_batch<S>;
+}
+#else
+template <class S>
+void attach_batch(ShapeOps &o);  // explicitly instantiated in the batch translation unit
+#endif
+
 template <class S> int atom_blocks(int N) { return (N + kAtomBlock - 1) / kAtomBlock; }
 template <class S> int gather_blocks(int N) { return (N + kGatherBlock - 1) / kGatherBlock; }
 
@@ -990,6 +1070,7 @@ ShapeOps make_ops() {
   o.gather = &launch_gather<S>;
   o.atom_blocks = &atom_blocks<S>;
   o.gather_blocks = &gather_blocks<S>;
+  attach_batch<S>(o);
   return o;
 }
 

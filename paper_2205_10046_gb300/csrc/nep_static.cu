@@ -91,7 +91,7 @@ int run_build(int N, int T, const Grid &g, const float4 *dtab, float rlR2, float
   std::memset(st_host, 0, sizeof(BuildStatus));
   st_host->rebuild = 1;
   SK(cudaMemcpyAsync(st_dev, st_host, sizeof(BuildStatus), cudaMemcpyHostToDevice, s), "status");
-  SK(launch_rebuild(N, T, g, dtab, rlR2, rlA2, rcR2, rcA2, a, L, count_only, st_dev, s), "neighbour build");
+  SK(launch_rebuild(N, T, g, Batch{}, dtab, rlR2, rlA2, rcR2, rcA2, a, L, count_only, st_dev, s), "neighbour build");
   SK(cudaMemcpyAsync(st_host, st_dev, sizeof(BuildStatus), cudaMemcpyDeviceToHost, s), "status");
   SK(cudaStreamSynchronize(s), "synchronise");
   if (st_host->bad_input & 1) return fail_static(NEP_ERR_ARG, "atom type out of range");

@@ -55,6 +55,7 @@ _SIGS = {
     "nep_last_error": (C.c_char_p, [_P]),
     "nep_compute": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "nep_compute_host": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "nep_compute_batch": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "nep_descriptors": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P]),
     "nep_n_des": (C.c_int, [_P]),
     "md_init": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P]),
@@ -193,6 +194,33 @@ def nep_compute_host(h, pos, types, box):
     return U, float(E.value), F, Wv, Wt
 
 
+def _offsets(offsets) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(offsets, dtype=np.int32).reshape(-1))
+
+
+def _boxes(boxes, n_struct: int) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(boxes, dtype=np.float64).reshape(n_struct, 9))
+
+
+def nep_compute_batch(h, offsets, pos, types, boxes, energy=None, energy_struct=None, force=None, virial=None,
+                      virial_struct=None):
+    """Batched evaluation of many structures: offsets [S+1] and boxes [S,3,3] on the host;
+    pos [N,3] f64, types [N] i32 and the preallocated outputs are CUDA tensors."""
+    import torch
+    off = _offsets(offsets)
+    ns = off.shape[0] - 1
+    n = int(off[-1]) if ns > 0 else 0
+    bx = _boxes(boxes, ns)
+    rc = load().nep_compute_batch(h, ns, off.ctypes.data, _dev(pos, torch.float64, (n, 3), "pos"),
+                                  _dev(types, torch.int32, (n,), "types"), bx.ctypes.data,
+                                  _dev(energy, torch.float64, (n,), "energy"),
+                                  _dev(energy_struct, torch.float64, (ns,), "energy_struct"),
+                                  _dev(force, torch.float64, (n, 3), "force"),
+                                  _dev(virial, torch.float64, (n, 9), "virial"),
+                                  _dev(virial_struct, torch.float64, (ns, 9), "virial_struct"), _stream())
+    _check(rc, h)
+
+
 def nep_descriptors(h, pos, types, box, q):
     import torch
     n = int(pos.shape[0])
@@ -328,4 +356,21 @@ class NEP:
         if per_atom_virial:
             out["W"] = torch.empty((n, 9), dtype=torch.float64, device=dev)
         nep_compute(self.h, pos, types, box, out["U"], out["E"], out["F"], out.get("W"), out["W_total"])
+        return out
+
+    def compute_batch(self, offsets, pos, types, boxes, per_atom: bool = False):
+        """Batched evaluation; returns dict of CUDA tensors (E_struct [S], F [N,3],
+        W_struct [S,9], and U [N], W [N,9] when per_atom)."""
+        import torch
+        off = _offsets(offsets)
+        ns, n = off.shape[0] - 1, int(off[-1])
+        dev = pos.device
+        out = dict(E_struct=torch.empty(ns, dtype=torch.float64, device=dev),
+                   F=torch.empty((n, 3), dtype=torch.float64, device=dev),
+                   W_struct=torch.empty((ns, 9), dtype=torch.float64, device=dev))
+        if per_atom:
+            out["U"] = torch.empty(n, dtype=torch.float64, device=dev)
+            out["W"] = torch.empty((n, 9), dtype=torch.float64, device=dev)
+        nep_compute_batch(self.h, off, pos, types, boxes, out.get("U"), out["E_struct"], out["F"], out.get("W"),
+                          out["W_struct"])
         return out

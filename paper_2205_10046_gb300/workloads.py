@@ -242,10 +242,12 @@ def random_structure(seed: int, n_atoms: int, n_types_model: int = 3, sigma: flo
     cells = int(math.ceil(n_atoms / nb))
     best = None
     for nx in range(1, cells + 1):
+        if int(math.ceil(cells / (nx * nx))) < nx:
+            break  # nz >= ny >= nx is impossible from here on
         for ny in range(nx, cells + 1):
             nz = int(math.ceil(cells / (nx * ny)))
             if nz < ny:
-                continue
+                break  # nz only falls and ny only grows along this loop
             key = (nx * ny * nz, nz - nx)
             if best is None or key < best[0]:
                 best = (key, (nx, ny, nz))
@@ -261,3 +263,60 @@ def random_structure(seed: int, n_atoms: int, n_types_model: int = 3, sigma: flo
     pos = frac @ box
     pos = pos + rng.normal(0.0, sigma, pos.shape)
     return pos, types, box
+
+
+def mixed_model(seed: int = 0) -> NepModel:
+    """The three-species model of the batch and serving workloads (rc 5.5 / 4.0 A,
+    n_max 8 / 4, N_neu = 40; types 0, 1, 2 with the masses of Si, Ge and C)."""
+    return random_model(MIXED_MODEL, seed, [MASS_SI, MASS_GE, MASS_C])
+
+
+@dataclass
+class Batch:
+    """Concatenated independent structures: structure s owns atoms [offsets[s], offsets[s+1])."""
+    offsets: np.ndarray  # [S+1] int32
+    pos: np.ndarray      # [N, 3]
+    types: np.ndarray    # [N] int32
+    boxes: np.ndarray    # [S, 3, 3]
+    seeds: np.ndarray    # [S] structure seeds
+
+    @property
+    def n_struct(self) -> int:
+        return self.boxes.shape[0]
+
+    @property
+    def n_atoms(self) -> int:
+        return int(self.offsets[-1])
+
+    def structure(self, s: int):
+        a, b = int(self.offsets[s]), int(self.offsets[s + 1])
+        return self.pos[a:b], self.types[a:b], self.boxes[s]
+
+    def subset(self, idx) -> "Batch":
+        parts = [self.structure(int(s)) for s in idx]
+        return concat_structures(parts, self.seeds[np.asarray(idx, dtype=np.int64)])
+
+
+def concat_structures(parts, seeds=None) -> Batch:
+    """Batch from a list of (pos, types, box)."""
+    sizes = [p[0].shape[0] for p in parts]
+    offsets = np.zeros(len(parts) + 1, np.int32)
+    offsets[1:] = np.cumsum(sizes)
+    pos = np.concatenate([p[0] for p in parts]) if parts else np.zeros((0, 3))
+    types = np.concatenate([p[1] for p in parts]).astype(np.int32) if parts else np.zeros(0, np.int32)
+    boxes = np.stack([p[2] for p in parts]) if parts else np.zeros((0, 3, 3))
+    seeds = np.asarray(seeds if seeds is not None else np.arange(len(parts)), dtype=np.int64)
+    return Batch(offsets, np.ascontiguousarray(pos, dtype=np.float64), np.ascontiguousarray(types),
+                 np.ascontiguousarray(boxes, dtype=np.float64), seeds)
+
+
+def batch_structures(n_struct: int = 4096, seed: int = 3, n_min: int = 8, n_max: int = 512,
+                     n_types_model: int = 3, sigma: float = 0.1, max_shear: float = 0.1) -> Batch:
+    """The structure batch: n_struct random structures (``random_structure``) with atom
+    counts uniform in [n_min, n_max]; structure s uses seed 1000003 * seed + s."""
+    rng = _rng(seed)
+    sizes = rng.integers(n_min, n_max + 1, n_struct)
+    seeds = 1000003 * seed + np.arange(n_struct, dtype=np.int64)
+    parts = [random_structure(int(seeds[s]), int(sizes[s]), n_types_model, sigma, max_shear)
+             for s in range(n_struct)]
+    return concat_structures(parts, seeds)
