@@ -140,6 +140,43 @@ int nep_compute_batch(nep_handle *h, int n_struct, const int *offsets, const dou
                       const double *boxes, double *energy, double *energy_struct, double *force,
                       double *virial, double *virial_struct, nep_stream_t stream);
 
+/* Number of trainable parameters N_par of the handle's model (Sec. II E): the length of one
+ * candidate vector z of nep_eval_population, ordered c^R [T][T][n_R+1][K_R+1],
+ * c^A [T][T][n_A+1][K_A+1], w0 [N_neu][N_des], b0 [N_neu], w1 [N_neu], b1. */
+int nep_n_par(const nep_handle *h);
+
+/* Loss of Eq. loss for a population of candidate parameter vectors on one structure set,
+ * the inner step of the evolutionary training of Sec. III. Every candidate gets its own
+ * descriptor coefficients and network; the hyper-parameters (cut-offs, basis sizes, types)
+ * are the handle's, its own weights are not used.
+ *   z       DEVICE [n_pop][N_par] FP64 candidate vectors (order of nep_n_par)
+ *   offsets HOST [n_struct+1], boxes HOST [n_struct][9], pos DEVICE [N][3], types DEVICE [N]:
+ *           the structure set, as nep_compute_batch (N = offsets[n_struct] > 0)
+ *   e_tar   DEVICE [n_struct] target energy per atom (eV/atom; empty structures ignored)
+ *   f_tar   DEVICE [N][3] target forces (eV/Angstrom)
+ *   w_tar   DEVICE [n_struct][6] target virial per atom (eV/atom; xx, yy, zz, xy, yz, zx,
+ *           compared with the symmetric part of W_s / N_s), or NULL (no virial term)
+ *   lambda  HOST [5]: lambda_e, lambda_f, lambda_v, lambda_1, lambda_2
+ *   loss    DEVICE [n_pop][6] out: L, RMSE_E, RMSE_F, RMSE_W, sum|z|/N_par, sqrt(sum z^2/N_par)
+ * Members are evaluated several per launch (grid.y; nep_set_tuning), in FP32 (or with the
+ * BF16 tensor-core network after nep_set_precision(h, 1)); every sum is FP64 in a fixed
+ * order, so the losses do not depend on the grouping. Synchronises `stream` once (list
+ * sizing); errors as nep_compute_batch. */
+int nep_eval_population(nep_handle *h, int n_pop, const double *z, int n_struct, const int *offsets,
+                        const double *pos, const int *types, const double *boxes, const double *e_tar,
+                        const double *f_tar, const double *w_tar, const double *lambda, double *loss,
+                        nep_stream_t stream);
+
+/* Launch shapes of the batched kernels. Zero fields select the defaults. */
+typedef struct {
+  int members_per_launch; /* population members per launch (grid.y); 0: as many as a workspace
+                             budget of min(half the free memory, 32 GiB) holds */
+  int last_members;       /* out: members per launch used by the last nep_eval_population */
+} nep_tuning;
+
+int nep_set_tuning(nep_handle *h, const nep_tuning *t);
+int nep_get_tuning(const nep_handle *h, nep_tuning *t);
+
 /* Descriptor vectors q^i (Eqs. qin and S_nk with the explicit components of Sec. II D)
  * into q [N][N_des] FP64 (DEVICE pointers, as nep_compute). */
 int nep_descriptors(nep_handle *h, int n_atoms, const double *pos, const int *types, const double *box,

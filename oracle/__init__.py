@@ -12,6 +12,7 @@ with g++ on first use (or via :func:`build`) and wraps it with ctypes.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -207,3 +208,59 @@ def md(model, pos, vel, types, box, n_steps, dt, n_threads=0):
     if rc != 0:
         raise ValueError("oracle_md failed")
     return pos, vel, thermo, F
+
+
+# --------------------------------------------------------------------------- Eq. loss
+def virial6(w9) -> np.ndarray:
+    """The six virial components of Eq. loss (xx, yy, zz, xy, yz, zx) as the symmetric part of
+    a 3x3 virial given in the order xx, yy, zz, xy, xz, yz, yx, zx, zy."""
+    w = np.asarray(w9, dtype=np.float64).reshape(-1, 9)
+    return np.stack([w[:, 0], w[:, 1], w[:, 2], 0.5 * (w[:, 3] + w[:, 6]), 0.5 * (w[:, 5] + w[:, 8]),
+                     0.5 * (w[:, 4] + w[:, 7])], axis=1)
+
+
+def eq_loss(e_pred, e_tar, f_pred, f_tar, z, lambdas, w_pred=None, w_tar=None):
+    """Eq. loss of Sec. III for one candidate z, written out term by term.
+
+    e_pred, e_tar: energy per atom of each (non-empty) structure [S]; f_pred, f_tar: forces
+    of all N atoms [N, 3]; w_pred, w_tar: virial per atom [S, 6] (``virial6`` order) or None;
+    lambdas = (lambda_e, lambda_f, lambda_v, lambda_1, lambda_2). The energy and virial terms
+    are root mean squares over structures (the virial also over its 6 components), the force
+    term over the 3N components, the regularisers the mean |z| and the root mean z^2.
+    Returns (L, RMSE_E, RMSE_F, RMSE_W, l1, l2)."""
+    e_pred = np.asarray(e_pred, dtype=np.float64)
+    e_tar = np.asarray(e_tar, dtype=np.float64)
+    n_str = e_pred.shape[0]
+    rmse_e = math.sqrt(np.sum((e_pred - e_tar) ** 2) / n_str) if n_str else 0.0
+    df = np.asarray(f_pred, dtype=np.float64) - np.asarray(f_tar, dtype=np.float64)
+    n_atoms = df.reshape(-1, 3).shape[0]
+    rmse_f = math.sqrt(np.sum(df ** 2) / (3 * n_atoms)) if n_atoms else 0.0
+    rmse_w = 0.0
+    if w_pred is not None and w_tar is not None and n_str:
+        dw = np.asarray(w_pred, dtype=np.float64) - np.asarray(w_tar, dtype=np.float64)
+        rmse_w = math.sqrt(np.sum(dw ** 2) / (6 * n_str))
+    z = np.asarray(z, dtype=np.float64).reshape(-1)
+    l1 = float(np.sum(np.abs(z)) / z.shape[0])
+    l2 = math.sqrt(float(np.sum(z ** 2)) / z.shape[0])
+    le, lf, lv, c1, c2 = (float(x) for x in lambdas)
+    total = le * rmse_e + lf * rmse_f + lv * rmse_w + c1 * l1 + c2 * l2
+    return total, rmse_e, rmse_f, rmse_w, l1, l2
+
+
+def batch_predictions(model, offsets, pos, types, boxes, n_threads=0):
+    """Oracle energy per atom [S], forces [N, 3] and virial per atom [S, 6] of every structure
+    of a batch (structure s owns atoms offsets[s]..offsets[s+1]); empty structures give 0."""
+    offsets = np.asarray(offsets)
+    ns = offsets.shape[0] - 1
+    e = np.zeros(ns)
+    w = np.zeros((ns, 6))
+    F = np.zeros((int(offsets[-1]), 3))
+    for s in range(ns):
+        a, b = int(offsets[s]), int(offsets[s + 1])
+        if b == a:
+            continue
+        U, Fs, Ws = compute(model, pos[a:b], types[a:b], boxes[s], n_threads=n_threads)
+        e[s] = U.sum() / (b - a)
+        F[a:b] = Fs
+        w[s] = virial6(Ws.sum(0))[0] / (b - a)
+    return e, F, w

@@ -217,6 +217,19 @@ namespace nep {
 void set_create_error(const char *msg) { g_create_error = msg ? msg : ""; }
 }  // namespace nep
 
+// Identity of a captured batch graph: every array it touches and the list capacities.
+struct BatchKey {
+  const void *p[16];
+  long long gen;
+  int N, cap_r, cap_a, precision;
+};
+
+// Launch shapes chosen by the autotuner (0 = automatic).
+struct Tuning {
+  int members = 0;       // population members per launch (grid.y)
+  int last_members = 0;  // members per launch of the last population evaluation
+};
+
 struct nep_handle {
   // model
   int T = 0, nR = 0, nA = 0, KR = 0, KA = 0, L3 = 0, L4 = 0, L5 = 0, H = 0, n_des = 0;
@@ -268,6 +281,14 @@ struct nep_handle {
   DevBuf<Grid> d_grids;
   DevBuf<int> d_sid, d_offsets;
   DevBuf<double> b_e, b_w;  // caller-order per-atom energies and virials when the caller keeps none
+  long long b_gen = 0;      // layout generation (bumped when the grids change)
+  cudaGraphExec_t b_graph = nullptr;
+  BatchKey b_key{}, b_last{};
+  // population evaluation: per-member kernel arrays and the sums of Eq. loss
+  DevBuf<float> pop_cr, pop_ca, pop_ann;
+  DevBuf<uint4> pop_tc;
+  DevBuf<double> pop_reg, pop_es, pop_ws;
+  Tuning tune;
   // profiling
   bool prof = false;
   cudaEvent_t ev[N_SLOTS][2] = {};
@@ -568,6 +589,7 @@ int setup_batch(nep_handle *h, int n_struct, const int *offsets, const double *b
     launch_shift_tables(n_struct, h->d_grids.p, ncode, obits, h->dtab.p, s);
     // the copies above read pageable host memory that changes on the next call
     CK(cudaStreamSynchronize(s), "batch setup");
+    h->b_gen += 1;
     h->b_offsets.assign(offsets, offsets + n_struct + 1);
     h->b_boxes.assign(boxes, boxes + 9 * (size_t)n_struct);
     h->nb_struct = n_struct;
@@ -584,6 +606,88 @@ Batch batch_of(nep_handle *h) {
   B.sid = h->d_sid.p;
   B.n = h->nb_struct;
   return B;
+}
+
+// Arrays of one batched evaluation.
+struct BatchOut {
+  const double *pos = nullptr;
+  const int *types = nullptr;
+  double *e_atom = nullptr, *w_atom = nullptr, *force = nullptr, *e_struct = nullptr, *w_struct = nullptr;
+};
+
+// Queue atom kernel, gather kernel and structure sums of a batch whose lists are built.
+int batch_kernels(nep_handle *h, int N, const BatchOut &o, cudaStream_t s, bool capturing) {
+  AtomArgs a = make_args(h, N);
+  a.energy = o.e_atom;
+  a.force = o.force;
+  a.virial = o.w_atom;
+  a.s_out = N;
+  ev_record(h, SLOT_ATOM, 0, s, capturing);
+  cudaError_t e = h->ops->atom_batch(a, h->mf, h->w0.data(), h->b0.data(), h->w1.data(), h->b1, 1, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "nep_atom kernel (batch)");
+  ev_record(h, SLOT_ATOM, 1, s, capturing);
+  ev_record(h, SLOT_GATHER, 0, s, capturing);
+  e = h->ops->gather_batch(a, 1, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "nep_gather kernel (batch)");
+  ev_record(h, SLOT_GATHER, 1, s, capturing);
+  ev_record(h, SLOT_FINAL, 0, s, capturing);
+  if (o.e_struct || o.w_struct)
+    launch_struct_sums(h->nb_struct, 1, h->d_offsets.p, N, o.e_struct ? o.e_atom : nullptr,
+                       o.w_struct ? o.w_atom : nullptr, o.e_struct, o.w_struct, s);
+  ev_record(h, SLOT_FINAL, 1, s, capturing);
+  CK(cudaGetLastError(), "structure sums");
+  return NEP_OK;
+}
+
+BatchKey batch_key(nep_handle *h, int N, const BatchOut &o) {
+  BatchKey k;
+  std::memset(&k, 0, sizeof(k));
+  const void *p[] = {o.pos, o.types, o.e_atom, o.w_atom, o.force, o.e_struct, o.w_struct, h->nl_r.p, h->nl_a.p,
+                     h->rev_a.p, h->p_ang.p, h->e_rad.p, h->x.p, h->dtab.p, h->d_grids.p, h->cell_start.p};
+  static_assert(sizeof(p) / sizeof(p[0]) == sizeof(k.p) / sizeof(k.p[0]), "key size");
+  for (size_t c = 0; c < sizeof(p) / sizeof(p[0]); ++c) k.p[c] = p[c];
+  k.gen = h->b_gen;
+  k.N = N;
+  k.cap_r = h->cap_r;
+  k.cap_a = h->cap_a;
+  k.precision = h->precision;
+  return k;
+}
+
+// Capture copy-in, forced neighbour build, kernels, structure sums and the status read of a
+// batch into one graph (replayed by the next identical call).
+int capture_batch(nep_handle *h, int N, const BatchOut &o, cudaStream_t s) {
+  if (h->b_graph) {
+    cudaGraphExecDestroy(h->b_graph);
+    h->b_graph = nullptr;
+  }
+  std::memset(&h->b_key, 0, sizeof(h->b_key));
+  CK(cudaStreamSynchronize(s), "sync");
+  cudaStream_t c = h->cap_stream;
+  CK(cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal), "capture");
+  cudaMemcpyAsync(h->x.p, o.pos, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, c);
+  cudaMemcpyAsync(h->types.p, o.types, sizeof(int) * N, cudaMemcpyDeviceToDevice, c);
+  launch_iota(N, h->perm.p, c);
+  launch_arm_rebuild(h->status.p, c);
+  const float rlR = (float)(h->rcR + h->skin), rlA = (float)(h->rcA + h->skin);
+  cudaError_t e = launch_rebuild(N, h->T, h->grid, batch_of(h), h->dtab.p, rlR * rlR, rlA * rlA, h->rcR2f(),
+                                 h->rcA2f(), atom_state(h), list_bufs(h), 0, h->status.p, c);
+  int rc = e == cudaSuccess ? batch_kernels(h, N, o, c, true) : cuda_fail(h, e, "batch rebuild");
+  if (!rc) cudaMemcpyAsync(h->h_status, h->status.p, sizeof(BuildStatus), cudaMemcpyDeviceToHost, c);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(c, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "end capture (batch)");
+  e = cudaGraphInstantiate(&h->b_graph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    h->b_graph = nullptr;
+    return cuda_fail(h, e, "graph instantiate (batch)");
+  }
+  return NEP_OK;
 }
 
 int check_offsets(nep_handle *h, int n_struct, const int *offsets) {
@@ -689,6 +793,9 @@ int nep_destroy(nep_handle *h) {
   h->thermo_ctl.release(); h->nl_r.release(); h->nl_a.release(); h->pos4.release(); h->dtab.release();
   h->p_ang.release(); h->e_rad.release(); h->status.release(); h->d_tc.release();
   h->d_grids.release(); h->d_sid.release(); h->d_offsets.release(); h->b_e.release(); h->b_w.release();
+  if (h->b_graph) cudaGraphExecDestroy(h->b_graph);
+  h->pop_cr.release(); h->pop_ca.release(); h->pop_ann.release(); h->pop_tc.release(); h->pop_reg.release();
+  h->pop_es.release(); h->pop_ws.release();
   delete h;
   return NEP_OK;
 }
@@ -743,47 +850,186 @@ int nep_compute_batch(nep_handle *h, int n_struct, const int *offsets, const dou
     if (virial_struct && n_struct) CK(cudaMemsetAsync(virial_struct, 0, 9 * sizeof(double) * n_struct, s), "memset");
     return NEP_OK;
   }
-  ev_record(h, SLOT_REBUILD, 0, s, false);
   rc = setup_batch(h, n_struct, offsets, boxes, N, s);
   if (rc) return rc;
+  BatchOut o;
+  o.pos = pos;
+  o.types = types;
+  o.e_atom = energy;
+  o.w_atom = virial;
+  o.force = force;
+  o.e_struct = energy_struct;
+  o.w_struct = virial_struct;
+  if (!o.e_atom && energy_struct) {
+    CK(h->b_e.ensure(N), "alloc");
+    o.e_atom = h->b_e.p;
+  }
+  if (!o.w_atom && virial_struct) {
+    CK(h->b_w.ensure(9 * (size_t)N), "alloc");
+    o.w_atom = h->b_w.p;
+  }
+  // a repeated call (same layout, arrays and list capacities) replays one captured graph:
+  // copy-in, neighbour build, both kernels and the structure sums, then one status read
+  BatchKey key = batch_key(h, N, o);
+  if (!h->prof && h->b_graph && std::memcmp(&key, &h->b_key, sizeof(key)) == 0) {
+    CK(cudaGraphLaunch(h->b_graph, s), "batch graph launch");
+    CK(cudaStreamSynchronize(s), "batch graph");
+    const BuildStatus &st = *h->h_status;
+    if (st.bad_input & 1) return fail(h, NEP_ERR_ARG, "atom type out of range");
+    if (st.bad_input & 2) return fail(h, NEP_ERR_NONFINITE, "non-finite position");
+    if (st.tc_timeout) return fail(h, NEP_ERR_TIMEOUT, "a tensor-core completion wait ran out");
+    if (!st.overflow && !st.rev_missing) return NEP_OK;
+    // the lists outgrew their capacity: size them again on the eager path below
+  }
+  ev_record(h, SLOT_REBUILD, 0, s, false);
   CK(cudaMemcpyAsync(h->x.p, pos, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s), "copy pos");
   CK(cudaMemcpyAsync(h->types.p, types, sizeof(int) * N, cudaMemcpyDeviceToDevice, s), "copy types");
   launch_iota(N, h->perm.p, s);
   h->N = N;
   h->stats_cache.n_atoms = N;
   for (int a = 0; a < 3; ++a) h->stats_cache.cells[a] = 0;
-  const Batch B = batch_of(h);
-  rc = rebuild_lists(h, N, s, B);
+  rc = rebuild_lists(h, N, s, batch_of(h));
   if (rc) return rc;
   ev_record(h, SLOT_REBUILD, 1, s, false);
-  double *e_atom = energy, *w_atom = virial;
-  if (!e_atom && energy_struct) {
-    CK(h->b_e.ensure(N), "alloc");
-    e_atom = h->b_e.p;
+  rc = batch_kernels(h, N, o, s, false);
+  if (rc) return rc;
+  if (!h->prof) {
+    key = batch_key(h, N, o);
+    if (std::memcmp(&key, &h->b_last, sizeof(key)) == 0) {
+      rc = capture_batch(h, N, o, s);  // the second identical call: capture for the next ones
+      if (rc) return rc;
+      h->b_key = key;
+    }
+    h->b_last = key;
   }
-  if (!w_atom && virial_struct) {
-    CK(h->b_w.ensure(9 * (size_t)N), "alloc");
-    w_atom = h->b_w.p;
+  return NEP_OK;
+}
+
+int nep_n_par(const nep_handle *h) {
+  if (!valid_handle(h)) return NEP_ERR_ARG;
+  const int T2 = h->T * h->T;
+  return T2 * (h->nR + 1) * (h->KR + 1) + T2 * (h->nA + 1) * (h->KA + 1) + h->H * h->n_des + 2 * h->H + 1;
+}
+
+int nep_eval_population(nep_handle *h, int n_pop, const double *z, int n_struct, const int *offsets,
+                        const double *pos, const int *types, const double *boxes, const double *e_tar,
+                        const double *f_tar, const double *w_tar, const double *lambda, double *loss,
+                        nep_stream_t stream) {
+  if (!valid_handle(h)) return NEP_ERR_ARG;
+  h->err.clear();
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = check_offsets(h, n_struct, offsets);
+  if (rc) return rc;
+  if (n_pop < 0) return fail(h, NEP_ERR_ARG, "n_pop < 0");
+  if (n_pop == 0) return NEP_OK;
+  const int N = n_struct > 0 ? offsets[n_struct] : 0;
+  if (N == 0) return fail(h, NEP_ERR_ARG, "the structure set holds no atoms");
+  if (!z || !boxes || !pos || !types || !e_tar || !f_tar || !lambda || !loss)
+    return fail(h, NEP_ERR_ARG, "z, boxes, pos, types, e_tar, f_tar, lambda and loss are required");
+  for (int c = 0; c < 5; ++c)
+    if (!std::isfinite(lambda[c])) return fail(h, NEP_ERR_ARG, "non-finite lambda");
+  h->md_ready = false;
+  for (int sl = 0; sl < N_SLOTS; ++sl) h->slot_ran[sl] = false;
+  rc = setup_batch(h, n_struct, offsets, boxes, N, s);
+  if (rc) return rc;
+  ev_record(h, SLOT_REBUILD, 0, s, false);
+  CK(cudaMemcpyAsync(h->x.p, pos, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s), "copy pos");
+  CK(cudaMemcpyAsync(h->types.p, types, sizeof(int) * N, cudaMemcpyDeviceToDevice, s), "copy types");
+  launch_iota(N, h->perm.p, s);
+  h->N = N;
+  h->stats_cache.n_atoms = N;
+  rc = rebuild_lists(h, N, s, batch_of(h));
+  if (rc) return rc;
+  ev_record(h, SLOT_REBUILD, 1, s, false);
+  // parameter vectors -> FP32 kernel arrays (and BF16 tiles for the tensor-core network)
+  const int T2 = h->T * h->T;
+  const int n_cr = T2 * (h->nR + 1) * (h->KR + 1), n_ca = T2 * (h->nA + 1) * (h->KA + 1);
+  const int n_par = nep_n_par(h), n_ann = n_par - n_cr - n_ca;
+  CK(h->pop_cr.ensure((size_t)n_pop * n_cr), "alloc population");
+  CK(h->pop_ca.ensure((size_t)n_pop * n_ca), "alloc population");
+  CK(h->pop_ann.ensure((size_t)n_pop * n_ann), "alloc population");
+  CK(h->pop_reg.ensure(2 * (size_t)n_pop), "alloc population");
+  launch_unpack_population(n_pop, z, n_par, n_cr, n_ca, h->pop_cr.p, h->pop_ca.p, h->pop_ann.p, h->pop_reg.p, s);
+  const long long s_tc = (long long)h->ops->np1 * h->ops->kp1 * 2 * 2 / 16;  // two tiles, uint4 units
+  if (h->precision == 1) {
+    CK(h->pop_tc.ensure((size_t)n_pop * s_tc), "alloc population");
+    CK(cudaMemsetAsync(h->pop_tc.p, 0, sizeof(uint4) * (size_t)n_pop * s_tc, s), "memset tiles");
+    launch_population_tiles(n_pop, h->pop_ann.p, n_ann, h->H, h->n_des, h->ops->kp1, h->ops->np1,
+                            reinterpret_cast<unsigned short *>(h->pop_tc.p), s);
   }
-  AtomArgs a = make_args(h, N);
-  a.energy = e_atom;
-  a.force = force;
-  a.virial = w_atom;
-  a.s_out = N;
-  ev_record(h, SLOT_ATOM, 0, s, false);
-  cudaError_t e = h->ops->atom_batch(a, h->mf, h->w0.data(), h->b0.data(), h->w1.data(), h->b1, 1, s);
-  if (e != cudaSuccess) return cuda_fail(h, e, "nep_atom kernel (batch)");
-  ev_record(h, SLOT_ATOM, 1, s, false);
-  ev_record(h, SLOT_GATHER, 0, s, false);
-  e = h->ops->gather_batch(a, 1, s);
-  if (e != cudaSuccess) return cuda_fail(h, e, "nep_gather kernel (batch)");
-  ev_record(h, SLOT_GATHER, 1, s, false);
-  ev_record(h, SLOT_FINAL, 0, s, false);
-  if (energy_struct || virial_struct)
-    launch_struct_sums(n_struct, 1, h->d_offsets.p, N, energy_struct ? e_atom : nullptr,
-                       virial_struct ? w_atom : nullptr, energy_struct, virial_struct, s);
-  ev_record(h, SLOT_FINAL, 1, s, false);
-  CK(cudaGetLastError(), "structure sums");
+  // members evaluated per launch (grid.y): the tuned value, else as many as the workspace
+  // budget holds
+  const int est = ((h->KR + 2) + 3) / 4 * 4;
+  const double per_member = 4.0 * N * h->T * est + 16.0 * h->cap_a * N + 8.0 * N + (w_tar ? 72.0 * N : 0.0) +
+                            80.0 * n_struct + 8.0 * kReduceSlots * (h->ops->gather_blocks(N) + h->ops->atom_blocks(N));
+  int pc = h->tune.members;
+  if (pc <= 0) {
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const double budget = std::min(0.5 * (double)free_b, 32.0 * (1ull << 30));
+    pc = (int)std::max(1.0, std::min((double)n_pop, budget / per_member));
+  }
+  pc = std::min(pc, n_pop);
+  const size_t nb_a = h->ops->atom_blocks(N), nb_g = h->ops->gather_blocks(N);
+  CK(h->e_rad.ensure((size_t)pc * N * h->T * est), "alloc population");
+  CK(h->p_ang.ensure((size_t)pc * h->cap_a * N), "alloc population");
+  CK(h->b_e.ensure((size_t)pc * N), "alloc population");
+  if (w_tar) CK(h->b_w.ensure((size_t)pc * N * 9), "alloc population");
+  CK(h->pop_es.ensure((size_t)pc * n_struct), "alloc population");
+  if (w_tar) CK(h->pop_ws.ensure((size_t)pc * n_struct * 9), "alloc population");
+  CK(h->partial_atom.ensure(pc * nb_a + 1), "alloc population");
+  CK(h->partial_gather.ensure((pc * nb_g + 1) * kReduceSlots), "alloc population");
+  for (int p0 = 0; p0 < n_pop; p0 += pc) {
+    const int m = std::min(pc, n_pop - p0);
+    AtomArgs a = make_args(h, N);
+    a.energy = h->b_e.p;
+    a.force = nullptr;
+    a.virial = w_tar ? h->b_w.p : nullptr;
+    a.s_out = N;
+    a.c_r = h->pop_cr.p + (size_t)p0 * n_cr;
+    a.s_cr = n_cr;
+    a.c_a = h->pop_ca.p + (size_t)p0 * n_ca;
+    a.s_ca = n_ca;
+    a.pop_ann = h->pop_ann.p + (size_t)p0 * n_ann;
+    a.s_ann = n_ann;
+    a.pop_tc = h->precision == 1 ? h->pop_tc.p + (size_t)p0 * s_tc : nullptr;
+    a.s_tc = s_tc;
+    a.s_erad = (long long)N * h->T * est;
+    a.s_pang = (long long)h->cap_a * N;
+    a.f_tar = f_tar;
+    ev_record(h, SLOT_ATOM, 0, s, false);
+    cudaError_t e = h->ops->atom_batch(a, h->mf, nullptr, nullptr, nullptr, 0.f, m, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "nep_atom kernel (population)");
+    ev_record(h, SLOT_ATOM, 1, s, false);
+    ev_record(h, SLOT_GATHER, 0, s, false);
+    e = h->ops->gather_batch(a, m, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "nep_gather kernel (population)");
+    ev_record(h, SLOT_GATHER, 1, s, false);
+    ev_record(h, SLOT_FINAL, 0, s, false);
+    launch_struct_sums(n_struct, m, h->d_offsets.p, N, h->b_e.p, w_tar ? h->b_w.p : nullptr, h->pop_es.p,
+                       w_tar ? h->pop_ws.p : nullptr, s);
+    launch_population_loss(m, n_struct, h->d_offsets.p, h->pop_es.p, w_tar ? h->pop_ws.p : nullptr, e_tar, w_tar,
+                           h->partial_gather.p, (int)nb_g, N, h->pop_reg.p + 2 * (size_t)p0, n_par, lambda,
+                           loss + 6 * (size_t)p0, s);
+    ev_record(h, SLOT_FINAL, 1, s, false);
+    CK(cudaGetLastError(), "population loss");
+  }
+  h->tune.last_members = pc;
+  return NEP_OK;
+}
+
+int nep_set_tuning(nep_handle *h, const nep_tuning *t) {
+  if (!valid_handle(h) || !t) return NEP_ERR_ARG;
+  if (t->members_per_launch < 0 || t->members_per_launch > 65535)
+    return fail(h, NEP_ERR_ARG, "members_per_launch must be in 0..65535");
+  h->tune.members = t->members_per_launch;
+  return NEP_OK;
+}
+
+int nep_get_tuning(const nep_handle *h, nep_tuning *t) {
+  if (!valid_handle(h) || !t) return NEP_ERR_ARG;
+  t->members_per_launch = h->tune.members;
+  t->last_members = h->tune.last_members;
   return NEP_OK;
 }
 

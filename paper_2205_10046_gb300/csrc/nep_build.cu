@@ -18,6 +18,8 @@
 //                  manipulations").
 // Every builder returns early unless a rebuild is pending, so the whole sequence sits in the
 // captured MD step graph and only works when an atom moved more than skin/2.
+#include <cuda_bf16.h>
+
 #include "nep_internal.cuh"
 
 namespace nep {
@@ -479,6 +481,150 @@ __global__ void struct_sums_kernel(int n_struct, int members, const int *offsets
     if (w_struct)
       for (int c = 0; c < 9; ++c) w_struct[9 * ((size_t)m * n_struct + s) + c] = acc[1 + c];
   }
+}
+
+// Marks a rebuild as pending and clears the per-build flags (the device form of the host
+// reset before a forced rebuild, for captured graphs).
+__global__ void arm_rebuild_kernel(BuildStatus *st) {
+  st->overflow = 0;
+  st->max_r = 0;
+  st->max_a = 0;
+  st->rev_missing = 0;
+  st->bad_input = 0;
+  st->rebuild = 1;
+}
+
+// ------------------------------------------------------------------ population evaluation
+// Candidate parameter vectors z [P][N_par], in the order c^R, c^A, w0, b0, w1, b1, become
+// the FP32 arrays of the batched kernels (c^R, c^A and the network [w0 | b0 | w1 | b1]);
+// reg[m] = (sum |z|, sum z^2) for the regularisation terms of Eq. loss. One block per member.
+__global__ void unpack_population_kernel(const double *z, int n_par, int n_cr, int n_ca, float *cr, float *ca,
+                                         float *ann, double *reg) {
+  const int m = blockIdx.x;
+  const int n_ann = n_par - n_cr - n_ca;
+  const double *zm = z + (size_t)m * n_par;
+  double s1 = 0.0, s2 = 0.0;
+  for (int v = threadIdx.x; v < n_par; v += blockDim.x) {
+    const double x = zm[v];
+    s1 += fabs(x);
+    s2 += x * x;
+    if (v < n_cr) cr[(size_t)m * n_cr + v] = (float)x;
+    else if (v < n_cr + n_ca) ca[(size_t)m * n_ca + (v - n_cr)] = (float)x;
+    else ann[(size_t)m * n_ann + (v - n_cr - n_ca)] = (float)x;
+  }
+  __shared__ double r1[256], r2[256];
+  r1[threadIdx.x] = s1;
+  r2[threadIdx.x] = s2;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      r1[threadIdx.x] += r1[threadIdx.x + o];
+      r2[threadIdx.x] += r2[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    reg[2 * m] = r1[0];
+    reg[2 * m + 1] = r2[0];
+  }
+}
+
+// BF16 operand tiles of every member's w0 (the layout of the single-model tiles): tile 1
+// [NP1 x KP1] holds (mu, nu) -> w0[mu][nu], tile 2 [KP1 x NP1] holds (nu, mu) -> w0[mu][nu].
+// The tiles must be zeroed before (padding).
+__global__ void population_tiles_kernel(int n_pop, const float *ann, int n_ann, int H, int D, int KP1, int NP1,
+                                        unsigned short *tiles) {
+  const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= (long long)n_pop * H * D) return;
+  const int m = (int)(v / ((long long)H * D));
+  const int r = (int)(v % ((long long)H * D));
+  const int mu = r / D, nu = r % D;
+  const unsigned short b = __bfloat16_as_ushort(__float2bfloat16_rn(ann[(size_t)m * n_ann + r]));
+  unsigned short *t1 = tiles + (size_t)m * 2 * NP1 * KP1, *t2 = t1 + (size_t)NP1 * KP1;
+  auto off = [](int row, int k, int kc) { return ((row / 8) * kc + k / 8) * 64 + (row % 8) * 8 + (k % 8); };
+  t1[off(mu, nu, KP1 / 8)] = b;
+  t2[off(nu, mu, NP1 / 8)] = b;
+}
+
+// Eq. loss for `members` candidates (one block each, fixed-order sums): RMSE of the energy
+// per atom over the non-empty structures, RMSE of the force components (from the gather
+// kernel's per-block sums), RMSE of the six virial components per atom (symmetric part of
+// W_s / N_s; skipped without targets), and the l1 / l2 regularisation of z.
+// loss[m] = (L, RMSE_E, RMSE_F, RMSE_W, sum|z| / N_par, sqrt(sum z^2 / N_par)).
+__global__ void population_loss_kernel(int n_struct, const int *offsets, const double *e_struct,
+                                       const double *w_struct, const double *e_tar, const double *w_tar,
+                                       const double *partial_gather, int nb_gather, int N, const double *reg,
+                                       int n_par, double le, double lf, double lv, double l1, double l2,
+                                       double *loss) {
+  const int m = blockIdx.x;
+  double se = 0.0, sv = 0.0, sf = 0.0, cnt = 0.0;
+  for (int s = threadIdx.x; s < n_struct; s += blockDim.x) {
+    const int n = offsets[s + 1] - offsets[s];
+    if (n <= 0) continue;
+    cnt += 1.0;
+    const double inv = 1.0 / n;
+    const double de = e_struct[(size_t)m * n_struct + s] * inv - e_tar[s];
+    se += de * de;
+    if (w_struct && w_tar) {
+      const double *w = w_struct + 9 * ((size_t)m * n_struct + s);
+      const double sym[6] = {w[0], w[1], w[2], 0.5 * (w[3] + w[6]), 0.5 * (w[5] + w[8]), 0.5 * (w[4] + w[7])};
+      for (int c = 0; c < 6; ++c) {
+        const double dw = sym[c] * inv - w_tar[6 * (size_t)s + c];
+        sv += dw * dw;
+      }
+    }
+  }
+  for (int b = threadIdx.x; b < nb_gather; b += blockDim.x)
+    sf += partial_gather[((size_t)m * nb_gather + b) * kReduceSlots + 11];
+  __shared__ double red[4][256];
+  red[0][threadIdx.x] = se;
+  red[1][threadIdx.x] = sv;
+  red[2][threadIdx.x] = sf;
+  red[3][threadIdx.x] = cnt;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int c = 0; c < 4; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double ns = red[3][0];
+    const double rmse_e = ns > 0 ? sqrt(red[0][0] / ns) : 0.0;
+    const double rmse_w = (ns > 0 && w_struct && w_tar) ? sqrt(red[1][0] / (6.0 * ns)) : 0.0;
+    const double rmse_f = N > 0 ? sqrt(red[2][0] / (3.0 * N)) : 0.0;
+    const double r1 = reg[2 * m] / n_par, r2 = sqrt(reg[2 * m + 1] / n_par);
+    double *o = loss + 6 * (size_t)m;
+    o[0] = le * rmse_e + lf * rmse_f + lv * rmse_w + l1 * r1 + l2 * r2;
+    o[1] = rmse_e;
+    o[2] = rmse_f;
+    o[3] = rmse_w;
+    o[4] = r1;
+    o[5] = r2;
+  }
+}
+
+void launch_arm_rebuild(BuildStatus *st, cudaStream_t s) { arm_rebuild_kernel<<<1, 1, 0, s>>>(st); }
+
+void launch_unpack_population(int n_pop, const double *z, int n_par, int n_cr, int n_ca, float *cr, float *ca,
+                              float *ann, double *reg, cudaStream_t s) {
+  if (n_pop > 0) unpack_population_kernel<<<n_pop, 256, 0, s>>>(z, n_par, n_cr, n_ca, cr, ca, ann, reg);
+}
+
+void launch_population_tiles(int n_pop, const float *ann, int n_ann, int H, int D, int KP1, int NP1,
+                             unsigned short *tiles, cudaStream_t s) {
+  const long long n = (long long)n_pop * H * D;
+  if (n > 0)
+    population_tiles_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n_pop, ann, n_ann, H, D, KP1, NP1, tiles);
+}
+
+void launch_population_loss(int members, int n_struct, const int *offsets, const double *e_struct,
+                            const double *w_struct, const double *e_tar, const double *w_tar,
+                            const double *partial_gather, int nb_gather, int N, const double *reg, int n_par,
+                            const double *lambda, double *loss, cudaStream_t s) {
+  if (members > 0)
+    population_loss_kernel<<<members, 256, 0, s>>>(n_struct, offsets, e_struct, w_struct, e_tar, w_tar,
+                                                    partial_gather, nb_gather, N, reg, n_par, lambda[0], lambda[1],
+                                                    lambda[2], lambda[3], lambda[4], loss);
 }
 
 void launch_struct_ids(int n_struct, const int *offsets, int *sid, cudaStream_t s) {

@@ -10,7 +10,7 @@ constexpr int kListBuf = 512;   // largest neighbour-list capacity per atom
 constexpr int kMaxImage = 3;    // largest cell/image offset searched per axis
 constexpr int kAtomBlock = 128; // threads per block of the per-atom kernel
 constexpr int kGatherBlock = 128;
-constexpr int kReduceSlots = 12; // per-block partial sums: U, KE, W[9], spare
+constexpr int kReduceSlots = 12; // per-block partial sums: U, KE, W[9], force error
 
 // Geometry of one neighbour build: the cell grid, the packing of list entries and the
 // table of pair shift vectors indexed by the packed image code.
@@ -133,6 +133,7 @@ struct AtomArgs {
   long long s_cr, s_ca, s_ann, s_tc;  // strides of c_r, c_a, pop_ann, pop_tc
   long long s_erad, s_pang;           // strides of e_rad, p_ang
   long long s_out;                    // atoms per member in energy (x1), force (x3), virial (x9)
+  const double *f_tar;     // [N][3] caller order, or null: sum of (F_i - F_tar,i)^2 per block
 };
 
 // Model constants of one handle, FP32.
@@ -177,5 +178,15 @@ void launch_struct_ids(int n_struct, const int *offsets, int *sid, cudaStream_t 
 void launch_shift_tables(int n_struct, const Grid *grids, int ncode, int obits, float4 *dtab, cudaStream_t s);
 void launch_struct_sums(int n_struct, int members, const int *offsets, int N, const double *e_atom,
                         const double *w_atom, double *e_struct, double *w_struct, cudaStream_t s);
+void launch_arm_rebuild(BuildStatus *st, cudaStream_t s);
+// population evaluation: parameter vectors into kernel arrays, BF16 tiles, Eq. loss
+void launch_unpack_population(int n_pop, const double *z, int n_par, int n_cr, int n_ca, float *cr, float *ca,
+                              float *ann, double *reg, cudaStream_t s);
+void launch_population_tiles(int n_pop, const float *ann, int n_ann, int H, int D, int KP1, int NP1,
+                             unsigned short *tiles, cudaStream_t s);
+void launch_population_loss(int members, int n_struct, const int *offsets, const double *e_struct,
+                            const double *w_struct, const double *e_tar, const double *w_tar,
+                            const double *partial_gather, int nb_gather, int N, const double *reg, int n_par,
+                            const double *lambda, double *loss, cudaStream_t s);
 
 }  // namespace nep

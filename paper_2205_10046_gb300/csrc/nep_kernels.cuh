@@ -934,6 +934,11 @@ __global__ void __launch_bounds__(kGatherBlock)
     }
 #pragma unroll
     for (int c = 0; c < 9; ++c) part[2 + c] = (double)w[c];
+    if (a.f_tar) {  // squared force error against target forces (the force term of Eq. loss)
+      const double *ft = a.f_tar + 3 * (a.perm ? (size_t)a.perm[i] : (size_t)i);
+      const double ex = Fx - ft[0], ey = Fy - ft[1], ez = Fz - ft[2];
+      part[11] = ex * ex + ey * ey + ez * ez;
+    }
     if (a.md_kick) {  // second half-kick of velocity Verlet, and kinetic energy
       double *v = a.vel + 3 * (size_t)i;
       const double s = a.half_dt * a.inv_mass_kappa[ti];
@@ -942,17 +947,17 @@ __global__ void __launch_bounds__(kGatherBlock)
       part[1] = a.mass_kappa_half[ti] * (vx * vx + vy * vy + vz * vz);
     }
   }
-  // deterministic block sums of (spare, KE, W[9])
+  // deterministic block sums of (KE, W[9], force error)
   __shared__ double red[kGatherBlock / 32][kReduceSlots];
 #pragma unroll
-  for (int s = 1; s < 11; ++s) {
+  for (int s = 1; s < kReduceSlots; ++s) {
     double v = part[s];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][s] = v;
   }
   __syncthreads();
-  if (threadIdx.x < 11 && threadIdx.x >= 1) {
+  if (threadIdx.x < kReduceSlots && threadIdx.x >= 1) {
     double s = 0.0;
     for (int wv = 0; wv < kGatherBlock / 32; ++wv) s += red[wv][threadIdx.x];
     a.partial_gather[((size_t)mem * gridDim.x + blockIdx.x) * kReduceSlots + threadIdx.x] = s;

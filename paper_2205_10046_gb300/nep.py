@@ -45,6 +45,10 @@ class nep_stats(C.Structure):
                 ("rebuild_kernels", C.c_int)]
 
 
+class nep_tuning(C.Structure):
+    _fields_ = [("members_per_launch", C.c_int), ("last_members", C.c_int)]
+
+
 _lib = None
 
 # exported symbol -> (restype, argtypes)
@@ -56,6 +60,10 @@ _SIGS = {
     "nep_compute": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "nep_compute_host": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P, _P, _P]),
     "nep_compute_batch": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "nep_n_par": (C.c_int, [_P]),
+    "nep_eval_population": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "nep_set_tuning": (C.c_int, [_P, C.POINTER(nep_tuning)]),
+    "nep_get_tuning": (C.c_int, [_P, C.POINTER(nep_tuning)]),
     "nep_descriptors": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P]),
     "nep_n_des": (C.c_int, [_P]),
     "md_init": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P]),
@@ -219,6 +227,46 @@ def nep_compute_batch(h, offsets, pos, types, boxes, energy=None, energy_struct=
                                   _dev(virial, torch.float64, (n, 9), "virial"),
                                   _dev(virial_struct, torch.float64, (ns, 9), "virial_struct"), _stream())
     _check(rc, h)
+
+
+def nep_n_par(h) -> int:
+    return int(load().nep_n_par(h))
+
+
+def nep_eval_population(h, z, offsets, pos, types, boxes, e_tar, f_tar, w_tar=None, lambdas=(1.0, 1.0, 0.0, 0.0, 0.0),
+                        loss=None):
+    """Eq. loss for each candidate vector: z [P, N_par] f64 CUDA; structure set as
+    nep_compute_batch; targets e_tar [S] (eV/atom), f_tar [N,3], w_tar [S,6] or None.
+    Returns loss [P, 6] (CUDA): L, RMSE_E, RMSE_F, RMSE_W, l1 term, l2 term."""
+    import torch
+    off = _offsets(offsets)
+    ns = off.shape[0] - 1
+    n = int(off[-1]) if ns > 0 else 0
+    bx = _boxes(boxes, ns)
+    npop = int(z.shape[0])
+    npar = nep_n_par(h)
+    if loss is None:
+        loss = torch.empty((npop, 6), dtype=torch.float64, device=z.device)
+    lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64).reshape(5))
+    rc = load().nep_eval_population(h, npop, _dev(z, torch.float64, (npop, npar), "z"), ns, off.ctypes.data,
+                                    _dev(pos, torch.float64, (n, 3), "pos"), _dev(types, torch.int32, (n,), "types"),
+                                    bx.ctypes.data, _dev(e_tar, torch.float64, (ns,), "e_tar"),
+                                    _dev(f_tar, torch.float64, (n, 3), "f_tar"),
+                                    _dev(w_tar, torch.float64, (ns, 6), "w_tar"), lam.ctypes.data,
+                                    _dev(loss, torch.float64, (npop, 6), "loss"), _stream())
+    _check(rc, h)
+    return loss
+
+
+def nep_set_tuning(h, members_per_launch: int = 0):
+    t = nep_tuning(int(members_per_launch), 0)
+    _check(load().nep_set_tuning(h, C.byref(t)), h)
+
+
+def nep_get_tuning(h) -> dict:
+    t = nep_tuning()
+    _check(load().nep_get_tuning(h, C.byref(t)), h)
+    return {f: getattr(t, f) for f, _ in nep_tuning._fields_}
 
 
 def nep_descriptors(h, pos, types, box, q):

@@ -93,6 +93,25 @@ class NepModel:
         return np.concatenate([self.c_radial.ravel(), self.c_angular.ravel(), self.w0.ravel(),
                                self.b0.ravel(), self.w1.ravel(), np.array([self.b1])])
 
+    def with_vector(self, z) -> "NepModel":
+        """A model with these hyper-parameters and masses and the parameters z (to_vector order)."""
+        z = np.asarray(z, dtype=np.float64).reshape(-1)
+        if z.shape[0] != self.n_par:
+            raise ValueError(f"z has {z.shape[0]} values, N_par = {self.n_par}")
+        T, nR, nA, KR, KA, H, D = (self.n_types, self.n_max_radial, self.n_max_angular, self.basis_radial,
+                                   self.basis_angular, self.n_neuron, self.n_des)
+        m = NepModel(**self.hyper())
+        sizes = [T * T * (nR + 1) * (KR + 1), T * T * (nA + 1) * (KA + 1), H * D, H, H, 1]
+        parts = np.split(z, np.cumsum(sizes)[:-1])
+        m.c_radial = parts[0].reshape(T, T, nR + 1, KR + 1).copy()
+        m.c_angular = parts[1].reshape(T, T, nA + 1, KA + 1).copy()
+        m.w0 = parts[2].reshape(H, D).copy()
+        m.b0 = parts[3].copy()
+        m.w1 = parts[4].copy()
+        m.b1 = float(parts[5][0])
+        m.mass = None if self.mass is None else np.array(self.mass)
+        return m
+
 
 def _rng(seed: int) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(int(seed)))

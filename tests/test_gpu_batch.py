@@ -199,3 +199,50 @@ def test_full_batch_sampled_structures(torch_cuda):
         U, F, Wv = oracle.compute(model, *b.structure(int(s)))
         _check_structure(g, b, int(s), U, F, Wv)
     h.close()
+
+
+def test_batch_graph_replay_and_regrow(torch_cuda):
+    """Repeated calls on the same arrays replay one captured graph; positions changed in
+    place are picked up; a structure compressed beyond the list capacity is caught by the
+    status read and evaluated again with grown lists."""
+    torch = torch_cuda
+    from paper_2205_10046_gb300 import nep
+    model = W.mixed_model(0)
+    b = W.batch_structures(16, seed=12, n_max=128)
+    h = nep.NEP(model)
+    p, t = _dev(torch, b)
+    n, ns = b.n_atoms, b.n_struct
+    f64 = dict(dtype=torch.float64, device="cuda")
+    out = dict(U=torch.empty(n, **f64), E_struct=torch.empty(ns, **f64), F=torch.empty((n, 3), **f64),
+               W=torch.empty((n, 9), **f64), W_struct=torch.empty((ns, 9), **f64))
+
+    def call():
+        nep.nep_compute_batch(h.h, b.offsets, p, t, b.boxes, out["U"], out["E_struct"], out["F"], out["W"],
+                              out["W_struct"])
+        torch.cuda.synchronize()
+        return {k: v.cpu().numpy().copy() for k, v in out.items()}
+
+    r0, r1 = call(), call()  # eager, eager + capture
+    for k in r0:
+        np.testing.assert_array_equal(r0[k], r1[k])
+    rng = np.random.default_rng(9)
+    pos2 = b.pos + rng.normal(0, 0.05, b.pos.shape)
+    p.copy_(torch.tensor(pos2, **f64))
+    r2, r3 = call(), call()  # replays
+    for k in r2:
+        np.testing.assert_array_equal(r2[k], r3[k])
+    b2 = W.Batch(b.offsets, pos2, b.types, b.boxes, b.seeds)
+    for s in (0, 7, 15):
+        U, F, Wv = oracle.compute(model, *b2.structure(s))
+        _check_structure(r2, b2, s, U, F, Wv)
+    # compress structure 3 towards its cell origin: about 4.6 times the neighbours per atom
+    a, e = int(b.offsets[3]), int(b.offsets[4])
+    pos3 = pos2.copy()
+    pos3[a:e] = 0.6 * pos2[a:e]
+    p.copy_(torch.tensor(pos3, **f64))
+    r4 = call()
+    b3 = W.Batch(b.offsets, pos3, b.types, b.boxes, b.seeds)
+    for s in (3, 4):
+        U, F, Wv = oracle.compute(model, *b3.structure(s))
+        _check_structure(r4, b3, s, U, F, Wv)
+    h.close()

@@ -1,0 +1,74 @@
+"""Pins of the oracle's Eq. loss (Sec. III) against closed forms."""
+import math
+
+import numpy as np
+
+import oracle
+from paper_2205_10046_gb300 import workloads as W
+
+
+def _targets(rng, ns=5, n=17):
+    return rng.normal(size=ns), rng.normal(size=(n, 3)), rng.normal(size=(ns, 6))
+
+
+def test_zero_error_leaves_only_the_regularisers():
+    rng = np.random.default_rng(0)
+    e, f, w = _targets(rng)
+    z = np.array([3.0, -4.0])
+    L, re, rf, rw, l1, l2 = oracle.eq_loss(e, e, f, f, z, (1, 1, 1, 0.5, 0.25), w, w)
+    assert re == rf == rw == 0.0
+    assert l1 == 3.5 and abs(l2 - math.sqrt(12.5)) < 1e-15
+    assert abs(L - (0.5 * 3.5 + 0.25 * math.sqrt(12.5))) < 1e-15
+
+
+def test_constant_offsets_give_their_magnitude():
+    rng = np.random.default_rng(1)
+    e, f, w = _targets(rng)
+    z = np.ones(4)
+    L, re, rf, rw, l1, l2 = oracle.eq_loss(e + 0.3, e, f + 0.2, f, z, (2.0, 3.0, 5.0, 0, 0), w - 0.1, w)
+    assert abs(re - 0.3) < 1e-14 and abs(rf - 0.2) < 1e-14 and abs(rw - 0.1) < 1e-14
+    assert abs(L - (2 * 0.3 + 3 * 0.2 + 5 * 0.1)) < 1e-13
+    assert l1 == 1.0 and l2 == 1.0
+
+
+def test_single_component_errors_are_normalised_by_their_counts():
+    # one wrong force component among 3N, one wrong virial component among 6 S
+    e, f, w = np.zeros(2), np.zeros((4, 3)), np.zeros((2, 6))
+    f2 = f.copy()
+    f2[3, 1] = 1.2
+    w2 = w.copy()
+    w2[1, 4] = -0.6
+    _, re, rf, rw, _, _ = oracle.eq_loss(e, e, f2, f, np.ones(1), (1, 1, 1, 0, 0), w2, w)
+    assert re == 0.0
+    assert abs(rf - 1.2 / math.sqrt(12)) < 1e-15
+    assert abs(rw - 0.6 / math.sqrt(12)) < 1e-15
+
+
+def test_virial6_is_the_symmetric_part():
+    a = np.arange(9, dtype=np.float64).reshape(3, 3)
+    order = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2), (1, 0), (2, 0), (2, 1)]
+    w9 = np.array([a[i, j] for i, j in order])
+    s = 0.5 * (a + a.T)
+    np.testing.assert_array_equal(oracle.virial6(w9)[0], [s[0, 0], s[1, 1], s[2, 2], s[0, 1], s[1, 2], s[2, 0]])
+
+
+def test_model_vector_round_trip():
+    m = W.mixed_model(3)
+    z = m.to_vector()
+    assert z.shape[0] == m.n_par
+    m2 = m.with_vector(z)
+    np.testing.assert_array_equal(m2.to_vector(), z)
+    np.testing.assert_array_equal(m2.w0, m.w0)
+    assert m2.b1 == m.b1
+
+
+def test_batch_predictions_match_single_structures():
+    m = W.mixed_model(0)
+    b = W.concat_structures([W.random_structure(1, 8), (np.zeros((0, 3)), np.zeros(0, np.int32), np.eye(3) * 9),
+                             W.random_structure(2, 12)])
+    e, F, w = oracle.batch_predictions(m, b.offsets, b.pos, b.types, b.boxes)
+    U, F2, W2 = oracle.compute(m, *b.structure(2))
+    assert abs(e[2] - U.sum() / 12) < 1e-15
+    np.testing.assert_array_equal(F[8:], F2)
+    assert e[1] == 0.0 and np.all(w[1] == 0.0)
+    np.testing.assert_allclose(w[2], oracle.virial6(W2.sum(0))[0] / 12, rtol=0, atol=1e-15)
