@@ -167,15 +167,31 @@ int nep_eval_population(nep_handle *h, int n_pop, const double *z, int n_struct,
                         const double *f_tar, const double *w_tar, const double *lambda, double *loss,
                         nep_stream_t stream);
 
-/* Launch shapes of the batched kernels. Zero fields select the defaults. */
+/* Launch shapes of the batched kernels (nep_compute_batch, nep_eval_population). Zero
+ * fields select the defaults. The shapes change the speed, not the per-atom results. */
 typedef struct {
   int members_per_launch; /* population members per launch (grid.y); 0: as many as a workspace
                              budget of min(half the free memory, 32 GiB) holds */
+  int atom_block;         /* atoms per CTA of the batched per-atom kernel: 64 or 128 (0: 128;
+                             the BF16 tensor-core network always uses 128-atom tiles) */
+  int gather_block;       /* atoms per CTA of the batched gather kernel: 64, 128, 256 (0: 128) */
   int last_members;       /* out: members per launch used by the last nep_eval_population */
+  int n_tried;            /* out: candidates timed by the last nep_autotune */
+  float best_ms;          /* out: time of one evaluation (per member) with the chosen shapes */
+  float default_ms;       /* out: the same with 128 / 128 atoms per CTA and one member */
 } nep_tuning;
 
+/* Set or read the launch shapes (NEP_ERR_ARG for values outside the lists above). */
 int nep_set_tuning(nep_handle *h, const nep_tuning *t);
 int nep_get_tuning(const nep_handle *h, nep_tuning *t);
+
+/* Autotuner: builds the neighbour lists of the structure set (arguments as
+ * nep_compute_batch), times the atom and gather kernels for every atoms-per-CTA pair (best of
+ * three launches after a warm-up, CUDA events on `stream`) and, when n_pop > 0, members per
+ * launch 1, 2, 4, ... up to n_pop (or the workspace budget) with the best pair; keeps the
+ * fastest shapes in the handle and returns them in *out (may be NULL). Synchronous. */
+int nep_autotune(nep_handle *h, int n_struct, const int *offsets, const double *pos, const int *types,
+                 const double *boxes, int n_pop, nep_tuning *out, nep_stream_t stream);
 
 /* Descriptor vectors q^i (Eqs. qin and S_nk with the explicit components of Sec. II D)
  * into q [N][N_des] FP64 (DEVICE pointers, as nep_compute). */

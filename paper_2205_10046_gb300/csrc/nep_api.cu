@@ -221,13 +221,17 @@ void set_create_error(const char *msg) { g_create_error = msg ? msg : ""; }
 struct BatchKey {
   const void *p[16];
   long long gen;
-  int N, cap_r, cap_a, precision;
+  int N, cap_r, cap_a, precision, blocks, pad;
 };
 
-// Launch shapes chosen by the autotuner (0 = automatic).
+// Launch shapes of the batched kernels, set by the caller or the autotuner (0 = default).
 struct Tuning {
   int members = 0;       // population members per launch (grid.y)
+  int atom_block = 0;    // atoms per CTA of the batched atom kernel (64, 128)
+  int gather_block = 0;  // atoms per CTA of the batched gather kernel (64, 128, 256)
   int last_members = 0;  // members per launch of the last population evaluation
+  int n_tried = 0;       // candidates timed by the last autotune
+  float best_ms = 0.f, default_ms = 0.f;  // per-evaluation times of the choice and of the defaults
 };
 
 struct nep_handle {
@@ -615,19 +619,33 @@ struct BatchOut {
   double *e_atom = nullptr, *w_atom = nullptr, *force = nullptr, *e_struct = nullptr, *w_struct = nullptr;
 };
 
+int atom_block(const nep_handle *h) { return (h->precision == 1 || h->tune.atom_block == 0) ? 128 : h->tune.atom_block; }
+int gather_block(const nep_handle *h) { return h->tune.gather_block == 0 ? 128 : h->tune.gather_block; }
+
+// Per-block partial sums of `members` batched evaluations.
+int ensure_partials(nep_handle *h, int N, int members) {
+  const size_t nb_a = (N + atom_block(h) - 1) / atom_block(h), nb_g = (N + gather_block(h) - 1) / gather_block(h);
+  CK(h->partial_atom.ensure((size_t)members * nb_a + 1), "alloc");
+  CK(h->partial_gather.ensure(((size_t)members * nb_g + 1) * kReduceSlots), "alloc");
+  return NEP_OK;
+}
+
 // Queue atom kernel, gather kernel and structure sums of a batch whose lists are built.
 int batch_kernels(nep_handle *h, int N, const BatchOut &o, cudaStream_t s, bool capturing) {
+  int rc = ensure_partials(h, N, 1);
+  if (rc) return rc;
   AtomArgs a = make_args(h, N);
   a.energy = o.e_atom;
   a.force = o.force;
   a.virial = o.w_atom;
   a.s_out = N;
   ev_record(h, SLOT_ATOM, 0, s, capturing);
-  cudaError_t e = h->ops->atom_batch(a, h->mf, h->w0.data(), h->b0.data(), h->w1.data(), h->b1, 1, s);
+  cudaError_t e =
+      h->ops->atom_batch(a, h->mf, h->w0.data(), h->b0.data(), h->w1.data(), h->b1, 1, atom_block(h), s);
   if (e != cudaSuccess) return cuda_fail(h, e, "nep_atom kernel (batch)");
   ev_record(h, SLOT_ATOM, 1, s, capturing);
   ev_record(h, SLOT_GATHER, 0, s, capturing);
-  e = h->ops->gather_batch(a, 1, s);
+  e = h->ops->gather_batch(a, 1, gather_block(h), s);
   if (e != cudaSuccess) return cuda_fail(h, e, "nep_gather kernel (batch)");
   ev_record(h, SLOT_GATHER, 1, s, capturing);
   ev_record(h, SLOT_FINAL, 0, s, capturing);
@@ -651,6 +669,7 @@ BatchKey batch_key(nep_handle *h, int N, const BatchOut &o) {
   k.cap_r = h->cap_r;
   k.cap_a = h->cap_a;
   k.precision = h->precision;
+  k.blocks = atom_block(h) * 1024 + gather_block(h);
   return k;
 }
 
@@ -961,7 +980,7 @@ int nep_eval_population(nep_handle *h, int n_pop, const double *z, int n_struct,
   // budget holds
   const int est = ((h->KR + 2) + 3) / 4 * 4;
   const double per_member = 4.0 * N * h->T * est + 16.0 * h->cap_a * N + 8.0 * N + (w_tar ? 72.0 * N : 0.0) +
-                            80.0 * n_struct + 8.0 * kReduceSlots * (h->ops->gather_blocks(N) + h->ops->atom_blocks(N));
+                            80.0 * n_struct + 8.0 * kReduceSlots * (N / 64.0 + 2);
   int pc = h->tune.members;
   if (pc <= 0) {
     size_t free_b = 0, total_b = 0;
@@ -970,15 +989,15 @@ int nep_eval_population(nep_handle *h, int n_pop, const double *z, int n_struct,
     pc = (int)std::max(1.0, std::min((double)n_pop, budget / per_member));
   }
   pc = std::min(pc, n_pop);
-  const size_t nb_a = h->ops->atom_blocks(N), nb_g = h->ops->gather_blocks(N);
+  const int nb_g = (N + gather_block(h) - 1) / gather_block(h);
   CK(h->e_rad.ensure((size_t)pc * N * h->T * est), "alloc population");
   CK(h->p_ang.ensure((size_t)pc * h->cap_a * N), "alloc population");
   CK(h->b_e.ensure((size_t)pc * N), "alloc population");
   if (w_tar) CK(h->b_w.ensure((size_t)pc * N * 9), "alloc population");
   CK(h->pop_es.ensure((size_t)pc * n_struct), "alloc population");
   if (w_tar) CK(h->pop_ws.ensure((size_t)pc * n_struct * 9), "alloc population");
-  CK(h->partial_atom.ensure(pc * nb_a + 1), "alloc population");
-  CK(h->partial_gather.ensure((pc * nb_g + 1) * kReduceSlots), "alloc population");
+  rc = ensure_partials(h, N, pc);
+  if (rc) return rc;
   for (int p0 = 0; p0 < n_pop; p0 += pc) {
     const int m = std::min(pc, n_pop - p0);
     AtomArgs a = make_args(h, N);
@@ -998,18 +1017,18 @@ int nep_eval_population(nep_handle *h, int n_pop, const double *z, int n_struct,
     a.s_pang = (long long)h->cap_a * N;
     a.f_tar = f_tar;
     ev_record(h, SLOT_ATOM, 0, s, false);
-    cudaError_t e = h->ops->atom_batch(a, h->mf, nullptr, nullptr, nullptr, 0.f, m, s);
+    cudaError_t e = h->ops->atom_batch(a, h->mf, nullptr, nullptr, nullptr, 0.f, m, atom_block(h), s);
     if (e != cudaSuccess) return cuda_fail(h, e, "nep_atom kernel (population)");
     ev_record(h, SLOT_ATOM, 1, s, false);
     ev_record(h, SLOT_GATHER, 0, s, false);
-    e = h->ops->gather_batch(a, m, s);
+    e = h->ops->gather_batch(a, m, gather_block(h), s);
     if (e != cudaSuccess) return cuda_fail(h, e, "nep_gather kernel (population)");
     ev_record(h, SLOT_GATHER, 1, s, false);
     ev_record(h, SLOT_FINAL, 0, s, false);
     launch_struct_sums(n_struct, m, h->d_offsets.p, N, h->b_e.p, w_tar ? h->b_w.p : nullptr, h->pop_es.p,
                        w_tar ? h->pop_ws.p : nullptr, s);
     launch_population_loss(m, n_struct, h->d_offsets.p, h->pop_es.p, w_tar ? h->pop_ws.p : nullptr, e_tar, w_tar,
-                           h->partial_gather.p, (int)nb_g, N, h->pop_reg.p + 2 * (size_t)p0, n_par, lambda,
+                           h->partial_gather.p, nb_g, N, h->pop_reg.p + 2 * (size_t)p0, n_par, lambda,
                            loss + 6 * (size_t)p0, s);
     ev_record(h, SLOT_FINAL, 1, s, false);
     CK(cudaGetLastError(), "population loss");
@@ -1018,18 +1037,137 @@ int nep_eval_population(nep_handle *h, int n_pop, const double *z, int n_struct,
   return NEP_OK;
 }
 
+int nep_autotune(nep_handle *h, int n_struct, const int *offsets, const double *pos, const int *types,
+                 const double *boxes, int n_pop, nep_tuning *out, nep_stream_t stream) {
+  if (!valid_handle(h)) return NEP_ERR_ARG;
+  h->err.clear();
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = check_offsets(h, n_struct, offsets);
+  if (rc) return rc;
+  const int N = n_struct > 0 ? offsets[n_struct] : 0;
+  if (N == 0 || !boxes || !pos || !types) return fail(h, NEP_ERR_ARG, "autotune needs a non-empty structure set");
+  if (n_pop < 0 || n_pop > 65535) return fail(h, NEP_ERR_ARG, "n_pop must be in 0..65535");
+  h->md_ready = false;
+  rc = setup_batch(h, n_struct, offsets, boxes, N, s);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(h->x.p, pos, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s), "copy pos");
+  CK(cudaMemcpyAsync(h->types.p, types, sizeof(int) * N, cudaMemcpyDeviceToDevice, s), "copy types");
+  launch_iota(N, h->perm.p, s);
+  h->N = N;
+  rc = rebuild_lists(h, N, s, batch_of(h));
+  if (rc) return rc;
+  // candidates: atoms per CTA of both kernels, then (for a population) members per launch
+  const int est = ((h->KR + 2) + 3) / 4 * 4;
+  const double per_member = 4.0 * N * h->T * est + 16.0 * h->cap_a * N + 8.0 * N + 8.0 * kReduceSlots * (N / 64.0 + 2);
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  const double budget = std::min(0.5 * (double)free_b, 32.0 * (1ull << 30));
+  const int max_members = std::max(1, std::min(std::max(n_pop, 1), (int)std::min(65535.0, budget / per_member)));
+  CK(h->e_rad.ensure((size_t)max_members * N * h->T * est), "alloc autotune");
+  CK(h->p_ang.ensure((size_t)max_members * h->cap_a * N), "alloc autotune");
+  CK(h->b_e.ensure((size_t)max_members * N), "alloc autotune");
+  const Tuning saved = h->tune;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  // time one batched evaluation (atom + gather kernels) of `m` members; best of 3 after a warm-up
+  auto time_eval = [&](int m, float *ms) -> int {
+    int r = ensure_partials(h, N, m);
+    if (r) return r;
+    AtomArgs a = make_args(h, N);
+    a.energy = h->b_e.p;
+    a.s_out = N;
+    a.s_erad = (long long)N * h->T * est;
+    a.s_pang = (long long)h->cap_a * N;
+    float best = 1e30f;
+    for (int it = 0; it < 4; ++it) {
+      cudaEventRecord(e0, s);
+      cudaError_t e = h->ops->atom_batch(a, h->mf, h->w0.data(), h->b0.data(), h->w1.data(), h->b1, m,
+                                         atom_block(h), s);
+      if (e == cudaSuccess) e = h->ops->gather_batch(a, m, gather_block(h), s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "autotune launch");
+      cudaEventRecord(e1, s);
+      CK(cudaEventSynchronize(e1), "autotune");
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (it > 0) best = std::min(best, t);
+    }
+    *ms = best;
+    return NEP_OK;
+  };
+  int n_tried = 0;
+  float best_ms = 1e30f, default_ms = 0.f;
+  int best_ab = 128, best_gb = 128;
+  const int abs_[2] = {64, 128}, gbs[3] = {64, 128, 256};
+  for (int ia = 0; ia < 2 && !rc; ++ia) {
+    if (h->precision == 1 && abs_[ia] != 128) continue;
+    for (int ig = 0; ig < 3 && !rc; ++ig) {
+      h->tune.atom_block = abs_[ia];
+      h->tune.gather_block = gbs[ig];
+      float t = 0.f;
+      rc = time_eval(1, &t);
+      ++n_tried;
+      if (abs_[ia] == 128 && gbs[ig] == 128) default_ms = t;
+      if (!rc && t < best_ms) {
+        best_ms = t;
+        best_ab = abs_[ia];
+        best_gb = gbs[ig];
+      }
+    }
+  }
+  h->tune.atom_block = best_ab;
+  h->tune.gather_block = best_gb;
+  int best_m = 0;
+  if (!rc && n_pop > 0) {
+    float best_per = best_ms;
+    best_m = 1;
+    for (int m = 2; m <= max_members && !rc; m *= 2) {
+      float t = 0.f;
+      rc = time_eval(m, &t);
+      ++n_tried;
+      if (!rc && t / m < best_per) {
+        best_per = t / m;
+        best_m = m;
+      }
+    }
+    best_ms = best_per;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) {
+    h->tune = saved;
+    return rc;
+  }
+  h->tune.members = best_m;
+  h->tune.n_tried = n_tried;
+  h->tune.best_ms = best_ms;
+  h->tune.default_ms = default_ms;
+  return out ? nep_get_tuning(h, out) : NEP_OK;
+}
+
 int nep_set_tuning(nep_handle *h, const nep_tuning *t) {
   if (!valid_handle(h) || !t) return NEP_ERR_ARG;
   if (t->members_per_launch < 0 || t->members_per_launch > 65535)
     return fail(h, NEP_ERR_ARG, "members_per_launch must be in 0..65535");
+  if (t->atom_block != 0 && t->atom_block != 64 && t->atom_block != 128)
+    return fail(h, NEP_ERR_ARG, "atom_block must be 0, 64 or 128");
+  if (t->gather_block != 0 && t->gather_block != 64 && t->gather_block != 128 && t->gather_block != 256)
+    return fail(h, NEP_ERR_ARG, "gather_block must be 0, 64, 128 or 256");
   h->tune.members = t->members_per_launch;
+  h->tune.atom_block = t->atom_block;
+  h->tune.gather_block = t->gather_block;
   return NEP_OK;
 }
 
 int nep_get_tuning(const nep_handle *h, nep_tuning *t) {
   if (!valid_handle(h) || !t) return NEP_ERR_ARG;
   t->members_per_launch = h->tune.members;
+  t->atom_block = h->tune.atom_block;
+  t->gather_block = h->tune.gather_block;
   t->last_members = h->tune.last_members;
+  t->n_tried = h->tune.n_tried;
+  t->best_ms = h->tune.best_ms;
+  t->default_ms = h->tune.default_ms;
   return NEP_OK;
 }
 

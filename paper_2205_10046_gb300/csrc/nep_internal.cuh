@@ -151,10 +151,12 @@ struct ShapeOps {
   cudaError_t (*atom)(const AtomArgs &, const ModelF &, const float *w0, const float *b0, const float *w1,
                       float b1, int descriptor_only, cudaStream_t s);
   cudaError_t (*gather)(const AtomArgs &, cudaStream_t s);
-  // batched kernels (per-structure shift tables; `members` population members along y)
+  // batched kernels (per-structure shift tables; `members` population members along y;
+  // `block` atoms per CTA: 64 or 128 for the atom kernel (128 with the tensor-core network),
+  // 64, 128 or 256 for the gather kernel)
   cudaError_t (*atom_batch)(const AtomArgs &, const ModelF &, const float *w0, const float *b0, const float *w1,
-                            float b1, int members, cudaStream_t s);
-  cudaError_t (*gather_batch)(const AtomArgs &, int members, cudaStream_t s);
+                            float b1, int members, int block, cudaStream_t s);
+  cudaError_t (*gather_batch)(const AtomArgs &, int members, int block, cudaStream_t s);
   int (*atom_blocks)(int N);
   int (*gather_blocks)(int N);
 };

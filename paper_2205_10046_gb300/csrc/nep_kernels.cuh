@@ -323,10 +323,12 @@ __device__ __forceinline__ void for_pairs_plain(const unsigned *__restrict__ nl,
 }
 
 // ------------------------------------------------------------------------ per-atom kernel
-template <class S, bool DESC_ONLY, int PREC, bool BATCH = false>
-__global__ void __launch_bounds__(kAtomBlock, 1)
+template <class S, bool DESC_ONLY, int PREC, bool BATCH = false, int AB = kAtomBlock>
+__global__ void __launch_bounds__(AB, 1)
     atom_kernel(const AtomArgs a, const __grid_constant__ AnnConst<S> w) {
   static_assert(PREC == 0 || !DESC_ONLY, "the descriptor-only kernel has no network");
+  static_assert(PREC == 0 || AB == 128, "the tensor-core network works on 128-atom tiles (UMMA M = 128)");
+  static_assert(AB % 32 == 0 && AB <= 256, "whole warps, at most 256 atoms per block");
   constexpr int NR = S::NR, KR = S::KR, NA = S::NA, KA = S::KA, NK = S::NK, NDES = S::NDES;
   extern __shared__ float4 smem4[];
   const int T = a.T;
@@ -511,7 +513,7 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
         if constexpr (!DESC_ONLY && PREC == 0) {
           // park S_n in shared memory while the network runs ([n][k][thread]: conflict-free)
 #pragma unroll
-          for (int k = 0; k < NK; ++k) S_s[(n * NK + k) * kAtomBlock + threadIdx.x] = Sv[c][k];
+          for (int k = 0; k < NK; ++k) S_s[(n * NK + k) * AB + threadIdx.x] = Sv[c][k];
         }
         if constexpr (PREC == 1) {
           // park S_n in this thread's TMEM lane, columns n NK .. n NK + NK - 1
@@ -675,7 +677,7 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
         float s[NK], dS[NK];
         if constexpr (PREC == 0) {
 #pragma unroll
-          for (int k = 0; k < NK; ++k) s[k] = Sme[(n * NK + k) * kAtomBlock];
+          for (int k = 0; k < NK; ++k) s[k] = Sme[(n * NK + k) * AB];
         } else {
           __syncwarp();
 #pragma unroll
@@ -709,7 +711,7 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
           dS[2] += d5 * common * s[2];
         }
 #pragma unroll
-        for (int k = 0; k < NK; ++k) Sme[(n * NK + k) * kAtomBlock] = dS[k];
+        for (int k = 0; k < NK; ++k) Sme[(n * NK + k) * AB] = dS[k];
       }
 
       // ---- angular partial forces dU_i/dr_ij (angular terms of Eq. partial_force)
@@ -743,7 +745,7 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
             float ak = 0.f, ck = 0.f;
 #pragma unroll
             for (int n = 0; n <= NA; ++n) {
-              const float ds = Sme[(n * NK + k) * kAtomBlock];
+              const float ds = Sme[(n * NK + k) * AB];
               ak = __fmaf_rn(ds, g[n], ak);
               ck = __fmaf_rn(ds, gp[n], ck);
             }
@@ -767,7 +769,7 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
   }
   if constexpr (!DESC_ONLY) {
     // deterministic block sum of U (fixed shuffle tree, then fixed warp order)
-    __shared__ double red[kAtomBlock / 32];
+    __shared__ double red[AB / 32];
     double v = Ublock;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -775,7 +777,7 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
     __syncthreads();
     if (threadIdx.x == 0) {
       double s = 0.0;
-      for (int wv = 0; wv < kAtomBlock / 32; ++wv) s += red[wv];
+      for (int wv = 0; wv < AB / 32; ++wv) s += red[wv];
       a.partial_atom[(size_t)mem * gridDim.x + blockIdx.x] = s;
     }
   }
@@ -790,8 +792,8 @@ __global__ void __launch_bounds__(kAtomBlock, 1)
 }
 
 // ------------------------------------------------------------------------ gather kernel
-template <class S, bool BATCH = false>
-__global__ void __launch_bounds__(kGatherBlock)
+template <class S, bool BATCH = false, int GB = kGatherBlock>
+__global__ void __launch_bounds__(GB)
     gather_kernel(const AtomArgs a) {
   constexpr int KR = S::KR, EST = S::EST;
   extern __shared__ float4 smem4[];
@@ -948,7 +950,7 @@ __global__ void __launch_bounds__(kGatherBlock)
     }
   }
   // deterministic block sums of (KE, W[9], force error)
-  __shared__ double red[kGatherBlock / 32][kReduceSlots];
+  __shared__ double red[GB / 32][kReduceSlots];
 #pragma unroll
   for (int s = 1; s < kReduceSlots; ++s) {
     double v = part[s];
@@ -959,19 +961,19 @@ __global__ void __launch_bounds__(kGatherBlock)
   __syncthreads();
   if (threadIdx.x < kReduceSlots && threadIdx.x >= 1) {
     double s = 0.0;
-    for (int wv = 0; wv < kGatherBlock / 32; ++wv) s += red[wv][threadIdx.x];
+    for (int wv = 0; wv < GB / 32; ++wv) s += red[wv][threadIdx.x];
     a.partial_gather[((size_t)mem * gridDim.x + blockIdx.x) * kReduceSlots + threadIdx.x] = s;
   }
 }
 
 // ------------------------------------------------------------------------ launchers
 template <class S>
-size_t atom_smem_bytes(int T, int ncode, int prec) {
+size_t atom_smem_bytes(int T, int ncode, int prec, int ab = kAtomBlock) {
   static_assert((size_t)(S::NA + 1) * S::NK * kAtomBlock * 4 >= (size_t)S::TILE_A + 2 * S::TILE_B + 128,
                 "the S region must hold the tensor-core operand tiles");
   size_t b = sizeof(float4) * ncode +
              sizeof(float) * ((prec == 0 ? S::H * S::NDP : 0) + 2 * S::H + T * T * (S::NR + 1) * (S::KR + 1) +
-                              T * T * (S::NA + 1) * (S::KA + 1) + (S::NA + 1) * S::NK * kAtomBlock);
+                              T * T * (S::NA + 1) * (S::KA + 1) + (size_t)(S::NA + 1) * S::NK * ab);
   // the tensor-core kernel holds 256 of the SM's 512 TMEM columns: keep at most two blocks
   // per SM (a third would wait in tcgen05.alloc) by asking for more than a third of the
   // 228 KB of shared memory
@@ -1015,15 +1017,17 @@ cudaError_t launch_gather(const AtomArgs &a, cudaStream_t st) {
 // Batched launches (grid.y = population members); instantiated in the nep_batch_*.cu units.
 template <class S>
 cudaError_t launch_atom_batch(const AtomArgs &a, const ModelF &mf, const float *w0, const float *b0,
-                              const float *w1, float b1, int members, cudaStream_t st);
+                              const float *w1, float b1, int members, int block, cudaStream_t st);
 template <class S>
-cudaError_t launch_gather_batch(const AtomArgs &a, int members, cudaStream_t st);
+cudaError_t launch_gather_batch(const AtomArgs &a, int members, int block, cudaStream_t st);
 
 #ifdef NEP_BATCH_KERNELS
 template <class S>
 cudaError_t launch_atom_batch(const AtomArgs &a, const ModelF &mf, const float *w0, const float *b0,
-                              const float *w1, float b1, int members, cudaStream_t st) {
+                              const float *w1, float b1, int members, int block, cudaStream_t st) {
   if (a.N <= 0 || members <= 0) return cudaSuccess;
+  if (block != 64 && block != 128) return cudaErrorInvalidValue;
+  if (a.precision == 1 && block != 128) return cudaErrorInvalidValue;
   AnnConst<S> w;
   for (int v = 0; v < S::H * S::NDES; ++v) w.w0[v] = w0 ? w0[v] : 0.f;
   for (int v = 0; v < S::H; ++v) {
@@ -1032,23 +1036,27 @@ cudaError_t launch_atom_batch(const AtomArgs &a, const ModelF &mf, const float *
   }
   w.b1 = b1;
   w.m = mf;
-  const dim3 grid((a.N + kAtomBlock - 1) / kAtomBlock, members);
-  const size_t smem = atom_smem_bytes<S>(a.T, 0, a.precision);
+  const dim3 grid((a.N + block - 1) / block, members);
+  const size_t smem = atom_smem_bytes<S>(a.T, 0, a.precision, block);
   auto go = [&](auto kern) -> cudaError_t {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kAtomBlock, smem, st>>>(a, w);
+    kern<<<grid, block, smem, st>>>(a, w);
     return cudaGetLastError();
   };
-  if (a.precision == 1) return go(atom_kernel<S, false, 1, true>);
-  return go(atom_kernel<S, false, 0, true>);
+  if (a.precision == 1) return go(atom_kernel<S, false, 1, true, 128>);
+  if (block == 64) return go(atom_kernel<S, false, 0, true, 64>);
+  return go(atom_kernel<S, false, 0, true, 128>);
 }
 
 template <class S>
-cudaError_t launch_gather_batch(const AtomArgs &a, int members, cudaStream_t st) {
+cudaError_t launch_gather_batch(const AtomArgs &a, int members, int block, cudaStream_t st) {
   if (a.N <= 0 || members <= 0) return cudaSuccess;
-  const dim3 grid((a.N + kGatherBlock - 1) / kGatherBlock, members);
-  gather_kernel<S, true><<<grid, kGatherBlock, 0, st>>>(a);
+  const dim3 grid((a.N + block - 1) / block, members);
+  if (block == 64) gather_kernel<S, true, 64><<<grid, 64, 0, st>>>(a);
+  else if (block == 128) gather_kernel<S, true, 128><<<grid, 128, 0, st>>>(a);
+  else if (block == 256) gather_kernel<S, true, 256><<<grid, 256, 0, st>>>(a);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

@@ -46,7 +46,9 @@ class nep_stats(C.Structure):
 
 
 class nep_tuning(C.Structure):
-    _fields_ = [("members_per_launch", C.c_int), ("last_members", C.c_int)]
+    _fields_ = [("members_per_launch", C.c_int), ("atom_block", C.c_int), ("gather_block", C.c_int),
+                ("last_members", C.c_int), ("n_tried", C.c_int), ("best_ms", C.c_float),
+                ("default_ms", C.c_float)]
 
 
 _lib = None
@@ -64,6 +66,7 @@ _SIGS = {
     "nep_eval_population": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "nep_set_tuning": (C.c_int, [_P, C.POINTER(nep_tuning)]),
     "nep_get_tuning": (C.c_int, [_P, C.POINTER(nep_tuning)]),
+    "nep_autotune": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, C.c_int, C.POINTER(nep_tuning), _P]),
     "nep_descriptors": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P]),
     "nep_n_des": (C.c_int, [_P]),
     "md_init": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P]),
@@ -258,9 +261,24 @@ def nep_eval_population(h, z, offsets, pos, types, boxes, e_tar, f_tar, w_tar=No
     return loss
 
 
-def nep_set_tuning(h, members_per_launch: int = 0):
-    t = nep_tuning(int(members_per_launch), 0)
+def nep_set_tuning(h, members_per_launch: int = 0, atom_block: int = 0, gather_block: int = 0):
+    t = nep_tuning(int(members_per_launch), int(atom_block), int(gather_block), 0, 0, 0.0, 0.0)
     _check(load().nep_set_tuning(h, C.byref(t)), h)
+
+
+def nep_autotune(h, offsets, pos, types, boxes, n_pop: int = 0) -> dict:
+    """Time the batched kernels' launch shapes on this structure set; keeps and returns the best."""
+    import torch
+    off = _offsets(offsets)
+    ns = off.shape[0] - 1
+    n = int(off[-1]) if ns > 0 else 0
+    bx = _boxes(boxes, ns)
+    t = nep_tuning()
+    rc = load().nep_autotune(h, ns, off.ctypes.data, _dev(pos, torch.float64, (n, 3), "pos"),
+                             _dev(types, torch.int32, (n,), "types"), bx.ctypes.data, int(n_pop), C.byref(t),
+                             _stream())
+    _check(rc, h)
+    return {f: getattr(t, f) for f, _ in nep_tuning._fields_}
 
 
 def nep_get_tuning(h) -> dict:

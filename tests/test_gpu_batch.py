@@ -246,3 +246,29 @@ def test_batch_graph_replay_and_regrow(torch_cuda):
         U, F, Wv = oracle.compute(model, *b3.structure(s))
         _check_structure(r4, b3, s, U, F, Wv)
     h.close()
+
+
+def test_block_shapes_and_autotune(torch_cuda):
+    """Atoms per CTA change the speed only: per-atom and per-structure results are identical
+    for every shape the autotuner may pick; the autotuner keeps the fastest of its candidates."""
+    torch = torch_cuda
+    from paper_2205_10046_gb300 import nep
+    b = W.batch_structures(64, seed=5)
+    h = nep.NEP(W.mixed_model(0))
+    ref = _run_batch(torch, h, b)
+    for ab in (64, 128):
+        for gb in (64, 128, 256):
+            nep.nep_set_tuning(h.h, 0, ab, gb)
+            g = _run_batch(torch, h, b)
+            for k in ref:
+                np.testing.assert_array_equal(g[k], ref[k], err_msg=f"{k} atom_block={ab} gather_block={gb}")
+    p, t = _dev(torch, b)
+    tune = nep.nep_autotune(h.h, b.offsets, p, t, b.boxes, n_pop=0)
+    assert tune["atom_block"] in (64, 128) and tune["gather_block"] in (64, 128, 256)
+    assert tune["n_tried"] == 6 and 0 < tune["best_ms"] <= tune["default_ms"]
+    g = _run_batch(torch, h, b)
+    for k in ref:
+        np.testing.assert_array_equal(g[k], ref[k])
+    with pytest.raises(nep.NepError):
+        nep.nep_set_tuning(h.h, 0, 96, 128)
+    h.close()

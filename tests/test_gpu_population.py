@@ -96,3 +96,22 @@ def test_population_bf16_form(torch_cuda, problem):
     # BF16 members in groups give the same values as one at a time
     g1, _ = _eval(torch_cuda, problem, precision=1, members=1)
     np.testing.assert_array_equal(g1, g)
+
+
+def test_population_autotuned_shapes(torch_cuda, problem):
+    torch = torch_cuda
+    from paper_2205_10046_gb300 import nep
+    base, _ = _eval(torch, problem)
+    h = nep.NEP(problem["label"])
+    b = problem["b"]
+    dev = lambda a, dt=torch.float64: torch.tensor(a, dtype=dt, device="cuda")
+    p, t = dev(b.pos), dev(b.types, torch.int32)
+    P = problem["z"].shape[0]
+    tune = nep.nep_autotune(h.h, b.offsets, p, t, b.boxes, n_pop=P)
+    assert tune["members_per_launch"] in (1, 2, 4) and tune["n_tried"] >= 7
+    loss = nep.nep_eval_population(h.h, dev(problem["z"]), b.offsets, p, t, b.boxes, dev(problem["e_t"]),
+                                   dev(problem["f_t"]), dev(problem["w_t"]), LAMBDAS).cpu().numpy()
+    assert nep.nep_get_tuning(h.h)["last_members"] == tune["members_per_launch"]
+    # the force term's block sums follow the gather CTA size: equal up to FP64 summation order
+    np.testing.assert_allclose(loss, base, rtol=1e-12, atol=1e-15)
+    h.close()
