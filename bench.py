@@ -48,6 +48,10 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--plain-graph", action="store_true",
                     help="capture the rebuild as ordinary kernel nodes (for kernel-level profilers)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the structure-batch and population forms")
+    ap.add_argument("--batch-only", action="store_true", help="only the structure-batch and population forms")
+    ap.add_argument("--batch-calls", type=int, default=20)
+    ap.add_argument("--pop-calls", type=int, default=5)
     return ap.parse_args()
 
 
@@ -282,6 +286,132 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- batched forms
+BATCH_SKIN = 0.01  # single-point evaluations rebuild their lists on every call: no skin needed
+
+
+def _events_timed(fn, calls, warmup, stream, flush):
+    """Per-call device time (CUDA events on `stream`, L2 flushed before each call outside the
+    events) and host wall time of `calls` calls after `warmup` untimed ones."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    dev_ms, wall = [], 0.0
+    for c in range(calls):
+        flush.fill_(c)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev0.record(stream)
+        fn()
+        ev1.record(stream)
+        ev1.synchronize()
+        wall += time.perf_counter() - t0
+        dev_ms.append(ev0.elapsed_time(ev1))
+    return sum(dev_ms) / 1e3, wall
+
+
+def run_batch_forms(args, dev, stream, flush, peak):
+    """The structure batch (4096 structures of 8-512 atoms in one evaluation) and the
+    population evaluation (64 candidate vectors on a fixed 1024-structure subset), FP32 and
+    BF16, with the autotuner's launch shapes."""
+    import numpy as np
+    import torch
+    from paper_2205_10046_gb300 import nep
+    from paper_2205_10046_gb300 import workloads as W
+
+    b = W.batch_structures(4096, seed=3)
+    model = W.mixed_model(0)
+    h = nep.NEP(model, skin=BATCH_SKIN)
+    N, S = b.n_atoms, b.n_struct
+    p = torch.tensor(b.pos, device=dev)
+    t = torch.tensor(b.types, device=dev)
+    f64 = dict(dtype=torch.float64, device=dev)
+    E = torch.empty(S, **f64)
+    F = torch.empty((N, 3), **f64)
+    Wv = torch.empty((S, 9), **f64)
+    call = lambda: nep.nep_compute_batch(h.h, b.offsets, p, t, b.boxes, None, E, F, None, Wv)
+    names = ["neighbor_rebuild", "nep_atom", "nep_gather", "finalize"]
+    out = {}
+    for prec in (0, 1):
+        nep.nep_set_precision(h.h, prec)
+        tune = nep.nep_autotune(h.h, b.offsets, p, t, b.boxes, 0)
+        dev_s, wall = _events_timed(call, args.batch_calls, 3, stream, flush)
+        nep.nep_set_profiling(h.h, True)  # one eager call with per-kernel events
+        call()
+        kt = nep.nep_kernel_times(h.h)
+        nep.nep_set_profiling(h.h, False)
+        st = nep.nep_get_stats(h.h)
+        atom_f, gather_f = flop_model(model, model.n_types, st["mean_radial"], st["mean_radial_in_rc"],
+                                      st["mean_angular"], st["mean_angular_in_rc"])
+        key = "fp32" if prec == 0 else "bf16"
+        out[key] = {
+            "value": N * args.batch_calls / dev_s, "unit": "atom-evaluations/s",
+            "structures_per_s": S * args.batch_calls / dev_s, "ms_per_call": 1e3 * dev_s / args.batch_calls,
+            "wall_ms_per_call": 1e3 * wall / args.batch_calls,
+            "kernel_ms": {k: kt.get(k, 0.0) for k in names},
+            "atom_kernel_roofline": {"bound": "alu", "achieved": atom_f * N / (kt["nep_atom"] / 1e3) / 1e12,
+                                     "peak": peak, "unit": "TFLOP/s",
+                                     "frac": atom_f * N / (kt["nep_atom"] / 1e3) / 1e12 / peak,
+                                     "flops_per_atom": atom_f},
+            "tuning": {k: tune[k] for k in ("atom_block", "gather_block", "n_tried", "best_ms", "default_ms")},
+            "neighbours": {"radial_list": st["mean_radial"], "angular_list": st["mean_angular"]},
+        }
+    out["workload"] = (f"{S} structures, {N} atoms: atom counts U[8,512], FCC/BCC/diamond with +-10% shear, "
+                       f"1-3 of 3 species, sigma 0.1 A; NEP rc 5.5/4.0 n_max 8/4 basis 8/4 l_max 4/2/1 "
+                       f"40 neurons (seed 0); lists r_c + {BATCH_SKIN} A rebuilt every call")
+    out["path"] = ("nep_compute_batch (graph replay: copy-in, neighbour build, atom + gather kernels, "
+                   "per-structure sums, status read)")
+    out["gpu_launches_per_call"] = nep.nep_get_stats(h.h)["batch_graph_kernels"]
+    out["l2"] = "flushed (256 MiB write) before every timed call"
+
+    # population: 64 candidates on the first 1024 structures
+    sub = b.subset(range(1024))
+    Ns = sub.n_atoms
+    ps = torch.tensor(sub.pos, device=dev)
+    ts = torch.tensor(sub.types, device=dev)
+    nep.nep_set_precision(h.h, 0)
+    nep.nep_set_tuning(h.h, 0, 0, 0)
+    Es = torch.empty(1024, **f64)
+    Fs = torch.empty((Ns, 3), **f64)
+    Ws = torch.empty((1024, 9), **f64)
+    nep.nep_compute_batch(h.h, sub.offsets, ps, ts, sub.boxes, None, Es, Fs, None, Ws)
+    torch.cuda.synchronize()
+    cnt = torch.tensor(np.diff(sub.offsets).astype(np.float64), device=dev)
+    e_tar = Es / cnt
+    w9 = Ws / cnt[:, None]
+    w_tar = torch.stack([w9[:, 0], w9[:, 1], w9[:, 2], 0.5 * (w9[:, 3] + w9[:, 6]), 0.5 * (w9[:, 5] + w9[:, 8]),
+                         0.5 * (w9[:, 4] + w9[:, 7])], 1).contiguous()
+    P = 64
+    z = torch.tensor(np.stack([W.mixed_model(100 + k).to_vector() for k in range(P)]), device=dev)
+    lam = (1.0, 1.0, 0.1, 0.0, 0.0)
+    pop = {}
+    for prec in (0, 1):
+        nep.nep_set_precision(h.h, prec)
+        tune = nep.nep_autotune(h.h, sub.offsets, ps, ts, sub.boxes, P)
+        loss = torch.empty((P, 6), **f64)
+        fn = lambda: nep.nep_eval_population(h.h, z, sub.offsets, ps, ts, sub.boxes, e_tar, Fs, w_tar, lam, loss)
+        dev_s, wall = _events_timed(fn, args.pop_calls, 1, stream, flush)
+        l = loss.cpu().numpy()
+        pop["fp32" if prec == 0 else "bf16"] = {
+            "value": P * Ns * args.pop_calls / dev_s, "unit": "member-atom-evaluations/s",
+            "candidates_per_s": P * args.pop_calls / dev_s, "ms_per_call": 1e3 * dev_s / args.pop_calls,
+            "wall_ms_per_call": 1e3 * wall / args.pop_calls,
+            "tuning": {k: tune[k] for k in ("members_per_launch", "atom_block", "gather_block", "n_tried",
+                                            "best_ms", "default_ms")},
+            "loss_min_median": [float(l[:, 0].min()), float(np.median(l[:, 0]))],
+        }
+    pop["workload"] = (f"{P} random candidate vectors (seeds 100..{100 + P - 1}) on 1024 structures "
+                       f"({Ns} atoms) of the batch; Eq. loss with lambda_e = lambda_f = 1, lambda_v = 0.1")
+    pop["targets"] = ("energies, forces and virials of the seed-0 model from the FP32 batch path; the cost does not "
+                      "depend on the target values, tests/test_gpu_population.py checks the losses against "
+                      "FP64 oracle labels")
+    h.close()
+    return out, pop
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_gb300(args):
     import numpy as np
@@ -303,6 +433,17 @@ def run_gb300(args):
         dist.barrier()
     nep.load()
 
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    props = torch.cuda.get_device_properties(dev)
+    if args.batch_only:
+        clk = ClockSampler(torch.cuda.current_device() if world == 1 else local)
+        with clk:
+            bf, pf = run_batch_forms(args, dev, stream, flush, props.multi_processor_count * 128 * 2 * 2070e6 / 1e12)
+        if rank == 0:
+            print(json.dumps({"batch_form": bf, "population": pf, "clocks": clk.summary()}), flush=True)
+        return 0
+
     w = make_workload(args.workload)
     N = w.n_atoms
     dt = w.dt_fs
@@ -313,8 +454,6 @@ def run_gb300(args):
     nep.md_init(h.h, pos_d, types_d, w.box, vel_d)
     nep.nep_set_profiling(h.h, True)
     nep.nep_set_graph_conditional(h.h, not args.plain_graph)
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
     names = ["md_drift", "neighbor_rebuild", "nep_atom", "nep_gather", "finalize"]
 
@@ -382,8 +521,13 @@ def run_gb300(args):
     d2h = N * 72 + th_host.numel() * 8
     etot = (th_host[:, 0] + th_host[:, 1]).numpy()
 
+    batch_forms = None
+    if not args.no_batch:
+        with ClockSampler(torch.cuda.current_device() if world == 1 else local) as bclk:
+            batch_forms = run_batch_forms(args, dev, stream, flush,
+                                          props.multi_processor_count * 128 * 2 * 2070e6 / 1e12)
+        batch_forms[0]["clocks"] = bclk.summary()
     if rank == 0:
-        props = torch.cuda.get_device_properties(dev)
         clocks = clk.summary()
         sm_max = clocks.get("sm_max_mhz") or 2070.0
         peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes
@@ -421,6 +565,8 @@ def run_gb300(args):
             "survey_flops_per_atom_step": survey_flop_model(w.model, stats["mean_radial_in_rc"],
                                                             stats["mean_angular_in_rc"]),
         }
+        if batch_forms is not None:
+            line["batch_form"], line["population"] = batch_forms
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
         print(json.dumps(line), flush=True)

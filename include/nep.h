@@ -251,6 +251,7 @@ typedef struct {
   int cells[3];                  /* cell grid */
   int graph_kernels;             /* kernel nodes in the captured MD step graph (0 before md_run) */
   int rebuild_kernels;           /* kernels of one neighbour rebuild (run only on rebuild steps) */
+  int batch_graph_kernels;       /* kernel nodes in the captured nep_compute_batch graph (0: none) */
 } nep_stats;
 
 int nep_get_stats(nep_handle *h, nep_stats *out);

@@ -287,6 +287,7 @@ struct nep_handle {
   DevBuf<double> b_e, b_w;  // caller-order per-atom energies and virials when the caller keeps none
   long long b_gen = 0;      // layout generation (bumped when the grids change)
   cudaGraphExec_t b_graph = nullptr;
+  int b_graph_kernels = 0;
   BatchKey b_key{}, b_last{};
   // population evaluation: per-member kernel arrays and the sums of Eq. loss
   DevBuf<float> pop_cr, pop_ca, pop_ann;
@@ -612,6 +613,20 @@ Batch batch_of(nep_handle *h) {
   return B;
 }
 
+// Kernel nodes of a graph (top level).
+int count_kernel_nodes(cudaGraph_t graph) {
+  size_t nn = 0;
+  cudaGraphGetNodes(graph, nullptr, &nn);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (nn) cudaGraphGetNodes(graph, nodes.data(), &nn);
+  int nk = 0;
+  for (size_t k = 0; k < nn; ++k) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[k], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+  }
+  return nk;
+}
+
 // Arrays of one batched evaluation.
 struct BatchOut {
   const double *pos = nullptr;
@@ -700,6 +715,7 @@ int capture_batch(nep_handle *h, int N, const BatchOut &o, cudaStream_t s) {
     return rc;
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "end capture (batch)");
+  h->b_graph_kernels = count_kernel_nodes(graph);
   e = cudaGraphInstantiate(&h->b_graph, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
@@ -1382,16 +1398,7 @@ int md_queue(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double 
       return rc;
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
-    size_t nn = 0;
-    cudaGraphGetNodes(graph, nullptr, &nn);
-    std::vector<cudaGraphNode_t> nodes(nn);
-    if (nn) cudaGraphGetNodes(graph, nodes.data(), &nn);
-    int nk = 0;
-    for (size_t k = 0; k < nn; ++k) {
-      cudaGraphNodeType t;
-      if (cudaGraphNodeGetType(nodes[k], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
-    }
-    h->graph_kernels = nk;
+    h->graph_kernels = count_kernel_nodes(graph);
     e = cudaGraphInstantiate(&h->graph, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
@@ -1527,6 +1534,7 @@ int nep_get_stats(nep_handle *h, nep_stats *out) {
   s.cap_angular = h->cap_a;
   s.graph_kernels = h->graph_kernels;
   s.rebuild_kernels = h->rebuild_kernels;
+  s.batch_graph_kernels = h->b_graph ? h->b_graph_kernels : 0;
   if (h->status.p) {
     cudaMemcpy(h->h_status, h->status.p, sizeof(BuildStatus), cudaMemcpyDeviceToHost);
     s.n_rebuilds = h->h_status->n_rebuilds;

@@ -42,7 +42,7 @@ class nep_stats(C.Structure):
                 ("mean_angular", C.c_double), ("mean_radial_in_rc", C.c_double),
                 ("mean_angular_in_rc", C.c_double), ("n_rebuilds", C.c_longlong),
                 ("md_steps", C.c_longlong), ("cells", C.c_int * 3), ("graph_kernels", C.c_int),
-                ("rebuild_kernels", C.c_int)]
+                ("rebuild_kernels", C.c_int), ("batch_graph_kernels", C.c_int)]
 
 
 class nep_tuning(C.Structure):
