@@ -193,6 +193,75 @@ int nep_get_tuning(const nep_handle *h, nep_tuning *t);
 int nep_autotune(nep_handle *h, int n_struct, const int *offsets, const double *pos, const int *types,
                  const double *boxes, int n_pop, nep_tuning *out, nep_stream_t stream);
 
+/* ------------------------------------------------------------------------ serving
+ * A persistent request loop (the paper has no counterpart): jobs on structures of any size
+ * are queued, admitted first in first out while their estimated device workspace fits the
+ * memory budget and a worker is free, and run concurrently, each on its own CUDA stream
+ * and handle (positions, neighbour lists and velocities stay on the device for the whole
+ * job; workspaces are stream-ordered allocations released when the job ends). Jobs that
+ * arrive while others run are admitted as soon as a worker and memory free up, so their
+ * work overlaps on the device. A job's results do not depend on what else runs. */
+#define NEP_JOB_SINGLE 0 /* one energy / force / virial evaluation (nep_compute) */
+#define NEP_JOB_FIRE 1   /* FIRE relaxation (fire_run), then one evaluation at the result */
+#define NEP_JOB_NVE 2    /* velocity-Verlet NVE (md_run), then one evaluation at the end */
+
+typedef struct nep_server nep_server;
+
+typedef struct {
+  size_t memory_budget; /* bytes of device workspace that running jobs may hold together */
+  int workers;          /* jobs on the device at once (1..256): one host thread and stream each */
+  int precision;        /* 0: FP32 network, 1: BF16 tensor-core network (nep_set_precision) */
+} nep_server_config;
+
+typedef struct {
+  int kind;             /* NEP_JOB_* */
+  int n_atoms;          /* >= 1 */
+  const double *pos;    /* HOST [N][3]; copied by nep_server_submit */
+  const int *types;     /* HOST [N] */
+  const double *vel;    /* HOST [N][3] initial velocities for NVE (A/fs), or NULL (zero) */
+  double box[9];        /* cell rows */
+  int n_steps;          /* FIRE: most steps; NVE: steps */
+  double dt_fs;         /* NVE time step; FIRE initial time step */
+  double fmax;          /* FIRE convergence threshold on max |F_i| (eV/A) */
+} nep_job;
+
+typedef struct {
+  long long id;
+  int status;           /* NEP_OK or the NEP_ERR_* code of the failed step */
+  int kind, n_atoms;
+  int steps;            /* MD or FIRE steps taken (FIRE: before convergence) */
+  double energy;        /* potential energy of the final state (eV) */
+  double virial[9];     /* total virial of the final state (eV) */
+  double t_submit, t_start, t_done; /* seconds since nep_server_create: queued, on a worker, done */
+  size_t workspace_est; /* device bytes reserved for the job by admission */
+  size_t workspace_used;/* device bytes the job held at its end */
+  char message[160];    /* error text when status != NEP_OK */
+} nep_result;
+
+typedef struct {
+  int queued, running;
+  long long completed, failed;
+  size_t bytes_reserved, peak_bytes_reserved; /* admission estimates of the running jobs */
+  double atom_evaluations;                    /* sum over finished jobs of N x force evaluations */
+} nep_server_stats;
+
+/* Start the workers (each creates its handle for `params`, copied). NEP_ERR_ARG for a bad
+ * configuration, as nep_create for bad parameters. */
+int nep_server_create(const nep_params *params, const nep_server_config *cfg, nep_server **out);
+/* Queue a job (HOST arrays copied); *id receives its id. Thread-safe; does not wait for the
+ * device. NEP_ERR_OOM if the job alone needs more than the memory budget. */
+int nep_server_submit(nep_server *s, const nep_job *job, long long *id);
+/* Next finished job in completion order: waits up to timeout_s seconds (< 0: no limit);
+ * NEP_ERR_TIMEOUT if none finished in time. */
+int nep_server_wait(nep_server *s, double timeout_s, nep_result *out);
+/* Final positions (wrapped into the cell), forces and velocities of a finished job into
+ * HOST buffers [N][3] (any may be NULL); the server then drops them. NEP_ERR_ARG for an
+ * unknown id or a second call. */
+int nep_server_arrays(nep_server *s, long long id, double *pos, double *force, double *vel);
+int nep_server_stats_get(nep_server *s, nep_server_stats *out);
+/* Finish the jobs on the workers, drop the queued ones, release everything. */
+int nep_server_destroy(nep_server *s);
+
 /* Descriptor vectors q^i (Eqs. qin and S_nk with the explicit components of Sec. II D)
  * into q [N][N_des] FP64 (DEVICE pointers, as nep_compute). */
 int nep_descriptors(nep_handle *h, int n_atoms, const double *pos, const int *types, const double *box,
@@ -220,6 +289,20 @@ int md_init_host(nep_handle *h, int n_atoms, const double *pos, const int *types
  * Returns NEP_ERR_NEIGHBOR_OVERFLOW if a rebuild found more neighbours than the lists
  * hold (the state is then unusable; call md_init again). */
 int md_run(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *thermo, nep_stream_t stream);
+
+/* FIRE energy minimisation (Bitzek et al., Phys. Rev. Lett. 97, 170201 (2006); the paper
+ * has no counterpart) from the state of md_init, with its velocities set to zero. A step is
+ * one velocity-Verlet step of the current length dt followed by the FIRE update with
+ * P = F . v, |F| and |v| over all atoms: P > 0 mixes v <- (1 - alpha) v + alpha |v| F/|F|
+ * and, after more than N_min = 5 such steps in a row, sets dt <- min(1.1 dt, 10 dt0) and
+ * alpha <- 0.99 alpha; P <= 0 sets v <- 0, dt <- dt/2, alpha <- alpha_start = 0.1. The
+ * relaxation stops (nothing moves again) once max_i |F_i| < fmax, checked on the starting
+ * forces and after every step, or after n_steps. thermo: as md_run with thermo_every = 1
+ * (n_steps rows; rows after convergence repeat the last state), or NULL. *steps_taken
+ * (HOST, or NULL) receives the steps taken before convergence. The state stays resident
+ * (md_get_state, md_run). Synchronous; errors as md_run. */
+int fire_run(nep_handle *h, int n_steps, double dt0_fs, double fmax, double *thermo, int *steps_taken,
+             nep_stream_t stream);
 
 /* md_run without the final synchronisation: queues the n_steps graph replays on `stream`
  * and returns. A neighbour-list overflow during these steps is reported by the next

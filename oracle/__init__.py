@@ -264,3 +264,64 @@ def batch_predictions(model, offsets, pos, types, boxes, n_threads=0):
         F[a:b] = Fs
         w[s] = virial6(Ws.sum(0))[0] / (b - a)
     return e, F, w
+
+
+# --------------------------------------------------------------------------- FIRE
+# Constants of the FIRE minimiser (Bitzek et al., Phys. Rev. Lett. 97, 170201 (2006)).
+FIRE_NMIN, FIRE_FINC, FIRE_FDEC, FIRE_ALPHA_START, FIRE_FALPHA, FIRE_DTMAX_FACTOR = 5, 1.1, 0.5, 0.1, 0.99, 10.0
+KAPPA = 1.66053906660e-27 * 1e-20 / 1e-30 / 1.602176634e-19  # 1 u A^2 / fs^2 in eV
+
+
+def fire_minimize(force_fn, x0, inv_mass, n_steps, dt0, fmax):
+    """FIRE from rest, written out step by step: a velocity-Verlet step of length dt
+    (a = F * inv_mass), then with P = F . v: for P > 0, v <- (1 - alpha) v + alpha |v| F/|F|
+    and, once more than N_min steps in a row had P > 0, dt <- min(f_inc dt, dt_max) and
+    alpha <- f_alpha alpha; for P <= 0, v <- 0, dt <- f_dec dt, alpha <- alpha_start. Stops
+    when max_i |F_i| < fmax (tested on the starting forces and after every step).
+
+    force_fn(x) -> (E, F). Returns (x, E, F, steps, energies) with energies after each step."""
+    x = np.array(x0, dtype=np.float64)
+    im = np.asarray(inv_mass, dtype=np.float64).reshape(-1, 1)
+    v = np.zeros_like(x)
+    E, F = force_fn(x)
+    dt, alpha, npos, steps = float(dt0), FIRE_ALPHA_START, 0, 0
+    dt_max = FIRE_DTMAX_FACTOR * dt0
+    energies = []
+    if np.max(np.sum(F * F, axis=1)) < fmax * fmax:
+        return x, E, F, 0, energies
+    for _ in range(n_steps):
+        v = v + 0.5 * dt * F * im
+        x = x + dt * v
+        E, F = force_fn(x)
+        v = v + 0.5 * dt * F * im
+        steps += 1
+        energies.append(E)
+        if np.max(np.sum(F * F, axis=1)) < fmax * fmax:
+            break
+        P = float(np.sum(F * v))
+        if P > 0.0:
+            fn = math.sqrt(float(np.sum(F * F)))
+            vn = math.sqrt(float(np.sum(v * v)))
+            v = (1.0 - alpha) * v + (alpha * vn / fn if fn > 0 else 0.0) * F
+            if npos > FIRE_NMIN:
+                dt = min(dt * FIRE_FINC, dt_max)
+                alpha *= FIRE_FALPHA
+            npos += 1
+        else:
+            v = np.zeros_like(v)
+            dt *= FIRE_FDEC
+            alpha = FIRE_ALPHA_START
+            npos = 0
+    return x, E, F, steps, energies
+
+
+def fire(model, pos, types, box, n_steps, dt0, fmax, n_threads=0):
+    """FIRE relaxation of one structure with the oracle's energy and forces."""
+    types = _i32(types)
+    inv_mass = 1.0 / (np.asarray(model.mass, dtype=np.float64)[types] * KAPPA)
+
+    def force_fn(x):
+        U, F, _ = compute(model, x, types, box, n_threads=n_threads)
+        return float(np.sum(U)), F
+
+    return fire_minimize(force_fn, pos, inv_mass, n_steps, dt0, fmax)

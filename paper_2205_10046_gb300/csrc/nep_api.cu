@@ -15,7 +15,7 @@
 namespace nep {
 void launch_rebuild_condition(cudaGraphConditionalHandle hc, const BuildStatus *st, cudaStream_t s);
 void launch_drift(int N, const AtomState &a, const double *inv_mass_kappa, double dt, double half_skin2,
-                  BuildStatus *st, cudaStream_t s);
+                  BuildStatus *st, cudaStream_t s, const FireState *fire);
 void launch_finalize(int nb_atom, const double *partial_atom, int nb_gather, const double *partial_gather,
                      double *energy_total, double *virial_total, double *thermo_stage, int *thermo_ctl, int N,
                      double volume, cudaStream_t s);
@@ -188,27 +188,41 @@ const double kKappa = 1.66053906660e-27 * 1e-20 / 1e-30 / 1.602176634e-19;
 enum Slot { SLOT_DRIFT = 0, SLOT_REBUILD, SLOT_ATOM, SLOT_GATHER, SLOT_FINAL, N_SLOTS };
 const char *kSlotNames[N_SLOTS] = {"md_drift", "neighbor_rebuild", "nep_atom", "nep_gather", "finalize"};
 
-std::string g_create_error;
+thread_local std::string g_create_error;  // per calling thread (serving workers create handles)
+
+// Device buffers of the calling thread are stream-ordered (cudaMallocAsync / cudaFreeAsync
+// on this stream) when it is set: the serving workers use this so that growing or releasing
+// a workspace never synchronises the device.
+thread_local cudaStream_t t_alloc_stream = nullptr;
+thread_local bool t_alloc_async = false;
 
 template <class Tp>
 struct DevBuf {
   Tp *p = nullptr;
   size_t n = 0;
+  bool async = false;
+  cudaStream_t st = nullptr;
   cudaError_t ensure(size_t want) {
     if (want <= n && p) return cudaSuccess;
-    if (p) cudaFree(p);
-    p = nullptr;
-    n = 0;
+    release();
     if (want == 0) want = 1;
-    cudaError_t e = cudaMalloc(&p, want * sizeof(Tp));
+    async = t_alloc_async;
+    st = t_alloc_stream;
+    cudaError_t e = async ? cudaMallocAsync(reinterpret_cast<void **>(&p), want * sizeof(Tp), st)
+                          : cudaMalloc(reinterpret_cast<void **>(&p), want * sizeof(Tp));
     if (e == cudaSuccess) n = want;
+    else p = nullptr;
     return e;
   }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      if (async) cudaFreeAsync(p, st);
+      else cudaFree(p);
+    }
     p = nullptr;
     n = 0;
   }
+  size_t bytes() const { return p ? n * sizeof(Tp) : 0; }
 };
 
 }  // namespace
@@ -267,6 +281,8 @@ struct nep_handle {
   // md
   bool md_ready = false;
   cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t fire_graph = nullptr;  // one FIRE step (its time step lives on the device)
+  DevBuf<FireState> fire, ck_fire;
   double graph_dt = 0;
   bool graph_prof = false;
   const double *graph_thermo = nullptr;
@@ -300,6 +316,16 @@ struct nep_handle {
   bool slot_ran[N_SLOTS] = {};
   nep_stats stats_cache{};
   int graph_kernels = 0;
+  // every per-structure device buffer (not the model copies, the status word or the tiles)
+  template <class Fn>
+  void for_workspace(Fn &&f) {
+    f(x); f(v); f(F); f(x_ref); f(origin); f(partial_atom); f(partial_gather); f(thermo_stage);
+    f(ck_x); f(ck_v); f(ck_F); f(ck_types); f(ck_perm); f(x2); f(v2); f(F2); f(types2); f(perm2); f(cell2);
+    f(perm); f(types); f(cell_of); f(cell_count); f(cell_cursor); f(cell_start); f(cell_atoms); f(nn_r);
+    f(nn_a); f(rev_a); f(thermo_ctl); f(nl_r); f(nl_a); f(pos4); f(dtab); f(p_ang); f(e_rad); f(d_grids);
+    f(d_sid); f(d_offsets); f(b_e); f(b_w); f(pop_cr); f(pop_ca); f(pop_ann); f(pop_tc); f(pop_reg); f(pop_es);
+    f(pop_ws); f(fire); f(ck_fire);
+  }
   // the kernels compare r^2 with the FP32 square of the FP32 cutoff
   float rcR2f() const { return (float)rcR * (float)rcR; }
   float rcA2f() const { return (float)rcA * (float)rcA; }
@@ -520,8 +546,9 @@ int load_structure(nep_handle *h, int N, const double *pos, const int *types, co
 // Outputs for the caller (nep_compute) are scattered to the caller's atom order; the MD
 // forces (force == h->F) stay in the internal order.
 int run_forces(nep_handle *h, int N, double *energy, double *force, double *virial, int md_kick, double half_dt,
-               cudaStream_t s, bool capturing) {
+               cudaStream_t s, bool capturing, const FireState *fire = nullptr) {
   AtomArgs a = make_args(h, N);
+  a.fire = fire;
   if (force == h->F.p) a.perm = nullptr;
   a.energy = energy;
   a.force = force;
@@ -735,6 +762,36 @@ int check_offsets(nep_handle *h, int n_struct, const int *offsets) {
 
 }  // namespace
 
+namespace nep {
+void set_thread_alloc_stream(cudaStream_t s) {
+  t_alloc_stream = s;
+  t_alloc_async = s != nullptr;
+}
+
+void release_workspace(nep_handle *h) {
+  for (cudaGraphExec_t *g : {&h->graph, &h->fire_graph, &h->b_graph})
+    if (*g) {
+      cudaGraphExecDestroy(*g);
+      *g = nullptr;
+    }
+  h->for_workspace([](auto &b) { b.release(); });
+  h->N = 0;
+  h->cap_r = h->cap_a = 0;
+  h->md_ready = false;
+  h->nb_struct = 0;
+  h->b_offsets.clear();
+  h->b_boxes.clear();
+  std::memset(&h->b_key, 0, sizeof(h->b_key));
+  std::memset(&h->b_last, 0, sizeof(h->b_last));
+}
+
+size_t workspace_bytes(nep_handle *h) {
+  size_t t = 0;
+  h->for_workspace([&](auto &b) { t += b.bytes(); });
+  return t;
+}
+}  // namespace nep
+
 // ======================================================================== C ABI
 extern "C" {
 
@@ -811,6 +868,9 @@ int nep_create(const nep_params *p, nep_handle **out) {
 int nep_destroy(nep_handle *h) {
   if (!h) return NEP_OK;
   if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->fire_graph) cudaGraphExecDestroy(h->fire_graph);
+  h->fire.release();
+  h->ck_fire.release();
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
   for (int sl = 0; sl < N_SLOTS; ++sl)
@@ -1273,10 +1333,11 @@ int md_init(nep_handle *h, int n_atoms, const double *pos, const int *types, con
   h->h_status->md_steps = 0;
   h->h_status->rebuild = 0;
   CK(cudaMemcpy(h->status.p, h->h_status, sizeof(BuildStatus), cudaMemcpyHostToDevice), "status");
-  if (h->graph) {
-    cudaGraphExecDestroy(h->graph);
-    h->graph = nullptr;
-  }
+  for (cudaGraphExec_t *g : {&h->graph, &h->fire_graph})
+    if (*g) {
+      cudaGraphExecDestroy(*g);
+      *g = nullptr;
+    }
   h->md_ready = true;
   return NEP_OK;
 }
@@ -1310,11 +1371,13 @@ int md_init_host(nep_handle *h, int n_atoms, const double *pos, const int *types
 
 namespace {
 // Launch one MD step on stream s (used both for capture and, if needed, directly).
-int md_step_launch(nep_handle *h, double dt, cudaStream_t s, bool capturing) {
+// One velocity-Verlet step (with `fire`: one FIRE step, the time step read on the device).
+int md_step_launch(nep_handle *h, double dt, cudaStream_t s, bool capturing, bool fire = false) {
   const int N = h->N;
   const double half_skin2 = 0.25 * h->skin * h->skin;
+  FireState *fs = fire ? h->fire.p : nullptr;
   ev_record(h, SLOT_DRIFT, 0, s, capturing);
-  launch_drift(N, atom_state(h), h->d_inv_mk.p, dt, half_skin2, h->status.p, s);
+  launch_drift(N, atom_state(h), h->d_inv_mk.p, dt, half_skin2, h->status.p, s, fs);
   ev_record(h, SLOT_DRIFT, 1, s, capturing);
   ev_record(h, SLOT_REBUILD, 0, s, capturing);
   const float rlR = (float)(h->rcR + h->skin), rlA = (float)(h->rcA + h->skin);
@@ -1359,11 +1422,12 @@ int md_step_launch(nep_handle *h, double dt, cudaStream_t s, bool capturing) {
     h->rebuild_kernels = 0;
   }
   ev_record(h, SLOT_REBUILD, 1, s, capturing);
-  int rc = run_forces(h, N, nullptr, h->F.p, nullptr, 1, 0.5 * dt, s, capturing);
+  int rc = run_forces(h, N, nullptr, h->F.p, nullptr, 1, 0.5 * dt, s, capturing, fs);
   if (rc) return rc;
   ev_record(h, SLOT_FINAL, 0, s, capturing);
   launch_finalize(h->ops->atom_blocks(N), h->partial_atom.p, h->ops->gather_blocks(N), h->partial_gather.p, nullptr,
                   nullptr, h->thermo_stage.p, h->thermo_ctl.p, N, h->volume, s);
+  if (fire) launch_fire_mix(N, atom_state(h), fs, 0, s);
   ev_record(h, SLOT_FINAL, 1, s, capturing);
   CK(cudaGetLastError(), "md step launch");
   return NEP_OK;
@@ -1371,7 +1435,8 @@ int md_step_launch(nep_handle *h, double dt, cudaStream_t s, bool capturing) {
 }  // namespace
 
 namespace {
-int md_queue(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *thermo, cudaStream_t s) {
+int md_queue(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *thermo, cudaStream_t s,
+             bool fire = false) {
   if (!h->md_ready) return fail(h, NEP_ERR_STATE, "md_run before md_init");
   if (n_steps < 0 || !(dt_fs > 0) || !std::isfinite(dt_fs) || thermo_every < 1)
     return fail(h, NEP_ERR_ARG, "need n_steps >= 0, dt > 0, thermo_every >= 1");
@@ -1382,15 +1447,23 @@ int md_queue(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double 
   CK(cudaMemcpyAsync(h->thermo_ctl.p, ctl, sizeof(ctl), cudaMemcpyHostToDevice, s), "thermo ctl");
   // (re)capture the one-step graph when the step size, the profiling mode or the thermo
   // staging buffer changed
-  if (!h->graph || h->graph_dt != dt_fs || h->graph_prof != h->prof || h->graph_thermo != h->thermo_stage.p ||
+  cudaGraphExec_t &gx = fire ? h->fire_graph : h->graph;
+  if (fire && gx && (h->graph_prof != h->prof || h->graph_thermo != h->thermo_stage.p ||
+                     h->graph_cond_used != h->graph_cond || h->graph_prec != h->precision)) {
+    cudaGraphExecDestroy(gx);
+    gx = nullptr;
+  }
+  if (!gx || (!fire && h->graph_dt != dt_fs) || h->graph_prof != h->prof || h->graph_thermo != h->thermo_stage.p ||
       h->graph_cond_used != h->graph_cond || h->graph_prec != h->precision) {
-    if (h->graph) {
-      cudaGraphExecDestroy(h->graph);
-      h->graph = nullptr;
-    }
+    // the MD and FIRE graphs share the capture settings: drop both when they change
+    for (cudaGraphExec_t *g : {&h->graph, &h->fire_graph})
+      if (*g) {
+        cudaGraphExecDestroy(*g);
+        *g = nullptr;
+      }
     CK(cudaStreamSynchronize(s), "sync");
     CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "capture");
-    int rc = md_step_launch(h, dt_fs, h->cap_stream, true);
+    int rc = md_step_launch(h, dt_fs, h->cap_stream, true, fire);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
     if (rc) {
@@ -1399,16 +1472,16 @@ int md_queue(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double 
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
     h->graph_kernels = count_kernel_nodes(graph);
-    e = cudaGraphInstantiate(&h->graph, graph, 0);
+    e = cudaGraphInstantiate(&gx, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
-    h->graph_dt = dt_fs;
+    if (!fire) h->graph_dt = dt_fs;
     h->graph_prof = h->prof;
     h->graph_thermo = h->thermo_stage.p;
     h->graph_cond_used = h->graph_cond;
     h->graph_prec = h->precision;
   }
-  for (int st = 0; st < n_steps; ++st) CK(cudaGraphLaunch(h->graph, s), "graph launch");
+  for (int st = 0; st < n_steps; ++st) CK(cudaGraphLaunch(gx, s), "graph launch");
   if (thermo && rows > 0)
     CK(cudaMemcpyAsync(thermo, h->thermo_stage.p, sizeof(double) * 4 * rows, cudaMemcpyDeviceToDevice, s), "thermo");
   return NEP_OK;
@@ -1434,13 +1507,13 @@ int md_run_async(nep_handle *h, int n_steps, double dt_fs, int thermo_every, dou
   return md_queue(h, n_steps, dt_fs, thermo_every, thermo, (cudaStream_t)stream);
 }
 
-int md_run(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *thermo, nep_stream_t stream) {
-  if (!valid_handle(h)) return NEP_ERR_ARG;
-  h->err.clear();
-  if (!h->md_ready) return fail(h, NEP_ERR_STATE, "md_run before md_init");
-  if (n_steps < 0 || !(dt_fs > 0) || !std::isfinite(dt_fs) || thermo_every < 1)
-    return fail(h, NEP_ERR_ARG, "need n_steps >= 0, dt > 0, thermo_every >= 1");
-  cudaStream_t s = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+// Velocity-Verlet (or FIRE) steps in chunks of whole thermo periods; each chunk starts from
+// a checkpoint so that a list overflow during it can be undone: restore, grow the lists,
+// rebuild, replay. A converged relaxation stops at the end of its chunk.
+int run_steps(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *thermo, cudaStream_t s, bool fire) {
   const int N = h->N;
   const size_t b = sizeof(double) * 3 * (size_t)N;
   CK(h->ck_x.ensure(3 * (size_t)N), "alloc checkpoint");
@@ -1448,6 +1521,7 @@ int md_run(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *t
   CK(h->ck_F.ensure(3 * (size_t)N), "alloc checkpoint");
   CK(h->ck_types.ensure((size_t)N), "alloc checkpoint");
   CK(h->ck_perm.ensure((size_t)N), "alloc checkpoint");
+  if (fire) CK(h->ck_fire.ensure(1), "alloc checkpoint");
   const size_t bi = sizeof(int) * (size_t)N;
   // chunks of whole thermo periods; each chunk starts from a checkpoint so that a list
   // overflow during it can be undone: restore, grow the lists, rebuild, replay
@@ -1460,12 +1534,13 @@ int md_run(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *t
     CK(cudaMemcpyAsync(h->ck_F.p, h->F.p, b, cudaMemcpyDeviceToDevice, s), "checkpoint");
     CK(cudaMemcpyAsync(h->ck_types.p, h->types.p, bi, cudaMemcpyDeviceToDevice, s), "checkpoint");
     CK(cudaMemcpyAsync(h->ck_perm.p, h->perm.p, bi, cudaMemcpyDeviceToDevice, s), "checkpoint");
+    if (fire) CK(cudaMemcpyAsync(h->ck_fire.p, h->fire.p, sizeof(FireState), cudaMemcpyDeviceToDevice, s), "checkpoint");
     int rc = read_status(h, s);
     if (rc) return rc;
     const long long steps0 = h->h_status->md_steps, rebuilds0 = h->h_status->n_rebuilds;
     for (int attempt = 0;; ++attempt) {
       double *th = thermo ? thermo + 4 * (size_t)(done / thermo_every) : nullptr;
-      rc = md_queue(h, c, dt_fs, thermo_every, th, s);
+      rc = md_queue(h, c, dt_fs, thermo_every, th, s, fire);
       if (rc) return rc;
       rc = read_status(h, s);
       if (rc) return rc;
@@ -1482,6 +1557,7 @@ int md_run(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *t
       CK(cudaMemcpyAsync(h->F.p, h->ck_F.p, b, cudaMemcpyDeviceToDevice, s), "restore");
       CK(cudaMemcpyAsync(h->types.p, h->ck_types.p, bi, cudaMemcpyDeviceToDevice, s), "restore");
       CK(cudaMemcpyAsync(h->perm.p, h->ck_perm.p, bi, cudaMemcpyDeviceToDevice, s), "restore");
+      if (fire) CK(cudaMemcpyAsync(h->fire.p, h->ck_fire.p, sizeof(FireState), cudaMemcpyDeviceToDevice, s), "restore");
       rc = ensure_lists(h, N, round_cap(st.max_r), round_cap(st.max_a));
       if (rc) return rc;
       rc = rebuild_lists(h, N, s);
@@ -1490,13 +1566,68 @@ int md_run(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *t
       h->h_status->n_rebuilds = rebuilds0;
       h->h_status->rebuild = 0;
       CK(cudaMemcpyAsync(h->status.p, h->h_status, sizeof(BuildStatus), cudaMemcpyHostToDevice, s), "status");
-      if (h->graph) {
-        cudaGraphExecDestroy(h->graph);
-        h->graph = nullptr;
-      }
+      for (cudaGraphExec_t *g : {&h->graph, &h->fire_graph})
+        if (*g) {
+          cudaGraphExecDestroy(*g);
+          *g = nullptr;
+        }
     }
     done += c;
+    if (fire && done < n_steps) {
+      FireState fs;
+      CK(cudaMemcpyAsync(&fs, h->fire.p, sizeof(fs), cudaMemcpyDeviceToHost, s), "fire state");
+      CK(cudaStreamSynchronize(s), "sync");
+      if (fs.converged) {
+        // the remaining steps would change nothing; keep the thermo rows complete
+        if (thermo) {
+          const int r0 = done / thermo_every, r1 = n_steps / thermo_every;
+          for (int r = r0; r < r1 && r > 0; ++r)
+            CK(cudaMemcpyAsync(thermo + 4 * (size_t)r, thermo + 4 * (size_t)(r0 - 1), 4 * sizeof(double),
+                               cudaMemcpyDeviceToDevice, s), "thermo");
+        }
+        break;
+      }
+    }
   }
+  return NEP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int md_run(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *thermo, nep_stream_t stream) {
+  if (!valid_handle(h)) return NEP_ERR_ARG;
+  h->err.clear();
+  if (!h->md_ready) return fail(h, NEP_ERR_STATE, "md_run before md_init");
+  if (n_steps < 0 || !(dt_fs > 0) || !std::isfinite(dt_fs) || thermo_every < 1)
+    return fail(h, NEP_ERR_ARG, "need n_steps >= 0, dt > 0, thermo_every >= 1");
+  return run_steps(h, n_steps, dt_fs, thermo_every, thermo, (cudaStream_t)stream, false);
+}
+
+int fire_run(nep_handle *h, int n_steps, double dt0_fs, double fmax, double *thermo, int *steps_taken,
+             nep_stream_t stream) {
+  if (!valid_handle(h)) return NEP_ERR_ARG;
+  h->err.clear();
+  if (!h->md_ready) return fail(h, NEP_ERR_STATE, "fire_run before md_init");
+  if (n_steps < 0 || !(dt0_fs > 0) || !std::isfinite(dt0_fs) || !(fmax >= 0) || !std::isfinite(fmax))
+    return fail(h, NEP_ERR_ARG, "need n_steps >= 0, dt0 > 0, fmax >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int N = h->N;
+  CK(h->fire.ensure(1), "alloc fire");
+  FireState fs{};
+  fs.dt = dt0_fs;
+  fs.alpha = 0.1;
+  fs.dt_max = 10.0 * dt0_fs;
+  fs.fmax2 = fmax * fmax;
+  CK(cudaMemsetAsync(h->v.p, 0, sizeof(double) * 3 * (size_t)N, s), "zero velocities");
+  CK(cudaMemcpyAsync(h->fire.p, &fs, sizeof(fs), cudaMemcpyHostToDevice, s), "fire state");
+  launch_fire_mix(N, atom_state(h), h->fire.p, 1, s);  // already converged at the start?
+  CK(cudaGetLastError(), "fire start");
+  int rc = run_steps(h, n_steps, dt0_fs, 1, thermo, s, true);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(&fs, h->fire.p, sizeof(fs), cudaMemcpyDeviceToHost, s), "fire state");
+  CK(cudaStreamSynchronize(s), "sync");
+  if (steps_taken) *steps_taken = fs.steps;
   return NEP_OK;
 }
 

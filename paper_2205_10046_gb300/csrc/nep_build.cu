@@ -337,8 +337,13 @@ __global__ void iota_kernel(int N, int *perm) {
 
 // Velocity Verlet, first half: v += dt/2 F/m; x += dt v; refresh cell-local coordinates;
 // request a rebuild when an atom moved more than skin/2 since the last build.
+// With a FIRE state, its time step is used and a converged relaxation stays where it is.
 __global__ void md_drift_kernel(int N, AtomState a, const double *inv_mass_kappa, double dt, double half_skin2,
-                                BuildStatus *st) {
+                                BuildStatus *st, const FireState *fire) {
+  if (fire) {
+    if (fire->converged) return;
+    dt = fire->dt;
+  }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) st->md_steps += 1;
   if (i >= N) return;
@@ -672,8 +677,82 @@ void launch_rebuild_condition(cudaGraphConditionalHandle hc, const BuildStatus *
 void launch_iota(int N, int *perm, cudaStream_t s) { iota_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, perm); }
 
 void launch_drift(int N, const AtomState &a, const double *inv_mass_kappa, double dt, double half_skin2,
-                  BuildStatus *st, cudaStream_t s) {
-  md_drift_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, a, inv_mass_kappa, dt, half_skin2, st);
+                  BuildStatus *st, cudaStream_t s, const FireState *fire) {
+  md_drift_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, a, inv_mass_kappa, dt, half_skin2, st, fire);
+}
+
+// FIRE velocity mixing after a velocity-Verlet step (Bitzek et al. 2006), one block, FP64
+// sums in a fixed order: P = F . v, |F|, |v| over all atoms and max_i |F_i|^2. Converged
+// when max_i |F_i| < fmax (then nothing moves again). Otherwise, for P > 0:
+// v <- (1 - alpha) v + alpha |v| F / |F|, and after more than N_min such steps in a row the
+// step grows (dt <- min(f_inc dt, dt_max)) and alpha shrinks (alpha <- f_alpha alpha); for
+// P <= 0: v <- 0, dt <- f_dec dt, alpha <- alpha_start. check_only: only the convergence test
+// (for the starting forces).
+constexpr int kFireNmin = 5;
+constexpr double kFireFinc = 1.1, kFireFdec = 0.5, kFireAlphaStart = 0.1, kFireFalpha = 0.99;
+
+__global__ void fire_mix_kernel(int N, AtomState a, FireState *fire, int check_only) {
+  __shared__ double red[4][1024];
+  __shared__ int decision;
+  if (fire->converged) return;
+  double p = 0.0, ff = 0.0, vv = 0.0, fm = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const double *F = a.F + 3 * (size_t)i, *v = a.v + 3 * (size_t)i;
+    const double f2 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
+    p += F[0] * v[0] + F[1] * v[1] + F[2] * v[2];
+    ff += f2;
+    vv += v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    fm = fmax(fm, f2);
+  }
+  red[0][threadIdx.x] = p;
+  red[1][threadIdx.x] = ff;
+  red[2][threadIdx.x] = vv;
+  red[3][threadIdx.x] = fm;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + o];
+      red[1][threadIdx.x] += red[1][threadIdx.x + o];
+      red[2][threadIdx.x] += red[2][threadIdx.x + o];
+      red[3][threadIdx.x] = fmax(red[3][threadIdx.x], red[3][threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  const double P = red[0][0], FF = red[1][0], VV = red[2][0], FM = red[3][0];
+  if (threadIdx.x == 0) {
+    decision = 0;
+    if (!check_only) fire->steps += 1;  // velocity-Verlet steps taken
+    if (FM < fire->fmax2) fire->converged = 1;
+    else if (!check_only) decision = P > 0.0 ? 1 : 2;
+  }
+  __syncthreads();
+  if (decision == 0) return;
+  const double alpha = fire->alpha;
+  const double c1 = decision == 1 ? 1.0 - alpha : 0.0;
+  const double c2 = (decision == 1 && FF > 0.0) ? alpha * sqrt(VV / FF) : 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    double *v = a.v + 3 * (size_t)i;
+    const double *F = a.F + 3 * (size_t)i;
+    for (int b = 0; b < 3; ++b) v[b] = c1 * v[b] + c2 * F[b];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (decision == 1) {
+      if (fire->n_pos > kFireNmin) {
+        fire->dt = fmin(fire->dt * kFireFinc, fire->dt_max);
+        fire->alpha = alpha * kFireFalpha;
+      }
+      fire->n_pos += 1;
+    } else {
+      fire->dt *= kFireFdec;
+      fire->alpha = kFireAlphaStart;
+      fire->n_pos = 0;
+    }
+  }
+}
+
+void launch_fire_mix(int N, const AtomState &a, FireState *fire, int check_only, cudaStream_t s) {
+  fire_mix_kernel<<<1, 1024, 0, s>>>(N, a, fire, check_only);
 }
 
 void launch_export(int N, const AtomState &a, const Grid &g, const Batch &B, double *pos, double *vel, double *force,

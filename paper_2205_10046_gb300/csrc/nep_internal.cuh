@@ -72,6 +72,19 @@ struct BuildStatus {
   long long md_steps;
 };
 
+// FIRE minimisation state (Bitzek et al., Phys. Rev. Lett. 97, 170201 (2006)), kept on the
+// device so that a relaxation step needs no host round trip.
+struct FireState {
+  double dt;         // current time step (fs)
+  double alpha;      // current mixing factor
+  double dt_max;     // largest time step
+  double fmax2;      // convergence threshold on max_i |F_i|^2
+  int n_pos;         // consecutive steps with P = F . v > 0
+  int converged;     // set once max_i |F_i| < fmax: later steps change nothing
+  int steps;         // steps taken before convergence
+  int pad;
+};
+
 // Pair vector d = r_j - r_i from cell-local FP32 coordinates and the shift of the image
 // code. The explicitly rounded operations make d_ji the exact negation of d_ij, so both
 // atoms of a pair take the same inclusion decision in every kernel.
@@ -134,6 +147,7 @@ struct AtomArgs {
   long long s_erad, s_pang;           // strides of e_rad, p_ang
   long long s_out;                    // atoms per member in energy (x1), force (x3), virial (x9)
   const double *f_tar;     // [N][3] caller order, or null: sum of (F_i - F_tar,i)^2 per block
+  const FireState *fire;   // FIRE relaxation: kick with its dt, none once converged (or null)
 };
 
 // Model constants of one handle, FP32.
@@ -181,6 +195,7 @@ void launch_shift_tables(int n_struct, const Grid *grids, int ncode, int obits, 
 void launch_struct_sums(int n_struct, int members, const int *offsets, int N, const double *e_atom,
                         const double *w_atom, double *e_struct, double *w_struct, cudaStream_t s);
 void launch_arm_rebuild(BuildStatus *st, cudaStream_t s);
+void launch_fire_mix(int N, const AtomState &a, FireState *fire, int check_only, cudaStream_t s);
 // population evaluation: parameter vectors into kernel arrays, BF16 tiles, Eq. loss
 void launch_unpack_population(int n_pop, const double *z, int n_par, int n_cr, int n_ca, float *cr, float *ca,
                               float *ann, double *reg, cudaStream_t s);

@@ -941,9 +941,9 @@ __global__ void __launch_bounds__(GB)
       const double ex = Fx - ft[0], ey = Fy - ft[1], ez = Fz - ft[2];
       part[11] = ex * ex + ey * ey + ez * ez;
     }
-    if (a.md_kick) {  // second half-kick of velocity Verlet, and kinetic energy
+    if (a.md_kick && !(a.fire && a.fire->converged)) {  // second half-kick of velocity Verlet, kinetic energy
       double *v = a.vel + 3 * (size_t)i;
-      const double s = a.half_dt * a.inv_mass_kappa[ti];
+      const double s = (a.fire ? 0.5 * a.fire->dt : a.half_dt) * a.inv_mass_kappa[ti];
       const double vx = v[0] + s * Fx, vy = v[1] + s * Fy, vz = v[2] + s * Fz;
       v[0] = vx; v[1] = vy; v[2] = vz;
       part[1] = a.mass_kappa_half[ti] * (vx * vx + vy * vy + vz * vz);

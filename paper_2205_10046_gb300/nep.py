@@ -51,6 +51,31 @@ class nep_tuning(C.Structure):
                 ("default_ms", C.c_float)]
 
 
+class nep_server_config(C.Structure):
+    _fields_ = [("memory_budget", C.c_size_t), ("workers", C.c_int), ("precision", C.c_int)]
+
+
+class nep_job(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n_atoms", C.c_int), ("pos", C.c_void_p), ("types", C.c_void_p),
+                ("vel", C.c_void_p), ("box", C.c_double * 9), ("n_steps", C.c_int), ("dt_fs", C.c_double),
+                ("fmax", C.c_double)]
+
+
+class nep_result(C.Structure):
+    _fields_ = [("id", C.c_longlong), ("status", C.c_int), ("kind", C.c_int), ("n_atoms", C.c_int),
+                ("steps", C.c_int), ("energy", C.c_double), ("virial", C.c_double * 9), ("t_submit", C.c_double),
+                ("t_start", C.c_double), ("t_done", C.c_double), ("workspace_est", C.c_size_t),
+                ("workspace_used", C.c_size_t), ("message", C.c_char * 160)]
+
+
+class nep_server_stats(C.Structure):
+    _fields_ = [("queued", C.c_int), ("running", C.c_int), ("completed", C.c_longlong), ("failed", C.c_longlong),
+                ("bytes_reserved", C.c_size_t), ("peak_bytes_reserved", C.c_size_t),
+                ("atom_evaluations", C.c_double)]
+
+
+JOB_SINGLE, JOB_FIRE, JOB_NVE = 0, 1, 2
+
 _lib = None
 
 # exported symbol -> (restype, argtypes)
@@ -73,6 +98,7 @@ _SIGS = {
     "md_init_host": (C.c_int, [_P, C.c_int, _P, _P, _P, _P]),
     "md_run": (C.c_int, [_P, C.c_int, C.c_double, C.c_int, _P, _P]),
     "md_run_async": (C.c_int, [_P, C.c_int, C.c_double, C.c_int, _P, _P]),
+    "fire_run": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, _P, C.POINTER(C.c_int), _P]),
     "md_status": (C.c_int, [_P, _P]),
     "md_get_state": (C.c_int, [_P, _P, _P, _P, _P]),
     "md_get_state_host": (C.c_int, [_P, _P, _P, _P]),
@@ -85,6 +111,12 @@ _SIGS = {
     "nep_kernel_times": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int]),
     "nep_supported": (C.c_int, [C.POINTER(C.c_int), C.c_int]),
     "nep_descriptors_static": (C.c_int, [C.POINTER(nep_params), C.c_int, _P, _P, _P, _P, _P]),
+    "nep_server_create": (C.c_int, [C.POINTER(nep_params), C.POINTER(nep_server_config), C.POINTER(_P)]),
+    "nep_server_submit": (C.c_int, [_P, C.POINTER(nep_job), C.POINTER(C.c_longlong)]),
+    "nep_server_wait": (C.c_int, [_P, C.c_double, C.POINTER(nep_result)]),
+    "nep_server_arrays": (C.c_int, [_P, C.c_longlong, _P, _P, _P]),
+    "nep_server_stats_get": (C.c_int, [_P, C.POINTER(nep_server_stats)]),
+    "nep_server_destroy": (C.c_int, [_P]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -341,6 +373,16 @@ def md_run_async(h, n_steps: int, dt_fs: float, thermo_every: int = 1, thermo=No
     _check(rc, h)
 
 
+def fire_run(h, n_steps: int, dt0_fs: float, fmax: float, thermo=None) -> int:
+    """FIRE relaxation from the md_init state; returns the steps taken before convergence."""
+    import torch
+    steps = C.c_int(0)
+    rc = load().fire_run(h, int(n_steps), float(dt0_fs), float(fmax),
+                         _dev(thermo, torch.float64, (n_steps, 4), "thermo"), C.byref(steps), _stream())
+    _check(rc, h)
+    return int(steps.value)
+
+
 def md_status(h, stream=None):
     _check(load().md_status(h, _stream() if stream is None else stream), h)
 
@@ -440,3 +482,69 @@ class NEP:
         nep_compute_batch(self.h, off, pos, types, boxes, out.get("U"), out["E_struct"], out["F"], out.get("W"),
                           out["W_struct"])
         return out
+
+
+# ----------------------------------------------------------------------------- serving
+class Server:
+    """A running nep_server: submit jobs (host arrays), collect results in completion order."""
+
+    def __init__(self, model, memory_budget: int, workers: int = 16, precision: int = 0, skin: float = 1.0):
+        lib = load()
+        p, self._keep = _params(model, skin)
+        cfg = nep_server_config(int(memory_budget), int(workers), int(precision))
+        h = C.c_void_p()
+        _check(lib.nep_server_create(C.byref(p), C.byref(cfg), C.byref(h)), None)
+        self.h = h
+        self.n = {}
+
+    def submit(self, kind: int, pos, types, box, n_steps: int = 0, dt_fs: float = 1.0, fmax: float = 0.0,
+               vel=None) -> int:
+        pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+        types = np.ascontiguousarray(types, dtype=np.int32)
+        v = None if vel is None else np.ascontiguousarray(vel, dtype=np.float64).reshape(-1, 3)
+        j = nep_job(int(kind), pos.shape[0], pos.ctypes.data, types.ctypes.data, None if v is None else v.ctypes.data,
+                    (C.c_double * 9)(*_box(box).ravel()), int(n_steps), float(dt_fs), float(fmax))
+        jid = C.c_longlong(0)
+        rc = load().nep_server_submit(self.h, C.byref(j), C.byref(jid))
+        if rc != NEP_OK:
+            raise NepError(rc, "nep_server_submit")
+        self.n[int(jid.value)] = pos.shape[0]
+        return int(jid.value)
+
+    def wait(self, timeout_s: float = -1.0):
+        """Next finished job as a dict, or None on timeout."""
+        r = nep_result()
+        rc = load().nep_server_wait(self.h, float(timeout_s), C.byref(r))
+        if rc == -8:
+            return None
+        if rc != NEP_OK:
+            raise NepError(rc, "nep_server_wait")
+        out = {f: getattr(r, f) for f, _ in nep_result._fields_}
+        out["virial"] = np.array(r.virial[:])
+        out["message"] = r.message.decode(errors="replace")
+        return out
+
+    def arrays(self, job_id: int):
+        """(pos, force, vel) of a finished job."""
+        n = self.n.pop(job_id)
+        pos, force, vel = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 3))
+        rc = load().nep_server_arrays(self.h, int(job_id), pos.ctypes.data, force.ctypes.data, vel.ctypes.data)
+        if rc != NEP_OK:
+            raise NepError(rc, "nep_server_arrays")
+        return pos, force, vel
+
+    def stats(self) -> dict:
+        st = nep_server_stats()
+        _check(load().nep_server_stats_get(self.h, C.byref(st)), None)
+        return {f: getattr(st, f) for f, _ in nep_server_stats._fields_}
+
+    def close(self):
+        if self.h:
+            load().nep_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

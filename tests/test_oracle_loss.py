@@ -72,3 +72,59 @@ def test_batch_predictions_match_single_structures():
     np.testing.assert_array_equal(F[8:], F2)
     assert e[1] == 0.0 and np.all(w[1] == 0.0)
     np.testing.assert_allclose(w[2], oracle.virial6(W2.sum(0))[0] / 12, rtol=0, atol=1e-15)
+
+
+# ----------------------------------------------------------------------------- FIRE pins
+def _quadratic(k, x0):
+    def f(x):
+        d = x - x0
+        return 0.5 * float(np.sum(k[:, None] * d * d)), -k[:, None] * d
+    return f
+
+
+def test_fire_reaches_the_minimum_of_a_quadratic():
+    rng = np.random.default_rng(0)
+    x0 = rng.normal(size=(6, 3))
+    k = rng.uniform(0.5, 2.0, 6)
+    start = x0 + rng.normal(0, 0.3, x0.shape)
+    x, E, F, steps, energies = oracle.fire_minimize(_quadratic(k, x0), start, np.ones(6), 500, 0.1, 1e-6)
+    assert np.max(np.linalg.norm(F, axis=1)) < 1e-6 and steps < 500
+    np.testing.assert_allclose(x, x0, atol=1e-5)
+    assert E < 1e-11
+
+
+def test_fire_first_steps_follow_the_definition():
+    # one particle, 1-D quadratic: the first step is plain velocity Verlet from rest, then the
+    # FIRE mixing with P > 0 leaves the velocity direction (it is parallel to F)
+    f = _quadratic(np.array([1.0]), np.zeros((1, 3)))
+    x_start = np.array([[1.0, 0.0, 0.0]])
+    x, E, F, steps, _ = oracle.fire_minimize(f, x_start, np.ones(1), 1, 0.1, 0.0)
+    dt = 0.1
+    v_half = 0.5 * dt * 1.0            # F(x=1) = -1 along -x
+    x1 = 1.0 - dt * v_half
+    assert steps == 1 and abs(x[0, 0] - x1) < 1e-15
+
+
+def test_fire_overshoot_resets_velocity_and_halves_the_step():
+    # worked by hand (binary fractions, exact): k = m = 1, x = 1, dt = 1.5.
+    # step 1: v = -0.75, x = -0.125, F = 0.125, v = -0.65625; P < 0: v = 0, dt = 0.75.
+    # step 2: v = 0.046875, x = -0.08984375, F = 0.08984375, v = 0.080566...; P > 0.
+    # step 3 (alpha = 0.1, velocity parallel to F: the mixing keeps it):
+    #   v = 0.0805664... + 0.375 F, x = x + 0.75 v.
+    f = _quadratic(np.array([1.0]), np.zeros((1, 3)))
+    x_start = np.array([[1.0, 0.0, 0.0]])
+    x, _, _, steps, _ = oracle.fire_minimize(f, x_start, np.ones(1), 1, 1.5, 0.0)
+    assert x[0, 0] == -0.125
+    x, _, F, steps, _ = oracle.fire_minimize(f, x_start, np.ones(1), 2, 1.5, 0.0)
+    assert steps == 2 and x[0, 0] == -0.08984375 and F[0, 0] == 0.08984375
+    v2 = 0.046875 + 0.375 * 0.08984375
+    v25 = v2 + 0.375 * 0.08984375
+    x3 = -0.08984375 + 0.75 * v25
+    x, _, _, _, _ = oracle.fire_minimize(f, x_start, np.ones(1), 3, 1.5, 0.0)
+    assert abs(x[0, 0] - x3) < 1e-15
+
+
+def test_fire_stops_on_the_starting_forces():
+    f = _quadratic(np.ones(2), np.zeros((2, 3)))
+    x, E, F, steps, en = oracle.fire_minimize(f, np.full((2, 3), 1e-9), np.ones(2), 10, 0.1, 1e-3)
+    assert steps == 0 and en == []
