@@ -27,6 +27,10 @@ import sys
 import threading
 import time
 
+# more hardware work queues than the default 8, so that the serving workers' streams
+# (one per concurrent job) do not share queues (read when the CUDA context is created)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -51,6 +55,11 @@ def parse_args():
     ap.add_argument("--no-batch", action="store_true", help="skip the structure-batch and population forms")
     ap.add_argument("--batch-only", action="store_true", help="only the structure-batch and population forms")
     ap.add_argument("--batch-calls", type=int, default=20)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-only", action="store_true", help="only the serving measurement")
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window of each serving run")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (requests/s)")
+    ap.add_argument("--serve-workers", type=int, default=16)
     ap.add_argument("--pop-calls", type=int, default=5)
     return ap.parse_args()
 
@@ -412,6 +421,126 @@ def run_batch_forms(args, dev, stream, flush, peak):
     return out, pop
 
 
+# ----------------------------------------------------------------------------- serving
+SERVE_BUDGET = 40 << 30  # bytes of device workspace admitted at once
+
+
+def serve_requests(rate, seconds, seed, pool):
+    """Poisson arrivals: (arrival time, structure index in the pool, kind, steps)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= seconds:
+            return out
+        u = rng.uniform()
+        kind, steps = (0, 0) if u < 0.5 else ((1, 50) if u < 0.8 else (2, int(rng.integers(10, 1001))))
+        out.append((t, int(rng.integers(0, len(pool))), kind, steps))
+
+
+def serve_pool(n_pool, seed):
+    """Structures of 32-20,000 atoms (log-uniform), 1-3 species, FCC/BCC/diamond, +-10% shear,
+    sigma 0.1 A, with 300 K velocities for the NVE jobs."""
+    import numpy as np
+    from paper_2205_10046_gb300 import workloads as W
+    rng = np.random.default_rng(seed)
+    m = W.mixed_model(0)
+    pool = []
+    for k in range(n_pool):
+        n = int(np.exp(rng.uniform(np.log(32), np.log(20000))))
+        pos, types, box = W.random_structure(200000 + k, n)
+        vel = W.maxwell_boltzmann(m.mass[types], 300.0, 300000 + k)
+        pool.append((pos, types, box, vel))
+    return pool
+
+
+def serve_run(model, pool, reqs, precision, workers):
+    """Submit the requests at their arrival times; collect every result."""
+    import numpy as np
+    from paper_2205_10046_gb300 import nep
+    srv = nep.Server(model, memory_budget=SERVE_BUDGET, workers=workers, precision=precision)
+    done = {}
+    offered = 0.0
+    lag = []
+
+    def collector():
+        while len(done) < len(reqs):
+            r = srv.wait(0.5)
+            if r is not None:
+                done[r["id"]] = r
+                srv.drop(r["id"])
+
+    th = threading.Thread(target=collector)
+    th.start()
+    t0 = time.perf_counter()
+    kinds = {}
+    for (t, k, kind, steps) in reqs:
+        delay = t - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        lag.append(max(0.0, -delay))
+        pos, types, box, vel = pool[k]
+        jid = srv.submit(kind, pos, types, box, n_steps=steps, dt_fs=1.0, fmax=0.0, vel=vel if kind == 2 else None)
+        kinds[jid] = kind
+        offered += pos.shape[0] * (1 if kind == 0 else steps + 2)
+    th.join()
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    res = list(done.values())
+    lat = np.array([r["t_done"] - r["t_submit"] for r in res])
+    wait = np.array([r["t_start"] - r["t_submit"] for r in res])
+    t_first = min(r["t_start"] for r in res)
+    t_last = max(r["t_done"] for r in res)
+    pct = lambda a, q: float(np.percentile(a, q)) * 1e3 if a.size else None
+    by_kind = {}
+    for kind, name in ((0, "single_point"), (1, "fire_50"), (2, "nve")):
+        lk = np.array([r["t_done"] - r["t_submit"] for r in res if kinds.get(r["id"]) == kind])
+        by_kind[name] = {"n": int(lk.size), "p50_ms": pct(lk, 50), "p99_ms": pct(lk, 99)}
+    return {
+        "requests": len(reqs), "completed": int(st["completed"]), "failed": int(st["failed"]),
+        "latency_ms": {"p50": pct(lat, 50), "p90": pct(lat, 90), "p99": pct(lat, 99), "max": pct(lat, 100)},
+        "queue_wait_ms": {"p50": pct(wait, 50), "p99": pct(wait, 99)},
+        "by_kind": by_kind,
+        "throughput_atom_evaluations_per_s": st["atom_evaluations"] / (t_last - t_first),
+        "offered_atom_evaluations_per_s": offered / reqs[-1][0],
+        "service_seconds": t_last - t_first, "wall_seconds": wall,
+        "peak_bytes_reserved": int(st["peak_bytes_reserved"]),
+        "submit_lag_ms_p99": float(np.percentile(lag, 99)) * 1e3,
+        "errors": sorted({r["message"] for r in res if r["status"] != 0})[:3],
+    }
+
+
+def run_serving(args):
+    """Config-4 serving: Poisson arrivals of single-point (50%), 50-step FIRE (30%) and NVE
+    (20%, 10-1000 steps of 1 fs) jobs on 32-20,000-atom structures, 40 GB admission budget,
+    FP32 and BF16 forms; then both forms again at half the measured FP32 capacity."""
+    from paper_2205_10046_gb300 import workloads as W
+    model = W.mixed_model(0)
+    pool = serve_pool(256, 4)
+    reqs = serve_requests(args.serve_rate, args.serve_seconds, 5, pool)
+    out = {"workload": (f"Poisson {args.serve_rate:.0f} req/s for {args.serve_seconds:.0f} s ({len(reqs)} requests); "
+                        f"structures drawn from a pool of 256 (32-20,000 atoms, log-uniform, FCC/BCC/diamond, "
+                        f"1-3 of 3 species); 50% single point, 30% 50-step FIRE, 20% NVE U{{10..1000}} steps "
+                        f"of 1 fs; NEP rc 5.5/4.0 n_max 8/4 40 neurons; {args.serve_workers} workers, "
+                        f"{SERVE_BUDGET >> 30} GB admission budget"),
+           "latency": "submission (arrival) to result on the host, server clock"}
+    for prec, key in ((0, "fp32"), (1, "bf16")):
+        out[key] = serve_run(model, pool, reqs, prec, args.serve_workers)
+    # a load the server sustains: half the FP32 capacity measured above
+    cap = out["fp32"]["throughput_atom_evaluations_per_s"]
+    work = out["fp32"]["offered_atom_evaluations_per_s"] / args.serve_rate  # per request
+    rate2 = max(10.0, 0.5 * cap / work)
+    reqs2 = serve_requests(rate2, args.serve_seconds, 6, pool)
+    out["half_capacity"] = {"rate_req_per_s": rate2, "requests": len(reqs2)}
+    for prec, key in ((0, "fp32"), (1, "bf16")):
+        out["half_capacity"][key] = serve_run(model, pool, reqs2, prec, args.serve_workers)
+    out["force_error_vs_fp64_oracle"] = ("FP32 form: relative force RMS <= 1e-5 (tests/test_gpu_serve.py); "
+                                         "BF16 form: force RMSE <= 1 meV/A (tests/test_gpu_bf16.py)")
+    return out
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_gb300(args):
     import numpy as np
@@ -436,6 +565,13 @@ def run_gb300(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     props = torch.cuda.get_device_properties(dev)
+    if args.serve_only:
+        clk = ClockSampler(torch.cuda.current_device() if world == 1 else local)
+        with clk:
+            sv = run_serving(args)
+        if rank == 0:
+            print(json.dumps({"serving": sv, "clocks": clk.summary()}), flush=True)
+        return 0
     if args.batch_only:
         clk = ClockSampler(torch.cuda.current_device() if world == 1 else local)
         with clk:
@@ -527,6 +663,11 @@ def run_gb300(args):
             batch_forms = run_batch_forms(args, dev, stream, flush,
                                           props.multi_processor_count * 128 * 2 * 2070e6 / 1e12)
         batch_forms[0]["clocks"] = bclk.summary()
+    serving = None
+    if not args.no_serve and world == 1:
+        with ClockSampler(torch.cuda.current_device()) as sclk:
+            serving = run_serving(args)
+        serving["clocks"] = sclk.summary()
     if rank == 0:
         clocks = clk.summary()
         sm_max = clocks.get("sm_max_mhz") or 2070.0
@@ -567,6 +708,8 @@ def run_gb300(args):
         }
         if batch_forms is not None:
             line["batch_form"], line["population"] = batch_forms
+        if serving is not None:
+            line["serving"] = serving
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
         print(json.dumps(line), flush=True)

@@ -3,7 +3,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <thread>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -195,6 +197,17 @@ thread_local std::string g_create_error;  // per calling thread (serving workers
 // a workspace never synchronises the device.
 thread_local cudaStream_t t_alloc_stream = nullptr;
 thread_local bool t_alloc_async = false;
+
+// Wait for a stream. Threads in the stream-ordered mode (the serving workers, many per CPU
+// core) poll with short sleeps instead of spinning in cudaStreamSynchronize.
+cudaError_t wait_stream(cudaStream_t s) {
+  if (!t_alloc_async) return cudaStreamSynchronize(s);
+  for (;;) {
+    const cudaError_t e = cudaStreamQuery(s);
+    if (e != cudaErrorNotReady) return e;
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
 
 template <class Tp>
 struct DevBuf {
@@ -410,7 +423,7 @@ int ensure_lists(nep_handle *h, int N, int cap_r, int cap_a) {
 
 int read_status(nep_handle *h, cudaStream_t s) {
   CK(cudaMemcpyAsync(h->h_status, h->status.p, sizeof(BuildStatus), cudaMemcpyDeviceToHost, s), "status");
-  CK(cudaStreamSynchronize(s), "sync");
+  CK(wait_stream(s), "sync");
   return NEP_OK;
 }
 
@@ -457,7 +470,7 @@ int rebuild_lists(nep_handle *h, int N, cudaStream_t s, const Batch &B = Batch{n
   for (int attempt = 0; attempt < 3; ++attempt) {
     const bool count_only = (h->cap_r == 0 || h->cap_a == 0);
     CK(cudaMemcpyAsync(h->h_status, h->status.p, sizeof(BuildStatus), cudaMemcpyDeviceToHost, s), "status");
-    CK(cudaStreamSynchronize(s), "sync");
+    CK(wait_stream(s), "sync");
     reset_status_counts(h);
     h->h_status->rebuild = 1;
     CK(cudaMemcpyAsync(h->status.p, h->h_status, sizeof(BuildStatus), cudaMemcpyHostToDevice, s), "status");
@@ -620,7 +633,7 @@ int setup_batch(nep_handle *h, int n_struct, const int *offsets, const double *b
        "copy offsets");
     launch_shift_tables(n_struct, h->d_grids.p, ncode, obits, h->dtab.p, s);
     // the copies above read pageable host memory that changes on the next call
-    CK(cudaStreamSynchronize(s), "batch setup");
+    CK(wait_stream(s), "batch setup");
     h->b_gen += 1;
     h->b_offsets.assign(offsets, offsets + n_struct + 1);
     h->b_boxes.assign(boxes, boxes + 9 * (size_t)n_struct);
@@ -723,7 +736,7 @@ int capture_batch(nep_handle *h, int N, const BatchOut &o, cudaStream_t s) {
     h->b_graph = nullptr;
   }
   std::memset(&h->b_key, 0, sizeof(h->b_key));
-  CK(cudaStreamSynchronize(s), "sync");
+  CK(wait_stream(s), "sync");
   cudaStream_t c = h->cap_stream;
   CK(cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal), "capture");
   cudaMemcpyAsync(h->x.p, o.pos, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, c);
@@ -784,6 +797,8 @@ void release_workspace(nep_handle *h) {
   std::memset(&h->b_key, 0, sizeof(h->b_key));
   std::memset(&h->b_last, 0, sizeof(h->b_last));
 }
+
+cudaError_t stream_sync(cudaStream_t s) { return wait_stream(s); }
 
 size_t workspace_bytes(nep_handle *h) {
   size_t t = 0;
@@ -968,7 +983,7 @@ int nep_compute_batch(nep_handle *h, int n_struct, const int *offsets, const dou
   BatchKey key = batch_key(h, N, o);
   if (!h->prof && h->b_graph && std::memcmp(&key, &h->b_key, sizeof(key)) == 0) {
     CK(cudaGraphLaunch(h->b_graph, s), "batch graph launch");
-    CK(cudaStreamSynchronize(s), "batch graph");
+    CK(wait_stream(s), "batch graph");
     const BuildStatus &st = *h->h_status;
     if (st.bad_input & 1) return fail(h, NEP_ERR_ARG, "atom type out of range");
     if (st.bad_input & 2) return fail(h, NEP_ERR_NONFINITE, "non-finite position");
@@ -1328,7 +1343,7 @@ int md_init(nep_handle *h, int n_atoms, const double *pos, const int *types, con
   if (rc) return rc;
   rc = run_forces(h, n_atoms, nullptr, h->F.p, nullptr, 0, 0.0, s, false);
   if (rc) return rc;
-  CK(cudaStreamSynchronize(s), "md_init");
+  CK(wait_stream(s), "md_init");
   h->h_status->n_rebuilds = 0;
   h->h_status->md_steps = 0;
   h->h_status->rebuild = 0;
@@ -1461,7 +1476,7 @@ int md_queue(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double 
         cudaGraphExecDestroy(*g);
         *g = nullptr;
       }
-    CK(cudaStreamSynchronize(s), "sync");
+    CK(wait_stream(s), "sync");
     CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "capture");
     int rc = md_step_launch(h, dt_fs, h->cap_stream, true, fire);
     cudaGraph_t graph = nullptr;
@@ -1576,7 +1591,7 @@ int run_steps(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double
     if (fire && done < n_steps) {
       FireState fs;
       CK(cudaMemcpyAsync(&fs, h->fire.p, sizeof(fs), cudaMemcpyDeviceToHost, s), "fire state");
-      CK(cudaStreamSynchronize(s), "sync");
+      CK(wait_stream(s), "sync");
       if (fs.converged) {
         // the remaining steps would change nothing; keep the thermo rows complete
         if (thermo) {
@@ -1626,7 +1641,7 @@ int fire_run(nep_handle *h, int n_steps, double dt0_fs, double fmax, double *the
   int rc = run_steps(h, n_steps, dt0_fs, 1, thermo, s, true);
   if (rc) return rc;
   CK(cudaMemcpyAsync(&fs, h->fire.p, sizeof(fs), cudaMemcpyDeviceToHost, s), "fire state");
-  CK(cudaStreamSynchronize(s), "sync");
+  CK(wait_stream(s), "sync");
   if (steps_taken) *steps_taken = fs.steps;
   return NEP_OK;
 }

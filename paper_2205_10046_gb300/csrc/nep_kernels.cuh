@@ -24,6 +24,9 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include <mutex>
+#include <unordered_map>
+
 #include "nep_internal.cuh"
 
 namespace nep {
@@ -967,6 +970,23 @@ __global__ void __launch_bounds__(GB)
 }
 
 // ------------------------------------------------------------------------ launchers
+// Raise a kernel's dynamic shared memory limit once, to a bound that covers every launch
+// (any type count up to kMaxTypes, the largest shift table). The attribute is per function
+// and process-wide: setting it per launch to that launch's size would race between threads
+// launching the same kernel with different sizes.
+template <class K>
+cudaError_t smem_limit_once(K kern, size_t bound) {
+  static std::mutex mu;
+  static std::unordered_map<const void *, size_t> done;
+  std::lock_guard<std::mutex> lk(mu);
+  const void *key = reinterpret_cast<const void *>(kern);
+  auto it = done.find(key);
+  if (it != done.end() && it->second >= bound) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bound);
+  if (e == cudaSuccess) done[key] = bound;
+  return e;
+}
+
 template <class S>
 size_t atom_smem_bytes(int T, int ncode, int prec, int ab = kAtomBlock) {
   static_assert((size_t)(S::NA + 1) * S::NK * kAtomBlock * 4 >= (size_t)S::TILE_A + 2 * S::TILE_B + 128,
@@ -995,8 +1015,9 @@ cudaError_t launch_atom(const AtomArgs &a, const ModelF &mf, const float *w0, co
   w.m = mf;
   const int blocks = (a.N + kAtomBlock - 1) / kAtomBlock;
   const size_t smem = atom_smem_bytes<S>(a.T, a.ncode, descriptor_only ? 0 : a.precision);
+  const size_t bound = atom_smem_bytes<S>(kMaxTypes, 1 << 9, descriptor_only ? 0 : a.precision);
   auto go = [&](auto kern) -> cudaError_t {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_limit_once(kern, bound);
     if (e != cudaSuccess) return e;
     kern<<<blocks, kAtomBlock, smem, st>>>(a, w);
     return cudaGetLastError();
@@ -1038,8 +1059,9 @@ cudaError_t launch_atom_batch(const AtomArgs &a, const ModelF &mf, const float *
   w.m = mf;
   const dim3 grid((a.N + block - 1) / block, members);
   const size_t smem = atom_smem_bytes<S>(a.T, 0, a.precision, block);
+  const size_t bound = atom_smem_bytes<S>(kMaxTypes, 0, a.precision, block);
   auto go = [&](auto kern) -> cudaError_t {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_limit_once(kern, bound);
     if (e != cudaSuccess) return e;
     kern<<<grid, block, smem, st>>>(a, w);
     return cudaGetLastError();

@@ -29,6 +29,7 @@ void set_thread_alloc_stream(cudaStream_t s);
 void release_workspace(nep_handle *h);
 size_t workspace_bytes(nep_handle *h);
 void set_create_error(const char *msg);
+cudaError_t stream_sync(cudaStream_t s);
 }  // namespace nep
 
 namespace {
@@ -189,7 +190,7 @@ void nep_server::run_job(nep_handle *h, cudaStream_t s, Job &job, nep_result &r,
   if (!out.vel.empty()) SCK(cudaMemcpyAsync(out.vel.data(), d_vel, b3, cudaMemcpyDeviceToHost, s));
   SCK(cudaMemcpyAsync(&r.energy, d_E, sizeof(double), cudaMemcpyDeviceToHost, s));
   SCK(cudaMemcpyAsync(r.virial, d_W, 9 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  SCK(cudaStreamSynchronize(s));
+  SCK(nep::stream_sync(s));
   r.workspace_used = nep::workspace_bytes(h);
   for (int k = 0; k < NBUF; ++k) r.workspace_used += buf[k].n;
   // the positions are reported wrapped into the cell, like md_get_state
@@ -268,7 +269,7 @@ void nep_server::worker_main(int w) {
       run_job(h, s, job, r, out, buf, evals);
       nep::release_workspace(h);
       for (auto &b : buf) b.release(s);
-      cudaStreamSynchronize(s);
+      nep::stream_sync(s);
     }
     r.t_done = now_since(t0);
     {

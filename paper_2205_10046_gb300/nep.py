@@ -533,6 +533,11 @@ class Server:
             raise NepError(rc, "nep_server_arrays")
         return pos, force, vel
 
+    def drop(self, job_id: int):
+        """Discard the arrays of a finished job without copying them."""
+        self.n.pop(job_id, None)
+        load().nep_server_arrays(self.h, int(job_id), None, None, None)
+
     def stats(self) -> dict:
         st = nep_server_stats()
         _check(load().nep_server_stats_get(self.h, C.byref(st)), None)
