@@ -290,6 +290,35 @@ int md_init_host(nep_handle *h, int n_atoms, const double *pos, const int *types
  * hold (the state is then unusable; call md_init again). */
 int md_run(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *thermo, nep_stream_t stream);
 
+/* Options of md_run_ex. */
+typedef struct {
+  int thermo_every;          /* >= 1: rows of thermo and heat_current every thermo_every steps */
+  double *thermo;            /* DEVICE [n_steps/thermo_every][4] as md_run, or NULL */
+  double *heat_current;      /* DEVICE [n_steps/thermo_every][3]: total heat current J = sum_i W_i . v_i
+                                (Eqs. Ji and J-1; eV A/fs) after the step, or NULL */
+  double temperature;        /* > 0: Bussi-Donadio-Parrinello thermostat at this temperature (K);
+                                <= 0: NVE */
+  double tau_fs;             /* thermostat coupling time (fs) */
+  const double *bdp_random;  /* DEVICE [n_steps][2]: per step R1 ~ N(0,1) and S ~ chi^2 with 3N-4
+                                degrees of freedom, drawn by the caller (thermostat only) */
+} md_options;
+
+/* md_run with options: the heat current of Eq. Ji summed over atoms (Eq. J-1) after every
+ * thermo row's step, and an NVT thermostat (the paper's MD engine offers several, Sec. III A;
+ * this is the Bussi-Donadio-Parrinello one, J. Chem. Phys. 126, 014101 (2007)): after each
+ * velocity-Verlet step every velocity is scaled by alpha with
+ *   alpha^2 = c + (1 - c)(S + R1^2) Kbar / (N_f K) + 2 R1 sqrt(c (1 - c) Kbar / (N_f K)),
+ * c = exp(-dt/tau), N_f = 3N - 3, Kbar = N_f k_B T / 2, K the kinetic energy after the step,
+ * and the sign of alpha that of R1 + sqrt(c N_f K / ((1 - c) Kbar)). thermo rows then hold the
+ * rescaled kinetic energy and temperature. Errors as md_run. */
+int md_run_ex(nep_handle *h, int n_steps, double dt_fs, const md_options *opt, nep_stream_t stream);
+
+/* Per-atom heat current J_i = W_i . v_i (Eq. Ji) of one configuration with the caller's
+ * velocities (DEVICE pointers, caller order): heat [N][3] (or NULL) and the total
+ * heat_total [3] (or NULL), in eV A/fs. Stream-ordered like nep_compute. */
+int nep_heat_current(nep_handle *h, int n_atoms, const double *pos, const int *types, const double *box,
+                     const double *vel, double *heat, double *heat_total, nep_stream_t stream);
+
 /* FIRE energy minimisation (Bitzek et al., Phys. Rev. Lett. 97, 170201 (2006); the paper
  * has no counterpart) from the state of md_init, with its velocities set to zero. A step is
  * one velocity-Verlet step of the current length dt followed by the FIRE update with

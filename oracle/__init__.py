@@ -70,6 +70,7 @@ def _load():
             lib.oracle_md.argtypes = [C.POINTER(_Model), C.c_int, _dp, _dp, _ip, _dp, _dp, C.c_int,
                                       C.c_double, C.c_void_p, C.c_void_p, C.c_int]
             lib.oracle_max_threads.argtypes = []
+            lib.oracle_heat_current_j2.argtypes = [C.POINTER(_Model), C.c_int, _dp, _ip, _dp, _dp, _dp, C.c_int]
             _lib = lib
     return _lib
 
@@ -325,3 +326,83 @@ def fire(model, pos, types, box, n_steps, dt0, fmax, n_threads=0):
         return float(np.sum(U)), F
 
     return fire_minimize(force_fn, pos, inv_mass, n_steps, dt0, fmax)
+
+
+# --------------------------------------------------------------------------- heat current
+def heat_current(model, pos, types, box, vel, n_threads=0):
+    """Per-atom heat current J_i = W_i . v_i (Eq. Ji) from the oracle's per-atom virials, and
+    the total J = sum_i J_i (Eq. J-1). Velocities in A/fs; J in eV A/fs."""
+    _, _, Wv = compute(model, pos, types, box, n_threads=n_threads)
+    v = _f64(vel, (-1, 3))
+    order = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2), (1, 0), (2, 0), (2, 1)]
+    Wm = np.zeros((Wv.shape[0], 3, 3))
+    for c, (a, b) in enumerate(order):
+        Wm[:, a, b] = Wv[:, c]
+    J = np.einsum("iab,ib->ia", Wm, v)
+    return J, J.sum(axis=0)
+
+
+def heat_current_j2(model, pos, types, box, vel, n_threads=0):
+    """Total heat current by Eq. J-2, from every atom's own partial forces and its neighbours'
+    velocities (a different data path from Eq. J-1)."""
+    b = _Bound(model)
+    pos = _f64(pos, (-1, 3))
+    J = np.zeros(3)
+    rc = _load().oracle_heat_current_j2(b.ref(), pos.shape[0], pos, _i32(types), _f64(box, (3, 3)),
+                                        _f64(vel, (-1, 3)), J, int(n_threads))
+    if rc != 0:
+        raise ValueError("oracle_heat_current_j2 failed")
+    return J
+
+
+# --------------------------------------------------------------------------- BDP thermostat
+KB = 8.617333262e-5  # eV/K
+
+
+def bdp_alpha(K, kbar, nf, c, R1, S):
+    """Velocity factor of the Bussi-Donadio-Parrinello thermostat (J. Chem. Phys. 126,
+    014101 (2007)) for kinetic energy K, target Kbar, N_f degrees of freedom, c = exp(-dt/tau)
+    and the step's random numbers R1 ~ N(0,1), S ~ chi^2(N_f - 1): the new kinetic energy is
+    alpha^2 K with alpha^2 = c + (1 - c)(S + R1^2) Kbar/(N_f K) + 2 R1 sqrt(c (1-c) Kbar/(N_f K)),
+    alpha taking the sign of R1 + sqrt(c N_f K / ((1 - c) Kbar))."""
+    if K <= 0.0:
+        return 1.0
+    q = kbar / (nf * K)
+    a2 = c + (1.0 - c) * (S + R1 * R1) * q + 2.0 * R1 * math.sqrt(c * (1.0 - c) * q)
+    alpha = math.sqrt(max(a2, 0.0))
+    if c < 1.0 and R1 + math.sqrt(c / ((1.0 - c) * q)) < 0.0:
+        alpha = -alpha
+    return alpha
+
+
+def md_bdp(model, pos, vel, types, box, n_steps, dt, temperature, tau, rand, n_threads=0):
+    """Velocity-Verlet steps, each followed by the BDP rescaling with rand[k] = (R1, S)
+    (temperature <= 0: plain NVE). Returns (pos, vel, thermo [n_steps, 3] = (E_pot, E_kin, T)
+    after each step, heat current [n_steps, 3] = sum_i W_i . v_i after each step)."""
+    types = _i32(types)
+    x = _f64(pos, (-1, 3)).copy()
+    v = _f64(vel, (-1, 3)).copy()
+    N = x.shape[0]
+    m = np.asarray(model.mass, dtype=np.float64)[types]
+    im = (1.0 / (m * KAPPA))[:, None]
+    nf = 3.0 * N - 3.0
+    c = math.exp(-dt / tau) if temperature > 0 else 1.0
+    kbar = 0.5 * nf * KB * temperature
+    U, F, Wv = compute(model, x, types, box, n_threads=n_threads)
+    thermo, heat = [], []
+    order = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2), (1, 0), (2, 0), (2, 1)]
+    for k in range(n_steps):
+        v = v + 0.5 * dt * F * im
+        x = x + dt * v
+        U, F, Wv = compute(model, x, types, box, n_threads=n_threads)
+        v = v + 0.5 * dt * F * im
+        if temperature > 0:
+            K = 0.5 * KAPPA * float(np.sum(m[:, None] * v * v))
+            v = v * bdp_alpha(K, kbar, nf, c, float(rand[k][0]), float(rand[k][1]))
+        ke = 0.5 * KAPPA * float(np.sum(m[:, None] * v * v))
+        thermo.append((float(U.sum()), ke, 2.0 * ke / (nf * KB)))
+        Wm = np.zeros((N, 3, 3))
+        for cc, (a, b) in enumerate(order):
+            Wm[:, a, b] = Wv[:, cc]
+        heat.append(np.einsum("iab,ib->ia", Wm, v).sum(axis=0))
+    return x, v, np.array(thermo), np.array(heat)

@@ -521,6 +521,37 @@ int compute(const Model &m, int N, const double *pos, const int *types, const Ce
   return 0;
 }
 
+/* Total heat current in the form of Eq. J-2: J = -sum_i sum_(j,n) r_ij (dU_i/dr_ij . v_j),
+ * from every atom's own partial forces and its neighbours' velocities. */
+int heat_current_j2(const Model &m, int N, const double *pos, const int *types, const Cell &cell, const double *vel,
+                    double *J, int n_threads) {
+  for (int i = 0; i < N; ++i)
+    if (types[i] < 0 || types[i] >= m.T) return -1;
+  const int nt = threads_or_default(n_threads);
+  std::vector<Env> env(N);
+  std::vector<std::array<double, 3>> part((size_t)N);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+  for (int i = 0; i < N; ++i) {
+    find_neighbours(cell, N, pos, i, m.rcR, env[i].pairs);
+    env[i].tj.resize(env[i].pairs.size());
+    for (size_t p = 0; p < env[i].pairs.size(); ++p) env[i].tj[p] = types[env[i].pairs[p].j];
+    std::vector<std::array<double, 3>> P;
+    partial_forces(m, types[i], env[i], P);
+    double acc[3] = {0, 0, 0};
+    for (size_t p = 0; p < env[i].pairs.size(); ++p) {
+      const Pair &pr = env[i].pairs[p];
+      const double *vj = vel + 3 * (size_t)pr.j;
+      const double dot = P[p][0] * vj[0] + P[p][1] * vj[1] + P[p][2] * vj[2];
+      for (int c = 0; c < 3; ++c) acc[c] -= pr.d[c] * dot;
+    }
+    for (int c = 0; c < 3; ++c) part[i][c] = acc[c];
+  }
+  for (int c = 0; c < 3; ++c) J[c] = 0.0;
+  for (int i = 0; i < N; ++i)
+    for (int c = 0; c < 3; ++c) J[c] += part[i][c];
+  return 0;
+}
+
 }  // namespace
 
 /* ==================================================================== C entry points */
@@ -685,5 +716,14 @@ int oracle_md(const oracle_model *pm, int N, double *pos, double *vel, const int
 
 /* Number of OpenMP threads a call with n_threads <= 0 uses. */
 int oracle_max_threads(void) { return threads_or_default(0); }
+
+/* Total heat current by Eq. J-2 (vel [N][3] in Angstrom/fs; J [3] in eV Angstrom/fs). */
+int oracle_heat_current_j2(const oracle_model *pm, int N, const double *pos, const int *types, const double *box,
+                           const double *vel, double *J, int n_threads) {
+  Model m;
+  Cell c;
+  if (!load_model(pm, m) || N < 1 || !make_cell(box, c)) return -1;
+  return heat_current_j2(m, N, pos, types, c, vel, J, n_threads);
+}
 
 }  // extern "C"

@@ -19,8 +19,9 @@ void launch_rebuild_condition(cudaGraphConditionalHandle hc, const BuildStatus *
 void launch_drift(int N, const AtomState &a, const double *inv_mass_kappa, double dt, double half_skin2,
                   BuildStatus *st, cudaStream_t s, const FireState *fire);
 void launch_finalize(int nb_atom, const double *partial_atom, int nb_gather, const double *partial_gather,
-                     double *energy_total, double *virial_total, double *thermo_stage, int *thermo_ctl, int N,
-                     double volume, cudaStream_t s);
+                     double *energy_total, double *virial_total, double *heat_total, double *thermo_stage,
+                     int *thermo_ctl, int N, double volume, const ThermoState *ts, cudaStream_t s);
+constexpr int kThermoCols = 8;  // staged thermo row: E, KE, T, P, J[3], thermostat factor
 const ShapeOps *shape_si();
 const ShapeOps *shape_pbte();
 const ShapeOps *shape_mixed();
@@ -296,6 +297,9 @@ struct nep_handle {
   cudaGraphExec_t graph = nullptr;
   cudaGraphExec_t fire_graph = nullptr;  // one FIRE step (its time step lives on the device)
   DevBuf<FireState> fire, ck_fire;
+  DevBuf<ThermoState> thermo_state, ck_thermo;  // BDP thermostat (md_run_ex)
+  bool nvt = false;                             // the MD step graph rescales velocities
+  bool graph_nvt = false;
   double graph_dt = 0;
   bool graph_prof = false;
   const double *graph_thermo = nullptr;
@@ -337,7 +341,7 @@ struct nep_handle {
     f(perm); f(types); f(cell_of); f(cell_count); f(cell_cursor); f(cell_start); f(cell_atoms); f(nn_r);
     f(nn_a); f(rev_a); f(thermo_ctl); f(nl_r); f(nl_a); f(pos4); f(dtab); f(p_ang); f(e_rad); f(d_grids);
     f(d_sid); f(d_offsets); f(b_e); f(b_w); f(pop_cr); f(pop_ca); f(pop_ann); f(pop_tc); f(pop_reg); f(pop_es);
-    f(pop_ws); f(fire); f(ck_fire);
+    f(pop_ws); f(fire); f(ck_fire); f(thermo_state); f(ck_thermo);
   }
   // the kernels compare r^2 with the FP32 square of the FP32 cutoff
   float rcR2f() const { return (float)rcR * (float)rcR; }
@@ -382,7 +386,7 @@ int setup_grid(nep_handle *h, int N, const double *box, std::vector<float4> &dta
   return NEP_OK;
 }
 
-int ensure_atoms(nep_handle *h, int N) {
+int ensure_atoms(nep_handle *h, int N, cudaStream_t s) {
   const size_t n = (size_t)std::max(N, 1);
   CK(h->x.ensure(3 * n), "alloc");
   CK(h->v.ensure(3 * n), "alloc");
@@ -405,7 +409,11 @@ int ensure_atoms(nep_handle *h, int N) {
   CK(h->e_rad.ensure(n * h->T * (size_t)(((h->KR + 2) + 3) / 4 * 4)), "alloc");
   CK(h->partial_atom.ensure(h->ops->atom_blocks(N) + 1), "alloc");
   CK(h->partial_gather.ensure((size_t)(h->ops->gather_blocks(N) + 1) * kReduceSlots), "alloc");
-  CK(h->status.ensure(1), "alloc");
+  if (!h->status.p) {  // a new status word starts cleared (device memory comes uninitialised)
+    CK(h->status.ensure(1), "alloc");
+    CK(cudaMemsetAsync(h->status.p, 0, sizeof(BuildStatus), s), "clear status");
+    std::memset(h->h_status, 0, sizeof(BuildStatus));
+  }
   CK(h->thermo_ctl.ensure(4), "alloc");
   return NEP_OK;
 }
@@ -437,6 +445,7 @@ void reset_status_counts(nep_handle *h) {
   h->h_status->bad_input = 0;
   h->h_status->in_r = 0;
   h->h_status->in_a = 0;
+  h->h_status->tc_timeout = 0;
 }
 
 AtomState atom_state(nep_handle *h) {
@@ -540,7 +549,7 @@ AtomArgs make_args(nep_handle *h, int N) {
 
 // Load positions (device, [N][3]) and types, set up the grid and build the lists.
 int load_structure(nep_handle *h, int N, const double *pos, const int *types, const double *box, cudaStream_t s) {
-  int rc = ensure_atoms(h, N);
+  int rc = ensure_atoms(h, N, s);
   if (rc) return rc;
   std::vector<float4> dtab;
   rc = setup_grid(h, N, box, dtab);
@@ -585,7 +594,7 @@ bool valid_handle(const nep_handle *h) { return h && h->ops; }
 // range; the cells are numbered structure by structure, the shift tables share one code
 // width (the largest), and list entries one atom-index width (for the whole batch).
 int setup_batch(nep_handle *h, int n_struct, const int *offsets, const double *boxes, int N, cudaStream_t s) {
-  int rc = ensure_atoms(h, N);
+  int rc = ensure_atoms(h, N, s);
   if (rc) return rc;
   const bool same = n_struct == h->nb_struct && (int)h->b_offsets.size() == n_struct + 1 &&
                     std::equal(offsets, offsets + n_struct + 1, h->b_offsets.begin()) &&
@@ -936,7 +945,8 @@ int nep_compute(nep_handle *h, int n_atoms, const double *pos, const int *types,
   if (rc) return rc;
   ev_record(h, SLOT_FINAL, 0, s, false);
   launch_finalize(h->ops->atom_blocks(n_atoms), h->partial_atom.p, h->ops->gather_blocks(n_atoms),
-                  h->partial_gather.p, energy_total, virial_total, nullptr, nullptr, n_atoms, h->volume, s);
+                  h->partial_gather.p, energy_total, virial_total, nullptr, nullptr, nullptr, n_atoms, h->volume,
+                  nullptr, s);
   ev_record(h, SLOT_FINAL, 1, s, false);
   CK(cudaGetLastError(), "finalize");
   return NEP_OK;
@@ -1335,7 +1345,7 @@ int md_init(nep_handle *h, int n_atoms, const double *pos, const int *types, con
   h->md_ready = false;
   // velocities enter in the caller's order; the neighbour build below moves them into the
   // internal (cell) order together with positions, types and perm
-  int rc = ensure_atoms(h, n_atoms);
+  int rc = ensure_atoms(h, n_atoms, s);
   if (rc) return rc;
   if (vel) CK(cudaMemcpyAsync(h->v.p, vel, sizeof(double) * 3 * n_atoms, cudaMemcpyDeviceToDevice, s), "copy vel");
   else CK(cudaMemsetAsync(h->v.p, 0, sizeof(double) * 3 * n_atoms, s), "memset vel");
@@ -1440,8 +1450,10 @@ int md_step_launch(nep_handle *h, double dt, cudaStream_t s, bool capturing, boo
   int rc = run_forces(h, N, nullptr, h->F.p, nullptr, 1, 0.5 * dt, s, capturing, fs);
   if (rc) return rc;
   ev_record(h, SLOT_FINAL, 0, s, capturing);
+  ThermoState *ts = (!fire && h->nvt) ? h->thermo_state.p : nullptr;
+  if (ts) launch_thermostat(N, atom_state(h), h->ops->gather_blocks(N), h->partial_gather.p, ts, s);
   launch_finalize(h->ops->atom_blocks(N), h->partial_atom.p, h->ops->gather_blocks(N), h->partial_gather.p, nullptr,
-                  nullptr, h->thermo_stage.p, h->thermo_ctl.p, N, h->volume, s);
+                  nullptr, nullptr, h->thermo_stage.p, h->thermo_ctl.p, N, h->volume, ts, s);
   if (fire) launch_fire_mix(N, atom_state(h), fs, 0, s);
   ev_record(h, SLOT_FINAL, 1, s, capturing);
   CK(cudaGetLastError(), "md step launch");
@@ -1451,25 +1463,27 @@ int md_step_launch(nep_handle *h, double dt, cudaStream_t s, bool capturing, boo
 
 namespace {
 int md_queue(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *thermo, cudaStream_t s,
-             bool fire = false) {
+             bool fire = false, double *heat = nullptr) {
   if (!h->md_ready) return fail(h, NEP_ERR_STATE, "md_run before md_init");
   if (n_steps < 0 || !(dt_fs > 0) || !std::isfinite(dt_fs) || thermo_every < 1)
     return fail(h, NEP_ERR_ARG, "need n_steps >= 0, dt > 0, thermo_every >= 1");
   if (n_steps == 0) return NEP_OK;
-  const int rows = thermo ? n_steps / thermo_every : 0;
-  CK(h->thermo_stage.ensure((size_t)4 * (rows + 1)), "alloc thermo");
-  int ctl[4] = {0, 0, thermo ? thermo_every : (n_steps + 1), 0};
+  const bool rows_out = thermo || heat;
+  const int rows = rows_out ? n_steps / thermo_every : 0;
+  CK(h->thermo_stage.ensure((size_t)kThermoCols * (rows + 1)), "alloc thermo");
+  int ctl[4] = {0, 0, rows_out ? thermo_every : (n_steps + 1), 0};
   CK(cudaMemcpyAsync(h->thermo_ctl.p, ctl, sizeof(ctl), cudaMemcpyHostToDevice, s), "thermo ctl");
   // (re)capture the one-step graph when the step size, the profiling mode or the thermo
   // staging buffer changed
   cudaGraphExec_t &gx = fire ? h->fire_graph : h->graph;
   if (fire && gx && (h->graph_prof != h->prof || h->graph_thermo != h->thermo_stage.p ||
-                     h->graph_cond_used != h->graph_cond || h->graph_prec != h->precision)) {
+                     h->graph_cond_used != h->graph_cond || h->graph_prec != h->precision ||
+                     h->graph_nvt != h->nvt)) {
     cudaGraphExecDestroy(gx);
     gx = nullptr;
   }
   if (!gx || (!fire && h->graph_dt != dt_fs) || h->graph_prof != h->prof || h->graph_thermo != h->thermo_stage.p ||
-      h->graph_cond_used != h->graph_cond || h->graph_prec != h->precision) {
+      h->graph_cond_used != h->graph_cond || h->graph_prec != h->precision || h->graph_nvt != h->nvt) {
     // the MD and FIRE graphs share the capture settings: drop both when they change
     for (cudaGraphExec_t *g : {&h->graph, &h->fire_graph})
       if (*g) {
@@ -1495,10 +1509,16 @@ int md_queue(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double 
     h->graph_thermo = h->thermo_stage.p;
     h->graph_cond_used = h->graph_cond;
     h->graph_prec = h->precision;
+    h->graph_nvt = h->nvt;
   }
   for (int st = 0; st < n_steps; ++st) CK(cudaGraphLaunch(gx, s), "graph launch");
+  // rows of the staging area -> the caller's [rows][4] thermo and [rows][3] heat current
   if (thermo && rows > 0)
-    CK(cudaMemcpyAsync(thermo, h->thermo_stage.p, sizeof(double) * 4 * rows, cudaMemcpyDeviceToDevice, s), "thermo");
+    CK(cudaMemcpy2DAsync(thermo, 4 * sizeof(double), h->thermo_stage.p, kThermoCols * sizeof(double),
+                         4 * sizeof(double), rows, cudaMemcpyDeviceToDevice, s), "thermo");
+  if (heat && rows > 0)
+    CK(cudaMemcpy2DAsync(heat, 3 * sizeof(double), h->thermo_stage.p + 4, kThermoCols * sizeof(double),
+                         3 * sizeof(double), rows, cudaMemcpyDeviceToDevice, s), "heat current");
   return NEP_OK;
 }
 }  // namespace
@@ -1528,7 +1548,8 @@ namespace {
 // Velocity-Verlet (or FIRE) steps in chunks of whole thermo periods; each chunk starts from
 // a checkpoint so that a list overflow during it can be undone: restore, grow the lists,
 // rebuild, replay. A converged relaxation stops at the end of its chunk.
-int run_steps(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *thermo, cudaStream_t s, bool fire) {
+int run_steps(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *thermo, cudaStream_t s, bool fire,
+              double *heat = nullptr) {
   const int N = h->N;
   const size_t b = sizeof(double) * 3 * (size_t)N;
   CK(h->ck_x.ensure(3 * (size_t)N), "alloc checkpoint");
@@ -1537,6 +1558,8 @@ int run_steps(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double
   CK(h->ck_types.ensure((size_t)N), "alloc checkpoint");
   CK(h->ck_perm.ensure((size_t)N), "alloc checkpoint");
   if (fire) CK(h->ck_fire.ensure(1), "alloc checkpoint");
+  const bool nvt = !fire && h->nvt;
+  if (nvt) CK(h->ck_thermo.ensure(1), "alloc checkpoint");
   const size_t bi = sizeof(int) * (size_t)N;
   // chunks of whole thermo periods; each chunk starts from a checkpoint so that a list
   // overflow during it can be undone: restore, grow the lists, rebuild, replay
@@ -1550,12 +1573,16 @@ int run_steps(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double
     CK(cudaMemcpyAsync(h->ck_types.p, h->types.p, bi, cudaMemcpyDeviceToDevice, s), "checkpoint");
     CK(cudaMemcpyAsync(h->ck_perm.p, h->perm.p, bi, cudaMemcpyDeviceToDevice, s), "checkpoint");
     if (fire) CK(cudaMemcpyAsync(h->ck_fire.p, h->fire.p, sizeof(FireState), cudaMemcpyDeviceToDevice, s), "checkpoint");
+    if (nvt)
+      CK(cudaMemcpyAsync(h->ck_thermo.p, h->thermo_state.p, sizeof(ThermoState), cudaMemcpyDeviceToDevice, s),
+         "checkpoint");
     int rc = read_status(h, s);
     if (rc) return rc;
     const long long steps0 = h->h_status->md_steps, rebuilds0 = h->h_status->n_rebuilds;
     for (int attempt = 0;; ++attempt) {
       double *th = thermo ? thermo + 4 * (size_t)(done / thermo_every) : nullptr;
-      rc = md_queue(h, c, dt_fs, thermo_every, th, s, fire);
+      double *hc = heat ? heat + 3 * (size_t)(done / thermo_every) : nullptr;
+      rc = md_queue(h, c, dt_fs, thermo_every, th, s, fire, hc);
       if (rc) return rc;
       rc = read_status(h, s);
       if (rc) return rc;
@@ -1573,6 +1600,9 @@ int run_steps(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double
       CK(cudaMemcpyAsync(h->types.p, h->ck_types.p, bi, cudaMemcpyDeviceToDevice, s), "restore");
       CK(cudaMemcpyAsync(h->perm.p, h->ck_perm.p, bi, cudaMemcpyDeviceToDevice, s), "restore");
       if (fire) CK(cudaMemcpyAsync(h->fire.p, h->ck_fire.p, sizeof(FireState), cudaMemcpyDeviceToDevice, s), "restore");
+      if (nvt)
+        CK(cudaMemcpyAsync(h->thermo_state.p, h->ck_thermo.p, sizeof(ThermoState), cudaMemcpyDeviceToDevice, s),
+           "restore");
       rc = ensure_lists(h, N, round_cap(st.max_r), round_cap(st.max_a));
       if (rc) return rc;
       rc = rebuild_lists(h, N, s);
@@ -1617,6 +1647,60 @@ int md_run(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *t
   if (n_steps < 0 || !(dt_fs > 0) || !std::isfinite(dt_fs) || thermo_every < 1)
     return fail(h, NEP_ERR_ARG, "need n_steps >= 0, dt > 0, thermo_every >= 1");
   return run_steps(h, n_steps, dt_fs, thermo_every, thermo, (cudaStream_t)stream, false);
+}
+
+int md_run_ex(nep_handle *h, int n_steps, double dt_fs, const md_options *opt, nep_stream_t stream) {
+  if (!valid_handle(h)) return NEP_ERR_ARG;
+  h->err.clear();
+  if (!h->md_ready) return fail(h, NEP_ERR_STATE, "md_run_ex before md_init");
+  if (!opt) return fail(h, NEP_ERR_ARG, "options are null");
+  if (n_steps < 0 || !(dt_fs > 0) || !std::isfinite(dt_fs) || opt->thermo_every < 1)
+    return fail(h, NEP_ERR_ARG, "need n_steps >= 0, dt > 0, thermo_every >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool nvt = opt->temperature > 0;
+  if (nvt) {
+    if (!(opt->tau_fs > 0) || !std::isfinite(opt->temperature) || !opt->bdp_random)
+      return fail(h, NEP_ERR_ARG, "the thermostat needs tau_fs > 0 and bdp_random");
+    if (h->N < 2) return fail(h, NEP_ERR_ARG, "the thermostat needs at least 2 atoms");
+    CK(h->thermo_state.ensure(1), "alloc thermostat");
+    ThermoState ts{};
+    ts.nf = 3.0 * h->N - 3.0;
+    ts.c = std::exp(-dt_fs / opt->tau_fs);
+    ts.kbar = 0.5 * ts.nf * 8.617333262e-5 * opt->temperature;
+    ts.alpha = 1.0;
+    ts.rand = opt->bdp_random;
+    ts.step = 0;
+    CK(cudaMemcpyAsync(h->thermo_state.p, &ts, sizeof(ts), cudaMemcpyHostToDevice, s), "thermostat");
+    // the host copy must outlive the asynchronous copy
+    CK(wait_stream(s), "sync");
+  }
+  h->nvt = nvt;
+  const int rc = run_steps(h, n_steps, dt_fs, opt->thermo_every, opt->thermo, s, false, opt->heat_current);
+  h->nvt = false;
+  return rc;
+}
+
+int nep_heat_current(nep_handle *h, int n_atoms, const double *pos, const int *types, const double *box,
+                     const double *vel, double *heat, double *heat_total, nep_stream_t stream) {
+  if (!valid_handle(h)) return NEP_ERR_ARG;
+  h->err.clear();
+  if (n_atoms < 1 || !pos || !types || !box || !vel || (!heat && !heat_total))
+    return fail(h, NEP_ERR_ARG, "need atoms, velocities and an output");
+  cudaStream_t s = (cudaStream_t)stream;
+  h->md_ready = false;
+  int rc = load_structure(h, n_atoms, pos, types, box, s);
+  if (rc) return rc;
+  AtomArgs a = make_args(h, n_atoms);
+  a.vel_in = vel;
+  a.heat = heat;
+  cudaError_t e = h->ops->atom(a, h->mf, h->w0.data(), h->b0.data(), h->w1.data(), h->b1, 0, s);
+  if (e == cudaSuccess) e = h->ops->gather(a, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "heat current kernels");
+  launch_finalize(h->ops->atom_blocks(n_atoms), h->partial_atom.p, h->ops->gather_blocks(n_atoms),
+                  h->partial_gather.p, nullptr, nullptr, heat_total, nullptr, nullptr, n_atoms, h->volume, nullptr,
+                  s);
+  CK(cudaGetLastError(), "heat current");
+  return NEP_OK;
 }
 
 int fire_run(nep_handle *h, int n_steps, double dt0_fs, double fmax, double *thermo, int *steps_taken,

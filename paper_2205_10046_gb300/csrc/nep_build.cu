@@ -388,13 +388,17 @@ __global__ void export_state_kernel(int N, const AtomState a, const Grid g0, con
   }
 }
 
-// Deterministic totals: E = sum U_i, W = sum W_i, kinetic energy; optional thermo row.
-// One block; every thread sums a fixed strided subset, then a fixed tree. In MD mode
-// (thermo_ctl set) steps without a thermo row only advance the step counter.
+// Deterministic totals: E = sum U_i, W = sum W_i, kinetic energy, heat current J = sum J_i;
+// optional thermo row. One block; every thread sums a fixed strided subset, then a fixed
+// tree. In MD mode (thermo_ctl set) steps without a thermo row only advance the step
+// counter. A thermo row holds E_pot, E_kin, T, P, J_x, J_y, J_z and the thermostat factor;
+// with a thermostat (ts) the kinetic energy is that after the step's velocity rescaling.
+constexpr int kThermoCols = 8;
+
 __global__ void finalize_kernel(int nb_atom, const double *partial_atom, int nb_gather, const double *partial_gather,
-                                double *energy_total, double *virial_total, double *thermo_stage,
-                                int *thermo_ctl /* [0] step-in-call, [1] rows written, [2] every */, int N,
-                                double volume) {
+                                double *energy_total, double *virial_total, double *heat_total,
+                                double *thermo_stage, int *thermo_ctl /* [0] step-in-call, [1] rows written, [2] every */,
+                                int N, double volume, const ThermoState *ts) {
   __shared__ double red[256][kReduceSlots];
   __shared__ int emit;
   if (threadIdx.x == 0) {
@@ -410,7 +414,7 @@ __global__ void finalize_kernel(int nb_atom, const double *partial_atom, int nb_
   for (int s = 0; s < kReduceSlots; ++s) acc[s] = 0.0;
   for (int b = threadIdx.x; b < nb_atom; b += blockDim.x) acc[0] += partial_atom[b];
   for (int b = threadIdx.x; b < nb_gather; b += blockDim.x)
-    for (int s = 1; s < 11; ++s) acc[s] += partial_gather[(size_t)b * kReduceSlots + s];
+    for (int s = 1; s < kReduceSlots; ++s) acc[s] += partial_gather[(size_t)b * kReduceSlots + s];
   for (int s = 0; s < kReduceSlots; ++s) red[threadIdx.x][s] = acc[s];
   __syncthreads();
   for (int off = blockDim.x / 2; off > 0; off >>= 1) {
@@ -422,18 +426,67 @@ __global__ void finalize_kernel(int nb_atom, const double *partial_atom, int nb_
     if (energy_total) *energy_total = red[0][0];
     if (virial_total)
       for (int c = 0; c < 9; ++c) virial_total[c] = red[0][2 + c];
+    if (heat_total)
+      for (int c = 0; c < 3; ++c) heat_total[c] = red[0][12 + c];
     if (thermo_ctl) {
       const int row = thermo_ctl[1]++;
       const double kb = 8.617333262e-5;
-      const double ke = red[0][1];
+      const double alpha = ts ? ts->alpha : 1.0;
+      const double ke = red[0][1] * alpha * alpha;
       const double tr = red[0][2] + red[0][3] + red[0][4];
-      double *o = thermo_stage + 4 * (size_t)row;
+      double *o = thermo_stage + kThermoCols * (size_t)row;
       o[0] = red[0][0];
       o[1] = ke;
       o[2] = N > 1 ? 2.0 * ke / ((3.0 * N - 3.0) * kb) : 0.0;
       o[3] = (2.0 * ke + tr) / (3.0 * volume) * 160.21766208;  // eV/A^3 -> GPa
+      // J with the rescaled velocities: J is linear in v
+      for (int c = 0; c < 3; ++c) o[4 + c] = red[0][12 + c] * alpha;
+      o[7] = alpha;
     }
   }
+}
+
+// Bussi-Donadio-Parrinello rescaling after a velocity-Verlet step: K from the gather
+// kernel's block sums (fixed order), then with c = exp(-dt/tau), Kbar = N_f k_B T0 / 2 and
+// this step's R1, S: alpha^2 = c + (1 - c)(S + R1^2) Kbar / (N_f K)
+//                              + 2 R1 sqrt(c (1 - c) Kbar / (N_f K)),
+// alpha taking the sign of R1 + sqrt(c N_f K / ((1 - c) Kbar)); then v <- alpha v.
+__global__ void thermostat_factor_kernel(int nb_gather, const double *partial_gather, ThermoState *ts) {
+  __shared__ double red[256];
+  double k = 0.0;
+  for (int b = threadIdx.x; b < nb_gather; b += blockDim.x) k += partial_gather[(size_t)b * kReduceSlots + 1];
+  red[threadIdx.x] = k;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double K = red[0], c = ts->c, kbar = ts->kbar, nf = ts->nf;
+    const double R1 = ts->rand[2 * ts->step], S = ts->rand[2 * ts->step + 1];
+    double alpha = 1.0;
+    if (K > 0.0) {
+      const double q = kbar / (nf * K);
+      const double a2 = c + (1.0 - c) * (S + R1 * R1) * q + 2.0 * R1 * sqrt(c * (1.0 - c) * q);
+      alpha = sqrt(fmax(a2, 0.0));
+      if (c < 1.0 && R1 + sqrt(c / ((1.0 - c) * q)) < 0.0) alpha = -alpha;
+    }
+    ts->alpha = alpha;
+    ts->step += 1;
+  }
+}
+
+__global__ void scale_velocities_kernel(int N, double *v, const ThermoState *ts) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double a = ts->alpha;
+  for (int b = 0; b < 3; ++b) v[3 * (size_t)i + b] *= a;
+}
+
+void launch_thermostat(int N, const AtomState &a, int nb_gather, const double *partial_gather, ThermoState *ts,
+                       cudaStream_t s) {
+  thermostat_factor_kernel<<<1, 256, 0, s>>>(nb_gather, partial_gather, ts);
+  scale_velocities_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, a.v, ts);
 }
 
 // ------------------------------------------------------------------ batches
@@ -496,6 +549,7 @@ __global__ void arm_rebuild_kernel(BuildStatus *st) {
   st->max_a = 0;
   st->rev_missing = 0;
   st->bad_input = 0;
+  st->tc_timeout = 0;
   st->rebuild = 1;
 }
 
@@ -761,10 +815,10 @@ void launch_export(int N, const AtomState &a, const Grid &g, const Batch &B, dou
 }
 
 void launch_finalize(int nb_atom, const double *partial_atom, int nb_gather, const double *partial_gather,
-                     double *energy_total, double *virial_total, double *thermo_stage, int *thermo_ctl, int N,
-                     double volume, cudaStream_t s) {
+                     double *energy_total, double *virial_total, double *heat_total, double *thermo_stage,
+                     int *thermo_ctl, int N, double volume, const ThermoState *ts, cudaStream_t s) {
   finalize_kernel<<<1, 256, 0, s>>>(nb_atom, partial_atom, nb_gather, partial_gather, energy_total, virial_total,
-                                    thermo_stage, thermo_ctl, N, volume);
+                                    heat_total, thermo_stage, thermo_ctl, N, volume, ts);
 }
 
 }  // namespace nep

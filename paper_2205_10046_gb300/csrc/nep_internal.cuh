@@ -10,7 +10,7 @@ constexpr int kListBuf = 512;   // largest neighbour-list capacity per atom
 constexpr int kMaxImage = 3;    // largest cell/image offset searched per axis
 constexpr int kAtomBlock = 128; // threads per block of the per-atom kernel
 constexpr int kGatherBlock = 128;
-constexpr int kReduceSlots = 12; // per-block partial sums: U, KE, W[9], force error
+constexpr int kReduceSlots = 16; // per-block partial sums: U, KE, W[9], force error, J[3], spare
 
 // Geometry of one neighbour build: the cell grid, the packing of list entries and the
 // table of pair shift vectors indexed by the packed image code.
@@ -85,6 +85,18 @@ struct FireState {
   int pad;
 };
 
+// Bussi-Donadio-Parrinello velocity rescaling (J. Chem. Phys. 126, 014101 (2007)), device
+// resident: the caller's random numbers for every step (R1 ~ N(0,1), S ~ chi^2 with N_f - 1
+// degrees of freedom) and the factor of the current step.
+struct ThermoState {
+  double c;              // exp(-dt / tau)
+  double kbar;           // target kinetic energy N_f k_B T0 / 2 (eV)
+  double nf;             // degrees of freedom N_f = 3N - 3
+  double alpha;          // velocity factor of the last step
+  const double *rand;    // [n_steps][2] (R1, S)
+  long long step;        // steps thermostatted in this run
+};
+
 // Pair vector d = r_j - r_i from cell-local FP32 coordinates and the shift of the image
 // code. The explicitly rounded operations make d_ji the exact negation of d_ij, so both
 // atoms of a pair take the same inclusion decision in every kernel.
@@ -148,6 +160,10 @@ struct AtomArgs {
   long long s_out;                    // atoms per member in energy (x1), force (x3), virial (x9)
   const double *f_tar;     // [N][3] caller order, or null: sum of (F_i - F_tar,i)^2 per block
   const FireState *fire;   // FIRE relaxation: kick with its dt, none once converged (or null)
+  // heat current J_i = W_i . v_i (Eq. Ji) with the velocities after the kick (MD) or these
+  // caller-order velocities; per-atom values in caller order, or null
+  const double *vel_in;    // [N][3] caller order, or null
+  double *heat;            // [N][3] caller order, or null
 };
 
 // Model constants of one handle, FP32.
@@ -196,6 +212,8 @@ void launch_struct_sums(int n_struct, int members, const int *offsets, int N, co
                         const double *w_atom, double *e_struct, double *w_struct, cudaStream_t s);
 void launch_arm_rebuild(BuildStatus *st, cudaStream_t s);
 void launch_fire_mix(int N, const AtomState &a, FireState *fire, int check_only, cudaStream_t s);
+void launch_thermostat(int N, const AtomState &a, int nb_gather, const double *partial_gather, ThermoState *ts,
+                       cudaStream_t s);
 // population evaluation: parameter vectors into kernel arrays, BF16 tiles, Eq. loss
 void launch_unpack_population(int n_pop, const double *z, int n_par, int n_cr, int n_ca, float *cr, float *ca,
                               float *ann, double *reg, cudaStream_t s);

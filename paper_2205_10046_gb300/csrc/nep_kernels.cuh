@@ -939,6 +939,12 @@ __global__ void __launch_bounds__(GB)
     }
 #pragma unroll
     for (int c = 0; c < 9; ++c) part[2 + c] = (double)w[c];
+    // velocity of the heat current: after the kick below (MD), or given by the caller
+    double vh[3] = {0.0, 0.0, 0.0};
+    if (a.vel_in) {
+      const double *vi = a.vel_in + 3 * (a.perm ? (size_t)a.perm[i] : (size_t)i);
+      vh[0] = vi[0]; vh[1] = vi[1]; vh[2] = vi[2];
+    }
     if (a.f_tar) {  // squared force error against target forces (the force term of Eq. loss)
       const double *ft = a.f_tar + 3 * (a.perm ? (size_t)a.perm[i] : (size_t)i);
       const double ex = Fx - ft[0], ey = Fy - ft[1], ez = Fz - ft[2];
@@ -950,6 +956,23 @@ __global__ void __launch_bounds__(GB)
       const double vx = v[0] + s * Fx, vy = v[1] + s * Fy, vz = v[2] + s * Fz;
       v[0] = vx; v[1] = vy; v[2] = vz;
       part[1] = a.mass_kappa_half[ti] * (vx * vx + vy * vy + vz * vz);
+      vh[0] = vx; vh[1] = vy; vh[2] = vz;
+    } else if (a.md_kick) {  // converged FIRE: velocities unchanged
+      const double *v = a.vel + 3 * (size_t)i;
+      part[1] = a.mass_kappa_half[ti] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+      vh[0] = v[0]; vh[1] = v[1]; vh[2] = v[2];
+    }
+    // J_i = W_i . v_i, W_i[a][b] in the order xx, yy, zz, xy, xz, yz, yx, zx, zy (Eq. Ji)
+    const double Jx = (double)w[0] * vh[0] + (double)w[3] * vh[1] + (double)w[4] * vh[2];
+    const double Jy = (double)w[6] * vh[0] + (double)w[1] * vh[1] + (double)w[5] * vh[2];
+    const double Jz = (double)w[7] * vh[0] + (double)w[8] * vh[1] + (double)w[2] * vh[2];
+    part[12] = Jx;
+    part[13] = Jy;
+    part[14] = Jz;
+    if (a.heat) {
+      a.heat[3 * io] = Jx;
+      a.heat[3 * io + 1] = Jy;
+      a.heat[3 * io + 2] = Jz;
     }
   }
   // deterministic block sums of (KE, W[9], force error)

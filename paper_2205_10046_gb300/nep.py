@@ -51,6 +51,11 @@ class nep_tuning(C.Structure):
                 ("default_ms", C.c_float)]
 
 
+class md_options(C.Structure):
+    _fields_ = [("thermo_every", C.c_int), ("thermo", C.c_void_p), ("heat_current", C.c_void_p),
+                ("temperature", C.c_double), ("tau_fs", C.c_double), ("bdp_random", C.c_void_p)]
+
+
 class nep_server_config(C.Structure):
     _fields_ = [("memory_budget", C.c_size_t), ("workers", C.c_int), ("precision", C.c_int)]
 
@@ -99,6 +104,8 @@ _SIGS = {
     "md_run": (C.c_int, [_P, C.c_int, C.c_double, C.c_int, _P, _P]),
     "md_run_async": (C.c_int, [_P, C.c_int, C.c_double, C.c_int, _P, _P]),
     "fire_run": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, _P, C.POINTER(C.c_int), _P]),
+    "md_run_ex": (C.c_int, [_P, C.c_int, C.c_double, C.POINTER(md_options), _P]),
+    "nep_heat_current": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P, _P]),
     "md_status": (C.c_int, [_P, _P]),
     "md_get_state": (C.c_int, [_P, _P, _P, _P, _P]),
     "md_get_state_host": (C.c_int, [_P, _P, _P, _P]),
@@ -381,6 +388,30 @@ def fire_run(h, n_steps: int, dt0_fs: float, fmax: float, thermo=None) -> int:
                          _dev(thermo, torch.float64, (n_steps, 4), "thermo"), C.byref(steps), _stream())
     _check(rc, h)
     return int(steps.value)
+
+
+def md_run_ex(h, n_steps: int, dt_fs: float, thermo_every: int = 1, thermo=None, heat_current=None,
+              temperature: float = 0.0, tau_fs: float = 100.0, bdp_random=None):
+    """md_run with the total heat current per thermo row and an optional BDP thermostat
+    (bdp_random [n_steps, 2] CUDA f64: R1 ~ N(0,1), S ~ chi^2(3N-4) per step)."""
+    import torch
+    rows = n_steps // thermo_every
+    o = md_options(int(thermo_every), _dev(thermo, torch.float64, (rows, 4), "thermo"),
+                   _dev(heat_current, torch.float64, (rows, 3), "heat_current"), float(temperature), float(tau_fs),
+                   _dev(bdp_random, torch.float64, (n_steps, 2), "bdp_random"))
+    _check(load().md_run_ex(h, int(n_steps), float(dt_fs), C.byref(o), _stream()), h)
+
+
+def nep_heat_current(h, pos, types, box, vel, heat=None, heat_total=None):
+    """Per-atom heat current J_i = W_i . v_i [N, 3] and its total [3] (CUDA f64 outputs)."""
+    import torch
+    n = int(pos.shape[0])
+    b = _box(box)
+    rc = load().nep_heat_current(h, n, _dev(pos, torch.float64, (n, 3), "pos"), _dev(types, torch.int32, (n,), "types"),
+                                 b.ctypes.data, _dev(vel, torch.float64, (n, 3), "vel"),
+                                 _dev(heat, torch.float64, (n, 3), "heat"),
+                                 _dev(heat_total, torch.float64, (3,), "heat_total"), _stream())
+    _check(rc, h)
 
 
 def md_status(h, stream=None):

@@ -128,3 +128,59 @@ def test_fire_stops_on_the_starting_forces():
     f = _quadratic(np.ones(2), np.zeros((2, 3)))
     x, E, F, steps, en = oracle.fire_minimize(f, np.full((2, 3), 1e-9), np.ones(2), 10, 0.1, 1e-3)
     assert steps == 0 and en == []
+
+
+# ----------------------------------------------------------------------------- heat current, BDP
+def test_heat_current_forms_agree():
+    """Eq. J-1 (per-atom virials contracted with each atom's own velocity) equals Eq. J-2
+    (each atom's partial forces contracted with its neighbours' velocities)."""
+    m = W.mixed_model(0)
+    pos, types, box = W.random_structure(51, 24)
+    v = np.random.default_rng(1).normal(0, 0.01, pos.shape)
+    J_atoms, J1 = oracle.heat_current(m, pos, types, box, v)
+    J2 = oracle.heat_current_j2(m, pos, types, box, v)
+    assert np.abs(J1 - J2).max() <= 1e-10 * max(1.0, np.abs(J1).max())
+    np.testing.assert_allclose(J_atoms.sum(0), J1, rtol=0, atol=1e-15)
+    # J is linear in the velocities
+    _, J1b = oracle.heat_current(m, pos, types, box, 2.5 * v)
+    np.testing.assert_allclose(J1b, 2.5 * J1, rtol=1e-12, atol=1e-15)
+
+
+def test_bdp_limits():
+    # c = 1 (tau -> infinity): no rescaling
+    assert oracle.bdp_alpha(3.0, 1.0, 30.0, 1.0, 0.7, 25.0) == 1.0
+    # c = 0 (tau -> 0): K' = Kbar (S + R1^2) / N_f, = Kbar exactly when S + R1^2 = N_f
+    K, kbar, nf = 2.0, 5.0, 30.0
+    a = oracle.bdp_alpha(K, kbar, nf, 0.0, 1.0, nf - 1.0)
+    assert abs(a * a * K - kbar) < 1e-14
+
+
+def test_bdp_samples_the_canonical_kinetic_energy():
+    """Applied alone to a kinetic energy, the BDP update leaves the canonical distribution of
+    K (Gamma with shape N_f/2 and scale k_B T) stationary: mean Kbar, variance N_f (k_B T)^2 / 2."""
+    rng = np.random.default_rng(7)
+    nf, kT = 12.0, 0.025
+    kbar = 0.5 * nf * kT
+    c = np.exp(-0.1)
+    K, ks = 0.3 * kbar, []
+    for k in range(60000):
+        R1 = rng.normal()
+        S = rng.chisquare(nf - 1)
+        K = oracle.bdp_alpha(K, kbar, nf, c, R1, S) ** 2 * K
+        if k > 1000:
+            ks.append(K)
+    ks = np.array(ks)
+    assert abs(ks.mean() / kbar - 1.0) < 0.03
+    assert abs(ks.var() / (0.5 * nf * kT * kT) - 1.0) < 0.08
+
+
+def test_md_bdp_without_thermostat_is_velocity_verlet():
+    m = W.mixed_model(0)
+    pos, types, box = W.random_structure(52, 16)
+    v = W.maxwell_boltzmann(m.mass[types], 300.0, 3)
+    x1, v1, th1, J1 = oracle.md_bdp(m, pos, v, types, box, 4, 1.0, 0.0, 100.0, None)
+    x2, v2, th2, f2 = oracle.md(m, pos, v, types, box, 4, 1.0)
+    d = (x1 - x2) @ np.linalg.inv(box)
+    d -= np.round(d)
+    assert np.abs(d @ box).max() < 1e-12 and np.abs(v1 - v2).max() < 1e-13
+    np.testing.assert_allclose(th1[:, 0], th2[1:, 0], rtol=1e-12)
