@@ -287,8 +287,9 @@ struct nep_handle {
   DevBuf<double> x2, v2, F2;        // reorder scratch
   DevBuf<int> types2, perm2, cell2, perm;
   DevBuf<int> types, cell_of, cell_count, cell_cursor, cell_start, cell_atoms, nn_r, nn_a, rev_a, thermo_ctl;
-  DevBuf<unsigned> nl_r, nl_a;
-  DevBuf<float4> pos4, dtab, p_ang;
+  DevBuf<unsigned> nl_r, nl_a, stage_e;
+  DevBuf<unsigned char> stage_g;
+  DevBuf<float4> pos4, posA, dtab, p_ang;
   DevBuf<float> e_rad;
   DevBuf<BuildStatus> status;
   BuildStatus *h_status = nullptr;  // pinned mirror
@@ -339,9 +340,9 @@ struct nep_handle {
     f(x); f(v); f(F); f(x_ref); f(origin); f(partial_atom); f(partial_gather); f(thermo_stage);
     f(ck_x); f(ck_v); f(ck_F); f(ck_types); f(ck_perm); f(x2); f(v2); f(F2); f(types2); f(perm2); f(cell2);
     f(perm); f(types); f(cell_of); f(cell_count); f(cell_cursor); f(cell_start); f(cell_atoms); f(nn_r);
-    f(nn_a); f(rev_a); f(thermo_ctl); f(nl_r); f(nl_a); f(pos4); f(dtab); f(p_ang); f(e_rad); f(d_grids);
+    f(nn_a); f(rev_a); f(thermo_ctl); f(nl_r); f(nl_a); f(pos4); f(posA); f(dtab); f(p_ang); f(e_rad); f(d_grids);
     f(d_sid); f(d_offsets); f(b_e); f(b_w); f(pop_cr); f(pop_ca); f(pop_ann); f(pop_tc); f(pop_reg); f(pop_es);
-    f(pop_ws); f(fire); f(ck_fire); f(thermo_state); f(ck_thermo);
+    f(pop_ws); f(fire); f(ck_fire); f(thermo_state); f(ck_thermo); f(stage_e); f(stage_g);
   }
   // the kernels compare r^2 with the FP32 square of the FP32 cutoff
   float rcR2f() const { return (float)rcR * (float)rcR; }
@@ -397,6 +398,7 @@ int ensure_atoms(nep_handle *h, int N, cudaStream_t s) {
   CK(h->cell_of.ensure(n), "alloc");
   CK(h->cell_atoms.ensure(n), "alloc");
   CK(h->pos4.ensure(n), "alloc");
+  CK(h->posA.ensure(n), "alloc");
   CK(h->x2.ensure(3 * n), "alloc");
   CK(h->v2.ensure(3 * n), "alloc");
   CK(h->F2.ensure(3 * n), "alloc");
@@ -424,6 +426,8 @@ int ensure_lists(nep_handle *h, int N, int cap_r, int cap_a) {
   CK(h->nl_a.ensure(n * cap_a), "alloc lists");
   CK(h->rev_a.ensure(n * cap_a), "alloc lists");
   CK(h->p_ang.ensure(n * cap_a), "alloc lists");
+  CK(h->stage_e.ensure(n * cap_r), "alloc lists");
+  CK(h->stage_g.ensure(n * cap_r), "alloc lists");
   h->cap_r = cap_r;
   h->cap_a = cap_a;
   return NEP_OK;
@@ -451,7 +455,7 @@ void reset_status_counts(nep_handle *h) {
 AtomState atom_state(nep_handle *h) {
   AtomState a;
   a.x = h->x.p; a.v = h->v.p; a.F = h->F.p; a.x_ref = h->x_ref.p; a.origin = h->origin.p;
-  a.types = h->types.p; a.perm = h->perm.p; a.cell_of = h->cell_of.p; a.pos4 = h->pos4.p;
+  a.types = h->types.p; a.perm = h->perm.p; a.cell_of = h->cell_of.p; a.pos4 = h->pos4.p; a.posA = h->posA.p;
   a.x2 = h->x2.p; a.v2 = h->v2.p; a.F2 = h->F2.p; a.types2 = h->types2.p; a.perm2 = h->perm2.p;
   a.cell2 = h->cell2.p;
   return a;
@@ -462,6 +466,7 @@ ListBufs list_bufs(nep_handle *h) {
   L.cell_count = h->cell_count.p; L.cell_cursor = h->cell_cursor.p; L.cell_start = h->cell_start.p;
   L.cell_atoms = h->cell_atoms.p; L.nl_r = h->nl_r.p; L.nn_r = h->nn_r.p; L.nl_a = h->nl_a.p; L.nn_a = h->nn_a.p;
   L.rev_a = h->rev_a.p; L.cap_r = h->cap_r; L.cap_a = h->cap_a;
+  L.stage_e = h->stage_e.p; L.stage_g = h->stage_g.p;
   return L;
 }
 
@@ -910,6 +915,8 @@ int nep_destroy(nep_handle *h) {
   h->types.release(); h->cell_of.release(); h->cell_count.release(); h->cell_cursor.release();
   h->cell_start.release(); h->cell_atoms.release(); h->nn_r.release(); h->nn_a.release(); h->rev_a.release();
   h->thermo_ctl.release(); h->nl_r.release(); h->nl_a.release(); h->pos4.release(); h->dtab.release();
+  h->posA.release();
+  h->stage_e.release(); h->stage_g.release();
   h->p_ang.release(); h->e_rad.release(); h->status.release(); h->d_tc.release();
   h->d_grids.release(); h->d_sid.release(); h->d_offsets.release(); h->b_e.release(); h->b_w.release();
   if (h->b_graph) cudaGraphExecDestroy(h->b_graph);

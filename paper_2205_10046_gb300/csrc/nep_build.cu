@@ -169,38 +169,62 @@ __global__ void reorder_commit_kernel(int N, AtomState a, const Grid g0, const B
   const int sidp = B.grids ? B.sid[p] : 0;
   a.pos4[p] = make_float4((float)(r[0] - o[0]), (float)(r[1] - o[1]), (float)(r[2] - o[2]),
                           __int_as_float(t | (sidp << 8)));
+  a.posA[p] = make_float4((float)r[0], (float)r[1], (float)r[2], __int_as_float(t | (sidp << 8)));
 }
 
-// Visit every neighbour candidate (j, image) of atom i: f(j, entry, r2, type_j). Atoms are
-// in cell order, so the atoms of cell c are j in [start[c], start[c+1]).
+// floor(x / n) and the remainder, for n >= 1 and x > -n * 8
+__device__ __forceinline__ int floor_div(int x, int n) { return (x + 8 * n) / n - 8; }
+
+// Visit every neighbour candidate (j, image) of atom i: f(j, entry, r2, type_j). Atoms are in
+// cell order, so the atoms of cell c are j in [start[c], start[c+1]). For each (x, y) column of
+// neighbouring cells the z cells are walked as runs that share one periodic image, so the
+// shift S is formed once per run and the distance comes from the FP32 positions in the cell
+// frame: d = (r_j - r_i) + S, exactly antisymmetric like pair_vector. The image code of an
+// entry is the cell offset (ox, oy, oz), as the force kernels' shift tables expect.
 template <class F>
-__device__ __forceinline__ void for_candidates(int i, const float4 &pi, int gid, const Grid &g, const float4 *dtab0,
-                                               const int *start, const float4 *pos4, F &&f) {
+__device__ __forceinline__ void for_candidates(int i, const float4 &pi, int gid, const Grid &g, const int *start,
+                                               const float4 *posA, F &&f) {
   const int id = gid - g.cell_off;
-  const float4 *dtab = dtab0 + g.dtab_off;
   const int cx = id / (g.nc[1] * g.nc[2]);
   const int cy = (id / g.nc[2]) % g.nc[1];
   const int cz = id % g.nc[2];
+  float Hf[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) Hf[a][b] = (float)g.H[a][b];
   for (int ox = -g.R[0]; ox <= g.R[0]; ++ox) {
-    int x = (cx + ox) % g.nc[0];
-    if (x < 0) x += g.nc[0];
+    const int kx = floor_div(cx + ox, g.nc[0]);
+    const int xm = cx + ox - kx * g.nc[0];
     for (int oy = -g.R[1]; oy <= g.R[1]; ++oy) {
-      int y = (cy + oy) % g.nc[1];
-      if (y < 0) y += g.nc[1];
-      for (int oz = -g.R[2]; oz <= g.R[2]; ++oz) {
-        int z = (cz + oz) % g.nc[2];
-        if (z < 0) z += g.nc[2];
-        const unsigned code = (unsigned)(ox + g.R[0]) | ((unsigned)(oy + g.R[1]) << g.obits) |
-                              ((unsigned)(oz + g.R[2]) << (2 * g.obits));
-        const float4 D = dtab[code];
-        const int cell = g.cell_off + (x * g.nc[1] + y) * g.nc[2] + z;
-        const bool self_image = (ox == 0 && oy == 0 && oz == 0);
-        const int pe = start[cell + 1];
-        for (int j = start[cell]; j < pe; ++j) {
-          if (self_image && j == i) continue;
-          const float4 pj = pos4[j];
-          f(j, (unsigned)j | (code << g.jbits), norm2(pair_vector(pi, pj, D)), type_of(pj));
+      const int ky = floor_div(cy + oy, g.nc[1]);
+      const int ym = cy + oy - ky * g.nc[1];
+      const int col = g.cell_off + (xm * g.nc[1] + ym) * g.nc[2];
+      const float sx = __fadd_rn(__fmul_rn((float)kx, Hf[0][0]), __fmul_rn((float)ky, Hf[1][0]));
+      const float sy = __fadd_rn(__fmul_rn((float)kx, Hf[0][1]), __fmul_rn((float)ky, Hf[1][1]));
+      const float sz = __fadd_rn(__fmul_rn((float)kx, Hf[0][2]), __fmul_rn((float)ky, Hf[1][2]));
+      const unsigned code_xy = (unsigned)(ox + g.R[0]) | ((unsigned)(oy + g.R[1]) << g.obits);
+      int z = cz - g.R[2];
+      while (z <= cz + g.R[2]) {
+        const int kz = floor_div(z, g.nc[2]);
+        const int zm = z - kz * g.nc[2];
+        const int run = min(cz + g.R[2] - z, g.nc[2] - 1 - zm) + 1;  // cells of this image
+        const float4 S = make_float4(__fadd_rn(sx, __fmul_rn((float)kz, Hf[2][0])),
+                                     __fadd_rn(sy, __fmul_rn((float)kz, Hf[2][1])),
+                                     __fadd_rn(sz, __fmul_rn((float)kz, Hf[2][2])), 0.f);
+        for (int c = 0; c < run; ++c) {
+          const int oz = z + c - cz;
+          const unsigned code = code_xy | ((unsigned)(oz + g.R[2]) << (2 * g.obits));
+          const bool self_image = (ox == 0 && oy == 0 && oz == 0);
+          const int cell = col + zm + c;
+          const int pe = start[cell + 1];
+          for (int j = start[cell]; j < pe; ++j) {
+            if (self_image && j == i) continue;
+            const float4 pj = posA[j];
+            f(j, (unsigned)j | (code << g.jbits), norm2(pair_vector(pi, pj, S)), type_of(pj));
+          }
         }
+        z += run;
       }
     }
   }
@@ -209,71 +233,127 @@ __device__ __forceinline__ void for_candidates(int i, const float4 &pi, int gid,
 // Two passes over the candidates: count, then write. The radial list is grouped by
 // neighbour type; inside every group (and in the angular list) the pairs already inside
 // r_c come before the skin pairs, so the warps of the pair loops stay convergent.
-// count_only: record only the length statistics (used to size the lists).
-__global__ void build_lists_kernel(int N, int T, const float4 *pos4, const int *cell_of, const int *start,
-                                   const Grid g0, const Batch B, const float4 *dtab, float rlR2, float rlA2,
-                                   float rcR2, float rcA2, ListBufs L, int count_only, BuildStatus *st) {
+// count_only: record only the length statistics (used to size the lists). TT: the number of
+// atom types (compile time, so the per-type counters of a candidate cost TT compares).
+template <int TT>
+__global__ void build_lists_kernel(int N, const float4 *posA, const int *cell_of, const int *start,
+                                   const Grid g0, const Batch B, float rlR2, float rlA2, float rcR2, float rcA2,
+                                   ListBufs L, int count_only, BuildStatus *st) {
   if (!rebuild_pending(st)) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  // lanes past the last atom stay until the warp-level statistics below
+  const bool active = i0 < N;
+  const int i = active ? i0 : 0;  // a valid index for the idle lanes (N >= 1)
   const Grid &g = grid_of(B, g0, i);
-  const float4 pi = pos4[i];
+  const float4 pi = posA[i];
   const int id = cell_of[i];
   // per-type counters stay in registers: every update is unrolled over the types
-  int cr0[kMaxTypes], cr1[kMaxTypes];
+  int cr0[TT], cr1[TT];
 #pragma unroll
-  for (int t = 0; t < kMaxTypes; ++t) cr0[t] = cr1[t] = 0;
+  for (int t = 0; t < TT; ++t) cr0[t] = cr1[t] = 0;
   int ca0 = 0, ca1 = 0;
-  for_candidates(i, pi, id, g, dtab, start, pos4, [&](int, unsigned, float r2, int tj) {
-    if (r2 < rlR2) {
-      const bool core = r2 < rcR2;
+  // with a staging area the accepted candidates are kept in visiting order together with
+  // their group (type, inside r_c or skin, angular or not), so the lists are written from
+  // them instead of a second candidate scan
+  const bool staged = !count_only && L.stage_e;
+  int n_seen = 0;
+  if (active) {
+    for_candidates(i, pi, id, g, start, posA, [&](int, unsigned ent, float r2, int tj) {
+      if (r2 < rlR2) {
+        const bool core = r2 < rcR2;
 #pragma unroll
-      for (int t = 0; t < kMaxTypes; ++t) {
-        cr0[t] += (tj == t && core) ? 1 : 0;
-        cr1[t] += (tj == t && !core) ? 1 : 0;
+        for (int t = 0; t < TT; ++t) {
+          cr0[t] += (tj == t && core) ? 1 : 0;
+          cr1[t] += (tj == t && !core) ? 1 : 0;
+        }
+        const int ang = r2 < rlA2 ? (r2 < rcA2 ? 1 : 2) : 0;
+        if (staged && n_seen < L.cap_r) {
+          L.stage_e[(size_t)n_seen * N + i] = ent;
+          L.stage_g[(size_t)n_seen * N + i] = (unsigned char)(tj | (core ? 0 : 8) | (ang << 4));
+        }
+        ++n_seen;
       }
-    }
-    if (r2 < rlA2) {
-      if (r2 < rcA2) ++ca0;
-      else ++ca1;
-    }
-  });
+      if (r2 < rlA2) {
+        if (r2 < rcA2) ++ca0;
+        else ++ca1;
+      }
+    });
+  }
   int nr = 0, inr = 0;
 #pragma unroll
-  for (int t = 0; t < kMaxTypes; ++t) {
+  for (int t = 0; t < TT; ++t) {
     nr += cr0[t] + cr1[t];
     inr += cr0[t];
   }
   const int nA = ca0 + ca1;
-  atomicMax(&st->max_r, nr);
-  atomicMax(&st->max_a, nA);
-  atomicAdd(&st->sum_r, (unsigned long long)nr);
-  atomicAdd(&st->sum_a, (unsigned long long)nA);
-  atomicAdd(&st->in_r, (unsigned long long)inr);
-  atomicAdd(&st->in_a, (unsigned long long)ca0);
-  if (count_only) return;
+  // list statistics: reduced over the warp first, one atomic per warp and counter (every
+  // thread updating the same few words serialises in the L2 atomic unit)
+  {
+    int mr = nr, ma = nA;
+    unsigned long long sr = nr, sa = nA, ir = inr, ia = ca0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mr = max(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+      ma = max(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      sa += __shfl_xor_sync(0xffffffffu, sa, o);
+      ir += __shfl_xor_sync(0xffffffffu, ir, o);
+      ia += __shfl_xor_sync(0xffffffffu, ia, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax(&st->max_r, mr);
+      atomicMax(&st->max_a, ma);
+      atomicAdd(&st->sum_r, sr);
+      atomicAdd(&st->sum_a, sa);
+      atomicAdd(&st->in_r, ir);
+      atomicAdd(&st->in_a, ia);
+    }
+  }
+  if (count_only || !active) return;
   if (nr > L.cap_r || nA > L.cap_a) {  // leave the lists empty; the host grows them and rebuilds
     atomicOr(&st->overflow, 1);
-    for (int t = 0; t < T; ++t) L.nn_r[t * N + i] = 0;
+    for (int t = 0; t < TT; ++t) L.nn_r[t * N + i] = 0;
     L.nn_a[i] = 0;
     return;
   }
-  int cur0[kMaxTypes], cur1[kMaxTypes];
+  int cur0[TT], cur1[TT];
   int off = 0;
 #pragma unroll
-  for (int t = 0; t < kMaxTypes; ++t) {
+  for (int t = 0; t < TT; ++t) {
     cur0[t] = off;
     cur1[t] = off + cr0[t];
     off += cr0[t] + cr1[t];
-    if (t < T) L.nn_r[t * N + i] = cr0[t] + cr1[t];
+    L.nn_r[t * N + i] = cr0[t] + cr1[t];
   }
   int ka0 = 0, ka1 = ca0;
-  for_candidates(i, pi, id, g, dtab, start, pos4, [&](int, unsigned ent, float r2, int tj) {
+  if (staged) {
+    for (int m = 0; m < nr; ++m) {
+      const unsigned ent = L.stage_e[(size_t)m * N + i];
+      const unsigned gb = L.stage_g[(size_t)m * N + i];
+      const int tj = (int)(gb & 7u);
+      const bool core = (gb & 8u) == 0;
+      int slot = 0;
+#pragma unroll
+      for (int t = 0; t < TT; ++t) {
+        if (tj == t) {
+          slot = core ? cur0[t] : cur1[t];
+          cur0[t] += core ? 1 : 0;
+          cur1[t] += core ? 0 : 1;
+        }
+      }
+      L.nl_r[(size_t)slot * N + i] = ent;
+      const unsigned ang = gb >> 4;
+      if (ang) L.nl_a[(size_t)(ang == 1u ? ka0++ : ka1++) * N + i] = ent;
+    }
+    L.nn_a[i] = nA;
+    return;
+  }
+  for_candidates(i, pi, id, g, start, posA, [&](int, unsigned ent, float r2, int tj) {
     if (r2 < rlR2) {
       const bool core = r2 < rcR2;
       int slot = 0;
 #pragma unroll
-      for (int t = 0; t < kMaxTypes; ++t) {
+      for (int t = 0; t < TT; ++t) {
         if (tj == t) {
           slot = core ? cur0[t] : cur1[t];
           cur0[t] += core ? 1 : 0;
@@ -717,8 +797,20 @@ cudaError_t launch_rebuild(int N, int T, const Grid &g, const Batch &B, const fl
   sort_cells_kernel<<<cb, tb, 0, s>>>(g.ncell, L.cell_start, L.cell_atoms, st);
   reorder_gather_kernel<<<nb, tb, 0, s>>>(N, L.cell_atoms, a, st);
   reorder_commit_kernel<<<nb, tb, 0, s>>>(N, a, g, B, st);
-  build_lists_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, T, a.pos4, a.cell_of, L.cell_start, g, B, dtab, rlR2,
-                                                     rlA2, rcR2, rcA2, L, count_only, st);
+  auto lists = [&](auto kern) {
+    kern<<<(N + 127) / 128, 128, 0, s>>>(N, a.posA, a.cell_of, L.cell_start, g, B, rlR2, rlA2, rcR2, rcA2, L,
+                                         count_only, st);
+  };
+  switch (T) {
+    case 1: lists(build_lists_kernel<1>); break;
+    case 2: lists(build_lists_kernel<2>); break;
+    case 3: lists(build_lists_kernel<3>); break;
+    case 4: lists(build_lists_kernel<4>); break;
+    case 5: lists(build_lists_kernel<5>); break;
+    case 6: lists(build_lists_kernel<6>); break;
+    case 7: lists(build_lists_kernel<7>); break;
+    default: lists(build_lists_kernel<8>); break;
+  }
   if (!count_only) build_rev_kernel<<<nb, tb, 0, s>>>(N, L, g, B, st);
   finish_build_kernel<<<1, 1, 0, s>>>(st);
   return cudaGetLastError();

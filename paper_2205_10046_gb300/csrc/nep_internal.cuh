@@ -43,6 +43,8 @@ struct AtomState {
   double *x, *v, *F, *x_ref, *origin;  // [N][3]
   int *types, *perm, *cell_of;         // [N]
   float4 *pos4;                        // [N] cell-local FP32 coordinates + type bits
+  float4 *posA;                        // [N] FP32 coordinates in the structure's cell frame at the
+                                       // last build (neighbour search only) + type bits
   double *x2, *v2, *F2;                // reorder scratch [N][3]
   int *types2, *perm2, *cell2;         // reorder scratch [N]
 };
@@ -56,6 +58,8 @@ struct ListBufs {
   int *nn_a;       // [N]
   int *rev_a;      // [cap_a][N]
   int cap_r, cap_a;
+  unsigned *stage_e;        // [cap_r][N] accepted candidates of one build, or null (second scan)
+  unsigned char *stage_g;   // [cap_r][N] their groups
 };
 
 // Device-visible status written by the builders.

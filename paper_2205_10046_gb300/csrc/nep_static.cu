@@ -167,6 +167,7 @@ int nep_descriptors_static(const nep_params *params, int n_atoms, const double *
   a.perm2 = arena.take<int>(N);
   a.cell2 = arena.take<int>(N);
   a.pos4 = arena.take<float4>(N);
+  a.posA = arena.take<float4>(N);
   ListBufs L;
   std::memset(&L, 0, sizeof(L));
   L.cell_count = arena.take<int>(g.ncell + 1);
@@ -176,7 +177,7 @@ int nep_descriptors_static(const nep_params *params, int n_atoms, const double *
   L.nn_r = arena.take<int>((size_t)T * N);
   L.nn_a = arena.take<int>(N);
   if (!st || !dtab || !dcR || !dcA || !a.x || !a.v || !a.F || !a.x_ref || !a.origin || !a.x2 || !a.v2 || !a.F2 ||
-      !a.types || !a.perm || !a.cell_of || !a.types2 || !a.perm2 || !a.cell2 || !a.pos4 || !L.cell_count ||
+      !a.types || !a.perm || !a.cell_of || !a.types2 || !a.perm2 || !a.cell2 || !a.pos4 || !a.posA || !L.cell_count ||
       !L.cell_cursor || !L.cell_start || !L.cell_atoms || !L.nn_r || !L.nn_a)
     return fail_static(NEP_ERR_ARG, "structure too large for the static scratch (NEP_STATIC_SCRATCH_BYTES)");
 
