@@ -47,7 +47,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--workload", choices=["pbte", "si", "si_large"], default="pbte")
-    ap.add_argument("--skin", type=float, default=1.0)
+    ap.add_argument("--skin", type=float, default=0.4, help="neighbour-list skin (A) of the MD workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--plain-graph", action="store_true",
@@ -682,7 +682,8 @@ def run_gb300(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(workload_config(w, args.workload), parallelism=f"replicas x{world}"),
+            "config": dict(workload_config(w, args.workload), parallelism=f"replicas x{world}",
+                           neighbour_skin_A=args.skin),
             "roofline": {"kernel": "nep_atom", "bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                          "flops_per_atom": atom_f,
