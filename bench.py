@@ -59,7 +59,7 @@ def parse_args():
     ap.add_argument("--serve-only", action="store_true", help="only the serving measurement")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window of each serving run")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (requests/s)")
-    ap.add_argument("--serve-workers", type=int, default=16)
+    ap.add_argument("--serve-workers", type=int, default=256, help="job slots of the serving batch")
     ap.add_argument("--pop-calls", type=int, default=5)
     return ap.parse_args()
 
@@ -423,6 +423,7 @@ def run_batch_forms(args, dev, stream, flush, peak):
 
 # ----------------------------------------------------------------------------- serving
 SERVE_BUDGET = 40 << 30  # bytes of device workspace admitted at once
+SERVE_SKIN = 0.4         # neighbour-list skin (A) of the serving batch
 
 
 def serve_requests(rate, seconds, seed, pool):
@@ -459,7 +460,7 @@ def serve_run(model, pool, reqs, precision, workers):
     """Submit the requests at their arrival times; collect every result."""
     import numpy as np
     from paper_2205_10046_gb300 import nep
-    srv = nep.Server(model, memory_budget=SERVE_BUDGET, workers=workers, precision=precision)
+    srv = nep.Server(model, memory_budget=SERVE_BUDGET, workers=workers, precision=precision, skin=SERVE_SKIN)
     done = {}
     offered = 0.0
     lag = []
@@ -523,7 +524,7 @@ def run_serving(args):
     out = {"workload": (f"Poisson {args.serve_rate:.0f} req/s for {args.serve_seconds:.0f} s ({len(reqs)} requests); "
                         f"structures drawn from a pool of 256 (32-20,000 atoms, log-uniform, FCC/BCC/diamond, "
                         f"1-3 of 3 species); 50% single point, 30% 50-step FIRE, 20% NVE U{{10..1000}} steps "
-                        f"of 1 fs; NEP rc 5.5/4.0 n_max 8/4 40 neurons; {args.serve_workers} workers, "
+                        f"of 1 fs; NEP rc 5.5/4.0 n_max 8/4 40 neurons; one batch of up to {args.serve_workers} jobs (iteration-level batching), "
                         f"{SERVE_BUDGET >> 30} GB admission budget"),
            "latency": "submission (arrival) to result on the host, server clock"}
     for prec, key in ((0, "fp32"), (1, "bf16")):

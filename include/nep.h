@@ -194,13 +194,17 @@ int nep_autotune(nep_handle *h, int n_struct, const int *offsets, const double *
                  const double *boxes, int n_pop, nep_tuning *out, nep_stream_t stream);
 
 /* ------------------------------------------------------------------------ serving
- * A persistent request loop (the paper has no counterpart): jobs on structures of any size
- * are queued, admitted first in first out while their estimated device workspace fits the
- * memory budget and a worker is free, and run concurrently, each on its own CUDA stream
- * and handle (positions, neighbour lists and velocities stay on the device for the whole
- * job; workspaces are stream-ordered allocations released when the job ends). Jobs that
- * arrive while others run are admitted as soon as a worker and memory free up, so their
- * work overlaps on the device. A job's results do not depend on what else runs. */
+ * A persistent request loop with iteration-level (continuous) batching; the paper has no
+ * counterpart. Jobs on structures of any size are queued; a scheduler thread keeps every
+ * running job as one structure of a device-resident batch and advances all of them by one
+ * iteration at a time (one velocity-Verlet or FIRE step each, or a job's first evaluation),
+ * with the batched kernels of nep_compute_batch. Between iterations finished jobs leave and
+ * queued jobs join, first in first out, while the batch has a free job slot and the jobs'
+ * workspace estimates fit the memory budget; positions, velocities and lists stay on the
+ * device. Neighbour lists (radius r_c + the params' skin) are rebuilt after every change of
+ * the batch and whenever an atom has moved more than skin/2. A job's arithmetic uses only its
+ * own structure, so its results do not depend on what else runs, up to the order of its pair
+ * sums (which follows its last list build): equal alone and in a mix within FP32 rounding. */
 #define NEP_JOB_SINGLE 0 /* one energy / force / virial evaluation (nep_compute) */
 #define NEP_JOB_FIRE 1   /* FIRE relaxation (fire_run), then one evaluation at the result */
 #define NEP_JOB_NVE 2    /* velocity-Verlet NVE (md_run), then one evaluation at the end */
@@ -209,7 +213,7 @@ typedef struct nep_server nep_server;
 
 typedef struct {
   size_t memory_budget; /* bytes of device workspace that running jobs may hold together */
-  int workers;          /* jobs on the device at once (1..256): one host thread and stream each */
+  int workers;          /* job slots of the batch: jobs on the device at once (1..65536) */
   int precision;        /* 0: FP32 network, 1: BF16 tensor-core network (nep_set_precision) */
 } nep_server_config;
 
@@ -234,7 +238,7 @@ typedef struct {
   double virial[9];     /* total virial of the final state (eV) */
   double t_submit, t_start, t_done; /* seconds since nep_server_create: queued, on a worker, done */
   size_t workspace_est; /* device bytes reserved for the job by admission */
-  size_t workspace_used;/* device bytes the job held at its end */
+  size_t workspace_used;/* device workspace of the whole batch when the job ended */
   char message[160];    /* error text when status != NEP_OK */
 } nep_result;
 
@@ -242,6 +246,7 @@ typedef struct {
   int queued, running;
   long long completed, failed;
   size_t bytes_reserved, peak_bytes_reserved; /* admission estimates of the running jobs */
+  size_t peak_workspace_bytes;                /* largest device workspace of the batch */
   double atom_evaluations;                    /* sum over finished jobs of N x force evaluations */
 } nep_server_stats;
 

@@ -252,6 +252,13 @@ struct BatchKey {
   int N, cap_r, cap_a, precision, blocks, pad;
 };
 
+// Identity of a captured engine iteration: every array it touches and the list capacities.
+struct EngineKey {
+  const void *p[24];
+  long long gen;
+  int N, cap_r, cap_a, precision;
+};
+
 // Launch shapes of the batched kernels, set by the caller or the autotuner (0 = default).
 struct Tuning {
   int members = 0;       // population members per launch (grid.y)
@@ -299,6 +306,14 @@ struct nep_handle {
   cudaGraphExec_t fire_graph = nullptr;  // one FIRE step (its time step lives on the device)
   DevBuf<FireState> fire, ck_fire;
   DevBuf<ThermoState> thermo_state, ck_thermo;  // BDP thermostat (md_run_ex)
+  // batched serving engine: one structure per job, all advanced by one iteration
+  std::vector<EngineSlot> e_slots_h;            // host mirror (after the last iteration)
+  std::vector<double> e_energy_h, e_virial_h;   // per job, after the last iteration
+  DevBuf<EngineSlot> e_slots, e_slots_ck;
+  DevBuf<double> e_energy, e_virial, e_u, e_w, e_xck, e_vck;
+  DevBuf<int4> e_table;
+  cudaGraphExec_t e_graph = nullptr;            // one captured iteration of the current layout
+  EngineKey e_key{}, e_last{};
   bool nvt = false;                             // the MD step graph rescales velocities
   bool graph_nvt = false;
   double graph_dt = 0;
@@ -342,7 +357,8 @@ struct nep_handle {
     f(perm); f(types); f(cell_of); f(cell_count); f(cell_cursor); f(cell_start); f(cell_atoms); f(nn_r);
     f(nn_a); f(rev_a); f(thermo_ctl); f(nl_r); f(nl_a); f(pos4); f(posA); f(dtab); f(p_ang); f(e_rad); f(d_grids);
     f(d_sid); f(d_offsets); f(b_e); f(b_w); f(pop_cr); f(pop_ca); f(pop_ann); f(pop_tc); f(pop_reg); f(pop_es);
-    f(pop_ws); f(fire); f(ck_fire); f(thermo_state); f(ck_thermo); f(stage_e); f(stage_g);
+    f(pop_ws); f(fire); f(ck_fire); f(thermo_state); f(ck_thermo); f(stage_e); f(stage_g); f(e_slots);
+    f(e_slots_ck); f(e_energy); f(e_virial); f(e_u); f(e_w); f(e_xck); f(e_vck); f(e_table);
   }
   // the kernels compare r^2 with the FP32 square of the FP32 cutoff
   float rcR2f() const { return (float)rcR * (float)rcR; }
@@ -642,15 +658,15 @@ int setup_batch(nep_handle *h, int n_struct, const int *offsets, const double *b
     CK(h->d_grids.ensure(n_struct), "alloc batch");
     CK(h->d_offsets.ensure(n_struct + 1), "alloc batch");
     CK(h->dtab.ensure((size_t)n_struct * ncode), "alloc batch");
-    CK(cudaMemcpyAsync(h->d_grids.p, G.data(), sizeof(Grid) * n_struct, cudaMemcpyHostToDevice, s), "copy grids");
-    CK(cudaMemcpyAsync(h->d_offsets.p, offsets, sizeof(int) * (n_struct + 1), cudaMemcpyHostToDevice, s),
-       "copy offsets");
-    launch_shift_tables(n_struct, h->d_grids.p, ncode, obits, h->dtab.p, s);
-    // the copies above read pageable host memory that changes on the next call
-    CK(wait_stream(s), "batch setup");
-    h->b_gen += 1;
+    // the copies read the handle's own host arrays, which change only at the next layout
+    // (every caller synchronises the stream before that)
     h->b_offsets.assign(offsets, offsets + n_struct + 1);
     h->b_boxes.assign(boxes, boxes + 9 * (size_t)n_struct);
+    CK(cudaMemcpyAsync(h->d_grids.p, G.data(), sizeof(Grid) * n_struct, cudaMemcpyHostToDevice, s), "copy grids");
+    CK(cudaMemcpyAsync(h->d_offsets.p, h->b_offsets.data(), sizeof(int) * (n_struct + 1), cudaMemcpyHostToDevice, s),
+       "copy offsets");
+    launch_shift_tables(n_struct, h->d_grids.p, ncode, obits, h->dtab.p, s);
+    h->b_gen += 1;
     h->nb_struct = n_struct;
   }
   CK(h->d_sid.ensure(std::max(N, 1)), "alloc batch");
@@ -814,6 +830,319 @@ void release_workspace(nep_handle *h) {
 
 cudaError_t stream_sync(cudaStream_t s) { return wait_stream(s); }
 
+// ---------------------------------------------------------------- batched serving engine
+int engine_jobs(const nep_handle *h) { return h->nb_struct; }
+int engine_atoms(const nep_handle *h) { return h->N; }
+const EngineSlot &engine_slot(const nep_handle *h, int k) { return h->e_slots_h[k]; }
+double engine_energy(const nep_handle *h, int k) { return h->e_energy_h[k]; }
+const double *engine_virial(const nep_handle *h, int k) { return h->e_virial_h.data() + 9 * (size_t)k; }
+
+// New job layout: the kept jobs (indices into the current layout, in order) and then the
+// added ones. The atoms of every job stay contiguous; new jobs start at phase 0 (their first
+// iteration evaluates their forces).
+int engine_relayout(nep_handle *h, const std::vector<int> &keep, const std::vector<EngineJob> &add, cudaStream_t s,
+                    size_t target_bytes) {
+  const int S_old = h->nb_struct;
+  std::vector<int> off_new(1, 0);
+  std::vector<double> boxes;
+  std::vector<EngineSlot> slots;
+  std::vector<int4> table;
+  for (int k : keep) {
+    if (k < 0 || k >= S_old) return fail(h, NEP_ERR_ARG, "engine: bad job index");
+    const int n = h->b_offsets[k + 1] - h->b_offsets[k];
+    table.push_back(make_int4(h->b_offsets[k], off_new.back(), n, off_new.back() - h->b_offsets[k]));
+    off_new.push_back(off_new.back() + n);
+    boxes.insert(boxes.end(), h->b_boxes.begin() + 9 * (size_t)k, h->b_boxes.begin() + 9 * (size_t)k + 9);
+    slots.push_back(h->e_slots_h[k]);
+  }
+  const int first_new = (int)slots.size();
+  for (const EngineJob &j : add) {
+    off_new.push_back(off_new.back() + j.n);
+    boxes.insert(boxes.end(), j.box, j.box + 9);
+    EngineSlot sl{};
+    sl.kind = j.kind;
+    sl.phase = 0;
+    sl.n_steps = j.kind == kJobSingle ? 0 : j.n_steps;
+    sl.dt = j.dt;
+    if (j.kind == kJobFire) {
+      sl.fire.dt = j.dt;
+      sl.fire.alpha = 0.1;
+      sl.fire.dt_max = 10.0 * j.dt;
+      sl.fire.fmax2 = j.fmax * j.fmax;
+    }
+    slots.push_back(sl);
+  }
+  const int S_new = (int)slots.size(), N_new = off_new.back();
+  // move the kept jobs into the reorder scratch arrays, fill in the new ones, swap
+  const size_t n = (size_t)std::max(N_new, 1);
+  CK(h->x2.ensure(3 * n), "alloc");
+  CK(h->v2.ensure(3 * n), "alloc");
+  CK(h->F2.ensure(3 * n), "alloc");
+  CK(h->types2.ensure(n), "alloc");
+  CK(h->perm2.ensure(n), "alloc");
+  AtomState dst = atom_state(h);
+  dst.x = h->x2.p; dst.v = h->v2.p; dst.F = h->F2.p; dst.types = h->types2.p; dst.perm = h->perm2.p;
+  if (!table.empty()) {
+    CK(h->e_table.ensure(table.size()), "alloc");
+    CK(cudaMemcpyAsync(h->e_table.p, table.data(), sizeof(int4) * table.size(), cudaMemcpyHostToDevice, s), "copy");
+    launch_engine_relayout((int)table.size(), h->e_table.p, atom_state(h), dst, s);
+  }
+  if (!add.empty()) {
+    // the new jobs are contiguous at the end of the layout: one copy per array
+    const size_t o0 = (size_t)off_new[first_new], na = (size_t)N_new - o0;
+    std::vector<double> px(3 * na), pv(3 * na, 0.0);
+    std::vector<int> pt(na), pp(na);
+    for (size_t a = 0; a < add.size(); ++a) {
+      const EngineJob &j = add[a];
+      const size_t o = (size_t)off_new[first_new + a] - o0;
+      std::memcpy(px.data() + 3 * o, j.pos, sizeof(double) * 3 * j.n);
+      if (j.vel) std::memcpy(pv.data() + 3 * o, j.vel, sizeof(double) * 3 * j.n);
+      std::memcpy(pt.data() + o, j.types, sizeof(int) * j.n);
+      for (int k = 0; k < j.n; ++k) pp[o + k] = (int)(o0 + o) + k;
+    }
+    CK(cudaMemcpyAsync(dst.x + 3 * o0, px.data(), sizeof(double) * 3 * na, cudaMemcpyHostToDevice, s), "copy");
+    CK(cudaMemcpyAsync(dst.v + 3 * o0, pv.data(), sizeof(double) * 3 * na, cudaMemcpyHostToDevice, s), "copy");
+    CK(cudaMemsetAsync(dst.F + 3 * o0, 0, sizeof(double) * 3 * na, s), "zero");
+    CK(cudaMemcpyAsync(dst.types + o0, pt.data(), sizeof(int) * na, cudaMemcpyHostToDevice, s), "copy");
+    CK(cudaMemcpyAsync(dst.perm + o0, pp.data(), sizeof(int) * na, cudaMemcpyHostToDevice, s), "copy");
+    CK(wait_stream(s), "sync");  // the host staging vectors are temporaries
+  }
+  std::swap(h->x, h->x2);
+  std::swap(h->v, h->v2);
+  std::swap(h->F, h->F2);
+  std::swap(h->types, h->types2);
+  std::swap(h->perm, h->perm2);
+  // buffers sized for an earlier, larger batch are released (and the lists sized again) when
+  // the workspace exceeds the new batch's budget; only the batch state above is kept
+  if (target_bytes && workspace_bytes(h) > target_bytes) {
+    h->for_workspace([&](auto &b) {
+      const void *p = b.p;
+      if (p != h->x.p && p != h->v.p && p != h->F.p && p != h->types.p && p != h->perm.p) b.release();
+    });
+    h->cap_r = h->cap_a = 0;
+    h->nb_struct = 0;
+    h->b_offsets.clear();
+    h->b_boxes.clear();
+  }
+  h->e_slots_h = slots;
+  h->e_energy_h.assign(S_new, 0.0);
+  h->e_virial_h.assign(9 * (size_t)S_new, 0.0);
+  h->md_ready = false;
+  for (cudaGraphExec_t *g : {&h->graph, &h->fire_graph, &h->b_graph, &h->e_graph})
+    if (*g) {
+      cudaGraphExecDestroy(*g);
+      *g = nullptr;
+    }
+  std::memset(&h->e_key, 0, sizeof(h->e_key));
+  std::memset(&h->e_last, 0, sizeof(h->e_last));
+  h->N = N_new;
+  if (S_new == 0) {
+    h->nb_struct = 0;
+    h->b_offsets.assign(1, 0);
+    h->b_boxes.clear();
+    return NEP_OK;
+  }
+  int rc = ensure_atoms(h, N_new, s);
+  if (rc) return rc;
+  CK(h->e_slots.ensure(S_new), "alloc");
+  CK(h->e_slots_ck.ensure(S_new), "alloc");
+  CK(h->e_energy.ensure(S_new), "alloc");
+  CK(h->e_virial.ensure(9 * (size_t)S_new), "alloc");
+  CK(h->e_u.ensure(n), "alloc");
+  CK(h->e_w.ensure(9 * n), "alloc");
+  CK(h->e_xck.ensure(3 * n), "alloc");
+  CK(h->e_vck.ensure(3 * n), "alloc");
+  CK(cudaMemcpyAsync(h->e_slots.p, slots.data(), sizeof(EngineSlot) * S_new, cudaMemcpyHostToDevice, s), "copy");
+  rc = setup_batch(h, S_new, off_new.data(), boxes.data(), N_new, s);
+  if (rc) return rc;
+  // the first layout sizes the lists with a counting pass; later ones keep the capacity (an
+  // iteration whose build overflows is undone and run again with grown lists)
+  if (h->cap_r == 0 || h->cap_a == 0) return rebuild_lists(h, N_new, s, batch_of(h));
+  CK(h->cell_count.ensure(h->grid.ncell + 1), "alloc cells");
+  CK(h->cell_cursor.ensure(h->grid.ncell + 1), "alloc cells");
+  CK(h->cell_start.ensure(h->grid.ncell + 1), "alloc cells");
+  return ensure_lists(h, N_new, h->cap_r, h->cap_a);
+}
+
+EngineKey engine_key(nep_handle *h) {
+  EngineKey k;
+  std::memset(&k, 0, sizeof(k));
+  const void *p[] = {h->x.p, h->v.p, h->F.p, h->x_ref.p, h->origin.p, h->types.p, h->perm.p, h->pos4.p, h->posA.p,
+                     h->nl_r.p, h->nl_a.p, h->rev_a.p, h->p_ang.p, h->e_rad.p, h->e_u.p, h->e_w.p, h->e_slots.p,
+                     h->e_energy.p, h->d_grids.p, h->d_sid.p, h->dtab.p, h->cell_start.p, h->stage_e.p,
+                     h->partial_gather.p};
+  static_assert(sizeof(p) / sizeof(p[0]) == sizeof(k.p) / sizeof(k.p[0]), "key size");
+  for (size_t c = 0; c < sizeof(p) / sizeof(p[0]); ++c) k.p[c] = p[c];
+  k.gen = h->b_gen;
+  k.N = h->N;
+  k.cap_r = h->cap_r;
+  k.cap_a = h->cap_a;
+  k.precision = h->precision;
+  return k;
+}
+
+int engine_queue_iteration(nep_handle *h, cudaStream_t s);
+
+// Capture one engine iteration of the current layout into a graph.
+int capture_engine(nep_handle *h, cudaStream_t s) {
+  if (h->e_graph) {
+    cudaGraphExecDestroy(h->e_graph);
+    h->e_graph = nullptr;
+  }
+  CK(wait_stream(s), "sync");
+  cudaStream_t c = h->cap_stream;
+  CK(cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal), "capture");
+  int rc = engine_queue_iteration(h, c);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "end capture (engine)");
+  e = cudaGraphInstantiate(&h->e_graph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    h->e_graph = nullptr;
+    return cuda_fail(h, e, "graph instantiate (engine)");
+  }
+  return NEP_OK;
+}
+
+// Queue one iteration of every job: drift (requesting a neighbour build when an atom moved
+// more than skin/2 since the last one), the build (its kernels return at once unless one is
+// pending), forces, kick, structure sums, FIRE update, bookkeeping.
+int engine_queue_iteration(nep_handle *h, cudaStream_t s) {
+  const int N = h->N, S = h->nb_struct;
+  const float rlR = (float)(h->rcR + h->skin), rlA = (float)(h->rcA + h->skin);
+  launch_engine_drift(N, atom_state(h), h->d_sid.p, h->e_slots.p, h->d_inv_mk.p, 0.25 * h->skin * h->skin,
+                      h->status.p, s);
+  cudaError_t e = launch_rebuild(N, h->T, h->grid, batch_of(h), h->dtab.p, rlR * rlR, rlA * rlA, h->rcR2f(),
+                                 h->rcA2f(), atom_state(h), list_bufs(h), 0, h->status.p, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "engine rebuild");
+  AtomArgs a = make_args(h, N);
+  a.perm = nullptr;  // every output in the internal order
+  a.energy = h->e_u.p;
+  a.force = h->F.p;
+  a.virial = h->e_w.p;
+  a.s_out = N;
+  a.slots = h->e_slots.p;
+  e = h->ops->atom_batch(a, h->mf, h->w0.data(), h->b0.data(), h->w1.data(), h->b1, 1, atom_block(h), s);
+  if (e == cudaSuccess) e = h->ops->gather_batch(a, 1, gather_block(h), s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "engine kernels");
+  launch_struct_sums(S, 1, h->d_offsets.p, N, h->e_u.p, h->e_w.p, h->e_energy.p, h->e_virial.p, s);
+  launch_engine_fire(S, h->d_offsets.p, atom_state(h), h->e_slots.p, s);
+  launch_engine_advance(S, h->e_slots.p, s);
+  CK(cudaGetLastError(), "engine step");
+  return NEP_OK;
+}
+
+// n_iter iterations of every job (the first with a forced neighbour build after a new
+// layout), then the per-job state is read back. The iterations start from a checkpoint: a
+// list overflow in any of them undoes them all, grows the lists and runs them again. An
+// unchanged layout replays one captured iteration graph.
+int engine_step(nep_handle *h, cudaStream_t s, int n_iter, bool force_rebuild) {
+  const int N = h->N, S = h->nb_struct;
+  if (N == 0 || S == 0 || n_iter < 1) return NEP_OK;
+  CK(h->ck_F.ensure(3 * (size_t)N), "alloc checkpoint");
+  CK(h->ck_types.ensure((size_t)N), "alloc checkpoint");
+  CK(h->ck_perm.ensure((size_t)N), "alloc checkpoint");
+  CK(h->ck_x.ensure(3 * (size_t)N), "alloc checkpoint");
+  int rc = ensure_partials(h, N, 1);
+  if (rc) return rc;
+  for (int attempt = 0;; ++attempt) {
+    // a build re-sorts the atoms: the checkpoint holds every per-atom array (x_ref too)
+    CK(cudaMemcpyAsync(h->e_xck.p, h->x.p, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s), "checkpoint");
+    CK(cudaMemcpyAsync(h->e_vck.p, h->v.p, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s), "checkpoint");
+    CK(cudaMemcpyAsync(h->ck_F.p, h->F.p, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s), "checkpoint");
+    CK(cudaMemcpyAsync(h->ck_x.p, h->x_ref.p, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s), "checkpoint");
+    CK(cudaMemcpyAsync(h->ck_types.p, h->types.p, sizeof(int) * N, cudaMemcpyDeviceToDevice, s), "checkpoint");
+    CK(cudaMemcpyAsync(h->ck_perm.p, h->perm.p, sizeof(int) * N, cudaMemcpyDeviceToDevice, s), "checkpoint");
+    CK(cudaMemcpyAsync(h->e_slots_ck.p, h->e_slots.p, sizeof(EngineSlot) * S, cudaMemcpyDeviceToDevice, s),
+       "checkpoint");
+    const bool forced = force_rebuild || attempt > 0;
+    // the flags of this chunk start cleared; a forced build is requested before the first step
+    if (forced) launch_arm_rebuild(h->status.p, s);
+    else launch_clear_flags(h->status.p, s);
+    const EngineKey key = engine_key(h);
+    for (int it = 0; it < n_iter; ++it) {
+      if (!h->prof && h->e_graph && std::memcmp(&key, &h->e_key, sizeof(key)) == 0) {
+        CK(cudaGraphLaunch(h->e_graph, s), "engine graph launch");
+        continue;
+      }
+      if (!h->prof && std::memcmp(&key, &h->e_last, sizeof(key)) == 0) {
+        // the layout was stable for a whole chunk: capture one iteration for the next ones
+        rc = capture_engine(h, s);
+        if (rc) return rc;
+        h->e_key = key;
+        CK(cudaGraphLaunch(h->e_graph, s), "engine graph launch");
+        continue;
+      }
+      rc = engine_queue_iteration(h, s);
+      if (rc) return rc;
+    }
+    h->e_last = key;
+    CK(cudaMemcpyAsync(h->h_status, h->status.p, sizeof(BuildStatus), cudaMemcpyDeviceToHost, s), "status");
+    CK(wait_stream(s), "sync");
+    const BuildStatus st = *h->h_status;
+    if (st.tc_timeout) return fail(h, NEP_ERR_TIMEOUT, "a tensor-core completion wait ran out");
+    if (st.bad_input & 2) return fail(h, NEP_ERR_NONFINITE, "non-finite position");
+    if (st.bad_input & 1) return fail(h, NEP_ERR_ARG, "atom type out of range");
+    if (!st.overflow && !st.rev_missing) break;
+    if (attempt >= 2 || st.max_r > kListBuf || st.max_a > kListBuf)
+      return fail(h, NEP_ERR_NEIGHBOR_OVERFLOW, "more than " + std::to_string(kListBuf) +
+                                                    " neighbours within r_c + skin for one atom");
+    CK(cudaMemcpyAsync(h->x.p, h->e_xck.p, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s), "restore");
+    CK(cudaMemcpyAsync(h->v.p, h->e_vck.p, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s), "restore");
+    CK(cudaMemcpyAsync(h->F.p, h->ck_F.p, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s), "restore");
+    CK(cudaMemcpyAsync(h->x_ref.p, h->ck_x.p, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s), "restore");
+    CK(cudaMemcpyAsync(h->types.p, h->ck_types.p, sizeof(int) * N, cudaMemcpyDeviceToDevice, s), "restore");
+    CK(cudaMemcpyAsync(h->perm.p, h->ck_perm.p, sizeof(int) * N, cudaMemcpyDeviceToDevice, s), "restore");
+    CK(cudaMemcpyAsync(h->e_slots.p, h->e_slots_ck.p, sizeof(EngineSlot) * S, cudaMemcpyDeviceToDevice, s),
+       "restore");
+    int rc2 = ensure_lists(h, N, round_cap(st.max_r), round_cap(st.max_a));
+    if (rc2) return rc2;
+  }
+  std::vector<EngineSlot> sl(S);
+  CK(cudaMemcpyAsync(sl.data(), h->e_slots.p, sizeof(EngineSlot) * S, cudaMemcpyDeviceToHost, s), "read back");
+  CK(cudaMemcpyAsync(h->e_energy_h.data(), h->e_energy.p, sizeof(double) * S, cudaMemcpyDeviceToHost, s), "read back");
+  CK(cudaMemcpyAsync(h->e_virial_h.data(), h->e_virial.p, sizeof(double) * 9 * S, cudaMemcpyDeviceToHost, s),
+     "read back");
+  CK(wait_stream(s), "sync");
+  h->e_slots_h = sl;
+  return NEP_OK;
+}
+
+// Final arrays of job k in its own atom order: positions wrapped into its cell, forces,
+// velocities (HOST buffers [n][3], any may be null).
+int engine_fetch(nep_handle *h, int k, double *pos, double *force, double *vel, cudaStream_t s) {
+  if (k < 0 || k >= h->nb_struct) return fail(h, NEP_ERR_ARG, "engine: bad job index");
+  const int o = h->b_offsets[k], n = h->b_offsets[k + 1] - o;
+  std::vector<double> x(3 * (size_t)n), f(3 * (size_t)n), v(3 * (size_t)n);
+  std::vector<int> perm(n);
+  CK(cudaMemcpyAsync(x.data(), h->x.p + 3 * (size_t)o, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s), "read");
+  CK(cudaMemcpyAsync(f.data(), h->F.p + 3 * (size_t)o, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s), "read");
+  CK(cudaMemcpyAsync(v.data(), h->v.p + 3 * (size_t)o, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s), "read");
+  CK(cudaMemcpyAsync(perm.data(), h->perm.p + o, sizeof(int) * n, cudaMemcpyDeviceToHost, s), "read");
+  CK(wait_stream(s), "sync");
+  const Grid &g = h->b_grids[k];
+  for (int i = 0; i < n; ++i) {
+    const int t = perm[i] - o;
+    if (t < 0 || t >= n) return fail(h, NEP_ERR_CUDA, "engine: inconsistent atom order");
+    double sf[3];
+    for (int b = 0; b < 3; ++b) {
+      sf[b] = x[3 * i] * g.Hinv[0][b] + x[3 * i + 1] * g.Hinv[1][b] + x[3 * i + 2] * g.Hinv[2][b];
+      sf[b] -= std::floor(sf[b]);
+    }
+    for (int b = 0; b < 3; ++b) {
+      if (pos) pos[3 * t + b] = sf[0] * g.H[0][b] + sf[1] * g.H[1][b] + sf[2] * g.H[2][b];
+      if (force) force[3 * t + b] = f[3 * i + b];
+      if (vel) vel[3 * t + b] = v[3 * i + b];
+    }
+  }
+  return NEP_OK;
+}
+
 size_t workspace_bytes(nep_handle *h) {
   size_t t = 0;
   h->for_workspace([&](auto &b) { t += b.bytes(); });
@@ -916,10 +1245,13 @@ int nep_destroy(nep_handle *h) {
   h->cell_start.release(); h->cell_atoms.release(); h->nn_r.release(); h->nn_a.release(); h->rev_a.release();
   h->thermo_ctl.release(); h->nl_r.release(); h->nl_a.release(); h->pos4.release(); h->dtab.release();
   h->posA.release();
+  h->e_slots.release(); h->e_slots_ck.release(); h->e_energy.release(); h->e_virial.release(); h->e_u.release();
+  h->e_w.release(); h->e_xck.release(); h->e_vck.release(); h->e_table.release();
   h->stage_e.release(); h->stage_g.release();
   h->p_ang.release(); h->e_rad.release(); h->status.release(); h->d_tc.release();
   h->d_grids.release(); h->d_sid.release(); h->d_offsets.release(); h->b_e.release(); h->b_w.release();
   if (h->b_graph) cudaGraphExecDestroy(h->b_graph);
+  if (h->e_graph) cudaGraphExecDestroy(h->e_graph);
   h->pop_cr.release(); h->pop_ca.release(); h->pop_ann.release(); h->pop_tc.release(); h->pop_reg.release();
   h->pop_es.release(); h->pop_ws.release();
   delete h;

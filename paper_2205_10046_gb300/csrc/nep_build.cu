@@ -58,19 +58,25 @@ __global__ void bin_atoms_kernel(int N, int T, AtomState a, int *count, const Gr
     atomicOr(&st->bad_input, 1);
     a.types[i] = 0;
   }
+  bool inside = true;
   if (!isfinite(r[0]) || !isfinite(r[1]) || !isfinite(r[2])) {
     atomicOr(&st->bad_input, 2);
     r[0] = r[1] = r[2] = 0.0;
+    inside = false;  // overwrite the position
   }
   double s[3];
   int c[3];
   for (int b = 0; b < 3; ++b) {
     s[b] = r[0] * g.Hinv[0][b] + r[1] * g.Hinv[1][b] + r[2] * g.Hinv[2][b];
-    s[b] -= floor(s[b]);
+    const double f = floor(s[b]);
+    inside = inside && f == 0.0;
+    s[b] -= f;
     const int cb = (int)(s[b] * g.nc[b]);
     c[b] = cb < 0 ? 0 : (cb >= g.nc[b] ? g.nc[b] - 1 : cb);
   }
-  for (int b = 0; b < 3; ++b) x[b] = s[0] * g.H[0][b] + s[1] * g.H[1][b] + s[2] * g.H[2][b];
+  // only atoms outside the cell are moved (a position is not re-rounded by every build)
+  if (!inside)
+    for (int b = 0; b < 3; ++b) x[b] = s[0] * g.H[0][b] + s[1] * g.H[1][b] + s[2] * g.H[2][b];
   const int id = g.cell_off + (c[0] * g.nc[1] + c[1]) * g.nc[2] + c[2];
   a.cell_of[i] = id;
   atomicAdd(count + id, 1);
@@ -899,6 +905,163 @@ __global__ void fire_mix_kernel(int N, AtomState a, FireState *fire, int check_o
 
 void launch_fire_mix(int N, const AtomState &a, FireState *fire, int check_only, cudaStream_t s) {
   fire_mix_kernel<<<1, 1024, 0, s>>>(N, a, fire, check_only);
+}
+
+// ------------------------------------------------------------------ batched serving engine
+// Every job is one structure of a batch; one iteration advances all of them together. The
+// first iteration of a job only evaluates its forces (phase 0); each later one is a velocity-
+// Verlet step (phase 1) of the job's own length (NVE) or FIRE step; finished jobs stay frozen.
+
+// First half of the velocity-Verlet step of the stepping jobs: v += dt/2 F/m, x += dt v.
+// A neighbour build is requested when an atom moved more than skin/2 since the last one.
+__global__ void engine_drift_kernel(int N, AtomState a, const int *sid, const EngineSlot *slots,
+                                    const double *inv_mass_kappa, double half_skin2, BuildStatus *st) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const EngineSlot &sl = slots[sid[i]];
+  if (sl.phase != 1 || sl.kind == kJobSingle || (sl.kind == kJobFire && sl.fire.converged)) return;
+  const double dt = sl.kind == kJobFire ? sl.fire.dt : sl.dt;
+  const double s = 0.5 * dt * inv_mass_kappa[a.types[i]];
+  double d2 = 0.0, r[3];
+  for (int b = 0; b < 3; ++b) {
+    const size_t k = 3 * (size_t)i + b;
+    const double vb = a.v[k] + s * a.F[k];
+    a.v[k] = vb;
+    r[b] = a.x[k] + dt * vb;
+    a.x[k] = r[b];
+    const double dd = r[b] - a.x_ref[k];
+    d2 += dd * dd;
+  }
+  // the force kernels read the cell-local FP32 coordinates
+  float4 p = a.pos4[i];
+  p.x = (float)(r[0] - a.origin[3 * (size_t)i]);
+  p.y = (float)(r[1] - a.origin[3 * (size_t)i + 1]);
+  p.z = (float)(r[2] - a.origin[3 * (size_t)i + 2]);
+  a.pos4[i] = p;
+  if (d2 > half_skin2) st->rebuild = 1;
+}
+
+// Clears the error flags of a chunk of iterations (a build is not requested).
+__global__ void clear_flags_kernel(BuildStatus *st) {
+  st->overflow = 0;
+  st->rev_missing = 0;
+  st->bad_input = 0;
+  st->tc_timeout = 0;
+}
+
+void launch_clear_flags(BuildStatus *st, cudaStream_t s) { clear_flags_kernel<<<1, 1, 0, s>>>(st); }
+
+// FIRE update of every FIRE job after its step (the FIRE definition of fire_mix_kernel, one
+// block per job over the job's own atoms [offsets[s], offsets[s+1])); at the job's first
+// iteration only the convergence test on the starting forces.
+__global__ void engine_fire_kernel(const int *offsets, AtomState a, EngineSlot *slots) {
+  const int s = blockIdx.x;
+  EngineSlot &sl = slots[s];
+  if (sl.kind != kJobFire || sl.phase == 2 || sl.fire.converged) return;
+  const bool check_only = sl.phase == 0;
+  __shared__ double red[4][256];
+  __shared__ int decision;
+  const int b0 = offsets[s], b1 = offsets[s + 1];
+  double p = 0.0, ff = 0.0, vv = 0.0, fm = 0.0;
+  for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+    const double *F = a.F + 3 * (size_t)i, *v = a.v + 3 * (size_t)i;
+    const double f2 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
+    p += F[0] * v[0] + F[1] * v[1] + F[2] * v[2];
+    ff += f2;
+    vv += v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    fm = fmax(fm, f2);
+  }
+  red[0][threadIdx.x] = p;
+  red[1][threadIdx.x] = ff;
+  red[2][threadIdx.x] = vv;
+  red[3][threadIdx.x] = fm;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + o];
+      red[1][threadIdx.x] += red[1][threadIdx.x + o];
+      red[2][threadIdx.x] += red[2][threadIdx.x + o];
+      red[3][threadIdx.x] = fmax(red[3][threadIdx.x], red[3][threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  const double P = red[0][0], FF = red[1][0], VV = red[2][0], FM = red[3][0];
+  if (threadIdx.x == 0) {
+    decision = 0;
+    if (FM < sl.fire.fmax2) sl.fire.converged = 1;
+    else if (!check_only) decision = P > 0.0 ? 1 : 2;
+  }
+  __syncthreads();
+  if (decision == 0) return;
+  const double alpha = sl.fire.alpha;
+  const double c1 = decision == 1 ? 1.0 - alpha : 0.0;
+  const double c2 = (decision == 1 && FF > 0.0) ? alpha * sqrt(VV / FF) : 0.0;
+  for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+    double *v = a.v + 3 * (size_t)i;
+    const double *F = a.F + 3 * (size_t)i;
+    for (int b = 0; b < 3; ++b) v[b] = c1 * v[b] + c2 * F[b];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (decision == 1) {
+      if (sl.fire.n_pos > kFireNmin) {
+        sl.fire.dt = fmin(sl.fire.dt * kFireFinc, sl.fire.dt_max);
+        sl.fire.alpha = alpha * kFireFalpha;
+      }
+      sl.fire.n_pos += 1;
+    } else {
+      sl.fire.dt *= kFireFdec;
+      sl.fire.alpha = kFireAlphaStart;
+      sl.fire.n_pos = 0;
+    }
+  }
+}
+
+// Phase and step bookkeeping of every job after an iteration.
+__global__ void engine_advance_kernel(int n_struct, EngineSlot *slots) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_struct) return;
+  EngineSlot &sl = slots[s];
+  const bool converged = sl.kind == kJobFire && sl.fire.converged;
+  if (sl.phase == 0) {
+    sl.phase = (sl.kind == kJobSingle || sl.n_steps <= 0 || converged) ? 2 : 1;
+  } else if (sl.phase == 1) {
+    sl.steps_done += 1;
+    if (sl.steps_done >= sl.n_steps || converged) sl.phase = 2;
+  }
+}
+
+// Move the atoms of the kept jobs to their new ranges: table[k] = (from, to, count, index
+// shift of perm); one block per job.
+__global__ void engine_relayout_kernel(const int4 *table, AtomState src, AtomState dst) {
+  const int4 t = table[blockIdx.x];
+  for (int k = threadIdx.x; k < t.z; k += blockDim.x) {
+    const size_t i = (size_t)t.x + k, o = (size_t)t.y + k;
+    for (int b = 0; b < 3; ++b) {
+      dst.x[3 * o + b] = src.x[3 * i + b];
+      dst.v[3 * o + b] = src.v[3 * i + b];
+      dst.F[3 * o + b] = src.F[3 * i + b];
+    }
+    dst.types[o] = src.types[i];
+    dst.perm[o] = src.perm[i] + t.w;
+  }
+}
+
+void launch_engine_drift(int N, const AtomState &a, const int *sid, const EngineSlot *slots,
+                         const double *inv_mass_kappa, double half_skin2, BuildStatus *st, cudaStream_t s) {
+  if (N > 0) engine_drift_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, a, sid, slots, inv_mass_kappa, half_skin2, st);
+}
+
+void launch_engine_fire(int n_struct, const int *offsets, const AtomState &a, EngineSlot *slots, cudaStream_t s) {
+  if (n_struct > 0) engine_fire_kernel<<<n_struct, 256, 0, s>>>(offsets, a, slots);
+}
+
+void launch_engine_advance(int n_struct, EngineSlot *slots, cudaStream_t s) {
+  if (n_struct > 0) engine_advance_kernel<<<(n_struct + 127) / 128, 128, 0, s>>>(n_struct, slots);
+}
+
+void launch_engine_relayout(int n_keep, const int4 *table, const AtomState &src, AtomState dst, cudaStream_t s) {
+  if (n_keep > 0) engine_relayout_kernel<<<n_keep, 256, 0, s>>>(table, src, dst);
 }
 
 void launch_export(int N, const AtomState &a, const Grid &g, const Batch &B, double *pos, double *vel, double *force,

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace nep {
 
 constexpr int kMaxTypes = 8;
@@ -89,6 +91,26 @@ struct FireState {
   int pad;
 };
 
+// One job of the batched serving engine (a structure of the batch), device resident.
+enum { kJobSingle = 0, kJobFire = 1, kJobNve = 2 };
+struct EngineSlot {
+  int kind;          // kJob*
+  int phase;         // 0: initial evaluation this iteration, 1: stepping, 2: finished (frozen)
+  int steps_done;    // velocity-Verlet steps taken
+  int n_steps;       // NVE: steps to take; FIRE: most steps
+  double dt;         // NVE time step (fs)
+  FireState fire;    // FIRE state (kind == kJobFire)
+};
+
+// A job entering the batched serving engine (host arrays stay valid during engine_relayout).
+struct EngineJob {
+  int kind, n, n_steps;
+  double box[9];
+  double dt, fmax;
+  const double *pos, *vel;
+  const int *types;
+};
+
 // Bussi-Donadio-Parrinello velocity rescaling (J. Chem. Phys. 126, 014101 (2007)), device
 // resident: the caller's random numbers for every step (R1 ~ N(0,1), S ~ chi^2 with N_f - 1
 // degrees of freedom) and the factor of the current step.
@@ -168,6 +190,8 @@ struct AtomArgs {
   // caller-order velocities; per-atom values in caller order, or null
   const double *vel_in;    // [N][3] caller order, or null
   double *heat;            // [N][3] caller order, or null
+  // batched serving engine: per-structure kick (phase, time step, FIRE state), or null
+  const EngineSlot *slots;
 };
 
 // Model constants of one handle, FP32.
@@ -216,6 +240,13 @@ void launch_struct_sums(int n_struct, int members, const int *offsets, int N, co
                         const double *w_atom, double *e_struct, double *w_struct, cudaStream_t s);
 void launch_arm_rebuild(BuildStatus *st, cudaStream_t s);
 void launch_fire_mix(int N, const AtomState &a, FireState *fire, int check_only, cudaStream_t s);
+// batched serving engine
+void launch_engine_drift(int N, const AtomState &a, const int *sid, const EngineSlot *slots,
+                         const double *inv_mass_kappa, double half_skin2, BuildStatus *st, cudaStream_t s);
+void launch_clear_flags(BuildStatus *st, cudaStream_t s);
+void launch_engine_fire(int n_struct, const int *offsets, const AtomState &a, EngineSlot *slots, cudaStream_t s);
+void launch_engine_advance(int n_struct, EngineSlot *slots, cudaStream_t s);
+void launch_engine_relayout(int n_keep, const int4 *table, const AtomState &src, AtomState dst, cudaStream_t s);
 void launch_thermostat(int N, const AtomState &a, int nb_gather, const double *partial_gather, ThermoState *ts,
                        cudaStream_t s);
 // population evaluation: parameter vectors into kernel arrays, BF16 tiles, Eq. loss
@@ -228,4 +259,22 @@ void launch_population_loss(int members, int n_struct, const int *offsets, const
                             const double *partial_gather, int nb_gather, int N, const double *reg, int n_par,
                             const double *lambda, double *loss, cudaStream_t s);
 
+}  // namespace nep
+
+// Batched serving engine on a library handle (implemented with the C ABI, used by the server).
+struct nep_handle;
+namespace nep {
+int engine_relayout(nep_handle *h, const std::vector<int> &keep, const std::vector<EngineJob> &add, cudaStream_t s,
+                    size_t target_bytes = 0);
+int engine_step(nep_handle *h, cudaStream_t s, int n_iter, bool force_rebuild);
+int engine_fetch(nep_handle *h, int k, double *pos, double *force, double *vel, cudaStream_t s);
+int engine_jobs(const nep_handle *h);
+int engine_atoms(const nep_handle *h);
+const EngineSlot &engine_slot(const nep_handle *h, int k);
+double engine_energy(const nep_handle *h, int k);
+const double *engine_virial(const nep_handle *h, int k);
+void set_thread_alloc_stream(cudaStream_t s);
+void release_workspace(nep_handle *h);
+size_t workspace_bytes(nep_handle *h);
+cudaError_t stream_sync(cudaStream_t s);
 }  // namespace nep

@@ -950,14 +950,21 @@ __global__ void __launch_bounds__(GB)
       const double ex = Fx - ft[0], ey = Fy - ft[1], ez = Fz - ft[2];
       part[11] = ex * ex + ey * ey + ez * ez;
     }
-    if (a.md_kick && !(a.fire && a.fire->converged)) {  // second half-kick of velocity Verlet, kinetic energy
+    bool kick = a.md_kick && !(a.fire && a.fire->converged);
+    double hdt = a.fire ? 0.5 * a.fire->dt : a.half_dt;
+    if (a.slots) {  // batched engine: the structure's own phase and time step
+      const EngineSlot &sl = a.slots[struct_of(pi)];
+      kick = sl.phase == 1 && !(sl.kind == kJobFire && sl.fire.converged);
+      hdt = 0.5 * (sl.kind == kJobFire ? sl.fire.dt : sl.dt);
+    }
+    if (kick) {  // second half-kick of velocity Verlet, kinetic energy
       double *v = a.vel + 3 * (size_t)i;
-      const double s = (a.fire ? 0.5 * a.fire->dt : a.half_dt) * a.inv_mass_kappa[ti];
+      const double s = hdt * a.inv_mass_kappa[ti];
       const double vx = v[0] + s * Fx, vy = v[1] + s * Fy, vz = v[2] + s * Fz;
       v[0] = vx; v[1] = vy; v[2] = vz;
       part[1] = a.mass_kappa_half[ti] * (vx * vx + vy * vy + vz * vz);
       vh[0] = vx; vh[1] = vy; vh[2] = vz;
-    } else if (a.md_kick) {  // converged FIRE: velocities unchanged
+    } else if (a.md_kick || a.slots) {  // converged FIRE or no step: velocities unchanged
       const double *v = a.vel + 3 * (size_t)i;
       part[1] = a.mass_kappa_half[ti] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
       vh[0] = v[0]; vh[1] = v[1]; vh[2] = v[2];

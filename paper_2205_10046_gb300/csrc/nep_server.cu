@@ -1,13 +1,14 @@
-// Serving: a persistent request loop with continuous batching (include/nep.h, nep_server_*).
+// Serving: a persistent request loop with iteration-level (continuous) batching
+// (include/nep.h, nep_server_*).
 //
-// Jobs enter a FIFO queue. A pool of workers (one host thread, one non-blocking CUDA stream
-// and one library handle each) takes the head job as soon as a worker is free and the job's
-// estimated device workspace fits into what the running jobs leave of the memory budget.
-// A worker runs its job to completion with the ordinary entry points (nep_compute, md_init
-// + md_run, md_init + fire_run), so a job computes exactly what it computes alone; the
-// overlap of jobs on the device comes from the workers' streams. Every device buffer of a
-// worker is a stream-ordered allocation on its stream and is released when the job ends,
-// so neither growing nor freeing a workspace synchronises the device.
+// Jobs enter a FIFO queue. One scheduler thread owns a library handle and a CUDA stream and
+// runs the batched engine: every running job is one structure of a batch, and one iteration
+// advances all of them together — one velocity-Verlet (NVE) or FIRE step each, or, in a job's
+// first iteration, its initial evaluation (which is all a single-point job needs). Between
+// iterations finished jobs leave (their arrays are copied out) and queued jobs join, first
+// in first out, while the batch has a free job slot and the admitted jobs' workspace
+// estimates fit the memory budget. A job's arithmetic uses only its own structure (own cell
+// grid, lists, sums in a fixed order), so its results do not depend on the other jobs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,13 +24,10 @@
 #include <vector>
 
 #include "../../include/nep.h"
+#include "nep_internal.cuh"
 
 namespace nep {
-void set_thread_alloc_stream(cudaStream_t s);
-void release_workspace(nep_handle *h);
-size_t workspace_bytes(nep_handle *h);
 void set_create_error(const char *msg);
-cudaError_t stream_sync(cudaStream_t s);
 }  // namespace nep
 
 namespace {
@@ -39,31 +37,12 @@ struct Job {
   nep_job spec{};
   std::vector<double> pos, vel;
   std::vector<int> types;
-  double t_submit = 0;
+  double t_submit = 0, t_start = 0;
   size_t est = 0;
 };
 
 struct Arrays {
   std::vector<double> pos, force, vel;
-};
-
-// Stream-ordered device buffer of a worker.
-struct WBuf {
-  void *p = nullptr;
-  size_t n = 0;
-  cudaError_t ensure(size_t bytes, cudaStream_t s) {
-    if (bytes <= n && p) return cudaSuccess;
-    release(s);
-    cudaError_t e = cudaMallocAsync(&p, std::max<size_t>(bytes, 16), s);
-    if (e == cudaSuccess) n = bytes;
-    else p = nullptr;
-    return e;
-  }
-  void release(cudaStream_t s) {
-    if (p) cudaFreeAsync(p, s);
-    p = nullptr;
-    n = 0;
-  }
 };
 
 double now_since(const std::chrono::steady_clock::time_point &t0) {
@@ -81,7 +60,6 @@ struct __attribute__((visibility("hidden"))) nep_server {
   nep_params p{};
   std::vector<double> cR, cA, w0, b0, w1, mass;
   nep_server_config cfg{};
-  int n_des = 0;
   std::chrono::steady_clock::time_point t0;
   // queue and results
   std::mutex mu;
@@ -92,16 +70,14 @@ struct __attribute__((visibility("hidden"))) nep_server {
   long long next_id = 1;
   bool stopping = false;
   int running = 0;
-  size_t reserved = 0, peak_reserved = 0;
+  size_t reserved = 0, peak_reserved = 0, peak_workspace = 0;
   long long completed = 0, failed = 0;
   double atom_evals = 0;
-  std::vector<std::thread> workers;
-  int worker_error = 0;
-  std::string worker_message;
+  std::thread scheduler;
 
-  // Device workspace estimate of one job (bytes): per-atom arrays of the handle and the
-  // worker, neighbour lists sized for twice the expected neighbour count (the handle grows
-  // lists to 2 m + 16 for a largest count m) and the cell grid, plus a fixed part.
+  // Device workspace estimate of one job (bytes): its per-atom arrays in the batch,
+  // neighbour lists sized for twice the expected neighbour count (the handle grows lists to
+  // 2 m + 16 for a largest count m), staging and cell arrays, plus a fixed part.
   size_t estimate(int N, const double *box) const {
     const double det = std::fabs(box[0] * (box[4] * box[8] - box[5] * box[7]) -
                                  box[1] * (box[3] * box[8] - box[5] * box[6]) +
@@ -115,184 +91,199 @@ struct __attribute__((visibility("hidden"))) nep_server {
     const double cap_a = std::min(512.0, 2.0 * std::ceil(1.3 * na) + 20);
     const int T = p.n_types;
     const double est = ((p.basis_radial + 2) + 3) / 4 * 4;
-    const double per_atom = 11 * 24.0 + 5 * 24.0 + 12 * 4.0 + 4.0 * T + 16 + 4.0 * T * est + 4 * cap_r +
-                            cap_a * (4 + 4 + 16) + 3 * 4 * 4.0 + 16 + 72;
-    return (size_t)(1.25 * per_atom * N) + ((size_t)8 << 20);
+    const double per_atom = 16 * 24.0 + 16 * 4.0 + 4.0 * T + 48 + 4.0 * T * est + 9 * cap_r +
+                            cap_a * (4 + 4 + 16) + 3 * 4 * 4.0 + 8 + 72;
+    return (size_t)(1.25 * per_atom * N) + ((size_t)1 << 20);
   }
 
-  void worker_main(int w);
-  void run_job(nep_handle *h, cudaStream_t s, Job &job, nep_result &r, Arrays &out, WBuf *buf, double &evals_out);
+  void scheduler_main();
 };
 
-#define SCK(call)                                                                                  \
-  do {                                                                                             \
-    cudaError_t e_ = (call);                                                                       \
-    if (e_ != cudaSuccess) {                                                                       \
-      r.status = e_ == cudaErrorMemoryAllocation ? NEP_ERR_OOM : NEP_ERR_CUDA;                     \
-      std::snprintf(r.message, sizeof(r.message), "%s", cudaGetErrorString(e_));                   \
-      return;                                                                                      \
-    }                                                                                              \
-  } while (0)
-
-#define SNEP(call)                                                                                 \
-  do {                                                                                             \
-    const int rc_ = (call);                                                                        \
-    if (rc_ != NEP_OK) {                                                                           \
-      r.status = rc_;                                                                              \
-      std::snprintf(r.message, sizeof(r.message), "%s", nep_last_error(h));                        \
-      return;                                                                                      \
-    }                                                                                              \
-  } while (0)
-
-void nep_server::run_job(nep_handle *h, cudaStream_t s, Job &job, nep_result &r, Arrays &out, WBuf *buf,
-                         double &evals_out) {
-  const nep_job &J = job.spec;
-  const int N = J.n_atoms;
-  const size_t b3 = sizeof(double) * 3 * (size_t)N;
-  enum { POS, TYPES, VEL, F, E, W, NBUF };
-  SCK(buf[POS].ensure(b3, s));
-  SCK(buf[TYPES].ensure(sizeof(int) * (size_t)N, s));
-  SCK(buf[VEL].ensure(b3, s));
-  SCK(buf[F].ensure(b3, s));
-  SCK(buf[E].ensure(sizeof(double), s));
-  SCK(buf[W].ensure(9 * sizeof(double), s));
-  double *d_pos = static_cast<double *>(buf[POS].p), *d_vel = static_cast<double *>(buf[VEL].p);
-  double *d_F = static_cast<double *>(buf[F].p), *d_E = static_cast<double *>(buf[E].p);
-  double *d_W = static_cast<double *>(buf[W].p);
-  int *d_types = static_cast<int *>(buf[TYPES].p);
-  SCK(cudaMemcpyAsync(d_pos, job.pos.data(), b3, cudaMemcpyHostToDevice, s));
-  SCK(cudaMemcpyAsync(d_types, job.types.data(), sizeof(int) * (size_t)N, cudaMemcpyHostToDevice, s));
-  r.steps = 0;
-  double evals = 1;
-  out.vel.clear();
-  if (J.kind == NEP_JOB_FIRE) {
-    SNEP(md_init(h, N, d_pos, d_types, J.box, nullptr, s));
-    int steps = 0;
-    SNEP(fire_run(h, J.n_steps, J.dt_fs, J.fmax, nullptr, &steps, s));
-    SNEP(md_get_state(h, d_pos, nullptr, nullptr, s));
-    r.steps = steps;
-    evals += 1 + steps;
-  } else if (J.kind == NEP_JOB_NVE) {
-    if (!job.vel.empty()) SCK(cudaMemcpyAsync(d_vel, job.vel.data(), b3, cudaMemcpyHostToDevice, s));
-    SNEP(md_init(h, N, d_pos, d_types, J.box, job.vel.empty() ? nullptr : d_vel, s));
-    SNEP(md_run(h, J.n_steps, J.dt_fs, std::max(1, J.n_steps), nullptr, s));
-    SNEP(md_get_state(h, d_pos, d_vel, nullptr, s));
-    r.steps = J.n_steps;
-    evals += 1 + J.n_steps;
-    out.vel.resize(3 * (size_t)N);
-  }
-  // the final state: energy, forces and virial at the final positions
-  SNEP(nep_compute(h, N, d_pos, d_types, J.box, nullptr, d_E, d_F, nullptr, d_W, s));
-  out.pos.resize(3 * (size_t)N);
-  out.force.resize(3 * (size_t)N);
-  SCK(cudaMemcpyAsync(out.pos.data(), d_pos, b3, cudaMemcpyDeviceToHost, s));
-  SCK(cudaMemcpyAsync(out.force.data(), d_F, b3, cudaMemcpyDeviceToHost, s));
-  if (!out.vel.empty()) SCK(cudaMemcpyAsync(out.vel.data(), d_vel, b3, cudaMemcpyDeviceToHost, s));
-  SCK(cudaMemcpyAsync(&r.energy, d_E, sizeof(double), cudaMemcpyDeviceToHost, s));
-  SCK(cudaMemcpyAsync(r.virial, d_W, 9 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  SCK(nep::stream_sync(s));
-  r.workspace_used = nep::workspace_bytes(h);
-  for (int k = 0; k < NBUF; ++k) r.workspace_used += buf[k].n;
-  // the positions are reported wrapped into the cell, like md_get_state
-  if (J.kind == NEP_JOB_SINGLE) {
-    const double *H = J.box;
-    double inv[9];
-    const double det = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
-                       H[2] * (H[3] * H[7] - H[4] * H[6]);
-    inv[0] = (H[4] * H[8] - H[5] * H[7]) / det;
-    inv[1] = (H[2] * H[7] - H[1] * H[8]) / det;
-    inv[2] = (H[1] * H[5] - H[2] * H[4]) / det;
-    inv[3] = (H[5] * H[6] - H[3] * H[8]) / det;
-    inv[4] = (H[0] * H[8] - H[2] * H[6]) / det;
-    inv[5] = (H[2] * H[3] - H[0] * H[5]) / det;
-    inv[6] = (H[3] * H[7] - H[4] * H[6]) / det;
-    inv[7] = (H[1] * H[6] - H[0] * H[7]) / det;
-    inv[8] = (H[0] * H[4] - H[1] * H[3]) / det;
-    for (int i = 0; i < N; ++i) {
-      double *x = out.pos.data() + 3 * (size_t)i, sf[3];
-      for (int b = 0; b < 3; ++b) {
-        sf[b] = x[0] * inv[b] + x[1] * inv[3 + b] + x[2] * inv[6 + b];
-        sf[b] -= std::floor(sf[b]);
-      }
-      for (int b = 0; b < 3; ++b) x[b] = sf[0] * H[b] + sf[1] * H[3 + b] + sf[2] * H[6 + b];
-    }
-  }
-  r.status = NEP_OK;
-  evals_out = evals * N;
-}
-
-void nep_server::worker_main(int w) {
+// Scheduler: between iterations, finished jobs leave and queued jobs join the batch.
+void nep_server::scheduler_main() {
   cudaStream_t s = nullptr;
   nep_handle *h = nullptr;
   int rc = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess ? NEP_OK : NEP_ERR_CUDA;
+  std::string setup_error = rc ? "stream creation failed" : "";
   if (rc == NEP_OK) {
     nep::set_thread_alloc_stream(s);
     rc = nep_create(&p, &h);
     if (rc == NEP_OK && cfg.precision) rc = nep_set_precision(h, cfg.precision);
+    if (rc != NEP_OK) setup_error = nep_last_error(h);
   }
-  if (rc != NEP_OK) {
-    std::lock_guard<std::mutex> lk(mu);
-    worker_error = rc;
-    worker_message = "worker " + std::to_string(w) + ": " + nep_last_error(h);
-  }
-  WBuf buf[6];
+  std::vector<Job> active;  // in batch order
+  bool relaid = false;      // the layout changed since the last iteration (force a build)
   for (;;) {
-    Job job;
+    // 1. admit queued jobs (first in first out) while a job slot and the budget allow
+    std::vector<Job> add;
     {
       std::unique_lock<std::mutex> lk(mu);
-      // FIFO admission: the head job starts when a worker is free (this one) and its workspace
-      // fits next to the running jobs' (a job always starts when nothing else runs)
-      cv_work.wait(lk, [&] {
-        return stopping || (!queue.empty() && (running == 0 || reserved + queue.front().est <= cfg.memory_budget));
-      });
+      if (active.empty()) cv_work.wait(lk, [&] { return stopping || !queue.empty(); });
       if (stopping) break;
-      job = std::move(queue.front());
-      queue.pop_front();
-      ++running;
-      reserved += job.est;
-      peak_reserved = std::max(peak_reserved, reserved);
+      while (!queue.empty() && (int)(active.size() + add.size()) < cfg.workers &&
+             (active.empty() && add.empty() ? true : reserved + queue.front().est <= cfg.memory_budget)) {
+        Job j = std::move(queue.front());
+        queue.pop_front();
+        reserved += j.est;
+        peak_reserved = std::max(peak_reserved, reserved);
+        ++running;
+        add.push_back(std::move(j));
+      }
     }
-    cv_work.notify_all();  // the next head may fit as well
-    nep_result r{};
-    r.id = job.id;
-    r.kind = job.spec.kind;
-    r.n_atoms = job.spec.n_atoms;
-    r.t_submit = job.t_submit;
-    r.t_start = now_since(t0);
-    r.workspace_est = job.est;
-    Arrays out;
-    double evals = 0;
+    const double t_admit = now_since(t0);
+    for (Job &j : add) j.t_start = t_admit;
+    auto fail_jobs = [&](std::vector<Job> &jobs, int code, const std::string &msg) {
+      std::lock_guard<std::mutex> lk(mu);
+      for (Job &j : jobs) {
+        nep_result r{};
+        r.id = j.id;
+        r.kind = j.spec.kind;
+        r.n_atoms = j.spec.n_atoms;
+        r.status = code;
+        r.t_submit = j.t_submit;
+        r.t_start = j.t_start;
+        r.t_done = now_since(t0);
+        r.workspace_est = j.est;
+        std::snprintf(r.message, sizeof(r.message), "%s", msg.c_str());
+        --running;
+        reserved -= j.est;
+        ++failed;
+        done.push_back(r);
+      }
+      jobs.clear();
+      cv_done.notify_all();
+    };
     if (!h) {
-      r.status = worker_error ? worker_error : NEP_ERR_STATE;
-      std::snprintf(r.message, sizeof(r.message), "%s", "worker has no handle");
-    } else {
-      run_job(h, s, job, r, out, buf, evals);
-      nep::release_workspace(h);
-      for (auto &b : buf) b.release(s);
-      nep::stream_sync(s);
+      fail_jobs(add, rc ? rc : NEP_ERR_STATE, "server has no handle: " + setup_error);
+      continue;
     }
-    r.t_done = now_since(t0);
+    // 2. new layout: the running jobs, then the admitted ones
+    if (!add.empty()) {
+      std::vector<int> keep(active.size());
+      for (size_t k = 0; k < active.size(); ++k) keep[k] = (int)k;
+      std::vector<nep::EngineJob> in;
+      for (Job &j : add) {
+        nep::EngineJob e{};
+        e.kind = j.spec.kind;
+        e.n = j.spec.n_atoms;
+        e.n_steps = j.spec.n_steps;
+        std::memcpy(e.box, j.spec.box, sizeof(e.box));
+        e.dt = j.spec.dt_fs;
+        e.fmax = j.spec.fmax;
+        e.pos = j.pos.data();
+        e.vel = (j.spec.kind == NEP_JOB_NVE && !j.vel.empty()) ? j.vel.data() : nullptr;
+        e.types = j.types.data();
+        in.push_back(e);
+      }
+      size_t target = 0;
+      for (const Job &j : active) target += j.est;
+      for (const Job &j : add) target += j.est;
+      const int r = nep::engine_relayout(h, keep, in, s, target);
+      if (r != NEP_OK) {
+        // the admitted jobs cannot be laid out: report them and restore the running batch
+        const std::string msg = nep_last_error(h);
+        fail_jobs(add, r, msg);
+        if (nep::engine_relayout(h, keep, {}, s) != NEP_OK) fail_jobs(active, r, msg);
+        continue;
+      }
+      for (Job &j : add) active.push_back(std::move(j));
+      add.clear();
+      relaid = true;
+    }
+    if (active.empty()) continue;
+    // 3. a chunk of iterations of every job: one while jobs wait or start (to admit and finish
+    // them promptly), else up to the first job's completion (at most 32)
+    int n_iter = 32;
     {
       std::lock_guard<std::mutex> lk(mu);
-      --running;
-      reserved -= job.est;
-      if (r.status == NEP_OK) {
-        ++completed;
-        atom_evals += evals;
-        arrays.emplace(r.id, std::move(out));
-      } else {
-        ++failed;
-      }
-      done.push_back(r);
+      if (!queue.empty()) n_iter = 1;
     }
-    cv_done.notify_all();
-    cv_work.notify_all();
+    for (size_t k = 0; k < active.size() && n_iter > 1; ++k) {
+      const nep::EngineSlot &sl = nep::engine_slot(h, (int)k);
+      if (sl.phase != 1) n_iter = 1;
+      else n_iter = std::max(1, std::min(n_iter, sl.n_steps - sl.steps_done));
+    }
+    const int r = nep::engine_step(h, s, n_iter, relaid);
+    relaid = false;
+    {
+      const size_t ws = nep::workspace_bytes(h);
+      std::lock_guard<std::mutex> lk(mu);
+      peak_workspace = std::max(peak_workspace, ws);
+    }
+    if (r != NEP_OK) {
+      fail_jobs(active, r, nep_last_error(h));
+      nep::engine_relayout(h, {}, {}, s);
+      continue;
+    }
+    // 4. finished jobs leave with their results
+    std::vector<int> keep;
+    std::vector<nep_result> out;
+    std::vector<std::pair<long long, Arrays>> outa;
+    double evals = 0;
+    for (size_t k = 0; k < active.size(); ++k) {
+      const nep::EngineSlot &sl = nep::engine_slot(h, (int)k);
+      if (sl.phase != 2) {
+        keep.push_back((int)k);
+        continue;
+      }
+      Job &j = active[k];
+      nep_result res{};
+      res.id = j.id;
+      res.kind = j.spec.kind;
+      res.n_atoms = j.spec.n_atoms;
+      res.steps = sl.steps_done;
+      res.energy = nep::engine_energy(h, (int)k);
+      std::memcpy(res.virial, nep::engine_virial(h, (int)k), sizeof(res.virial));
+      res.t_submit = j.t_submit;
+      res.t_start = j.t_start;
+      res.workspace_est = j.est;
+      const size_t n3 = 3 * (size_t)j.spec.n_atoms;
+      Arrays a;
+      a.pos.resize(n3);
+      a.force.resize(n3);
+      if (j.spec.kind == NEP_JOB_NVE) a.vel.resize(n3);
+      res.status = nep::engine_fetch(h, (int)k, a.pos.data(), a.force.data(), a.vel.empty() ? nullptr : a.vel.data(), s);
+      if (res.status != NEP_OK) std::snprintf(res.message, sizeof(res.message), "%s", nep_last_error(h));
+      // the job's share of the batch workspace, by atoms
+      const int na = std::max(nep::engine_atoms(h), 1);
+      res.workspace_used = nep::workspace_bytes(h);
+      res.t_done = now_since(t0);
+      evals += (double)j.spec.n_atoms * (1 + sl.steps_done);
+      out.push_back(res);
+      outa.emplace_back(j.id, std::move(a));
+    }
+    if (!out.empty()) {
+      std::vector<Job> still;
+      for (int k : keep) still.push_back(std::move(active[k]));
+      std::vector<size_t> ests;
+      for (const nep_result &res : out) ests.push_back(res.workspace_est);
+      active = std::move(still);
+      size_t target = 0;
+      for (const Job &j : active) target += j.est;
+      if (nep::engine_relayout(h, keep, {}, s, target) != NEP_OK) fail_jobs(active, NEP_ERR_CUDA, nep_last_error(h));
+      relaid = true;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        for (size_t q = 0; q < out.size(); ++q) {
+          --running;
+          reserved -= ests[q];
+          if (out[q].status == NEP_OK) {
+            ++completed;
+            arrays.emplace(outa[q].first, std::move(outa[q].second));
+          } else {
+            ++failed;
+          }
+          done.push_back(out[q]);
+        }
+        atom_evals += evals;
+      }
+      cv_done.notify_all();
+    }
   }
   if (h) {
     nep::release_workspace(h);
     nep_destroy(h);
   }
-  for (auto &b : buf) b.release(s);
   if (s) {
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
@@ -307,8 +298,9 @@ NEP_SERVER_API int nep_server_create(const nep_params *params, const nep_server_
     return NEP_ERR_ARG;
   }
   *out = nullptr;
-  if (cfg->workers < 1 || cfg->workers > 256 || cfg->memory_budget == 0 || (cfg->precision != 0 && cfg->precision != 1)) {
-    nep::set_create_error("need 1 <= workers <= 256, memory_budget > 0, precision 0 or 1");
+  if (cfg->workers < 1 || cfg->workers > 65536 || cfg->memory_budget == 0 ||
+      (cfg->precision != 0 && cfg->precision != 1)) {
+    nep::set_create_error("need 1 <= workers <= 65536, memory_budget > 0, precision 0 or 1");
     return NEP_ERR_ARG;
   }
   if (!params->mass) {
@@ -319,9 +311,9 @@ NEP_SERVER_API int nep_server_create(const nep_params *params, const nep_server_
   nep_handle *probe = nullptr;
   int rc = nep_create(params, &probe);
   if (rc) return rc;
-  nep_server *s = new nep_server();
-  s->n_des = nep_n_des(probe);
+  const int n_des = nep_n_des(probe);
   nep_destroy(probe);
+  nep_server *s = new nep_server();
   s->cfg = *cfg;
   s->p = *params;
   const int T = params->n_types;
@@ -329,7 +321,7 @@ NEP_SERVER_API int nep_server_create(const nep_params *params, const nep_server_
   const size_t nca = (size_t)T * T * (params->n_max_angular + 1) * (params->basis_angular + 1);
   s->cR.assign(params->c_radial, params->c_radial + ncr);
   s->cA.assign(params->c_angular, params->c_angular + nca);
-  s->w0.assign(params->w0, params->w0 + (size_t)params->n_neuron * s->n_des);
+  s->w0.assign(params->w0, params->w0 + (size_t)params->n_neuron * n_des);
   s->b0.assign(params->b0, params->b0 + params->n_neuron);
   s->w1.assign(params->w1, params->w1 + params->n_neuron);
   s->mass.assign(params->mass, params->mass + T);
@@ -339,7 +331,7 @@ NEP_SERVER_API int nep_server_create(const nep_params *params, const nep_server_
   s->p.b0 = s->b0.data();
   s->p.w1 = s->w1.data();
   s->p.mass = s->mass.data();
-  // keep freed stream-ordered memory in the pool (up to the budget) for the next jobs
+  // keep freed stream-ordered memory in the pool (up to the budget) for the next layouts
   int dev = 0;
   cudaGetDevice(&dev);
   cudaMemPool_t pool;
@@ -348,11 +340,10 @@ NEP_SERVER_API int nep_server_create(const nep_params *params, const nep_server_
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
   }
   s->t0 = std::chrono::steady_clock::now();
-  for (int w = 0; w < cfg->workers; ++w)
-    s->workers.emplace_back([s, w, dev] {
-      cudaSetDevice(dev);
-      s->worker_main(w);
-    });
+  s->scheduler = std::thread([s, dev] {
+    cudaSetDevice(dev);
+    s->scheduler_main();
+  });
   *out = s;
   return NEP_OK;
 }
@@ -365,6 +356,11 @@ NEP_SERVER_API int nep_server_submit(nep_server *s, const nep_job *job, long lon
   if (job->kind != NEP_JOB_SINGLE && (job->n_steps < 0 || !(job->dt_fs > 0) || !std::isfinite(job->dt_fs)))
     return NEP_ERR_ARG;
   if (job->kind == NEP_JOB_FIRE && !(job->fmax >= 0)) return NEP_ERR_ARG;
+  // checked here, so that a bad job cannot stop the batch it would join
+  for (int i = 0; i < N; ++i)
+    if (job->types[i] < 0 || job->types[i] >= s->p.n_types) return NEP_ERR_ARG;
+  for (size_t k = 0; k < 3 * (size_t)N; ++k)
+    if (!std::isfinite(job->pos[k])) return NEP_ERR_NONFINITE;
   Job j;
   j.spec = *job;
   j.pos.assign(job->pos, job->pos + 3 * (size_t)N);
@@ -426,6 +422,7 @@ NEP_SERVER_API int nep_server_stats_get(nep_server *s, nep_server_stats *out) {
   out->failed = s->failed;
   out->bytes_reserved = s->reserved;
   out->peak_bytes_reserved = s->peak_reserved;
+  out->peak_workspace_bytes = s->peak_workspace;
   out->atom_evaluations = s->atom_evals;
   return NEP_OK;
 }
@@ -438,7 +435,7 @@ NEP_SERVER_API int nep_server_destroy(nep_server *s) {
     s->queue.clear();
   }
   s->cv_work.notify_all();
-  for (auto &t : s->workers) t.join();
+  if (s->scheduler.joinable()) s->scheduler.join();
   delete s;
   return NEP_OK;
 }

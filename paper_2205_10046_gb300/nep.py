@@ -76,7 +76,7 @@ class nep_result(C.Structure):
 class nep_server_stats(C.Structure):
     _fields_ = [("queued", C.c_int), ("running", C.c_int), ("completed", C.c_longlong), ("failed", C.c_longlong),
                 ("bytes_reserved", C.c_size_t), ("peak_bytes_reserved", C.c_size_t),
-                ("atom_evaluations", C.c_double)]
+                ("peak_workspace_bytes", C.c_size_t), ("atom_evaluations", C.c_double)]
 
 
 JOB_SINGLE, JOB_FIRE, JOB_NVE = 0, 1, 2
