@@ -42,6 +42,18 @@ struct Shape {
   static constexpr int OFF4 = (NR + 1) + (NA + 1) * L3;
   static constexpr int OFF5 = OFF4 + (L4 >= 2 ? NA + 1 : 0);
   static constexpr int NDP = (NDES + 3) / 4 * 4;  // padded w0 row in shared memory
+  // Shared-memory rows padded to whole float4s: c^A rows over k (KAP) and S_nk rows over k
+  // (NKP). Each thread keeps its S_nk (then dU/dS_nk) block of SPT floats, n-major; SPT/4 is
+  // odd so the 16-byte loads of 8 consecutive threads fall on 8 distinct bank groups.
+  static constexpr int KAP = (KA + 1 + 3) / 4 * 4;
+  static constexpr int NKP = (NK + 3) / 4 * 4;
+  static constexpr int SPT = ((NA + 1) * NKP / 4) % 2 ? (NA + 1) * NKP : (NA + 1) * NKP + 4;
+  // float offsets of the shared regions after the shift table, each a whole number of float4s
+  static constexpr int r4(int x) { return (x + 3) / 4 * 4; }
+  static constexpr int off_b0(int prec) { return prec == 0 ? H * NDP : 0; }
+  static constexpr int off_cR(int prec) { return off_b0(prec) + r4(2 * H); }
+  static constexpr int off_cA(int prec, int T) { return off_cR(prec) + r4(T * T * (NR + 1) * (KR + 1)); }
+  static constexpr int off_S(int prec, int T) { return off_cA(prec, T) + T * T * (NA + 1) * KAP; }
   // S_nk is accumulated in NPASS passes over the angular neighbours, NCH values of n per
   // pass, so that at most ~4 x 24 accumulators are live at once
   static constexpr int NPASS = ((NA + 1) * NK > 144) ? ((NA + 1) + 3) / 4 : 1;
@@ -341,14 +353,16 @@ __global__ void __launch_bounds__(AB, 1)
   const int mem = BATCH ? (int)blockIdx.y : 0;
   const float *pw = (BATCH && a.pop_ann) ? a.pop_ann + mem * a.s_ann : nullptr;
   float4 *dtab_s = smem4;                                        // [ncode] (one structure)
+  constexpr int KAP = S::KAP, NKP = S::NKP, SPT = S::SPT;
   float *w0_s = reinterpret_cast<float *>(smem4 + (BATCH ? 0 : a.ncode));  // [H][NDP] (FP32 network)
-  float *b0_s = w0_s + (PREC == 0 ? S::H * NDP : 0);             // [H]
+  float *b0_s = w0_s + S::off_b0(PREC);                          // [H]
   float *w1_s = b0_s + S::H;                                     // [H]
-  float *cR_s = w1_s + S::H;                                     // [T][T][NR+1][KR+1]
-  float *cA_s = cR_s + T * T * (NR + 1) * (KR + 1);              // [T][T][NA+1][KA+1]
-  // [NA+1][NK][block]: S_nk while the FP32 network runs, then dU/dS_nk. For the tensor-core
-  // network S_nk waits in TMEM instead and this region first holds the BF16 operand tiles.
-  float *S_s = cA_s + T * T * (NA + 1) * (KA + 1);
+  float *cR_s = w0_s + S::off_cR(PREC);                          // [T][T][NR+1][KR+1]
+  float *cA_s = w0_s + S::off_cA(PREC, T);                       // [T][T][NA+1][KAP]
+  // [block][SPT]: each thread's S_nk ([n][NKP]) while the FP32 network runs, then dU/dS_nk.
+  // For the tensor-core network S_nk waits in TMEM instead and this region first holds the
+  // BF16 operand tiles.
+  float *S_s = w0_s + S::off_S(PREC, T);
   if constexpr (!BATCH)
     for (int v = threadIdx.x; v < a.ncode; v += blockDim.x) dtab_s[v] = a.dtab[v];
   if constexpr (PREC == 0) {
@@ -365,7 +379,10 @@ __global__ void __launch_bounds__(AB, 1)
   if (threadIdx.x == 0) b1_s = pw ? pw[S::H * NDES + 2 * S::H] : w.b1;
   const float *c_r = a.c_r + mem * a.s_cr, *c_a = a.c_a + mem * a.s_ca;
   for (int v = threadIdx.x; v < T * T * (NR + 1) * (KR + 1); v += blockDim.x) cR_s[v] = c_r[v];
-  for (int v = threadIdx.x; v < T * T * (NA + 1) * (KA + 1); v += blockDim.x) cA_s[v] = c_a[v];
+  for (int v = threadIdx.x; v < T * T * (NA + 1) * KAP; v += blockDim.x) {
+    const int row = v / KAP, k = v - row * KAP;
+    cA_s[v] = k <= KA ? c_a[row * (KA + 1) + k] : 0.f;
+  }
   // tensor-core network: operand tiles (128-byte aligned) and TMEM for S_nk and the results
   __shared__ __align__(8) uint64_t tc_mbar;
   __shared__ uint32_t tc_tmem;
@@ -473,13 +490,19 @@ __global__ void __launch_bounds__(AB, 1)
           const float rinv = rsqrtf(r2);
           float f[KA + 1];
           cheb_basis<KA>(r2 * rinv, inv_rcA, f);
-          const float *cc = cA_s + ((ti * T + tj) * (NA + 1) + n0) * (KA + 1);
+          const float4 *cc = reinterpret_cast<const float4 *>(cA_s + ((ti * T + tj) * (NA + 1) + n0) * KAP);
           float g[NC];
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
             float acc = 0.f;
 #pragma unroll
-            for (int k = 0; k <= KA; ++k) acc = __fmaf_rn(cc[c * (KA + 1) + k], f[k], acc);
+            for (int k4 = 0; k4 < KAP / 4; ++k4) {
+              const float4 cv = cc[c * (KAP / 4) + k4];
+              const float cw[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+              for (int j = 0; j < 4; ++j)
+                if (4 * k4 + j <= KA) acc = __fmaf_rn(cw[j], f[4 * k4 + j], acc);
+            }
             g[c] = acc;
           }
           const float rl[5] = {1.f, rinv, rinv * rinv, rinv * rinv * rinv, (rinv * rinv) * (rinv * rinv)};
@@ -514,9 +537,15 @@ __global__ void __launch_bounds__(AB, 1)
           q[S::OFF5 + n] = w.m.c5b[0] * s0 * s0 * s0 * s0 + w.m.c5b[1] * s0 * s0 * s12 + w.m.c5b[2] * s12 * s12;
         }
         if constexpr (!DESC_ONLY && PREC == 0) {
-          // park S_n in shared memory while the network runs ([n][k][thread]: conflict-free)
+          // park S_n in this thread's shared block while the network runs
+          float4 *dst = reinterpret_cast<float4 *>(S_s + threadIdx.x * SPT + n * NKP);
 #pragma unroll
-          for (int k = 0; k < NK; ++k) S_s[(n * NK + k) * AB + threadIdx.x] = Sv[c][k];
+          for (int k4 = 0; k4 < NKP / 4; ++k4) {
+            float v4[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v4[j] = 4 * k4 + j < NK ? Sv[c][4 * k4 + j] : 0.f;
+            dst[k4] = make_float4(v4[0], v4[1], v4[2], v4[3]);
+          }
         }
         if constexpr (PREC == 1) {
           // park S_n in this thread's TMEM lane, columns n NK .. n NK + NK - 1
@@ -534,7 +563,7 @@ __global__ void __launch_bounds__(AB, 1)
         for (int v = 0; v < NDES; ++v) a.q_out[io * NDES + v] = (double)q[v];
       }
     } else {
-      float *Sme = S_s + threadIdx.x;
+      float4 *Sme = reinterpret_cast<float4 *>(S_s + threadIdx.x * SPT);  // [n][NKP / 4]
 
       // ---- network, Eq. Ui, and dU/dq
       float U = 0.f;
@@ -677,17 +706,20 @@ __global__ void __launch_bounds__(AB, 1)
       // ---- dU/dS_nk from the explicit 3/4/5-body forms, written over S in shared memory
 #pragma unroll
       for (int n = 0; n <= NA; ++n) {
-        float s[NK], dS[NK];
+        float s[NKP], dS[NKP];
         if constexpr (PREC == 0) {
 #pragma unroll
-          for (int k = 0; k < NK; ++k) s[k] = Sme[(n * NK + k) * AB];
+          for (int k4 = 0; k4 < NKP / 4; ++k4) {
+            const float4 v = Sme[n * (NKP / 4) + k4];
+            s[4 * k4] = v.x, s[4 * k4 + 1] = v.y, s[4 * k4 + 2] = v.z, s[4 * k4 + 3] = v.w;
+          }
         } else {
           __syncwarp();
 #pragma unroll
           for (int k8 = 0; k8 < NK / 8; ++k8) tmem_ld8(tmem_row + n * NK + 8 * k8, &s[8 * k8]);
         }
 #pragma unroll
-        for (int k = 0; k < NK; ++k) {
+        for (int k = 0; k < NKP; ++k) {
           if (k < S::KEND3) {
             const float d3 = dq[(NR + 1) + (l_of_k(k) - 1) * (NA + 1) + n];
             dS[k] = 2.f * w.m.c3b[k] * s[k] * d3;
@@ -714,7 +746,8 @@ __global__ void __launch_bounds__(AB, 1)
           dS[2] += d5 * common * s[2];
         }
 #pragma unroll
-        for (int k = 0; k < NK; ++k) Sme[(n * NK + k) * AB] = dS[k];
+        for (int k4 = 0; k4 < NKP / 4; ++k4)
+          Sme[n * (NKP / 4) + k4] = make_float4(dS[4 * k4], dS[4 * k4 + 1], dS[4 * k4 + 2], dS[4 * k4 + 3]);
       }
 
       // ---- angular partial forces dU_i/dr_ij (angular terms of Eq. partial_force)
@@ -726,16 +759,21 @@ __global__ void __launch_bounds__(AB, 1)
           const float rinv = rsqrtf(r2);
           float f[KA + 1], fp[KA + 1];
           cheb_basis_d<KA>(r2 * rinv, inv_rcA, f, fp);
-          const float *c = cA_s + (ti * T + tj) * (NA + 1) * (KA + 1);
+          const float4 *c = reinterpret_cast<const float4 *>(cA_s + (ti * T + tj) * (NA + 1) * KAP);
           float g[NA + 1], gp[NA + 1];
 #pragma unroll
           for (int n = 0; n <= NA; ++n) {
             float acc = 0.f, accp = 0.f;
 #pragma unroll
-            for (int k = 0; k <= KA; ++k) {
-              const float cc = c[n * (KA + 1) + k];
-              acc = __fmaf_rn(cc, f[k], acc);
-              accp = __fmaf_rn(cc, fp[k], accp);
+            for (int k4 = 0; k4 < KAP / 4; ++k4) {
+              const float4 cv = c[n * (KAP / 4) + k4];
+              const float cw[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+              for (int j = 0; j < 4; ++j)
+                if (4 * k4 + j <= KA) {
+                  acc = __fmaf_rn(cw[j], f[4 * k4 + j], acc);
+                  accp = __fmaf_rn(cw[j], fp[4 * k4 + j], accp);
+                }
             }
             g[n] = acc;
             gp[n] = accp;
@@ -743,22 +781,30 @@ __global__ void __launch_bounds__(AB, 1)
           // G = sum_k a_k r^-l grad b_k (tangential part used), Y = sum_k c_k r^-l b_k
           const float rl[5] = {1.f, rinv, rinv * rinv, rinv * rinv * rinv, (rinv * rinv) * (rinv * rinv)};
           float gx = 0.f, gy = 0.f, gz = 0.f, yy = 0.f;
-          static_for<0, NK>([&](auto kc) {
-            constexpr int k = decltype(kc)::value;
-            float ak = 0.f, ck = 0.f;
+          static_for<0, NKP / 4>([&](auto kq) {
+            constexpr int k0 = 4 * decltype(kq)::value;
+            float ak[4] = {0.f, 0.f, 0.f, 0.f}, ck[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int n = 0; n <= NA; ++n) {
-              const float ds = Sme[(n * NK + k) * AB];
-              ak = __fmaf_rn(ds, g[n], ak);
-              ck = __fmaf_rn(ds, gp[n], ck);
+              const float4 v = Sme[n * (NKP / 4) + k0 / 4];
+              const float ds[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                ak[j] = __fmaf_rn(ds[j], g[n], ak[j]);
+                ck[j] = __fmaf_rn(ds[j], gp[n], ck[j]);
+              }
             }
-            ak *= rl[l_of_k(k)];
-            ck *= rl[l_of_k(k)];
-            const float3 gb = poly_grad<k>(d.x, d.y, d.z, r2);
-            gx = __fmaf_rn(ak, gb.x, gx);
-            gy = __fmaf_rn(ak, gb.y, gy);
-            gz = __fmaf_rn(ak, gb.z, gz);
-            yy = __fmaf_rn(ck, poly_b<k>(d.x, d.y, d.z, r2), yy);
+            static_for<0, 4>([&](auto jc) {
+              constexpr int j = decltype(jc)::value, k = k0 + j;
+              if constexpr (k < NK) {
+                const float akr = ak[j] * rl[l_of_k(k)], ckr = ck[j] * rl[l_of_k(k)];
+                const float3 gb = poly_grad<k>(d.x, d.y, d.z, r2);
+                gx = __fmaf_rn(akr, gb.x, gx);
+                gy = __fmaf_rn(akr, gb.y, gy);
+                gz = __fmaf_rn(akr, gb.z, gz);
+                yy = __fmaf_rn(ckr, poly_b<k>(d.x, d.y, d.z, r2), yy);
+              }
+            });
           });
           const float ux = d.x * rinv, uy = d.y * rinv, uz = d.z * rinv;
           const float gu = gx * ux + gy * uy + gz * uz;
@@ -1019,11 +1065,9 @@ cudaError_t smem_limit_once(K kern, size_t bound) {
 
 template <class S>
 size_t atom_smem_bytes(int T, int ncode, int prec, int ab = kAtomBlock) {
-  static_assert((size_t)(S::NA + 1) * S::NK * kAtomBlock * 4 >= (size_t)S::TILE_A + 2 * S::TILE_B + 128,
+  static_assert((size_t)S::SPT * kAtomBlock * 4 >= (size_t)S::TILE_A + 2 * S::TILE_B + 128,
                 "the S region must hold the tensor-core operand tiles");
-  size_t b = sizeof(float4) * ncode +
-             sizeof(float) * ((prec == 0 ? S::H * S::NDP : 0) + 2 * S::H + T * T * (S::NR + 1) * (S::KR + 1) +
-                              T * T * (S::NA + 1) * (S::KA + 1) + (size_t)(S::NA + 1) * S::NK * ab);
+  size_t b = sizeof(float4) * ncode + sizeof(float) * ((size_t)S::off_S(prec, T) + (size_t)S::SPT * ab);
   // the tensor-core kernel holds 256 of the SM's 512 TMEM columns: keep at most two blocks
   // per SM (a third would wait in tcgen05.alloc) by asking for more than a third of the
   // 228 KB of shared memory
