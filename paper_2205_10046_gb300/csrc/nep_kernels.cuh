@@ -703,10 +703,12 @@ __global__ void __launch_bounds__(AB, 1)
         }
       }
 
-      // ---- dU/dS_nk from the explicit 3/4/5-body forms, written over S in shared memory
+      // ---- dU/dS_nk from the explicit 3/4/5-body forms, kept in registers for the force loop
+      float dSr[NA + 1][NKP];
 #pragma unroll
       for (int n = 0; n <= NA; ++n) {
-        float s[NKP], dS[NKP];
+        float s[NKP];
+        float *dS = dSr[n];
         if constexpr (PREC == 0) {
 #pragma unroll
           for (int k4 = 0; k4 < NKP / 4; ++k4) {
@@ -745,9 +747,6 @@ __global__ void __launch_bounds__(AB, 1)
           dS[1] += d5 * common * s[1];
           dS[2] += d5 * common * s[2];
         }
-#pragma unroll
-        for (int k4 = 0; k4 < NKP / 4; ++k4)
-          Sme[n * (NKP / 4) + k4] = make_float4(dS[4 * k4], dS[4 * k4 + 1], dS[4 * k4 + 2], dS[4 * k4 + 3]);
       }
 
       // ---- angular partial forces dU_i/dr_ij (angular terms of Eq. partial_force)
@@ -786,13 +785,12 @@ __global__ void __launch_bounds__(AB, 1)
             float ak[4] = {0.f, 0.f, 0.f, 0.f}, ck[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int n = 0; n <= NA; ++n) {
-              const float4 v = Sme[n * (NKP / 4) + k0 / 4];
-              const float ds[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                ak[j] = __fmaf_rn(ds[j], g[n], ak[j]);
-                ck[j] = __fmaf_rn(ds[j], gp[n], ck[j]);
-              }
+              for (int j = 0; j < 4; ++j)
+                if (k0 + j < NK) {
+                  ak[j] = __fmaf_rn(dSr[n][k0 + j], g[n], ak[j]);
+                  ck[j] = __fmaf_rn(dSr[n][k0 + j], gp[n], ck[j]);
+                }
             }
             static_for<0, 4>([&](auto jc) {
               constexpr int j = decltype(jc)::value, k = k0 + j;
