@@ -343,6 +343,10 @@ __global__ void __launch_bounds__(AB, 1)
     atom_kernel(const AtomArgs a, const __grid_constant__ AnnConst<S> w) {
   static_assert(PREC == 0 || !DESC_ONLY, "the descriptor-only kernel has no network");
   static_assert(PREC == 0 || AB == 128, "the tensor-core network works on 128-atom tiles (UMMA M = 128)");
+  // S_nk waits for the network in this thread's TMEM lane (128-atom blocks, whole groups of 8
+  // columns), else in a per-thread block of shared memory
+  constexpr bool TM = !DESC_ONLY && AB == 128 && S::NK % 8 == 0;
+  static_assert(PREC == 0 || TM, "the tensor-core network keeps S_nk in TMEM");
   static_assert(AB % 32 == 0 && AB <= 256, "whole warps, at most 256 atoms per block");
   constexpr int NR = S::NR, KR = S::KR, NA = S::NA, KA = S::KA, NK = S::NK, NDES = S::NDES;
   extern __shared__ float4 smem4[];
@@ -359,9 +363,8 @@ __global__ void __launch_bounds__(AB, 1)
   float *w1_s = b0_s + S::H;                                     // [H]
   float *cR_s = w0_s + S::off_cR(PREC);                          // [T][T][NR+1][KR+1]
   float *cA_s = w0_s + S::off_cA(PREC, T);                       // [T][T][NA+1][KAP]
-  // [block][SPT]: each thread's S_nk ([n][NKP]) while the FP32 network runs, then dU/dS_nk.
-  // For the tensor-core network S_nk waits in TMEM instead and this region first holds the
-  // BF16 operand tiles.
+  // [block][SPT]: each thread's S_nk ([n][NKP]) while the network runs (without TMEM), or
+  // the BF16 operand tiles of the tensor-core network
   float *S_s = w0_s + S::off_S(PREC, T);
   if constexpr (!BATCH)
     for (int v = threadIdx.x; v < a.ncode; v += blockDim.x) dtab_s[v] = a.dtab[v];
@@ -406,6 +409,8 @@ __global__ void __launch_bounds__(AB, 1)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&tc_mbar)));
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+  }
+  if constexpr (TM) {
     if (threadIdx.x < 32) {
       asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tc_tmem)),
                    "r"(S::TMEM_COLS));
@@ -415,7 +420,7 @@ __global__ void __launch_bounds__(AB, 1)
   }
   __syncthreads();
   uint32_t tmem_row = 0;  // TMEM address of this warp's 32 lanes, column 0
-  if constexpr (PREC == 1) {
+  if constexpr (TM) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     tmem_row = tc_tmem + ((uint32_t)((threadIdx.x >> 5) * 32) << 16);
   }
@@ -536,7 +541,7 @@ __global__ void __launch_bounds__(AB, 1)
           const float s0 = Sv[c][0], s12 = Sv[c][1] * Sv[c][1] + Sv[c][2] * Sv[c][2];
           q[S::OFF5 + n] = w.m.c5b[0] * s0 * s0 * s0 * s0 + w.m.c5b[1] * s0 * s0 * s12 + w.m.c5b[2] * s12 * s12;
         }
-        if constexpr (!DESC_ONLY && PREC == 0) {
+        if constexpr (!DESC_ONLY && !TM) {
           // park S_n in this thread's shared block while the network runs
           float4 *dst = reinterpret_cast<float4 *>(S_s + threadIdx.x * SPT + n * NKP);
 #pragma unroll
@@ -547,7 +552,7 @@ __global__ void __launch_bounds__(AB, 1)
             dst[k4] = make_float4(v4[0], v4[1], v4[2], v4[3]);
           }
         }
-        if constexpr (PREC == 1) {
+        if constexpr (TM) {
           // park S_n in this thread's TMEM lane, columns n NK .. n NK + NK - 1
           __syncwarp();
 #pragma unroll
@@ -564,6 +569,7 @@ __global__ void __launch_bounds__(AB, 1)
       }
     } else {
       float4 *Sme = reinterpret_cast<float4 *>(S_s + threadIdx.x * SPT);  // [n][NKP / 4]
+      if constexpr (TM) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 
       // ---- network, Eq. Ui, and dU/dq
       float U = 0.f;
@@ -709,7 +715,7 @@ __global__ void __launch_bounds__(AB, 1)
       for (int n = 0; n <= NA; ++n) {
         float s[NKP];
         float *dS = dSr[n];
-        if constexpr (PREC == 0) {
+        if constexpr (!TM) {
 #pragma unroll
           for (int k4 = 0; k4 < NKP / 4; ++k4) {
             const float4 v = Sme[n * (NKP / 4) + k4];
@@ -828,7 +834,7 @@ __global__ void __launch_bounds__(AB, 1)
       a.partial_atom[(size_t)mem * gridDim.x + blockIdx.x] = s;
     }
   }
-  if constexpr (PREC == 1) {
+  if constexpr (TM) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -1063,14 +1069,37 @@ cudaError_t smem_limit_once(K kern, size_t bound) {
 
 template <class S>
 size_t atom_smem_bytes(int T, int ncode, int prec, int ab = kAtomBlock) {
-  static_assert((size_t)S::SPT * kAtomBlock * 4 >= (size_t)S::TILE_A + 2 * S::TILE_B + 128,
-                "the S region must hold the tensor-core operand tiles");
-  size_t b = sizeof(float4) * ncode + sizeof(float) * ((size_t)S::off_S(prec, T) + (size_t)S::SPT * ab);
-  // the tensor-core kernel holds 256 of the SM's 512 TMEM columns: keep at most two blocks
-  // per SM (a third would wait in tcgen05.alloc) by asking for more than a third of the
-  // 228 KB of shared memory
-  if (prec == 1 && b < 80 * 1024) b = 80 * 1024;
-  return b;
+  // the last region: BF16 operand tiles (tensor-core network), nothing (S_nk in TMEM) or the
+  // per-thread S_nk blocks
+  const bool tm = ab == 128 && S::NK % 8 == 0;
+  const size_t last = prec == 1 ? (size_t)S::TILE_A + 2 * S::TILE_B + 128 : tm ? 0 : sizeof(float) * S::SPT * ab;
+  return sizeof(float4) * ncode + sizeof(float) * (size_t)S::off_S(prec, T) + last;
+}
+
+// A block that holds TMEM takes 256 of the SM's 512 columns; a third such block on one SM
+// would wait in tcgen05.alloc until one of the others ends. When the registers alone would
+// admit three blocks, ask for more than a third of the SM's 228 KB of shared memory.
+constexpr size_t kTmemBlockSmem = 80 * 1024;
+template <class K>
+size_t tmem_block_smem(K kern, int block, size_t smem) {
+  static std::mutex mu;
+  static std::unordered_map<const void *, int> regs;  // registers per thread of each kernel
+  int nr = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    const void *key = reinterpret_cast<const void *>(kern);
+    auto it = regs.find(key);
+    if (it != regs.end()) {
+      nr = it->second;
+    } else {
+      cudaFuncAttributes fa;
+      if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return smem < kTmemBlockSmem ? kTmemBlockSmem : smem;
+      nr = regs[key] = fa.numRegs;
+    }
+  }
+  const int regs_warp = (nr * 32 + 255) / 256 * 256;
+  const int by_regs = 65536 / (regs_warp * ((block + 31) / 32));
+  return by_regs > 2 && smem < kTmemBlockSmem ? kTmemBlockSmem : smem;
 }
 
 template <class S>
@@ -1086,11 +1115,14 @@ cudaError_t launch_atom(const AtomArgs &a, const ModelF &mf, const float *w0, co
   w.b1 = b1;
   w.m = mf;
   const int blocks = (a.N + kAtomBlock - 1) / kAtomBlock;
-  const size_t smem = atom_smem_bytes<S>(a.T, a.ncode, descriptor_only ? 0 : a.precision);
-  const size_t bound = atom_smem_bytes<S>(kMaxTypes, 1 << 9, descriptor_only ? 0 : a.precision);
+  const bool tm = !descriptor_only && kAtomBlock == 128 && S::NK % 8 == 0;
+  size_t smem = atom_smem_bytes<S>(a.T, a.ncode, descriptor_only ? 0 : a.precision);
+  size_t bound = atom_smem_bytes<S>(kMaxTypes, 1 << 9, descriptor_only ? 0 : a.precision);
+  if (tm && bound < kTmemBlockSmem) bound = kTmemBlockSmem;
   auto go = [&](auto kern) -> cudaError_t {
     cudaError_t e = smem_limit_once(kern, bound);
     if (e != cudaSuccess) return e;
+    if (tm) smem = tmem_block_smem(kern, kAtomBlock, smem);
     kern<<<blocks, kAtomBlock, smem, st>>>(a, w);
     return cudaGetLastError();
   };
@@ -1130,11 +1162,14 @@ cudaError_t launch_atom_batch(const AtomArgs &a, const ModelF &mf, const float *
   w.b1 = b1;
   w.m = mf;
   const dim3 grid((a.N + block - 1) / block, members);
-  const size_t smem = atom_smem_bytes<S>(a.T, 0, a.precision, block);
-  const size_t bound = atom_smem_bytes<S>(kMaxTypes, 0, a.precision, block);
+  const bool tm = block == 128 && S::NK % 8 == 0;
+  size_t smem = atom_smem_bytes<S>(a.T, 0, a.precision, block);
+  size_t bound = atom_smem_bytes<S>(kMaxTypes, 0, a.precision, block);
+  if (tm && bound < kTmemBlockSmem) bound = kTmemBlockSmem;
   auto go = [&](auto kern) -> cudaError_t {
     cudaError_t e = smem_limit_once(kern, bound);
     if (e != cudaSuccess) return e;
+    if (tm) smem = tmem_block_smem(kern, block, smem);
     kern<<<grid, block, smem, st>>>(a, w);
     return cudaGetLastError();
   };
