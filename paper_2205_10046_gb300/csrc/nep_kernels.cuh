@@ -954,28 +954,49 @@ __global__ void __launch_bounds__(GB)
       base += cnt;
     }
     // ---- angular part (Algorithm 4): F_i += P_ij - P_ji, W_i += r_ij (x) P_ji
+    // Software-pipelined: list entry and reverse slot two entries ahead, the neighbour's
+    // position and both partial forces one entry ahead (every reverse slot is a valid slot,
+    // and a slot's partial force is used only when the pair is inside the cutoff, which is
+    // exactly when the per-atom kernel wrote it).
     const int na = a.nn_a[i];
-    for_pairs(a.nl_a, 0, na, N, i, a.pos4, a.jmask, [&](int m, unsigned e, const float4 &pj) {
-      const size_t slot = (size_t)m * N + i;
-      const float3 d = pair_vector(pi, pj, shift(e));
-      const float r2 = norm2(d);
-      if (r2 < rcA2) {
-        const float4 pij = p_ang[slot];
-        const float4 pji = p_ang[a.rev_a[slot]];
-        fx += pij.x - pji.x;
-        fy += pij.y - pji.y;
-        fz += pij.z - pji.z;
-        w[0] = __fmaf_rn(d.x, pji.x, w[0]);
-        w[1] = __fmaf_rn(d.y, pji.y, w[1]);
-        w[2] = __fmaf_rn(d.z, pji.z, w[2]);
-        w[3] = __fmaf_rn(d.x, pji.y, w[3]);
-        w[4] = __fmaf_rn(d.x, pji.z, w[4]);
-        w[5] = __fmaf_rn(d.y, pji.z, w[5]);
-        w[6] = __fmaf_rn(d.y, pji.x, w[6]);
-        w[7] = __fmaf_rn(d.z, pji.x, w[7]);
-        w[8] = __fmaf_rn(d.z, pji.y, w[8]);
+    if (na > 0) {
+      const unsigned *col = a.nl_a + i;
+      const int *rcol = a.rev_a + i;
+      unsigned e0 = __ldg(col), e1 = na > 1 ? __ldg(col + N) : 0u;
+      int r1 = na > 1 ? __ldg(rcol + N) : 0;
+      float4 p0 = __ldg(a.pos4 + (e0 & a.jmask));
+      float4 pij0 = __ldg(p_ang + i), pji0 = __ldg(p_ang + __ldg(rcol));
+      for (int m = 0; m < na; ++m) {
+        const unsigned e = e0;
+        const float4 pj = p0, pij = pij0, pji = pji0;
+        if (m + 1 < na) {
+          p0 = __ldg(a.pos4 + (e1 & a.jmask));
+          pij0 = __ldg(p_ang + (size_t)(m + 1) * N + i);
+          pji0 = __ldg(p_ang + r1);
+        }
+        e0 = e1;
+        if (m + 2 < na) {
+          e1 = __ldg(col + (size_t)(m + 2) * N);
+          r1 = __ldg(rcol + (size_t)(m + 2) * N);
+        }
+        const float3 d = pair_vector(pi, pj, shift(e));
+        const float r2 = norm2(d);
+        if (r2 < rcA2) {
+          fx += pij.x - pji.x;
+          fy += pij.y - pji.y;
+          fz += pij.z - pji.z;
+          w[0] = __fmaf_rn(d.x, pji.x, w[0]);
+          w[1] = __fmaf_rn(d.y, pji.y, w[1]);
+          w[2] = __fmaf_rn(d.z, pji.z, w[2]);
+          w[3] = __fmaf_rn(d.x, pji.y, w[3]);
+          w[4] = __fmaf_rn(d.x, pji.z, w[4]);
+          w[5] = __fmaf_rn(d.y, pji.z, w[5]);
+          w[6] = __fmaf_rn(d.y, pji.x, w[6]);
+          w[7] = __fmaf_rn(d.z, pji.x, w[7]);
+          w[8] = __fmaf_rn(d.z, pji.y, w[8]);
+        }
       }
-    });
+    }
     const double Fx = fx, Fy = fy, Fz = fz;
     const size_t io = mem * a.s_out + (a.perm ? (size_t)a.perm[i] : (size_t)i);
     if (a.force) {
