@@ -302,23 +302,31 @@ __device__ __forceinline__ void for_pairs(const unsigned *__restrict__ nl, int s
   }
 }
 
+// Load of a list entry: read-only cached, or streaming (evict-first) for a list that the
+// kernel reads only once, so that it does not push the neighbours' data out of L1.
+template <bool STREAM, class T>
+__device__ __forceinline__ T ld_list(const T *p) {
+  if constexpr (STREAM) return __ldcs(p);
+  else return __ldg(p);
+}
+
 // Batched variant for short pair bodies: the positions of D pairs are requested together and
 // the list entries of the next D pairs one batch ahead.
-template <int D, class Body>
+template <int D, bool STREAM = false, class Body>
 __device__ __forceinline__ void for_pairs_batch(const unsigned *__restrict__ nl, int slot0, int cnt, int N, int i,
                                                 const float4 *__restrict__ pos4, unsigned jmask, Body &&body) {
   if (cnt <= 0) return;
   const unsigned *col = nl + (size_t)slot0 * N + i;
   unsigned e[D];
 #pragma unroll
-  for (int d = 0; d < D; ++d) e[d] = d < cnt ? __ldg(col + (size_t)d * N) : 0u;
+  for (int d = 0; d < D; ++d) e[d] = d < cnt ? ld_list<STREAM>(col + (size_t)d * N) : 0u;
   for (int m0 = 0; m0 < cnt; m0 += D) {
     float4 p[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) p[d] = __ldg(pos4 + (e[d] & jmask));
     unsigned en[D];
 #pragma unroll
-    for (int d = 0; d < D; ++d) en[d] = (m0 + D + d < cnt) ? __ldg(col + (size_t)(m0 + D + d) * N) : 0u;
+    for (int d = 0; d < D; ++d) en[d] = (m0 + D + d < cnt) ? ld_list<STREAM>(col + (size_t)(m0 + D + d) * N) : 0u;
 #pragma unroll
     for (int d = 0; d < D; ++d)
       if (m0 + d < cnt) body(m0 + d, e[d], p[d]);
@@ -454,7 +462,7 @@ __global__ void __launch_bounds__(AB, 1)
       float Fk[KR + 1];
 #pragma unroll
       for (int k = 0; k <= KR; ++k) Fk[k] = 0.f;
-      for_pairs_batch<4>(a.nl_r, base, cnt, N, i, a.pos4, a.jmask, [&](int, unsigned e, const float4 &pj) {
+      for_pairs_batch<4, true>(a.nl_r, base, cnt, N, i, a.pos4, a.jmask, [&](int, unsigned e, const float4 &pj) {
         const float3 d = pair_vector(pi, pj, shift(e));
         const float r2 = norm2(d);
         if (r2 < rcR2) {
@@ -888,7 +896,7 @@ __global__ void __launch_bounds__(GB)
         const float4 v = src[k4];
         eo[4 * k4] = v.x; eo[4 * k4 + 1] = v.y; eo[4 * k4 + 2] = v.z; eo[4 * k4 + 3] = v.w;
       }
-      for_pairs_batch<4>(a.nl_r, base, cnt, N, i, a.pos4, a.jmask, [&](int, unsigned e, const float4 &pj) {
+      for_pairs_batch<4, true>(a.nl_r, base, cnt, N, i, a.pos4, a.jmask, [&](int, unsigned e, const float4 &pj) {
         const int j = e & a.jmask;
         const float3 d = pair_vector(pi, pj, shift(e));
         const float r2 = norm2(d);
@@ -962,22 +970,22 @@ __global__ void __launch_bounds__(GB)
     if (na > 0) {
       const unsigned *col = a.nl_a + i;
       const int *rcol = a.rev_a + i;
-      unsigned e0 = __ldg(col), e1 = na > 1 ? __ldg(col + N) : 0u;
-      int r1 = na > 1 ? __ldg(rcol + N) : 0;
+      unsigned e0 = __ldcs(col), e1 = na > 1 ? __ldcs(col + N) : 0u;
+      int r1 = na > 1 ? __ldcs(rcol + N) : 0;
       float4 p0 = __ldg(a.pos4 + (e0 & a.jmask));
-      float4 pij0 = __ldg(p_ang + i), pji0 = __ldg(p_ang + __ldg(rcol));
+      float4 pij0 = __ldcs(p_ang + i), pji0 = __ldg(p_ang + __ldcs(rcol));
       for (int m = 0; m < na; ++m) {
         const unsigned e = e0;
         const float4 pj = p0, pij = pij0, pji = pji0;
         if (m + 1 < na) {
           p0 = __ldg(a.pos4 + (e1 & a.jmask));
-          pij0 = __ldg(p_ang + (size_t)(m + 1) * N + i);
+          pij0 = __ldcs(p_ang + (size_t)(m + 1) * N + i);
           pji0 = __ldg(p_ang + r1);
         }
         e0 = e1;
         if (m + 2 < na) {
-          e1 = __ldg(col + (size_t)(m + 2) * N);
-          r1 = __ldg(rcol + (size_t)(m + 2) * N);
+          e1 = __ldcs(col + (size_t)(m + 2) * N);
+          r1 = __ldcs(rcol + (size_t)(m + 2) * N);
         }
         const float3 d = pair_vector(pi, pj, shift(e));
         const float r2 = norm2(d);
