@@ -355,6 +355,10 @@ __global__ void __launch_bounds__(AB, 1)
   // columns), else in a per-thread block of shared memory
   constexpr bool TM = !DESC_ONLY && AB == 128 && S::NK % 8 == 0;
   static_assert(PREC == 0 || TM, "the tensor-core network keeps S_nk in TMEM");
+  // With S_nk parked in TMEM the registers hold all (n_max^A + 1) x 24 sums at once: one pass
+  // over the angular neighbours (PbTe: 168 sums); otherwise NPASS passes of NCH values of n.
+  constexpr int NPASS = TM && (S::NA + 1) * S::NK <= 192 ? 1 : S::NPASS;
+  constexpr int NCH = (S::NA + 1 + NPASS - 1) / NPASS;
   static_assert(AB % 32 == 0 && AB <= 256, "whole warps, at most 256 atoms per block");
   constexpr int NR = S::NR, KR = S::KR, NA = S::NA, KA = S::KA, NK = S::NK, NDES = S::NDES;
   extern __shared__ float4 smem4[];
@@ -486,9 +490,9 @@ __global__ void __launch_bounds__(AB, 1)
     // ---- angular sums S_nk (Eq. S_nk, b_k(d) r^-l) and the angular descriptor components
     // (Sec. II D), one chunk of n per pass over the angular neighbours
     const int na = active ? a.nn_a[i] : 0;
-    static_for<0, S::NPASS>([&](auto pc) {
-      constexpr int n0 = decltype(pc)::value * S::NCH;
-      constexpr int n1 = (n0 + S::NCH < NA + 1) ? n0 + S::NCH : NA + 1;
+    static_for<0, NPASS>([&](auto pc) {
+      constexpr int n0 = decltype(pc)::value * NCH;
+      constexpr int n1 = (n0 + NCH < NA + 1) ? n0 + NCH : NA + 1;
       constexpr int NC = n1 - n0;
       float Sv[NC][NK];
 #pragma unroll
@@ -589,10 +593,11 @@ __global__ void __launch_bounds__(AB, 1)
   #pragma unroll 1
         for (int mu = 0; mu < S::H; ++mu) {
           const float4 *row = reinterpret_cast<const float4 *>(w0_s + mu * NDP);
+          float4 wrow[NDP / 4];  // the row serves both the forward and the backward sum
           float zp[4] = {-b0_s[mu], 0.f, 0.f, 0.f};
   #pragma unroll
           for (int v4 = 0; v4 < NDP / 4; ++v4) {
-            const float4 wv = row[v4];
+            const float4 wv = wrow[v4] = row[v4];
             const float wc[4] = {wv.x, wv.y, wv.z, wv.w};
   #pragma unroll
             for (int c = 0; c < 4; ++c)
@@ -604,7 +609,7 @@ __global__ void __launch_bounds__(AB, 1)
           const float beta = w1m * (1.f - h * h);
   #pragma unroll
           for (int v4 = 0; v4 < NDP / 4; ++v4) {
-            const float4 wv = row[v4];
+            const float4 wv = wrow[v4];
             const float wc[4] = {wv.x, wv.y, wv.z, wv.w};
   #pragma unroll
             for (int c = 0; c < 4; ++c)
