@@ -459,7 +459,9 @@ __global__ void __launch_bounds__(AB, 1)
 #pragma unroll
     for (int v = 0; v < NDES; ++v) q[v] = 0.f;
 
-    // ---- radial descriptor, Eq. qin: per neighbour type, F^t_k = sum_j f_k(r_ij)
+    // ---- radial descriptor, Eq. qin: per neighbour type, F^t_k = sum_j f_k(r_ij). With
+    // f_k = (T_k(x) + 1) fc/2 the sums are kept as sum_j T_k(x_j) fc_j/2 (k >= 1) and
+    // H = sum_j fc_j/2, added once at the end: F_0 = 2H, F_k = sum_j T_k fc_j/2 + H.
     int base = 0;
     for (int t = 0; t < T; ++t) {
       const int cnt = active ? a.nn_r[t * N + i] : 0;
@@ -470,12 +472,26 @@ __global__ void __launch_bounds__(AB, 1)
         const float3 d = pair_vector(pi, pj, shift(e));
         const float r2 = norm2(d);
         if (r2 < rcR2) {
-          float f[KR + 1];
-          cheb_basis<KR>(r2 * rsqrtf(r2), inv_rcR, f);
+          const float u = r2 * rsqrtf(r2) * inv_rcR;
+          const float hfc = 0.25f * (1.f + __cosf(3.14159265358979f * u));
+          const float t1 = u - 1.f;
+          const float x = 2.f * t1 * t1 - 1.f;
+          const float x2 = 2.f * x;
+          Fk[0] += hfc;
+          if constexpr (KR >= 1) Fk[1] = __fmaf_rn(x, hfc, Fk[1]);
+          float tkm1 = 1.f, tk = x;
 #pragma unroll
-          for (int k = 0; k <= KR; ++k) Fk[k] += f[k];
+          for (int k = 2; k <= KR; ++k) {
+            const float tn = __fmaf_rn(x2, tk, -tkm1);
+            tkm1 = tk;
+            tk = tn;
+            Fk[k] = __fmaf_rn(tn, hfc, Fk[k]);
+          }
         }
       });
+#pragma unroll
+      for (int k = 1; k <= KR; ++k) Fk[k] += Fk[0];
+      Fk[0] *= 2.f;
       const float *c = cR_s + (ti * T + t) * (NR + 1) * (KR + 1);
 #pragma unroll
       for (int n = 0; n <= NR; ++n) {
