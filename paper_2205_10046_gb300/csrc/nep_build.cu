@@ -83,28 +83,53 @@ __global__ void bin_atoms_kernel(int N, int T, AtomState a, int *count, const Gr
 }
 
 // Exclusive scan of count[0..ncell) into start[0..ncell]; one block of 1024 threads.
+// Exclusive prefix sum of the cell counts by one block of 1024 threads, in tiles of 4096
+// cells: every thread takes 4 consecutive counts (one 16-byte load), the block scans the
+// thread totals (warp shuffles, then the warp totals) and carries the tile total on.
 __global__ void scan_cells_kernel(int ncell, const int *count, int *start, const BuildStatus *st) {
   if (!rebuild_pending(st)) return;
-  __shared__ int part[1024];
-  const int per = (ncell + blockDim.x - 1) / blockDim.x;
-  const int b0 = threadIdx.x * per;
-  const int b1 = min(ncell, b0 + per);
-  int s = 0;
-  for (int c = b0; c < b1; ++c) s += count[c];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int off = 1; off < blockDim.x; off <<= 1) {
-    const int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+  __shared__ int wsum[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int carry = 0;
+  for (int base = 0; base < ncell; base += 4 * 1024) {
+    const int c0 = base + 4 * threadIdx.x;
+    int v[4];
+    if (c0 + 3 < ncell) {
+      const int4 q = *reinterpret_cast<const int4 *>(count + c0);
+      v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = c0 + k < ncell ? count[c0 + k] : 0;
+    }
+    const int tot = (v[0] + v[1]) + (v[2] + v[3]);
+    int x = tot;  // inclusive scan over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
     __syncthreads();
-    part[threadIdx.x] += v;
+    if (wid == 0) {
+      int w = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      wsum[lane] = w;
+    }
     __syncthreads();
+    int run = carry + (wid > 0 ? wsum[wid - 1] : 0) + (x - tot);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (c0 + k < ncell) start[c0 + k] = run;
+      run += v[k];
+    }
+    carry += wsum[31];
+    __syncthreads();  // wsum is rewritten by the next tile
   }
-  int run = part[threadIdx.x] - s;
-  for (int c = b0; c < b1; ++c) {
-    start[c] = run;
-    run += count[c];
-  }
-  if (threadIdx.x == blockDim.x - 1) start[ncell] = part[threadIdx.x];
+  if (threadIdx.x == 0) start[ncell] = carry;
 }
 
 __global__ void scatter_atoms_kernel(int N, const int *cell_of, const int *start, int *cursor, int *cell_atoms,

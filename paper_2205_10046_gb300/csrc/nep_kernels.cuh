@@ -311,27 +311,41 @@ __device__ __forceinline__ T ld_list(const T *p) {
 }
 
 // Batched variant for short pair bodies: the positions of D pairs are requested together and
-// the list entries of the next D pairs one batch ahead.
-template <int D, bool STREAM = false, class Body>
+// the list entries AHEAD (1 or 2) batches ahead (the lists stream from DRAM).
+template <int D, bool STREAM = false, int AHEAD = 2, class Body>
 __device__ __forceinline__ void for_pairs_batch(const unsigned *__restrict__ nl, int slot0, int cnt, int N, int i,
                                                 const float4 *__restrict__ pos4, unsigned jmask, Body &&body) {
   if (cnt <= 0) return;
   const unsigned *col = nl + (size_t)slot0 * N + i;
-  unsigned e[D];
+  unsigned e[D], en[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) e[d] = d < cnt ? ld_list<STREAM>(col + (size_t)d * N) : 0u;
+  if constexpr (AHEAD == 2) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) en[d] = D + d < cnt ? ld_list<STREAM>(col + (size_t)(D + d) * N) : 0u;
+  }
   for (int m0 = 0; m0 < cnt; m0 += D) {
     float4 p[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) p[d] = __ldg(pos4 + (e[d] & jmask));
-    unsigned en[D];
+    unsigned enn[D];
 #pragma unroll
-    for (int d = 0; d < D; ++d) en[d] = (m0 + D + d < cnt) ? ld_list<STREAM>(col + (size_t)(m0 + D + d) * N) : 0u;
+    for (int d = 0; d < D; ++d) {
+      const int m = m0 + AHEAD * D + d;
+      enn[d] = m < cnt ? ld_list<STREAM>(col + (size_t)m * N) : 0u;
+    }
 #pragma unroll
     for (int d = 0; d < D; ++d)
       if (m0 + d < cnt) body(m0 + d, e[d], p[d]);
 #pragma unroll
-    for (int d = 0; d < D; ++d) e[d] = en[d];
+    for (int d = 0; d < D; ++d) {
+      if constexpr (AHEAD == 2) {
+        e[d] = en[d];
+        en[d] = enn[d];
+      } else {
+        e[d] = enn[d];
+      }
+    }
   }
 }
 
@@ -917,7 +931,7 @@ __global__ void __launch_bounds__(GB)
         const float4 v = src[k4];
         eo[4 * k4] = v.x; eo[4 * k4 + 1] = v.y; eo[4 * k4 + 2] = v.z; eo[4 * k4 + 3] = v.w;
       }
-      for_pairs_batch<4, true>(a.nl_r, base, cnt, N, i, a.pos4, a.jmask, [&](int, unsigned e, const float4 &pj) {
+      for_pairs_batch<4, true, 1>(a.nl_r, base, cnt, N, i, a.pos4, a.jmask, [&](int, unsigned e, const float4 &pj) {
         const int j = e & a.jmask;
         const float3 d = pair_vector(pi, pj, shift(e));
         const float r2 = norm2(d);
