@@ -82,7 +82,6 @@ __global__ void bin_atoms_kernel(int N, int T, AtomState a, int *count, const Gr
   atomicAdd(count + id, 1);
 }
 
-// Exclusive scan of count[0..ncell) into start[0..ncell]; one block of 1024 threads.
 // Exclusive prefix sum of the cell counts by one block of 1024 threads, in tiles of 4096
 // cells: every thread takes 4 consecutive counts (one 16-byte load), the block scans the
 // thread totals (warp shuffles, then the warp totals) and carries the tile total on.
@@ -288,7 +287,43 @@ __global__ void build_lists_kernel(int N, const float4 *posA, const int *cell_of
   // them instead of a second candidate scan
   const bool staged = !count_only && L.stage_e;
   int n_seen = 0;
-  if (active) {
+  if (active && staged) {
+    // the scan only stages the accepted candidates (angular pairs are a subset of the radial
+    // ones, r_c^A <= r_c^R); their groups are counted afterwards from the staged bytes
+    unsigned *se = L.stage_e + i;
+    unsigned char *sg = L.stage_g + i;
+    for_candidates(i, pi, id, g, start, posA, [&](int, unsigned ent, float r2, int tj) {
+      if (r2 < rlR2) {
+        if (n_seen < L.cap_r) {
+          const int ang = r2 < rlA2 ? (r2 < rcA2 ? 1 : 2) : 0;
+          *se = ent;
+          *sg = (unsigned char)(tj | (r2 < rcR2 ? 0 : 8) | (ang << 4));
+          se += N;
+          sg += N;
+        }
+        ++n_seen;
+      }
+    });
+    const int ns = n_seen < L.cap_r ? n_seen : L.cap_r;
+    for (int m = 0; m < ns; ++m) {
+      const unsigned gb = L.stage_g[(size_t)m * N + i];
+      const int tj = (int)(gb & 7u);
+      const bool core = (gb & 8u) == 0;
+#pragma unroll
+      for (int t = 0; t < TT; ++t) {
+        cr0[t] += (tj == t && core) ? 1 : 0;
+        cr1[t] += (tj == t && !core) ? 1 : 0;
+      }
+      const unsigned ang = gb >> 4;
+      ca0 += ang == 1u ? 1 : 0;
+      ca1 += ang == 2u ? 1 : 0;
+    }
+    // past the staging capacity the groups are unknown: the build overflows and is redone
+    // with lists sized from these counts (the unstaged pairs counted as skin pairs of type 0,
+    // and as angular ones, an upper bound)
+    cr1[0] += n_seen - ns;
+    ca1 += n_seen - ns;
+  } else if (active) {
     for_candidates(i, pi, id, g, start, posA, [&](int, unsigned ent, float r2, int tj) {
       if (r2 < rlR2) {
         const bool core = r2 < rcR2;
@@ -296,11 +331,6 @@ __global__ void build_lists_kernel(int N, const float4 *posA, const int *cell_of
         for (int t = 0; t < TT; ++t) {
           cr0[t] += (tj == t && core) ? 1 : 0;
           cr1[t] += (tj == t && !core) ? 1 : 0;
-        }
-        const int ang = r2 < rlA2 ? (r2 < rcA2 ? 1 : 2) : 0;
-        if (staged && n_seen < L.cap_r) {
-          L.stage_e[(size_t)n_seen * N + i] = ent;
-          L.stage_g[(size_t)n_seen * N + i] = (unsigned char)(tj | (core ? 0 : 8) | (ang << 4));
         }
         ++n_seen;
       }
