@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(AB, 1)
       float Fk[KR + 1];
 #pragma unroll
       for (int k = 0; k <= KR; ++k) Fk[k] = 0.f;
-      for_pairs_batch<4, true>(a.nl_r, base, cnt, N, i, a.pos4, a.jmask, [&](int, unsigned e, const float4 &pj) {
+      for_pairs_batch<8, true>(a.nl_r, base, cnt, N, i, a.pos4, a.jmask, [&](int, unsigned e, const float4 &pj) {
         const float3 d = pair_vector(pi, pj, shift(e));
         const float r2 = norm2(d);
         if (r2 < rcR2) {
@@ -931,7 +931,7 @@ __global__ void __launch_bounds__(GB)
         const float4 v = src[k4];
         eo[4 * k4] = v.x; eo[4 * k4 + 1] = v.y; eo[4 * k4 + 2] = v.z; eo[4 * k4 + 3] = v.w;
       }
-      for_pairs_batch<4, true, 1>(a.nl_r, base, cnt, N, i, a.pos4, a.jmask, [&](int, unsigned e, const float4 &pj) {
+      for_pairs_batch<2, true, 1>(a.nl_r, base, cnt, N, i, a.pos4, a.jmask, [&](int, unsigned e, const float4 &pj) {
         const int j = e & a.jmask;
         const float3 d = pair_vector(pi, pj, shift(e));
         const float r2 = norm2(d);
