@@ -550,6 +550,8 @@ AtomArgs make_args(nep_handle *h, int N) {
   a.nl_a = h->nl_a.p;
   a.nn_a = h->nn_a.p;
   a.rev_a = h->rev_a.p;
+  a.cap_r = h->cap_r;
+  a.cap_a = h->cap_a;
   a.c_r = h->d_cR.p;
   a.c_a = h->d_cA.p;
   a.e_rad = h->e_rad.p;

@@ -151,6 +151,7 @@ struct AtomArgs {
   const unsigned *nl_a;    // [cap_a][N]
   const int *nn_a;         // [N]
   const int *rev_a;        // [cap_a][N] flat index of the reverse angular pair
+  int cap_r, cap_a;        // list capacities (slots per atom), bounds of the list prefetches
   const float *c_r;        // [T][T][nR+1][KR+1] FP32 copy
   const float *c_a;        // [T][T][nA+1][KA+1]
   float *e_rad;            // [N][T][est] radial force coefficients

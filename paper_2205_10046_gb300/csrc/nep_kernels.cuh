@@ -42,17 +42,18 @@ struct Shape {
   static constexpr int OFF4 = (NR + 1) + (NA + 1) * L3;
   static constexpr int OFF5 = OFF4 + (L4 >= 2 ? NA + 1 : 0);
   static constexpr int NDP = (NDES + 3) / 4 * 4;  // padded w0 row in shared memory
-  // Shared-memory rows padded to whole float4s: c^A rows over k (KAP) and S_nk rows over k
-  // (NKP). Each thread keeps its S_nk (then dU/dS_nk) block of SPT floats, n-major; SPT/4 is
+  // Shared-memory rows padded to whole float4s: c^A and c^R rows over k (KAP, KRP) and S_nk
+  // rows over k (NKP). Each thread keeps its S_nk (then dU/dS_nk) block of SPT floats, n-major; SPT/4 is
   // odd so the 16-byte loads of 8 consecutive threads fall on 8 distinct bank groups.
   static constexpr int KAP = (KA + 1 + 3) / 4 * 4;
+  static constexpr int KRP = (KR + 1 + 3) / 4 * 4;  // c^R rows over k, padded likewise
   static constexpr int NKP = (NK + 3) / 4 * 4;
   static constexpr int SPT = ((NA + 1) * NKP / 4) % 2 ? (NA + 1) * NKP : (NA + 1) * NKP + 4;
   // float offsets of the shared regions after the shift table, each a whole number of float4s
   static constexpr int r4(int x) { return (x + 3) / 4 * 4; }
   static constexpr int off_b0(int prec) { return prec == 0 ? H * NDP : 0; }
   static constexpr int off_cR(int prec) { return off_b0(prec) + r4(2 * H); }
-  static constexpr int off_cA(int prec, int T) { return off_cR(prec) + r4(T * T * (NR + 1) * (KR + 1)); }
+  static constexpr int off_cA(int prec, int T) { return off_cR(prec) + T * T * (NR + 1) * KRP; }
   static constexpr int off_S(int prec, int T) { return off_cA(prec, T) + T * T * (NA + 1) * KAP; }
   // S_nk is accumulated in NPASS passes over the angular neighbours, NCH values of n per
   // pass, so that at most ~4 x 24 accumulators are live at once
@@ -302,6 +303,12 @@ __device__ __forceinline__ void for_pairs(const unsigned *__restrict__ nl, int s
   }
 }
 
+// Request the line holding *p into L2 (no register, no wait). The address is always inside
+// the list allocation (the slot rows exist up to the list capacity or are simply unused).
+__device__ __forceinline__ void l2_prefetch(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Load of a list entry: read-only cached, or streaming (evict-first) for a list that the
 // kernel reads only once, so that it does not push the neighbours' data out of L1.
 template <bool STREAM, class T>
@@ -377,6 +384,25 @@ __global__ void __launch_bounds__(AB, 1)
   constexpr int NR = S::NR, KR = S::KR, NA = S::NA, KA = S::KA, NK = S::NK, NDES = S::NDES;
   extern __shared__ float4 smem4[];
   const int T = a.T;
+  const int N = a.N;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // Threads past the last atom run the same code with no neighbours (the tensor-core steps
+  // are block- and warp-collective); they write nothing.
+  const bool active = i < N;
+  // This atom's position, list lengths and first list entries are requested before the
+  // block's setup (shared tables, TMEM), which hides their DRAM latency: the counts into
+  // registers, the first 16 radial and 2 angular slots into L2.
+  const float4 pi = active ? __ldg(a.pos4 + i) : make_float4(0.f, 0.f, 0.f, __int_as_float(0));
+  const int na = active ? __ldg(a.nn_a + i) : 0;
+  int cnt_r = active ? __ldg(a.nn_r + i) : 0;
+  if (active) {
+#pragma unroll
+    for (int m = 0; m < 16; ++m)
+      if (m < a.cap_r) l2_prefetch(a.nl_r + (size_t)m * N + i);
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+      if (m < a.cap_a) l2_prefetch(a.nl_a + (size_t)m * N + i);
+  }
   constexpr int NDP = S::NDP;
   // batches: the shift tables stay in global memory, one per structure, and blockIdx.y is
   // the population member whose coefficients and network this block evaluates
@@ -387,7 +413,7 @@ __global__ void __launch_bounds__(AB, 1)
   float *w0_s = reinterpret_cast<float *>(smem4 + (BATCH ? 0 : a.ncode));  // [H][NDP] (FP32 network)
   float *b0_s = w0_s + S::off_b0(PREC);                          // [H]
   float *w1_s = b0_s + S::H;                                     // [H]
-  float *cR_s = w0_s + S::off_cR(PREC);                          // [T][T][NR+1][KR+1]
+  float *cR_s = w0_s + S::off_cR(PREC);                          // [T][T][NR+1][KRP]
   float *cA_s = w0_s + S::off_cA(PREC, T);                       // [T][T][NA+1][KAP]
   // [block][SPT]: each thread's S_nk ([n][NKP]) while the network runs (without TMEM), or
   // the BF16 operand tiles of the tensor-core network
@@ -407,7 +433,11 @@ __global__ void __launch_bounds__(AB, 1)
   __shared__ float b1_s;
   if (threadIdx.x == 0) b1_s = pw ? pw[S::H * NDES + 2 * S::H] : w.b1;
   const float *c_r = a.c_r + mem * a.s_cr, *c_a = a.c_a + mem * a.s_ca;
-  for (int v = threadIdx.x; v < T * T * (NR + 1) * (KR + 1); v += blockDim.x) cR_s[v] = c_r[v];
+  constexpr int KRP = S::KRP;
+  for (int v = threadIdx.x; v < T * T * (NR + 1) * KRP; v += blockDim.x) {
+    const int row = v / KRP, k = v - row * KRP;
+    cR_s[v] = k <= KR ? c_r[row * (KR + 1) + k] : 0.f;
+  }
   for (int v = threadIdx.x; v < T * T * (NA + 1) * KAP; v += blockDim.x) {
     const int row = v / KAP, k = v - row * KAP;
     cA_s[v] = k <= KA ? c_a[row * (KA + 1) + k] : 0.f;
@@ -451,14 +481,8 @@ __global__ void __launch_bounds__(AB, 1)
     tmem_row = tc_tmem + ((uint32_t)((threadIdx.x >> 5) * 32) << 16);
   }
 
-  const int N = a.N;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  // Threads past the last atom run the same code with no neighbours (the tensor-core steps
-  // are block- and warp-collective); they write nothing.
-  const bool active = i < N;
   double Ublock = 0.0;
   {
-    const float4 pi = active ? a.pos4[i] : make_float4(0.f, 0.f, 0.f, __int_as_float(0));
     const int ti = type_of(pi);
     const float inv_rcR = 1.f / a.rcR, inv_rcA = 1.f / a.rcA;
     const float rcR2 = a.rcR * a.rcR, rcA2 = a.rcA * a.rcA;
@@ -478,7 +502,14 @@ __global__ void __launch_bounds__(AB, 1)
     // H = sum_j fc_j/2, added once at the end: F_0 = 2H, F_k = sum_j T_k fc_j/2 + H.
     int base = 0;
     for (int t = 0; t < T; ++t) {
-      const int cnt = active ? a.nn_r[t * N + i] : 0;
+      const int cnt = cnt_r;
+      if (t + 1 < T) {  // the next type's count, and its first 16 slots into L2
+        cnt_r = active ? __ldg(a.nn_r + (size_t)(t + 1) * N + i) : 0;
+        if (active)
+#pragma unroll
+          for (int m = 0; m < 16; ++m)
+            if (base + cnt + m < a.cap_r) l2_prefetch(a.nl_r + (size_t)(base + cnt + m) * N + i);
+      }
       float Fk[KR + 1];
 #pragma unroll
       for (int k = 0; k <= KR; ++k) Fk[k] = 0.f;
@@ -506,12 +537,18 @@ __global__ void __launch_bounds__(AB, 1)
 #pragma unroll
       for (int k = 1; k <= KR; ++k) Fk[k] += Fk[0];
       Fk[0] *= 2.f;
-      const float *c = cR_s + (ti * T + t) * (NR + 1) * (KR + 1);
+      const float4 *c = reinterpret_cast<const float4 *>(cR_s + (ti * T + t) * (NR + 1) * KRP);
 #pragma unroll
       for (int n = 0; n <= NR; ++n) {
         float acc = q[n];
 #pragma unroll
-        for (int k = 0; k <= KR; ++k) acc = __fmaf_rn(c[n * (KR + 1) + k], Fk[k], acc);
+        for (int k4 = 0; k4 < KRP / 4; ++k4) {
+          const float4 cv = c[n * (KRP / 4) + k4];
+          const float cw[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (4 * k4 + j <= KR) acc = __fmaf_rn(cw[j], Fk[4 * k4 + j], acc);
+        }
         q[n] = acc;
       }
       base += cnt;
@@ -519,7 +556,6 @@ __global__ void __launch_bounds__(AB, 1)
 
     // ---- angular sums S_nk (Eq. S_nk, b_k(d) r^-l) and the angular descriptor components
     // (Sec. II D), one chunk of n per pass over the angular neighbours
-    const int na = active ? a.nn_a[i] : 0;
     static_for<0, NPASS>([&](auto pc) {
       constexpr int n0 = decltype(pc)::value * NCH;
       constexpr int n1 = (n0 + NCH < NA + 1) ? n0 + NCH : NA + 1;
@@ -730,17 +766,25 @@ __global__ void __launch_bounds__(AB, 1)
 
       // ---- radial force coefficients e^t_k = sum_n dU/dq_n c^{t_i t}_{nk} and their sum
       for (int t = 0; t < T; ++t) {
-        const float *c = cR_s + (ti * T + t) * (NR + 1) * (KR + 1);
-        float ev[S::EST];
+        const float4 *c = reinterpret_cast<const float4 *>(cR_s + (ti * T + t) * (NR + 1) * KRP);
+        float ev[S::EST > KRP ? S::EST : KRP];
+#pragma unroll
+        for (int k4 = 0; k4 < KRP / 4; ++k4) {
+          float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int n = 0; n <= NR; ++n) {
+            const float4 cv = c[n * (KRP / 4) + k4];
+            acc[0] = __fmaf_rn(dq[n], cv.x, acc[0]);
+            acc[1] = __fmaf_rn(dq[n], cv.y, acc[1]);
+            acc[2] = __fmaf_rn(dq[n], cv.z, acc[2]);
+            acc[3] = __fmaf_rn(dq[n], cv.w, acc[3]);
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) ev[4 * k4 + j] = acc[j];
+        }
         float tot = 0.f;
 #pragma unroll
-        for (int k = 0; k <= KR; ++k) {
-          float acc = 0.f;
-#pragma unroll
-          for (int n = 0; n <= NR; ++n) acc = __fmaf_rn(dq[n], c[n * (KR + 1) + k], acc);
-          ev[k] = acc;
-          tot += acc;
-        }
+        for (int k = 0; k <= KR; ++k) tot += ev[k];
         ev[KR + 1] = tot;
 #pragma unroll
         for (int k = KR + 2; k < S::EST; ++k) ev[k] = 0.f;

@@ -226,6 +226,8 @@ int nep_descriptors_static(const nep_params *params, int n_atoms, const double *
   args.nl_a = L.nl_a;
   args.nn_a = L.nn_a;
   args.rev_a = L.rev_a;
+  args.cap_r = L.cap_r;
+  args.cap_a = L.cap_a;
   args.c_r = dcR;
   args.c_a = dcA;
   args.perm = a.perm;
