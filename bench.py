@@ -184,10 +184,15 @@ class ClockSampler:
 
 
 def kernel_source_hash() -> str:
+    """Hash of the kernel sources with comments and blank lines removed (a comment edit does
+    not change the kernels the ncu counters were taken on)."""
     h = hashlib.sha1()
     for f in ("nep_kernels.cuh", "nep_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2205_10046_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2205_10046_gb300", "csrc", f)) as fh:
+            for line in fh:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:12]
 
 

@@ -20,7 +20,9 @@
 //     angular gradient uses the tangential projection of grad b_k (no unit-vector round-off);
 //   * pair vectors come from cell-local FP32 coordinates plus an image shift table, so no
 //     FP64 arithmetic (slow on GB300) runs in the pair loops;
-//   * S_nk wait in shared memory while the network runs, to bound register pressure.
+//   * all S_nk of an atom are summed in one pass in registers and wait in the thread's TMEM
+//     lane while the network runs; dU/dS_nk stay in registers for the force loop (shapes
+//     that do not fit fall back to passes over chunks of n and a shared-memory block).
 #pragma once
 #include <cuda_bf16.h>
 
