@@ -45,8 +45,9 @@ struct Shape {
   static constexpr int OFF5 = OFF4 + (L4 >= 2 ? NA + 1 : 0);
   static constexpr int NDP = (NDES + 3) / 4 * 4;  // padded w0 row in shared memory
   // Shared-memory rows padded to whole float4s: c^A and c^R rows over k (KAP, KRP) and S_nk
-  // rows over k (NKP). Each thread keeps its S_nk (then dU/dS_nk) block of SPT floats, n-major; SPT/4 is
-  // odd so the 16-byte loads of 8 consecutive threads fall on 8 distinct bank groups.
+  // rows over k (NKP). Without TMEM each thread parks its S_nk in a block of SPT floats,
+  // n-major; SPT/4 is odd so the 16-byte accesses of 8 consecutive threads fall on 8 distinct
+  // bank groups.
   static constexpr int KAP = (KA + 1 + 3) / 4 * 4;
   static constexpr int KRP = (KR + 1 + 3) / 4 * 4;  // c^R rows over k, padded likewise
   static constexpr int NKP = (NK + 3) / 4 * 4;
@@ -305,8 +306,8 @@ __device__ __forceinline__ void for_pairs(const unsigned *__restrict__ nl, int s
   }
 }
 
-// Request the line holding *p into L2 (no register, no wait). The address is always inside
-// the list allocation (the slot rows exist up to the list capacity or are simply unused).
+// Request the line holding *p into L2 (no register, no wait). Callers keep p inside the
+// list allocation: slot rows below the list capacity.
 __device__ __forceinline__ void l2_prefetch(const void *p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
@@ -557,7 +558,8 @@ __global__ void __launch_bounds__(AB, 1)
     }
 
     // ---- angular sums S_nk (Eq. S_nk, b_k(d) r^-l) and the angular descriptor components
-    // (Sec. II D), one chunk of n per pass over the angular neighbours
+    // (Sec. II D): one pass over the angular neighbours, or one chunk of n per pass when the
+    // sums do not fit the registers (NPASS above)
     static_for<0, NPASS>([&](auto pc) {
       constexpr int n0 = decltype(pc)::value * NCH;
       constexpr int n1 = (n0 + NCH < NA + 1) ? n0 + NCH : NA + 1;
