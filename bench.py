@@ -117,7 +117,7 @@ def flop_model(m, T, nr_list, nr_valid, na_list, na_valid):
     return atom, gather
 
 
-def survey_flop_model(m, nr, na):
+def naive_flop_model(m, nr, na):
     """The naive per-pair estimate of the method (g_n evaluated per pair for every n):
     NN_R [6 (n_R+1)(K_R+1) + 40] + NN_A [6 (n_A+1)(K_A+1) + 240 (n_A+1) + 60] + 4 N_des H + 90 (n_A+1)."""
     nR, KR, nA, KA, H = m.n_max_radial, m.basis_radial, m.n_max_angular, m.basis_angular, m.n_neuron
@@ -710,7 +710,7 @@ def run_gb300(args):
                           "kernel_ms_per_step": {k: v / args.steps for k, v in bf_ktime.items()},
                           "network": "descriptor->hidden and hidden->dU/dq as BF16 tcgen05 GEMMs, FP32 accumulate",
                           "force_rmse_vs_fp64_oracle": "0.10-0.15 meV/A on the parity cases (tests/test_gpu_bf16.py)"},
-            "survey_flops_per_atom_step": survey_flop_model(w.model, stats["mean_radial_in_rc"],
+            "naive_flops_per_atom_step": naive_flop_model(w.model, stats["mean_radial_in_rc"],
                                                             stats["mean_angular_in_rc"]),
         }
         if batch_forms is not None:
