@@ -11,7 +11,7 @@ Conventions (all FP64 numpy arrays):
   * ``types`` [N] int32 in [0, n_types);
   * model weights follow the ordering of Sec. II of the paper: c_radial[t_i][t_j][n][k]
     (ordered type pair, Eq. g_n), c_angular likewise, w0[mu][nu] neuron-major (Eq. Ui,
-    the layout of the paper's appendix listing), b0[mu], w1[mu], scalar b1.
+    the neuron-major layout of Appendix B), b0[mu], w1[mu], scalar b1.
 
 Random draws: one numpy PCG64 stream per purpose. The model uses the workload seed;
 displacements use seed + 1000 and velocities seed + 2000. Weights are drawn in the order
