@@ -59,7 +59,7 @@ def parse_args():
     ap.add_argument("--serve-only", action="store_true", help="only the serving measurement")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window of each serving run")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (requests/s)")
-    ap.add_argument("--serve-workers", type=int, default=256, help="job slots of the serving batch")
+    ap.add_argument("--serve-workers", type=int, default=1024, help="job slots of the serving batch")
     ap.add_argument("--pop-calls", type=int, default=5)
     return ap.parse_args()
 

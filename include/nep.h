@@ -254,7 +254,8 @@ typedef struct {
  * configuration, as nep_create for bad parameters. */
 int nep_server_create(const nep_params *params, const nep_server_config *cfg, nep_server **out);
 /* Queue a job (HOST arrays copied); *id receives its id. Thread-safe; does not wait for the
- * device. NEP_ERR_OOM if the job alone needs more than the memory budget. */
+ * device. NEP_ERR_OOM if the job alone needs more than the memory budget; NEP_ERR_UNSUPPORTED
+ * above 2^23 atoms (a batch holds at most 2^23 atoms in all; admission waits for room). */
 int nep_server_submit(nep_server *s, const nep_job *job, long long *id);
 /* Next finished job in completion order: waits up to timeout_s seconds (< 0: no limit);
  * NEP_ERR_TIMEOUT if none finished in time. */

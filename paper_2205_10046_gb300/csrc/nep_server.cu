@@ -32,6 +32,11 @@ void set_create_error(const char *msg);
 
 namespace {
 
+// Atoms one batch may hold: a neighbour-list entry packs the atom index with three 3-bit image
+// offsets into 32 bits, so the batch's atom index has 23 bits. Admission keeps the running
+// jobs' atoms within it (a job alone above it is refused at submission).
+constexpr long long kEngineMaxAtoms = 1LL << 23;
+
 struct Job {
   long long id = 0;
   nep_job spec{};
@@ -120,10 +125,14 @@ void nep_server::scheduler_main() {
       std::unique_lock<std::mutex> lk(mu);
       if (active.empty()) cv_work.wait(lk, [&] { return stopping || !queue.empty(); });
       if (stopping) break;
+      long long batch_atoms = 0;
+      for (const Job &j : active) batch_atoms += j.spec.n_atoms;
       while (!queue.empty() && (int)(active.size() + add.size()) < cfg.workers &&
+             batch_atoms + queue.front().spec.n_atoms <= kEngineMaxAtoms &&
              (active.empty() && add.empty() ? true : reserved + queue.front().est <= cfg.memory_budget)) {
         Job j = std::move(queue.front());
         queue.pop_front();
+        batch_atoms += j.spec.n_atoms;
         reserved += j.est;
         peak_reserved = std::max(peak_reserved, reserved);
         ++running;
@@ -369,6 +378,7 @@ NEP_SERVER_API int nep_server_submit(nep_server *s, const nep_job *job, long lon
   j.spec.pos = nullptr;
   j.spec.types = nullptr;
   j.spec.vel = nullptr;
+  if (N > kEngineMaxAtoms) return NEP_ERR_UNSUPPORTED;
   j.est = s->estimate(N, job->box);
   if (j.est > s->cfg.memory_budget) return NEP_ERR_OOM;
   {
