@@ -5,7 +5,8 @@ within 1e-5 eV/atom and positions within 1e-4 A after 30 steps (FP32 forces agai
 Serving: each job's result does not depend on the jobs around it (alone and in a mix of 20
 jobs sharing one batch: equal within the FP32 bar); single-point and NVE jobs match the oracle at the
 FP32 bar; admission never reserves more than the memory budget and every job's share of the
-workspace stays within its admission estimate; a bad job is refused and the server carries on.
+workspace stays within its admission estimate; a bad job (a wrong type, a job larger than the
+budget or than the 2^23 atoms a batch can index) is refused and the server carries on.
 """
 import numpy as np
 import pytest
@@ -198,4 +199,9 @@ def test_memory_budget_admission_and_failures(torch_cuda):
     with pytest.raises(nep.NepError) as ei:
         s.submit(0, *huge)
     assert ei.value.code == -2
+    # a job above the 2^23 atoms a batch can index is refused at submission
+    n_big = (1 << 23) + 1
+    with pytest.raises(nep.NepError) as ei:
+        s.submit(0, np.zeros((n_big, 3)), np.zeros(n_big, np.int32), np.eye(3) * 2000.0)
+    assert ei.value.code == -6
     s.close()
