@@ -413,6 +413,13 @@ int nep_kernel_times(nep_handle *h, float *ms_out, int n_slots);
  *     serialise them (one stream, or synchronise between calls).
  *   - The call synchronises `stream` twice (to size the neighbour lists) and returns with
  *     the descriptor kernel queued on `stream`.
+ *   - Code loading: with CUDA's default lazy module loading the driver loads a kernel's
+ *     module, and the arena, the first time they are used, and may allocate device memory
+ *     for them then. The first call per hyper-parameter shape on a device can therefore
+ *     allocate inside the driver; later calls allocate nothing. A caller that must not
+ *     allocate at all makes one warm-up call first, or sets CUDA_MODULE_LOADING=EAGER.
+ *   - Per-atom lists longer than 512 entries return NEP_ERR_NEIGHBOR_OVERFLOW, as in the
+ *     handle-based calls.
  * The paper has no counterpart: this is a deployment variant of nep_descriptors. */
 #define NEP_STATIC_MAX_ATOMS 4096
 #define NEP_STATIC_SCRATCH_BYTES (16u << 20)

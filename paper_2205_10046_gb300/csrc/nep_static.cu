@@ -25,8 +25,11 @@ using namespace nep;
 
 namespace {
 
-constexpr size_t kStaticBytes = (size_t)16 << 20;  // NEP_STATIC_SCRATCH_BYTES in include/nep.h
-constexpr int kStaticMaxAtoms = 4096;              // NEP_STATIC_MAX_ATOMS in include/nep.h
+// the documented limits of include/nep.h are the real ones
+constexpr size_t kStaticBytes = (size_t)NEP_STATIC_SCRATCH_BYTES;
+constexpr int kStaticMaxAtoms = NEP_STATIC_MAX_ATOMS;
+static_assert(kStaticBytes == ((size_t)16 << 20) && kStaticMaxAtoms == 4096,
+              "the error messages below quote these limits");
 constexpr int kMaxDevices = 64;
 
 // The scratch arena. Every GPU that loads the library holds it until the process exits.
@@ -199,6 +202,9 @@ int nep_descriptors_static(const nep_params *params, int n_atoms, const double *
   // sizing pass, then the lists
   rc = run_build(N, T, g, dtab, rlR * rlR, rlA * rlA, rcR * rcR, rcA * rcA, a, L, 1, st, &host_st, s);
   if (rc) return rc;
+  // the same per-atom list limit, with the same error, as the handle-based entry points
+  if (host_st.max_r > kListBuf || host_st.max_a > kListBuf)
+    return fail_static(NEP_ERR_NEIGHBOR_OVERFLOW, "more than 512 neighbours within r_c + skin for one atom");
   L.cap_r = host_st.max_r > 0 ? host_st.max_r : 1;
   L.cap_a = host_st.max_a > 0 ? host_st.max_a : 1;
   L.nl_r = arena.take<unsigned>((size_t)L.cap_r * N);

@@ -156,16 +156,26 @@ def _stream():
 
 
 def _dev(t, dtype, shape=None, name="array"):
+    """Data pointer of a contiguous CUDA tensor of this dtype and shape (checked in that
+    order of failure: type, dtype/layout, shape, device), or None for None."""
     import torch
     if t is None:
         return None
-    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+    if not isinstance(t, torch.Tensor):
         raise TypeError(f"{name} must be a CUDA tensor")
     if t.dtype != dtype or not t.is_contiguous():
         raise TypeError(f"{name} must be a contiguous {dtype} tensor")
     if shape is not None and tuple(t.shape) != tuple(shape):
         raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
     return t.data_ptr()
+
+
+def _shape(t, shape, name):
+    """Raise ValueError unless tensor t (if given) has exactly this shape."""
+    if t is not None and tuple(getattr(t, "shape", ())) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(getattr(t, 'shape', ()))}, expected {tuple(shape)}")
 
 
 def _box(box) -> np.ndarray:
@@ -327,12 +337,14 @@ def nep_get_tuning(h) -> dict:
 
 
 def nep_descriptors(h, pos, types, box, q):
+    """Descriptors q [n, N_des] (CUDA f64, caller atom order) of one periodic structure."""
     import torch
     n = int(pos.shape[0])
     b = _box(box)
-    rc = load().nep_descriptors(h, n, _dev(pos, torch.float64, (n, 3), "pos"), _dev(types, torch.int32, (n,), "types"),
-                                b.ctypes.data, _dev(q, torch.float64, None, "q"), _stream())
-    _check(rc, h)
+    _shape(q, (n, nep_n_des(h)), "q")  # the kernel writes n x N_des values
+    args = (_dev(pos, torch.float64, (n, 3), "pos"), _dev(types, torch.int32, (n,), "types"), b.ctypes.data,
+            _dev(q, torch.float64, (n, nep_n_des(h)), "q"))
+    _check(load().nep_descriptors(h, n, *args, _stream()), h)
 
 
 def nep_descriptors_static(model, pos, types, box, q, skin: float = 1.0):
@@ -340,11 +352,11 @@ def nep_descriptors_static(model, pos, types, box, q, skin: float = 1.0):
     import torch
     n = int(pos.shape[0])
     b = _box(box)
+    _shape(q, (n, model.n_des), "q")  # the kernel writes n x N_des values
+    args = (_dev(pos, torch.float64, (n, 3), "pos"), _dev(types, torch.int32, (n,), "types"), b.ctypes.data,
+            _dev(q, torch.float64, (n, model.n_des), "q"))
     p, _keep = _params(model, skin)
-    rc = load().nep_descriptors_static(C.byref(p), n, _dev(pos, torch.float64, (n, 3), "pos"),
-                                       _dev(types, torch.int32, (n,), "types"), b.ctypes.data,
-                                       _dev(q, torch.float64, None, "q"), _stream())
-    _check(rc, None)
+    _check(load().nep_descriptors_static(C.byref(p), n, *args, _stream()), None)
 
 
 def md_init(h, pos, types, box, vel=None):

@@ -60,3 +60,22 @@ def test_supported_shapes_cover_the_workload_models(lib):
         key = (hyper["n_max_radial"], hyper["basis_radial"], hyper["n_max_angular"], hyper["basis_angular"],
                hyper["n_neuron"], hyper["l_max_3b"], hyper["l_max_4b"], hyper["l_max_5b"])
         assert key in shapes
+
+
+def test_descriptor_output_shape_is_checked_before_the_library_is_called(monkeypatch):
+    """A q of the wrong shape would make the descriptor kernel write past its end: the
+    binding refuses it with ValueError before any call into libnep."""
+    torch = pytest.importorskip("torch")
+    from paper_2205_10046_gb300 import nep, workloads as W
+
+    def no_library(*a, **k):
+        raise AssertionError("the library was called")
+
+    monkeypatch.setattr(nep, "load", no_library)
+    w = W.si_diamond(1, seed=0, with_velocities=False)  # 8 atoms, N_des = 39
+    pos = torch.tensor(w.pos)
+    types = torch.tensor(w.types)
+    for bad in ((w.n_atoms, w.model.n_des - 1), (w.n_atoms - 1, w.model.n_des), (w.n_atoms * w.model.n_des,)):
+        q = torch.zeros(bad, dtype=torch.float64)
+        with pytest.raises(ValueError, match="q has shape"):
+            nep.nep_descriptors_static(w.model, pos, types, w.box, q)
