@@ -1,9 +1,13 @@
 #!/usr/bin/env python
 """NEP3 molecular-dynamics throughput on GB300: atom-steps/s of velocity-Verlet NVE.
 
-Default workload: rocksalt PbTe, 32^3 conventional cells (262,144 atoms), two species,
-NEP radial/angular cutoffs 6/4 A, n_max 10/6, basis 10/6, l_max 4/2/1, 30 neurons,
-random weights (seed 1), 300 K Maxwell-Boltzmann velocities, dt = 2 fs.
+Default workload: Si diamond, 100^3 conventional cells (8,000,000 atoms), a = 5.43 A,
+sigma = 0.05 A, NEP radial/angular cutoffs 5.0/4.0 A, n_max 8/4, basis 8/4, l_max 4/2/1,
+50 neurons, random weights (seed 0), 300 K Maxwell-Boltzmann velocities, dt = 1 fs; the
+plain FP32 form is `value`, the BF16 tensor-core network form is reported beside it, both
+with their force error against the FP64 oracle on the 4096-atom subcell (cells [0, 8)^3).
+The two-species PbTe workload (32^3 rocksalt cells, 262,144 atoms, 1000 steps of 2 fs) is
+reported as an extra key.
 
 One timed step = one MD step of the whole hot path (drift, neighbour rebuild when
 triggered, descriptor + network + angular partial forces, force/virial gather, kick,
@@ -46,10 +50,11 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["pbte", "si", "si_large"], default="pbte")
+    ap.add_argument("--workload", choices=["pbte", "si", "si_large"], default="si_large")
+    ap.add_argument("--pbte-steps", type=int, default=1000, help="timed steps of the extra PbTe key (0: skip)")
     ap.add_argument("--skin", type=float, default=0.4, help="neighbour-list skin (A) of the MD workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=8.0)
     ap.add_argument("--plain-graph", action="store_true",
                     help="capture the rebuild as ordinary kernel nodes (for kernel-level profilers)")
     ap.add_argument("--no-batch", action="store_true", help="skip the structure-batch and population forms")
@@ -236,28 +241,97 @@ def dist_env():
 # ----------------------------------------------------------------------------- CPU oracle
 def oracle_sample(w_name: str):
     """A bounded sample of the same workload for the FP64 oracle: the same lattice, model,
-    seed, jitter and temperature in a 4x4x4-cell box (512 atoms PbTe / 216 atoms Si)."""
+    seed, jitter and temperature in a small periodic box (512 atoms PbTe or Si)."""
     from paper_2205_10046_gb300 import workloads as W
     if w_name == "pbte":
         return W.pbte_rocksalt(4, seed=1), "rocksalt PbTe 4x4x4 cells (512 atoms), same model/seed/jitter/300 K"
-    return W.si_diamond(3, seed=0), "diamond Si 3x3x3 cells (216 atoms), same model/seed/jitter/300 K"
+    if w_name == "si":
+        return W.si_diamond(3, seed=0), "diamond Si 3x3x3 cells (216 atoms), same model/seed/jitter/300 K"
+    return (W.si_diamond(4, seed=0, n_steps=100, dt_fs=1.0),
+            "diamond Si 4x4x4 cells (512 atoms), same model/seed/jitter/300 K")
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_md_rate(s, seconds, n_threads):
+    """atom-steps/s of the oracle's velocity Verlet on sample s, run for about `seconds`."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.md(s.model, s.pos, s.vel, s.types, s.box, 1, s.dt_fs, n_threads=n_threads)  # 2 force evaluations
+    per_eval = (time.perf_counter() - t0) / 2.0
+    steps = max(1, int(seconds / per_eval) - 1)
+    t0 = time.perf_counter()
+    oracle.md(s.model, s.pos, s.vel, s.types, s.box, steps, s.dt_fs, n_threads=n_threads)
+    el = time.perf_counter() - t0
+    return s.n_atoms * steps / el, steps, el
 
 
 def cpu_baseline(w_name: str, seconds: float):
+    """The oracle as it stands, on the host cores: all threads (the reported value) and one
+    thread, on a bounded periodic sample of the workload."""
     import oracle
     s, desc = oracle_sample(w_name)
-    dt = s.dt_fs
-    t0 = time.perf_counter()
-    oracle.md(s.model, s.pos, s.vel, s.types, s.box, 1, dt)  # 2 force evaluations
-    t1 = time.perf_counter()
-    per_eval = (t1 - t0) / 2.0
-    steps = max(1, int(seconds / per_eval) - 1)
-    t0 = time.perf_counter()
-    oracle.md(s.model, s.pos, s.vel, s.types, s.box, steps, dt)
-    el = time.perf_counter() - t0
-    return {"value": s.n_atoms * steps / el, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+    value, steps, el = _oracle_md_rate(s, seconds, 0)
+    one, steps1, el1 = _oracle_md_rate(s, max(2.0, seconds / 2), 1)
+    return {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
             "sample": f"{desc}; {steps} velocity-Verlet steps (+1 initial force evaluation) in {el:.1f} s, "
-                      f"FP64, OpenMP over atoms"}
+                      f"FP64, OpenMP over atoms",
+            "single_thread": {"value": one, "unit": UNIT, "cores": 1,
+                              "sample": f"same sample, {steps1} steps in {el1:.1f} s on one thread"},
+            "cpu_model": cpu_model()}
+
+
+def subcell_reference(w, w_name):
+    """FP64 oracle energies and forces of the error sample: for the 8,000,000-atom box the 4096
+    atoms of conventional cells [0, 8)^3 (for PbTe the 512 atoms of cells [0, 4)^3), cut out
+    with every atom within 2 r_c^R as an open cluster; the small Si box is evaluated whole.
+    Returns (indices in the workload, U [n], F [n, 3], description, seconds)."""
+    import numpy as np
+    import oracle
+    from paper_2205_10046_gb300 import workloads as W
+    t0 = time.perf_counter()
+    if w_name == "si":
+        U, F, _ = oracle.compute(w.model, w.pos, w.types, w.box)
+        sel, desc = np.arange(w.n_atoms), "the whole periodic box"
+    else:
+        reps, cells = (100, 8) if w_name == "si_large" else (32, 4)
+        cpos, ctypes, cbox, inner, sel = W.subcell_cluster(w, reps, cells)
+        U, F, _ = oracle.compute(w.model, cpos, ctypes, cbox, sel=inner)
+        desc = (f"{sel.shape[0]} atoms of conventional cells [0,{cells})^3, cut out with every atom within "
+                f"2 r_c^R ({cpos.shape[0]} atoms) as an open cluster, step-0 positions")
+    return sel, U, F, desc, time.perf_counter() - t0
+
+
+def form_errors(step0, ref):
+    """Force and energy error of each form's step-0 evaluation against the oracle sample."""
+    import numpy as np
+    sel, U, F, desc, secs = ref
+    out = {"sample": desc, "oracle_seconds": secs, "f_rms_eV_per_A": float(np.sqrt(np.mean(F ** 2)))}
+    for key, (Fg, Ug) in step0.items():
+        d = Fg - F
+        out[key] = {"force_rmse_eV_per_A": float(np.sqrt(np.mean(d ** 2))),
+                    "force_rmse_meV_per_A": 1e3 * float(np.sqrt(np.mean(d ** 2))),
+                    "force_relative_rms": float(np.linalg.norm(d) / max(np.linalg.norm(F), 1e-30)),
+                    "energy_error_eV_per_atom": float(abs(Ug.sum() - U.sum()) / U.shape[0]),
+                    "site_energy_max_abs_error_eV": float(np.abs(Ug - U).max())}
+    return out
 
 
 def run_reference(args):
@@ -548,10 +622,99 @@ def run_serving(args):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+KERNELS = ["md_drift", "neighbor_rebuild", "nep_atom", "nep_gather", "finalize"]
+FORMS = ((0, "fp32"), (1, "bf16"), (2, "bf16_split"))
+NETWORK = {1: "descriptor->hidden and hidden->dU/dq as BF16 tcgen05 GEMMs, FP32 accumulate",
+           2: "as bf16, each operand split into two BF16 terms (hi + lo), products hi.hi + lo.hi + hi.lo"}
+
+
+def timed_md(nep, h, dt, steps, warmup, stream, flush, world, sampler=None):
+    """Warm up, then time `steps` MD steps one graph replay at a time (L2 flushed before
+    each, outside the events). Returns (seconds, per-kernel ms totals, rebuilds)."""
+    import torch
+    nep.md_run(h.h, max(warmup, 3), dt, 1, None)
+    torch.cuda.synchronize()
+    ktime = {k: 0.0 for k in KERNELS}
+    step_ms = []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    r0 = nep.nep_get_stats(h.h)["n_rebuilds"]
+    ctx = sampler if sampler is not None else _Null()
+    with ctx:
+        for s in range(steps):
+            flush.fill_(s)
+            ev0.record(stream)
+            nep.md_run_async(h.h, 1, dt, 1, None, stream.cuda_stream)
+            ev1.record(stream)
+            kt = nep.nep_kernel_times(h.h)  # synchronises on this step's last kernel
+            ev1.synchronize()
+            step_ms.append(ev0.elapsed_time(ev1))
+            for k in KERNELS:
+                ktime[k] += kt.get(k, 0.0)
+            if (s + 1) % 100 == 0:
+                nep.md_status(h.h, stream.cuda_stream)  # list health, outside the timed events
+    nep.md_status(h.h)
+    torch.cuda.synchronize()
+    tot = sum(step_ms) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([tot], device=flush.device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+    return tot, ktime, nep.nep_get_stats(h.h)["n_rebuilds"] - r0
+
+
+def atom_roofline(w, stats, atom_ms, peak, peak_basis, traffic=None):
+    atom_f, gather_f = flop_model(w.model, w.model.n_types, stats["mean_radial"], stats["mean_radial_in_rc"],
+                                  stats["mean_angular"], stats["mean_angular_in_rc"])
+    achieved = atom_f * w.n_atoms / (atom_ms / 1e3) / 1e12
+    return {"kernel": "nep_atom", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic, "flops_per_atom": atom_f, "peak_basis": peak_basis}, gather_f
+
+
+def md_forms(nep, w, name, skin, steps, warmup, stream, flush, world, clk=None, step0_sel=None,
+             plain_graph=False):
+    """Every network form of the MD workload w on one handle: optional step-0 evaluations
+    (forces and site energies of the atoms step0_sel, for the error against the oracle), then
+    `steps` timed MD steps per form from the same start state. Returns (handle, results)."""
+    import torch
+    dev = flush.device
+    h = nep.NEP(w.model, skin=skin)
+    pos_d = torch.tensor(w.pos, device=dev)
+    types_d = torch.tensor(w.types, device=dev)
+    vel_d = torch.tensor(w.vel, device=dev)
+    step0 = {}
+    if step0_sel is not None:
+        sel_d = torch.tensor(step0_sel, device=dev, dtype=torch.int64)
+        for prec, key in FORMS:
+            nep.nep_set_precision(h.h, prec)
+            r = h.compute(pos_d, types_d, w.box)
+            step0[key] = (r["F"][sel_d].cpu().numpy(), r["U"][sel_d].cpu().numpy())
+            del r
+        torch.cuda.synchronize()
+    nep.nep_set_profiling(h.h, True)
+    nep.nep_set_graph_conditional(h.h, not plain_graph)
+    res = {}
+    for prec, key in FORMS:
+        nep.nep_set_precision(h.h, prec)
+        nep.md_init(h.h, pos_d, types_d, w.box, vel_d)
+        tot, ktime, rebuilds = timed_md(nep, h, w.dt_fs, steps, warmup, stream, flush, world,
+                                        clk if prec == 0 else None)
+        res[key] = {"seconds": tot, "ktime": ktime, "rebuilds": rebuilds, "stats": nep.nep_get_stats(h.h)}
+    nep.nep_set_precision(h.h, 0)
+    del pos_d, types_d, vel_d
+    return h, res, step0
+
+
 def run_gb300(args):
     import numpy as np
     import torch
     from paper_2205_10046_gb300 import nep
+    from paper_2205_10046_gb300 import workloads as W
 
     rank, world, local = dist_env()
     if world > 1:
@@ -571,6 +734,7 @@ def run_gb300(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     props = torch.cuda.get_device_properties(dev)
+    fp32_peak_2070 = props.multi_processor_count * 128 * 2 * 2070e6 / 1e12
     if args.serve_only:
         clk = ClockSampler(torch.cuda.current_device() if world == 1 else local)
         with clk:
@@ -581,76 +745,32 @@ def run_gb300(args):
     if args.batch_only:
         clk = ClockSampler(torch.cuda.current_device() if world == 1 else local)
         with clk:
-            bf, pf = run_batch_forms(args, dev, stream, flush, props.multi_processor_count * 128 * 2 * 2070e6 / 1e12)
+            bf, pf = run_batch_forms(args, dev, stream, flush, fp32_peak_2070)
         if rank == 0:
             print(json.dumps({"batch_form": bf, "population": pf, "clocks": clk.summary()}), flush=True)
         return 0
 
     w = make_workload(args.workload)
     N = w.n_atoms
-    dt = w.dt_fs
-    h = nep.NEP(w.model, skin=args.skin)
-    pos_d = torch.tensor(w.pos, device=dev)
-    types_d = torch.tensor(w.types, device=dev)
-    vel_d = torch.tensor(w.vel, device=dev)
-    nep.md_init(h.h, pos_d, types_d, w.box, vel_d)
-    nep.nep_set_profiling(h.h, True)
-    nep.nep_set_graph_conditional(h.h, not args.plain_graph)
-
-    names = ["md_drift", "neighbor_rebuild", "nep_atom", "nep_gather", "finalize"]
-
-    def timed_md(steps, sampler=None):
-        """Warm up, then time `steps` MD steps one graph replay at a time (L2 flushed before
-        each, outside the events). Returns (seconds, per-kernel ms totals, rebuilds)."""
-        nep.md_run(h.h, max(args.warmup, 3), dt, 1, None)
-        torch.cuda.synchronize()
-        ktime = {k: 0.0 for k in names}
-        step_ms = []
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        r0 = nep.nep_get_stats(h.h)["n_rebuilds"]
-        ctx = sampler if sampler is not None else _Null()
-        with ctx:
-            for s in range(steps):
-                flush.fill_(s)
-                ev0.record(stream)
-                nep.md_run_async(h.h, 1, dt, 1, None, stream.cuda_stream)
-                ev1.record(stream)
-                kt = nep.nep_kernel_times(h.h)  # synchronises on this step's last kernel
-                ev1.synchronize()
-                step_ms.append(ev0.elapsed_time(ev1))
-                for k in names:
-                    ktime[k] += kt.get(k, 0.0)
-                if (s + 1) % 100 == 0:
-                    nep.md_status(h.h, stream.cuda_stream)  # list health, outside the timed events
-        nep.md_status(h.h)
-        torch.cuda.synchronize()
-        tot = sum(step_ms) / 1e3
-        if world > 1:
-            t = torch.tensor([tot], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
-        return tot, ktime, nep.nep_get_stats(h.h)["n_rebuilds"] - r0
-
-    # plain FP32 form (the headline), then the BF16 tensor-core network on the same start state
+    if args.workload == "si_large":
+        err_sel = W.subcell_cluster(w, 100, 8)[4]
+    elif args.workload == "pbte":
+        err_sel = W.subcell_cluster(w, 32, 4)[4]
+    else:
+        err_sel = np.arange(N)
     clk = ClockSampler(torch.cuda.current_device() if world == 1 else local)
-    total_s, ktime, timed_rebuilds = timed_md(args.steps, clk)
-    stats = nep.nep_get_stats(h.h)
-    nep.nep_set_precision(h.h, 1)
-    nep.md_init(h.h, pos_d, types_d, w.box, vel_d)
-    bf_s, bf_ktime, _ = timed_md(args.steps)
-    nep.nep_set_precision(h.h, 0)
+    h, md, step0 = md_forms(nep, w, args.workload, args.skin, args.steps, args.warmup, stream, flush, world, clk,
+                            err_sel, args.plain_graph)
+    stats = md["fp32"]["stats"]
+    total_s, ktime, timed_rebuilds = md["fp32"]["seconds"], md["fp32"]["ktime"], md["fp32"]["rebuilds"]
 
     # end-to-end through the host-pointer entry points: upload, run, read back
-    thermo_every = 100
+    thermo_every = min(100, args.steps)
     th = torch.zeros((max(1, args.steps // thermo_every), 4), dtype=torch.float64, device=dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     nep.md_init_host(h.h, w.pos, w.types, w.box, w.vel)
-    nep.md_run_async(h.h, args.steps, dt, thermo_every, th, stream.cuda_stream)
+    nep.md_run_async(h.h, args.steps, w.dt_fs, thermo_every, th, stream.cuda_stream)
     nep.md_status(h.h)
     th_host = th.cpu()
     p_out, v_out, f_out = nep.md_get_state_host(h.h, N)
@@ -662,12 +782,30 @@ def run_gb300(args):
     h2d = N * (24 + 4 + 24) + 72
     d2h = N * 72 + th_host.numel() * 8
     etot = (th_host[:, 0] + th_host[:, 1]).numpy()
+    h.close()
+    del p_out, v_out, f_out
+
+    # the two-species workload as an extra key, with its own fixed step count
+    pbte = None
+    if args.pbte_steps > 0 and args.workload != "pbte":
+        wp = W.pbte_rocksalt(32, seed=1)
+        hp, mp, _ = md_forms(nep, wp, "pbte", args.skin, args.pbte_steps, 20, stream, flush, world)
+        hp.close()
+        pbte = {"workload": workload_config(wp, "pbte")["workload"], "steps": args.pbte_steps, "warmup": 20}
+        for key in mp:
+            r = mp[key]
+            rl, _ = atom_roofline(wp, r["stats"], r["ktime"]["nep_atom"] / args.pbte_steps, fp32_peak_2070,
+                                  "152 SMs x 128 FP32 lanes x 2 x 2070 MHz")
+            pbte[key] = {"value": world * wp.n_atoms * args.pbte_steps / r["seconds"], "unit": UNIT,
+                         "ms_per_step": 1e3 * r["seconds"] / args.pbte_steps,
+                         "kernel_ms_per_step": {k: v / args.pbte_steps for k, v in r["ktime"].items()},
+                         "atom_kernel_frac_of_fp32_peak": rl["frac"], "rebuilds": r["rebuilds"]}
+        del wp
 
     batch_forms = None
     if not args.no_batch:
         with ClockSampler(torch.cuda.current_device() if world == 1 else local) as bclk:
-            batch_forms = run_batch_forms(args, dev, stream, flush,
-                                          props.multi_processor_count * 128 * 2 * 2070e6 / 1e12)
+            batch_forms = run_batch_forms(args, dev, stream, flush, fp32_peak_2070)
         batch_forms[0]["clocks"] = bclk.summary()
     serving = None
     if not args.no_serve and world == 1:
@@ -678,11 +816,9 @@ def run_gb300(args):
         clocks = clk.summary()
         sm_max = clocks.get("sm_max_mhz") or 2070.0
         peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes
-        atom_f, gather_f = flop_model(w.model, w.model.n_types, stats["mean_radial"], stats["mean_radial_in_rc"],
-                                      stats["mean_angular"], stats["mean_angular_in_rc"])
-        atom_ms = ktime["nep_atom"] / args.steps
-        achieved = atom_f * N / (atom_ms / 1e3) / 1e12
-        traffic = profiled_traffic(args.workload)
+        basis = f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"
+        roof, gather_f = atom_roofline(w, stats, ktime["nep_atom"] / args.steps, peak, basis,
+                                       profiled_traffic(args.workload))
         value = world * N * args.steps / total_s
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -690,37 +826,44 @@ def run_gb300(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(workload_config(w, args.workload), parallelism=f"replicas x{world}",
                            neighbour_skin_A=args.skin),
-            "roofline": {"kernel": "nep_atom", "bound": "alu", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                         "flops_per_atom": atom_f,
-                         "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"},
+            "roofline": roof,
             "kernel_ms_per_step": {k: v / args.steps for k, v in ktime.items()},
             "gather_roofline": {"achieved": gather_f * N / (ktime["nep_gather"] / args.steps / 1e3) / 1e12,
                                 "unit": "TFLOP/s", "flops_per_atom": gather_f},
             "e2e": {"value": world * N * args.steps / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-                    "path": "md_init_host + md_run_async + md_status + md_get_state_host (thermo every 100)"},
+                    "path": f"md_init_host + md_run_async + md_status + md_get_state_host (thermo every "
+                            f"{thermo_every})"},
             "gpu_launches": int(stats["graph_kernels"]) * args.steps + int(stats["rebuild_kernels"]) * timed_rebuilds,
             "clocks": clocks,
             "neighbours": {"radial_list": stats["mean_radial"], "radial_in_rc": stats["mean_radial_in_rc"],
                            "angular_list": stats["mean_angular"], "angular_in_rc": stats["mean_angular_in_rc"],
                            "rebuilds_in_timed_steps": timed_rebuilds},
-            "energy_drift_ev_per_atom": float((etot.max() - etot.min()) / N) if etot.size else None,
-            "bf16_form": {"value": world * N * args.steps / bf_s, "unit": UNIT, "ms_per_step": 1e3 * bf_s / args.steps,
-                          "kernel_ms_per_step": {k: v / args.steps for k, v in bf_ktime.items()},
-                          "network": "descriptor->hidden and hidden->dU/dq as BF16 tcgen05 GEMMs, FP32 accumulate",
-                          "force_rmse_vs_fp64_oracle": "0.10-0.15 meV/A on the parity cases (tests/test_gpu_bf16.py)"},
+            "energy_drift_ev_per_atom": float((etot.max() - etot.min()) / N) if etot.size > 1 else None,
             "naive_flops_per_atom_step": naive_flop_model(w.model, stats["mean_radial_in_rc"],
                                                             stats["mean_angular_in_rc"]),
         }
+        for prec, key in FORMS[1:]:
+            r = md[key]
+            rl, _ = atom_roofline(w, r["stats"], r["ktime"]["nep_atom"] / args.steps, peak, basis)
+            line[f"{key}_form"] = {
+                "value": world * N * args.steps / r["seconds"], "unit": UNIT,
+                "ms_per_step": 1e3 * r["seconds"] / args.steps,
+                "kernel_ms_per_step": {k: v / args.steps for k, v in r["ktime"].items()},
+                "atom_kernel_ms": r["ktime"]["nep_atom"] / args.steps,
+                "atom_kernel_frac_of_fp32_peak": rl["frac"],
+                "network": NETWORK[prec]}
+        if pbte is not None:
+            line["pbte"] = pbte
         if batch_forms is not None:
             line["batch_form"], line["population"] = batch_forms
         if serving is not None:
             line["serving"] = serving
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
+            ref = subcell_reference(w, args.workload)
+            line["force_error_vs_fp64_oracle"] = form_errors(step0, ref)
         print(json.dumps(line), flush=True)
-    h.close()
     if world > 1:
         dist.destroy_process_group()
     return 0

@@ -214,7 +214,7 @@ typedef struct nep_server nep_server;
 typedef struct {
   size_t memory_budget; /* bytes of device workspace that running jobs may hold together */
   int workers;          /* job slots of the batch: jobs on the device at once (1..65536) */
-  int precision;        /* 0: FP32 network, 1: BF16 tensor-core network (nep_set_precision) */
+  int precision;        /* 0: FP32 network, 1: BF16 / 2: split-BF16 tensor-core network (nep_set_precision) */
 } nep_server_config;
 
 typedef struct {
@@ -385,6 +385,11 @@ int nep_set_profiling(nep_handle *h, int enable);
  *   1 BF16 operands on the tensor cores (tcgen05.mma, FP32 accumulation in tensor memory):
  *     descriptor -> hidden and hidden -> dU/dq as two GEMMs per 128-atom tile. Descriptors,
  *     partial forces and all accumulations stay FP32; integration and totals FP64.
+ *     Operand rounding (2^-9 relative) gives forces about 1e-2 relative error.
+ *   2 split BF16: as 1, but every operand value x is carried as two BF16 terms
+ *     x = hi + lo (hi = bf16(x), lo = bf16(x - hi)) and each GEMM adds the three products
+ *     hi.hi + lo.hi + hi.lo (the lo.lo term, ~2^-18 relative, is dropped): three times the
+ *     tensor-core work, errors near the FP32 form's (about 1e-5 relative).
  * Applies to nep_compute and md_run (nep_descriptors has no network). */
 int nep_set_precision(nep_handle *h, int mode);
 
@@ -425,6 +430,21 @@ int nep_kernel_times(nep_handle *h, float *ms_out, int n_slots);
 #define NEP_STATIC_SCRATCH_BYTES (16u << 20)
 int nep_descriptors_static(const nep_params *params, int n_atoms, const double *pos, const int *types,
                            const double *box, double *q, nep_stream_t stream);
+
+/* The neighbour lists of the handle's last build, in the caller's atom order: the
+ * quantities NN_i^R, NL_im^R, NN_i^A and NL_im^A that the force kernels take as given
+ * (Appendix B), with the image of every entry made explicit by its pair vector.
+ *   nn_r [N], nn_a [N]        entries of atom i's radial and angular list;
+ *   j_r  [N][cap], j_a [N][cap]  caller index j of entry m (m < nn);
+ *   d_r  [N][cap][3], d_a [N][cap][3]  FP32 pair vector r_j - r_i (+ the periodic image) of
+ *                              entry m, as the kernels form it, at the current positions.
+ * Lists hold every pair within r_c + skin (radial) or r_c^A + skin (angular); the radial list
+ * is grouped by neighbour type (type 0 first). All outputs are HOST buffers owned by the
+ * caller; N is the atom count of the last nep_compute, nep_compute_batch (all structures,
+ * concatenated) or md_init/md_run. NEP_ERR_STATE if no lists exist; NEP_ERR_ARG if cap is
+ * below the longest list (nep_stats.max_radial / max_angular). Synchronises the device;
+ * allocates temporary device memory. For tests and inspection; not on the hot path. */
+int nep_export_lists(nep_handle *h, int cap, int *nn_r, int *j_r, float *d_r, int *nn_a, int *j_a, float *d_a);
 
 /* Compiled hyper-parameter shapes: writes up to `max` rows of 8 ints
  * (n_max^R, N_bas^R, n_max^A, N_bas^A, N_neu, l_max^3b, l_max^4b, l_max^5b) and

@@ -706,7 +706,7 @@ struct BatchOut {
   double *e_atom = nullptr, *w_atom = nullptr, *force = nullptr, *e_struct = nullptr, *w_struct = nullptr;
 };
 
-int atom_block(const nep_handle *h) { return (h->precision == 1 || h->tune.atom_block == 0) ? 128 : h->tune.atom_block; }
+int atom_block(const nep_handle *h) { return (h->precision >= 1 || h->tune.atom_block == 0) ? 128 : h->tune.atom_block; }
 int gather_block(const nep_handle *h) { return h->tune.gather_block == 0 ? 128 : h->tune.gather_block; }
 
 // Per-block partial sums of `members` batched evaluations.
@@ -1411,8 +1411,8 @@ int nep_eval_population(nep_handle *h, int n_pop, const double *z, int n_struct,
   CK(h->pop_ann.ensure((size_t)n_pop * n_ann), "alloc population");
   CK(h->pop_reg.ensure(2 * (size_t)n_pop), "alloc population");
   launch_unpack_population(n_pop, z, n_par, n_cr, n_ca, h->pop_cr.p, h->pop_ca.p, h->pop_ann.p, h->pop_reg.p, s);
-  const long long s_tc = (long long)h->ops->np1 * h->ops->kp1 * 2 * 2 / 16;  // two tiles, uint4 units
-  if (h->precision == 1) {
+  const long long s_tc = (long long)h->ops->np1 * h->ops->kp1 * 2 * 4 / 16;  // four tiles, uint4 units
+  if (h->precision >= 1) {
     CK(h->pop_tc.ensure((size_t)n_pop * s_tc), "alloc population");
     CK(cudaMemsetAsync(h->pop_tc.p, 0, sizeof(uint4) * (size_t)n_pop * s_tc, s), "memset tiles");
     launch_population_tiles(n_pop, h->pop_ann.p, n_ann, h->H, h->n_des, h->ops->kp1, h->ops->np1,
@@ -1453,7 +1453,7 @@ int nep_eval_population(nep_handle *h, int n_pop, const double *z, int n_struct,
     a.s_ca = n_ca;
     a.pop_ann = h->pop_ann.p + (size_t)p0 * n_ann;
     a.s_ann = n_ann;
-    a.pop_tc = h->precision == 1 ? h->pop_tc.p + (size_t)p0 * s_tc : nullptr;
+    a.pop_tc = h->precision >= 1 ? h->pop_tc.p + (size_t)p0 * s_tc : nullptr;
     a.s_tc = s_tc;
     a.s_erad = (long long)N * h->T * est;
     a.s_pang = (long long)h->cap_a * N;
@@ -1542,7 +1542,7 @@ int nep_autotune(nep_handle *h, int n_struct, const int *offsets, const double *
   int best_ab = 128, best_gb = 128;
   const int abs_[2] = {64, 128}, gbs[3] = {64, 128, 256};
   for (int ia = 0; ia < 2 && !rc; ++ia) {
-    if (h->precision == 1 && abs_[ia] != 128) continue;
+    if (h->precision >= 1 && abs_[ia] != 128) continue;
     for (int ig = 0; ig < 3 && !rc; ++ig) {
       h->tune.atom_block = abs_[ia];
       h->tune.gather_block = gbs[ig];
@@ -2098,6 +2098,45 @@ int md_get_state_host(nep_handle *h, double *pos, double *vel, double *force) {
   return NEP_OK;
 }
 
+int nep_export_lists(nep_handle *h, int cap, int *nn_r, int *j_r, float *d_r, int *nn_a, int *j_a, float *d_a) {
+  if (!valid_handle(h)) return NEP_ERR_ARG;
+  h->err.clear();
+  if (cap < 1 || !nn_r || !j_r || !d_r || !nn_a || !j_a || !d_a)
+    return fail(h, NEP_ERR_ARG, "cap >= 1 and every output are required");
+  if (h->N <= 0 || !h->nl_r.p || !h->nl_a.p || h->cap_r <= 0 || h->cap_a <= 0)
+    return fail(h, NEP_ERR_STATE, "no neighbour lists have been built");
+  const int N = h->N;
+  CK(cudaDeviceSynchronize(), "synchronise");
+  CK(cudaMemcpy(h->h_status, h->status.p, sizeof(BuildStatus), cudaMemcpyDeviceToHost), "status");
+  if (h->h_status->max_r > cap || h->h_status->max_a > cap)
+    return fail(h, NEP_ERR_ARG, "cap is below the longest list (nep_get_stats max_radial / max_angular)");
+  const size_t rows = (size_t)N * cap;
+  int *di = nullptr;
+  float *df = nullptr;
+  CK(cudaMalloc(&di, sizeof(int) * (2 * (size_t)N + 2 * rows)), "alloc");
+  cudaError_t e = cudaMalloc(&df, sizeof(float) * 6 * rows);
+  if (e != cudaSuccess) {
+    cudaFree(di);
+    return cuda_fail(h, e, "alloc");
+  }
+  int *dnr = di, *dna = di + N, *djr = di + 2 * (size_t)N, *dja = djr + rows;
+  float *ddr = df, *dda = df + 3 * rows;
+  launch_export_lists(N, h->T, h->pos4.p, h->perm.p, list_bufs(h), h->dtab.p, h->grid.ncode, h->grid.jbits,
+                      h->grid.jmask, cap, dnr, djr, ddr, dna, dja, dda, 0);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(nn_r, dnr, sizeof(int) * N, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(nn_a, dna, sizeof(int) * N, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(j_r, djr, sizeof(int) * rows, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(j_a, dja, sizeof(int) * rows, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(d_r, ddr, sizeof(float) * 3 * rows, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(d_a, dda, sizeof(float) * 3 * rows, cudaMemcpyDeviceToHost);
+  cudaFree(di);
+  cudaFree(df);
+  if (e != cudaSuccess) return cuda_fail(h, e, "nep_export_lists");
+  return NEP_OK;
+}
+
 int nep_get_stats(nep_handle *h, nep_stats *out) {
   if (!valid_handle(h) || !out) return NEP_ERR_ARG;
   nep_stats s = h->stats_cache;
@@ -2135,21 +2174,35 @@ static uint16_t to_bf16(float f) {
   return (uint16_t)(u >> 16);
 }
 
+static float from_bf16(uint16_t b) {
+  const uint32_t u = (uint32_t)b << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
 int nep_set_precision(nep_handle *h, int mode) {
   if (!valid_handle(h)) return NEP_ERR_ARG;
-  if (mode != 0 && mode != 1) return fail(h, NEP_ERR_ARG, "precision must be 0 (FP32) or 1 (BF16 tensor cores)");
-  if (mode == 1 && !h->d_tc.p) {
+  if (mode < 0 || mode > 2)
+    return fail(h, NEP_ERR_ARG, "precision must be 0 (FP32), 1 (BF16 tensor cores) or 2 (split BF16)");
+  if (mode >= 1 && !h->d_tc.p) {
     // W0 as the two GEMM operands, K-major no-swizzle UMMA layout, zero padded:
     //   B1 [NP1 x KP1]: (mu, nu) -> w0[mu][nu];  B2 [KP1 x NP1]: (nu, mu) -> w0[mu][nu]
+    // first rounded to BF16, then (for the split form) the BF16 of the remainder
     const int KP1 = h->ops->kp1, NP1 = h->ops->np1, D = h->n_des, H = h->H;
-    std::vector<uint16_t> t(2 * (size_t)NP1 * KP1, 0);
+    const size_t tile = (size_t)NP1 * KP1;
+    std::vector<uint16_t> t(4 * tile, 0);
     auto off = [](int r, int k, int KC) { return ((r / 8) * KC + k / 8) * 64 + (r % 8) * 8 + (k % 8); };
-    uint16_t *b1 = t.data(), *b2 = t.data() + (size_t)NP1 * KP1;
+    uint16_t *b1 = t.data(), *b2 = b1 + tile, *b1lo = b2 + tile, *b2lo = b1lo + tile;
     for (int mu = 0; mu < H; ++mu)
       for (int nu = 0; nu < D; ++nu) {
-        const uint16_t v = to_bf16(h->w0[(size_t)mu * D + nu]);
+        const float x = h->w0[(size_t)mu * D + nu];
+        const uint16_t v = to_bf16(x);
+        const uint16_t vl = to_bf16(x - from_bf16(v));
         b1[off(mu, nu, KP1 / 8)] = v;
         b2[off(nu, mu, NP1 / 8)] = v;
+        b1lo[off(mu, nu, KP1 / 8)] = vl;
+        b2lo[off(nu, mu, NP1 / 8)] = vl;
       }
     CK(h->d_tc.ensure(t.size() * 2 / 16), "alloc tiles");
     CK(cudaMemcpy(h->d_tc.p, t.data(), t.size() * 2, cudaMemcpyHostToDevice), "copy tiles");

@@ -739,11 +739,18 @@ __global__ void population_tiles_kernel(int n_pop, const float *ann, int n_ann, 
   const int m = (int)(v / ((long long)H * D));
   const int r = (int)(v % ((long long)H * D));
   const int mu = r / D, nu = r % D;
-  const unsigned short b = __bfloat16_as_ushort(__float2bfloat16_rn(ann[(size_t)m * n_ann + r]));
-  unsigned short *t1 = tiles + (size_t)m * 2 * NP1 * KP1, *t2 = t1 + (size_t)NP1 * KP1;
+  const float x = ann[(size_t)m * n_ann + r];
+  const __nv_bfloat16 bh = __float2bfloat16_rn(x);
+  const unsigned short b = __bfloat16_as_ushort(bh);
+  const unsigned short bl = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(bh)));
+  const size_t tile = (size_t)NP1 * KP1;
+  // per member: B1, B2, then the split form's B1_lo, B2_lo
+  unsigned short *t1 = tiles + (size_t)m * 4 * tile, *t2 = t1 + tile;
   auto off = [](int row, int k, int kc) { return ((row / 8) * kc + k / 8) * 64 + (row % 8) * 8 + (k % 8); };
   t1[off(mu, nu, KP1 / 8)] = b;
   t2[off(nu, mu, NP1 / 8)] = b;
+  t1[2 * tile + off(mu, nu, KP1 / 8)] = bl;
+  t2[2 * tile + off(nu, mu, NP1 / 8)] = bl;
 }
 
 // Eq. loss for `members` candidates (one block each, fixed-order sums): RMSE of the energy
@@ -1117,6 +1124,49 @@ void launch_engine_advance(int n_struct, EngineSlot *slots, cudaStream_t s) {
 
 void launch_engine_relayout(int n_keep, const int4 *table, const AtomState &src, AtomState dst, cudaStream_t s) {
   if (n_keep > 0) engine_relayout_kernel<<<n_keep, 256, 0, s>>>(table, src, dst);
+}
+
+// Neighbour lists of internal atom i written to row perm[i] (the caller's order): the caller
+// index of every neighbour and the FP32 pair vector the kernels use (cell-local coordinates
+// plus the image shift). Radial lists are the per-type groups in type order.
+__global__ void export_lists_kernel(int N, int T, const float4 *pos4, const int *perm, const ListBufs L,
+                                    const float4 *dtab, int ncode, int jbits, unsigned jmask, int cap,
+                                    int *nn_r, int *j_r, float *d_r, int *nn_a, int *j_a, float *d_a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const float4 pi = pos4[i];
+  const float4 *tab = dtab + (size_t)struct_of(pi) * ncode;  // structure 0 for a single structure
+  const size_t row = (size_t)perm[i];
+  int cnt = 0;
+  for (int t = 0; t < T; ++t) cnt += L.nn_r[(size_t)t * N + i];
+  nn_r[row] = cnt;
+  for (int m = 0; m < cnt && m < cap && m < L.cap_r; ++m) {
+    const unsigned e = L.nl_r[(size_t)m * N + i];
+    const unsigned j = e & jmask;
+    const float3 d = pair_vector(pi, pos4[j], tab[e >> jbits]);
+    j_r[row * cap + m] = perm[j];
+    d_r[(row * cap + m) * 3] = d.x;
+    d_r[(row * cap + m) * 3 + 1] = d.y;
+    d_r[(row * cap + m) * 3 + 2] = d.z;
+  }
+  const int na = L.nn_a[i];
+  nn_a[row] = na;
+  for (int m = 0; m < na && m < cap && m < L.cap_a; ++m) {
+    const unsigned e = L.nl_a[(size_t)m * N + i];
+    const unsigned j = e & jmask;
+    const float3 d = pair_vector(pi, pos4[j], tab[e >> jbits]);
+    j_a[row * cap + m] = perm[j];
+    d_a[(row * cap + m) * 3] = d.x;
+    d_a[(row * cap + m) * 3 + 1] = d.y;
+    d_a[(row * cap + m) * 3 + 2] = d.z;
+  }
+}
+
+void launch_export_lists(int N, int T, const float4 *pos4, const int *perm, const ListBufs &L, const float4 *dtab,
+                         int ncode, int jbits, unsigned jmask, int cap, int *nn_r, int *j_r, float *d_r,
+                         int *nn_a, int *j_a, float *d_a, cudaStream_t s) {
+  export_lists_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, T, pos4, perm, L, dtab, ncode, jbits, jmask, cap,
+                                                       nn_r, j_r, d_r, nn_a, j_a, d_a);
 }
 
 void launch_export(int N, const AtomState &a, const Grid &g, const Batch &B, double *pos, double *vel, double *force,

@@ -233,6 +233,9 @@ cudaError_t launch_rebuild(int N, int T, const Grid &g, const Batch &B, const fl
 void launch_iota(int N, int *perm, cudaStream_t s);
 void launch_export(int N, const AtomState &a, const Grid &g, const Batch &B, double *pos, double *vel, double *force,
                    cudaStream_t s);
+void launch_export_lists(int N, int T, const float4 *pos4, const int *perm, const ListBufs &L, const float4 *dtab,
+                         int ncode, int jbits, unsigned jmask, int cap, int *nn_r, int *j_r, float *d_r,
+                         int *nn_a, int *j_a, float *d_a, cudaStream_t s);
 // batches: structure index of every atom, the shift tables of all structures, and the
 // per-structure sums of per-atom energies and virials (caller order, per member)
 void launch_struct_ids(int n_struct, const int *offsets, int *sid, cudaStream_t s);

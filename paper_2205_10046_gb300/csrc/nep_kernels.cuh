@@ -373,6 +373,7 @@ __device__ __forceinline__ void for_pairs_plain(const unsigned *__restrict__ nl,
 template <class S, bool DESC_ONLY, int PREC, bool BATCH = false, int AB = kAtomBlock>
 __global__ void __launch_bounds__(AB, 1)
     atom_kernel(const AtomArgs a, const __grid_constant__ AnnConst<S> w) {
+  static_assert(PREC >= 0 && PREC <= 2, "network forms: 0 FP32, 1 BF16, 2 split BF16");
   static_assert(PREC == 0 || !DESC_ONLY, "the descriptor-only kernel has no network");
   static_assert(PREC == 0 || AB == 128, "the tensor-core network works on 128-atom tiles (UMMA M = 128)");
   // S_nk waits for the network in this thread's TMEM lane (128-atom blocks, whole groups of 8
@@ -448,13 +449,23 @@ __global__ void __launch_bounds__(AB, 1)
   // tensor-core network: operand tiles (128-byte aligned) and TMEM for S_nk and the results
   __shared__ __align__(8) uint64_t tc_mbar;
   __shared__ uint32_t tc_tmem;
+  // PREC 2 splits every operand value into two BF16 terms (hi + lo) and adds the products
+  // hi.hi + lo.hi + hi.lo: operand tiles A_lo, B1_lo, B2_lo follow the plain ones
+  constexpr bool SPLIT = PREC == 2;
   unsigned char *tileA = nullptr, *tileB1 = nullptr, *tileB2 = nullptr;
-  if constexpr (PREC == 1) {
+  unsigned char *tileAlo = nullptr, *tileB1lo = nullptr, *tileB2lo = nullptr;
+  if constexpr (PREC >= 1) {
     unsigned char *base = reinterpret_cast<unsigned char *>(S_s);
     base += (128u - (smem_addr(base) & 127u)) & 127u;
     tileA = base;
     tileB1 = tileA + S::TILE_A;
     tileB2 = tileB1 + S::TILE_B;
+    if constexpr (SPLIT) {
+      tileB1lo = tileB2 + S::TILE_B;
+      tileB2lo = tileB1lo + S::TILE_B;
+      tileAlo = tileB2lo + S::TILE_B;
+    }
+    // W0 tiles in global memory: B1, B2, then (split form) B1_lo, B2_lo
     const uint4 *b1t = a.tc_b1, *b2t = a.tc_b2;
     if (BATCH && a.pop_tc) {
       b1t = a.pop_tc + mem * a.s_tc;
@@ -463,6 +474,10 @@ __global__ void __launch_bounds__(AB, 1)
     for (int v = threadIdx.x; v < S::TILE_B / 16; v += blockDim.x) {
       reinterpret_cast<uint4 *>(tileB1)[v] = b1t[v];
       reinterpret_cast<uint4 *>(tileB2)[v] = b2t[v];
+      if constexpr (SPLIT) {
+        reinterpret_cast<uint4 *>(tileB1lo)[v] = b1t[v + 2 * (S::TILE_B / 16)];
+        reinterpret_cast<uint4 *>(tileB2lo)[v] = b2t[v + 2 * (S::TILE_B / 16)];
+      }
     }
     if (threadIdx.x == 0) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&tc_mbar)));
@@ -687,78 +702,104 @@ __global__ void __launch_bounds__(AB, 1)
           }
         }
       } else {
-        // BF16 tensor cores (tcgen05), FP32 accumulation in TMEM, one 128-atom tile per block
+        // BF16 tensor cores (tcgen05), FP32 accumulation in TMEM, one 128-atom tile per block.
+        // Every completion wait is bounded; if one runs out (all threads agree through the
+        // barrier), the block flags the error, waits once more (again bounded) so that the
+        // MMAs in flight finish before the TMEM is read or freed, and skips the rest of the
+        // network: its results are then invalid and the host reports NEP_ERR_TIMEOUT.
         static_assert(NK % 8 == 0, "S_nk is moved in groups of 8 TMEM columns");
         constexpr int KC1 = S::KP1 / 8, KC2 = S::KP2 / 8;
         const int r = threadIdx.x;
+        // operand row of 8 values: BF16 (round to nearest even) and, split form, the BF16 of
+        // the remainder
+        auto put8 = [&](unsigned char *hi, unsigned char *lo, int off, const float *x) {
+          uint32_t ph[4], pl[4];
+#pragma unroll
+          for (int h2 = 0; h2 < 4; ++h2) {
+            const __nv_bfloat162 b = __floats2bfloat162_rn(x[2 * h2], x[2 * h2 + 1]);
+            ph[h2] = *reinterpret_cast<const uint32_t *>(&b);
+            if constexpr (SPLIT)
+              pl[h2] = pack_bf16x2(x[2 * h2] - __low2float(b), x[2 * h2 + 1] - __high2float(b));
+          }
+          *reinterpret_cast<uint4 *>(hi + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+          if constexpr (SPLIT) *reinterpret_cast<uint4 *>(lo + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+        };
+        // one GEMM over K steps of 16: D = A.B^T (+ A_lo.B^T + A.B_lo^T in the split form)
+        auto gemm = [&](const unsigned char *A, const unsigned char *Alo, const unsigned char *B,
+                        const unsigned char *Blo, int ksteps, int KC, uint32_t idesc) {
+          for (int st = 0; st < ksteps; ++st) {
+            const uint64_t da = umma_desc(smem_addr(A) + 256 * st, 128, KC * 128);
+            const uint64_t db = umma_desc(smem_addr(B) + 256 * st, 128, KC * 128);
+            umma_bf16(tc_tmem + S::DCOL, da, db, idesc, st > 0 ? 1u : 0u);
+            if constexpr (SPLIT) {
+              umma_bf16(tc_tmem + S::DCOL, umma_desc(smem_addr(Alo) + 256 * st, 128, KC * 128), db, idesc, 1u);
+              umma_bf16(tc_tmem + S::DCOL, da, umma_desc(smem_addr(Blo) + 256 * st, 128, KC * 128), idesc, 1u);
+            }
+          }
+          umma_commit(&tc_mbar);
+        };
+        // wait for the commit of phase `parity`; false (block-uniform) if the wait ran out
+        auto tc_wait = [&](uint32_t parity) -> bool {
+          const bool ok = mbar_wait(&tc_mbar, parity);
+          if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) atomicOr(a.tc_err, 1);
+            mbar_wait(&tc_mbar, parity);
+            return false;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          return true;
+        };
         // q row -> operand tile A (bf16, K-major)
 #pragma unroll
         for (int kc = 0; kc < KC1; ++kc) {
-          uint32_t pk[4];
+          float x[8];
 #pragma unroll
-          for (int h2 = 0; h2 < 4; ++h2) {
-            const int k0 = 8 * kc + 2 * h2;
-            pk[h2] = pack_bf16x2(k0 < NDES ? q[k0] : 0.f, k0 + 1 < NDES ? q[k0 + 1] : 0.f);
-          }
-          *reinterpret_cast<uint4 *>(tileA + umma_off(r, 8 * kc, KC1)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          for (int j = 0; j < 8; ++j) x[j] = 8 * kc + j < NDES ? q[8 * kc + j] : 0.f;
+          put8(tileA, tileAlo, umma_off(r, 8 * kc, KC1), x);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (threadIdx.x == 0) {  // GEMM1: z = q . W0^T into TMEM columns DCOL ..
-          constexpr uint32_t idesc = umma_idesc_bf16<kAtomBlock, S::NP1>();
-#pragma unroll
-          for (int st = 0; st < S::KP1 / 16; ++st)
-            umma_bf16(tc_tmem + S::DCOL, umma_desc(smem_addr(tileA) + 256 * st, 128, KC1 * 128),
-                      umma_desc(smem_addr(tileB1) + 256 * st, 128, KC1 * 128), idesc, st > 0 ? 1u : 0u);
-          umma_commit(&tc_mbar);
-        }
+        if (threadIdx.x == 0)  // GEMM1: z = q . W0^T into TMEM columns DCOL ..
+          gemm(tileA, tileAlo, tileB1, tileB1lo, S::KP1 / 16, KC1, umma_idesc_bf16<kAtomBlock, S::NP1>());
         __syncwarp();
-        if (!mbar_wait(&tc_mbar, 0)) atomicOr(a.tc_err, 1);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // tanh layer from this row of z; beta = w1 (1 - h^2) -> operand tile A (reused)
+        if (tc_wait(0)) {
+          // tanh layer from this row of z; beta = w1 (1 - h^2) -> operand tile A (reused)
 #pragma unroll
-        for (int c8 = 0; c8 < S::NP1 / 8; ++c8) {
-          float z[8];
-          tmem_ld8(tmem_row + S::DCOL + 8 * c8, z);
-          float bt[8];
+          for (int c8 = 0; c8 < S::NP1 / 8; ++c8) {
+            float z[8];
+            tmem_ld8(tmem_row + S::DCOL + 8 * c8, z);
+            float bt[8];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int mu = 8 * c8 + j;
-            bt[j] = 0.f;
-            if (mu < S::H) {
-              const float h = tanhf(z[j] - b0_s[mu]);
-              U = __fmaf_rn(w1_s[mu], h, U);
-              bt[j] = w1_s[mu] * (1.f - h * h);
+            for (int j = 0; j < 8; ++j) {
+              const int mu = 8 * c8 + j;
+              bt[j] = 0.f;
+              if (mu < S::H) {
+                const float h = tanhf(z[j] - b0_s[mu]);
+                U = __fmaf_rn(w1_s[mu], h, U);
+                bt[j] = w1_s[mu] * (1.f - h * h);
+              }
+            }
+            put8(tileA, tileAlo, umma_off(r, 8 * c8, KC2), bt);
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncthreads();
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          if (threadIdx.x == 0)  // GEMM2: dq = beta . W0 into the same TMEM columns
+            gemm(tileA, tileAlo, tileB2, tileB2lo, S::KP2 / 16, KC2, umma_idesc_bf16<kAtomBlock, S::NP2>());
+          __syncwarp();
+          if (tc_wait(1)) {
+#pragma unroll
+            for (int c8 = 0; c8 < S::NP2 / 8; ++c8) {
+              float v[8];
+              tmem_ld8(tmem_row + S::DCOL + 8 * c8, v);
+#pragma unroll
+              for (int j = 0; j < 8; ++j)
+                if (8 * c8 + j < NDES) dq[8 * c8 + j] = v[j];
             }
           }
-          *reinterpret_cast<uint4 *>(tileA + umma_off(r, 8 * c8, KC2)) =
-              make_uint4(pack_bf16x2(bt[0], bt[1]), pack_bf16x2(bt[2], bt[3]), pack_bf16x2(bt[4], bt[5]),
-                         pack_bf16x2(bt[6], bt[7]));
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (threadIdx.x == 0) {  // GEMM2: dq = beta . W0 into the same TMEM columns
-          constexpr uint32_t idesc = umma_idesc_bf16<kAtomBlock, S::NP2>();
-#pragma unroll
-          for (int st = 0; st < S::KP2 / 16; ++st)
-            umma_bf16(tc_tmem + S::DCOL, umma_desc(smem_addr(tileA) + 256 * st, 128, KC2 * 128),
-                      umma_desc(smem_addr(tileB2) + 256 * st, 128, KC2 * 128), idesc, st > 0 ? 1u : 0u);
-          umma_commit(&tc_mbar);
-        }
-        __syncwarp();
-        if (!mbar_wait(&tc_mbar, 1)) atomicOr(a.tc_err, 1);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-        for (int c8 = 0; c8 < S::NP2 / 8; ++c8) {
-          float v[8];
-          tmem_ld8(tmem_row + S::DCOL + 8 * c8, v);
-#pragma unroll
-          for (int j = 0; j < 8; ++j)
-            if (8 * c8 + j < NDES) dq[8 * c8 + j] = v[j];
         }
       }
       if constexpr (BATCH) U -= b1_s;
@@ -1184,7 +1225,10 @@ size_t atom_smem_bytes(int T, int ncode, int prec, int ab = kAtomBlock) {
   // the last region: BF16 operand tiles (tensor-core network), nothing (S_nk in TMEM) or the
   // per-thread S_nk blocks
   const bool tm = ab == 128 && S::NK % 8 == 0;
-  const size_t last = prec == 1 ? (size_t)S::TILE_A + 2 * S::TILE_B + 128 : tm ? 0 : sizeof(float) * S::SPT * ab;
+  const size_t last = prec == 1   ? (size_t)S::TILE_A + 2 * S::TILE_B + 128
+                      : prec == 2 ? 2 * (size_t)S::TILE_A + 4 * S::TILE_B + 128
+                      : tm        ? 0
+                                  : sizeof(float) * S::SPT * ab;
   return sizeof(float4) * ncode + sizeof(float) * (size_t)S::off_S(prec, T) + last;
 }
 
@@ -1240,6 +1284,7 @@ cudaError_t launch_atom(const AtomArgs &a, const ModelF &mf, const float *w0, co
   };
   if (descriptor_only) return go(atom_kernel<S, true, 0>);
   if (a.precision == 1) return go(atom_kernel<S, false, 1>);
+  if (a.precision == 2) return go(atom_kernel<S, false, 2>);
   return go(atom_kernel<S, false, 0>);
 }
 
@@ -1264,7 +1309,7 @@ cudaError_t launch_atom_batch(const AtomArgs &a, const ModelF &mf, const float *
                               const float *w1, float b1, int members, int block, cudaStream_t st) {
   if (a.N <= 0 || members <= 0) return cudaSuccess;
   if (block != 64 && block != 128) return cudaErrorInvalidValue;
-  if (a.precision == 1 && block != 128) return cudaErrorInvalidValue;
+  if (a.precision >= 1 && block != 128) return cudaErrorInvalidValue;
   AnnConst<S> w;
   for (int v = 0; v < S::H * S::NDES; ++v) w.w0[v] = w0 ? w0[v] : 0.f;
   for (int v = 0; v < S::H; ++v) {
@@ -1286,6 +1331,7 @@ cudaError_t launch_atom_batch(const AtomArgs &a, const ModelF &mf, const float *
     return cudaGetLastError();
   };
   if (a.precision == 1) return go(atom_kernel<S, false, 1, true, 128>);
+  if (a.precision == 2) return go(atom_kernel<S, false, 2, true, 128>);
   if (block == 64) return go(atom_kernel<S, false, 0, true, 64>);
   return go(atom_kernel<S, false, 0, true, 128>);
 }

@@ -308,8 +308,8 @@ NEP_SERVER_API int nep_server_create(const nep_params *params, const nep_server_
   }
   *out = nullptr;
   if (cfg->workers < 1 || cfg->workers > 65536 || cfg->memory_budget == 0 ||
-      (cfg->precision != 0 && cfg->precision != 1)) {
-    nep::set_create_error("need 1 <= workers <= 65536, memory_budget > 0, precision 0 or 1");
+      cfg->precision < 0 || cfg->precision > 2) {
+    nep::set_create_error("need 1 <= workers <= 65536, memory_budget > 0, precision 0, 1 or 2");
     return NEP_ERR_ARG;
   }
   if (!params->mass) {

@@ -117,6 +117,7 @@ _SIGS = {
     "nep_kernel_name": (C.c_char_p, [C.c_int]),
     "nep_kernel_times": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int]),
     "nep_supported": (C.c_int, [C.POINTER(C.c_int), C.c_int]),
+    "nep_export_lists": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P]),
     "nep_descriptors_static": (C.c_int, [C.POINTER(nep_params), C.c_int, _P, _P, _P, _P, _P]),
     "nep_server_create": (C.c_int, [C.POINTER(nep_params), C.POINTER(nep_server_config), C.POINTER(_P)]),
     "nep_server_submit": (C.c_int, [_P, C.POINTER(nep_job), C.POINTER(C.c_longlong)]),
@@ -444,6 +445,20 @@ def md_get_state_host(h, n: int):
     rc = load().md_get_state_host(h, pos.ctypes.data, vel.ctypes.data, F.ctypes.data)
     _check(rc, h)
     return pos, vel, F
+
+
+def nep_export_lists(h, n_atoms: int, cap: int | None = None) -> dict:
+    """Neighbour lists of the last build in caller order (host numpy arrays): nn_r [N],
+    j_r [N, cap], d_r [N, cap, 3] (FP32 pair vectors), and the same for the angular list."""
+    if cap is None:
+        st = nep_get_stats(h)
+        cap = max(1, int(st["max_radial"]), int(st["max_angular"]))
+    n = int(n_atoms)
+    out = dict(nn_r=np.zeros(n, np.int32), j_r=np.zeros((n, cap), np.int32), d_r=np.zeros((n, cap, 3), np.float32),
+               nn_a=np.zeros(n, np.int32), j_a=np.zeros((n, cap), np.int32), d_a=np.zeros((n, cap, 3), np.float32))
+    rc = load().nep_export_lists(h, int(cap), *(out[k].ctypes.data for k in ("nn_r", "j_r", "d_r", "nn_a", "j_a", "d_a")))
+    _check(rc, h)
+    return out
 
 
 def nep_get_stats(h) -> dict:

@@ -339,3 +339,34 @@ def batch_structures(n_struct: int = 4096, seed: int = 3, n_min: int = 8, n_max:
     parts = [random_structure(int(seeds[s]), int(sizes[s]), n_types_model, sigma, max_shear)
              for s in range(n_struct)]
     return concat_structures(parts, seeds)
+
+
+def subcell_cluster(w: Workload, reps: int, cells: int = 8, halo: float | None = None):
+    """The atoms of conventional cells [0, cells)^3 of a cubic ``reps``^3 supercell workload
+    (lattice index order of ``lattice``), cut out with every atom within ``halo`` (default
+    2 r_c^R: the neighbours of the neighbours) as an open cluster in a cubic box wide enough
+    that no periodic image comes within r_c^R. Positions are the workload's own, taken by the
+    minimum image relative to the subcell centre.
+
+    Returns (pos [M, 3], types [M], box [3, 3], inner [n_inner] indices into the cluster,
+    sel [n_inner] the same atoms' indices in the workload), inner and sel in workload order."""
+    L = float(w.box[0, 0])
+    if not np.allclose(w.box, np.diag(np.diag(w.box))) or not np.allclose(np.diag(w.box), L):
+        raise ValueError("subcell_cluster needs a cubic box")
+    a = L / reps
+    nb = w.n_atoms // reps ** 3
+    rc = w.model.rc_radial
+    halo = 2.0 * rc if halo is None else float(halo)
+    ix, iy, iz = np.meshgrid(np.arange(cells), np.arange(cells), np.arange(cells), indexing="ij")
+    cell_idx = ((ix * reps + iy) * reps + iz).ravel()
+    sel = np.sort((cell_idx[:, None] * nb + np.arange(nb)[None, :]).ravel())
+    centre = np.full(3, 0.5 * cells * a)
+    d = w.pos - centre
+    d -= L * np.round(d / L)
+    half = 0.5 * cells * a + halo
+    keep = np.nonzero(np.all(np.abs(d) < half, axis=1))[0]
+    side = 2.0 * half + 2.0 * rc + 5.0
+    inner = np.searchsorted(keep, sel)
+    if not np.array_equal(keep[inner], sel):
+        raise ValueError("subcell atoms moved outside the cut")
+    return d[keep] + 0.5 * side, w.types[keep].copy(), np.eye(3) * side, inner, sel

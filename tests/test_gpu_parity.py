@@ -237,19 +237,3 @@ def test_md_rebuilds_keep_forces_exact(torch_cuda):
     etot = e[:, 0] + e[:, 1]
     assert np.ptp(etot) / w.n_atoms < 1e-4
     h.close()
-
-
-def test_si_8m_atoms_sampled_against_oracle(torch_cuda):
-    """The large single-GPU workload (100^3 diamond cells, 8,000,000 atoms): forces, energies and
-    virials of sampled atoms (including both ends of the index range) against the oracle, and
-    the totals' consistency."""
-    w = W.si_diamond(100, seed=0, with_velocities=False)
-    g = _gpu_compute(torch_cuda, w.model, w.pos, w.types, w.box)
-    rng = np.random.default_rng(1)
-    sel = np.r_[0, np.sort(rng.choice(w.n_atoms, 6, replace=False)), w.n_atoms - 1]
-    U, F, Wv = oracle.compute(w.model, w.pos, w.types, w.box, sel=sel)
-    assert _rel(g["F"][sel], F) <= REL_F
-    np.testing.assert_allclose(g["U"][sel], U, rtol=0, atol=2e-5)
-    assert _rel(g["W"][sel], Wv) <= REL_F
-    assert np.abs(g["F"].sum(0)).max() < 1e-6 * np.abs(g["F"]).sum() / 3
-    assert abs(g["E"][0] - g["U"].sum()) < 1e-9 * abs(g["E"][0])

@@ -423,3 +423,20 @@ def test_per_atom_virial_orientation_from_site_energy_differences():
         assert np.abs(Wi - Wi.T).max() > 5e-6  # the per-atom virial is not symmetric here
         for c, (a, b) in enumerate(ordr):
             assert Wv[i, c] == pytest.approx(Wi[a, b], rel=1e-6, abs=1e-9)
+
+
+def test_subcell_cluster_reproduces_the_periodic_box():
+    """The cut-out used for the 8,000,000-atom workload (inner cells plus a 2 r_c halo, as an
+    open cluster) gives the inner atoms exactly the energies, forces and virials they have in
+    the periodic box; a halo of only r_c does not (their neighbours' environments are cut)."""
+    w = W.si_diamond(8, seed=0, with_velocities=False)  # 43.4 A box, 4096 atoms
+    cpos, ctypes, cbox, inner, sel = W.subcell_cluster(w, 8, 2)
+    assert sel.shape[0] == 2 ** 3 * 8
+    U0, F0, W0 = oracle.compute(w.model, w.pos, w.types, w.box, sel=sel)
+    U1, F1, W1 = oracle.compute(w.model, cpos, ctypes, cbox, sel=inner)
+    np.testing.assert_allclose(U1, U0, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(F1, F0, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(W1, W0, rtol=0, atol=1e-12)
+    cpos2, ctypes2, cbox2, inner2, _ = W.subcell_cluster(w, 8, 2, halo=w.model.rc_radial)
+    _, F2, _ = oracle.compute(w.model, cpos2, ctypes2, cbox2, sel=inner2)
+    assert np.abs(F2 - F0).max() > 1e-6
