@@ -17,7 +17,7 @@ OUT = os.path.join(HERE, "libnep.so")
 BUILD = os.path.join(ROOT, "_build", "libnep")
 
 SOURCES = ["nep_api.cu", "nep_build.cu", "nep_static.cu", "nep_shape_si.cu", "nep_shape_pbte.cu",
-           "nep_shape_mixed.cu", "nep_batch_si.cu", "nep_batch_pbte.cu", "nep_batch_mixed.cu", "nep_server.cu"]
+           "nep_shape_mixed.cu", "nep_batch_si.cu", "nep_batch_pbte.cu", "nep_batch_mixed.cu", "nep_server.cu", "nep_generic.cu"]
 HEADERS = ["nep_internal.cuh", "nep_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code is compiled without FMA contraction, so host-side geometry (image shift tables)

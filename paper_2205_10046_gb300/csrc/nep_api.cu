@@ -174,10 +174,35 @@ int check_params(const nep_params *p, const ShapeOps **ops_out, const char **err
       *ops_out = o;
   }
   if (!*ops_out) {
-    *err = "no kernel compiled for these hyper-parameters";
-    return NEP_ERR_UNSUPPORTED;
+    // no compiled instantiation: the kernels that take the shape at run time
+    if (p->n_max_radial > kGenMaxN || p->n_max_angular > kGenMaxN || p->basis_radial > kGenMaxN ||
+        p->basis_angular > kGenMaxN || p->n_neuron > kGenMaxNeu) {
+      *err = "shape beyond the limits of the run-time-shape kernels (n_max, N_bas <= 19, N_neu <= 256)";
+      return NEP_ERR_UNSUPPORTED;
+    }
+    *ops_out = shape_generic();
   }
   return NEP_OK;
+}
+
+// Descriptor length N_des (Sec. II C) of a validated parameter set.
+int n_des_of(const nep_params *p) {
+  const int nb = p->l_max_3b + (p->l_max_4b >= 2 ? 1 : 0) + (p->l_max_5b >= 1 ? 1 : 0);
+  return (p->n_max_radial + 1) + (p->n_max_angular + 1) * nb;
+}
+
+// Run-time shape fields of the kernel arguments (read only by the run-time-shape kernels).
+void set_shape_args(AtomArgs &a, const nep_params &p, const float *ann) {
+  a.gR = p.n_max_radial;
+  a.gKR = p.basis_radial;
+  a.gA = p.n_max_angular;
+  a.gKA = p.basis_angular;
+  a.gH = p.n_neuron;
+  a.gL3 = p.l_max_3b;
+  a.gL4 = p.l_max_4b;
+  a.gL5 = p.l_max_5b;
+  a.gD = n_des_of(&p);
+  a.ann = ann;
 }
 
 }  // namespace nep
@@ -325,6 +350,8 @@ struct nep_handle {
   int precision = 0;        // network arithmetic: 0 FP32 SIMT, 1 BF16 tensor cores
   int graph_prec = 0;
   DevBuf<uint4> d_tc;       // BF16 W0 operand tiles for the tensor-core network
+  DevBuf<float> d_ann;      // FP32 network [w0 | b0 | w1 | b1] (run-time-shape kernels)
+  bool generic = false;     // no compiled instantiation of this shape
   bool graph_cond_used = true;
   // batches of structures: layout of the last batch (reused while unchanged)
   int nb_struct = 0;
@@ -567,6 +594,9 @@ AtomArgs make_args(nep_handle *h, int N) {
   a.tc_b1 = h->d_tc.p;
   a.tc_b2 = h->d_tc.p ? h->d_tc.p + (size_t)h->ops->np1 * h->ops->kp1 * 2 / 16 : nullptr;
   a.tc_err = h->status.p ? &h->status.p->tc_timeout : nullptr;
+  a.gR = h->nR; a.gKR = h->KR; a.gA = h->nA; a.gKA = h->KA; a.gH = h->H;
+  a.gL3 = h->L3; a.gL4 = h->L4; a.gL5 = h->L5; a.gD = h->n_des;
+  a.ann = h->d_ann.p;
   return a;
 }
 
@@ -1176,7 +1206,8 @@ int nep_create(const nep_params *p, nep_handle **out) {
   h->ops = ops;
   h->T = p->n_types; h->nR = p->n_max_radial; h->nA = p->n_max_angular; h->KR = p->basis_radial;
   h->KA = p->basis_angular; h->L3 = p->l_max_3b; h->L4 = p->l_max_4b; h->L5 = p->l_max_5b; h->H = p->n_neuron;
-  h->n_des = ops->n_des;
+  h->n_des = n_des_of(p);
+  h->generic = ops == shape_generic();
   h->rcR = p->rc_radial;
   h->rcA = p->rc_angular;
   h->skin = p->skin > 0 ? p->skin : 1.0;
@@ -1211,6 +1242,17 @@ int nep_create(const nep_params *p, nep_handle **out) {
   for (int t = 0; t < T && !h->mass.empty(); ++t) {
     imk[t] = 1.0 / (h->mass[t] * kKappa);
     mkh[t] = 0.5 * h->mass[t] * kKappa;
+  }
+  if (h->generic) {  // the run-time-shape kernels read the network from global memory
+    std::vector<float> ann(h->w0);
+    ann.insert(ann.end(), h->b0.begin(), h->b0.end());
+    ann.insert(ann.end(), h->w1.begin(), h->w1.end());
+    ann.push_back(h->b1);
+    if (h->d_ann.ensure(ann.size()) != cudaSuccess ||
+        cudaMemcpy(h->d_ann.p, ann.data(), ann.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+      nep_destroy(h);
+      return fail(nullptr, NEP_ERR_OOM, "device alloc failed");
+    }
   }
   cudaMemcpy(h->d_cR.p, h->cR.data(), h->cR.size() * sizeof(float), cudaMemcpyHostToDevice);
   cudaMemcpy(h->d_cA.p, h->cA.data(), h->cA.size() * sizeof(float), cudaMemcpyHostToDevice);
@@ -1250,7 +1292,7 @@ int nep_destroy(nep_handle *h) {
   h->e_slots.release(); h->e_slots_ck.release(); h->e_energy.release(); h->e_virial.release(); h->e_u.release();
   h->e_w.release(); h->e_xck.release(); h->e_vck.release(); h->e_table.release();
   h->stage_e.release(); h->stage_g.release();
-  h->p_ang.release(); h->e_rad.release(); h->status.release(); h->d_tc.release();
+  h->p_ang.release(); h->e_rad.release(); h->status.release(); h->d_tc.release(); h->d_ann.release();
   h->d_grids.release(); h->d_sid.release(); h->d_offsets.release(); h->b_e.release(); h->b_w.release();
   if (h->b_graph) cudaGraphExecDestroy(h->b_graph);
   if (h->e_graph) cudaGraphExecDestroy(h->e_graph);
@@ -1542,8 +1584,9 @@ int nep_autotune(nep_handle *h, int n_struct, const int *offsets, const double *
   int best_ab = 128, best_gb = 128;
   const int abs_[2] = {64, 128}, gbs[3] = {64, 128, 256};
   for (int ia = 0; ia < 2 && !rc; ++ia) {
-    if (h->precision >= 1 && abs_[ia] != 128) continue;
+    if ((h->precision >= 1 || h->generic) && abs_[ia] != 128) continue;
     for (int ig = 0; ig < 3 && !rc; ++ig) {
+      if (h->generic && gbs[ig] != 128) continue;  // one block shape for the run-time-shape kernels
       h->tune.atom_block = abs_[ia];
       h->tune.gather_block = gbs[ig];
       float t = 0.f;
@@ -1595,6 +1638,8 @@ int nep_set_tuning(nep_handle *h, const nep_tuning *t) {
     return fail(h, NEP_ERR_ARG, "atom_block must be 0, 64 or 128");
   if (t->gather_block != 0 && t->gather_block != 64 && t->gather_block != 128 && t->gather_block != 256)
     return fail(h, NEP_ERR_ARG, "gather_block must be 0, 64, 128 or 256");
+  if (h->generic && ((t->atom_block != 0 && t->atom_block != 128) || (t->gather_block != 0 && t->gather_block != 128)))
+    return fail(h, NEP_ERR_UNSUPPORTED, "the run-time-shape kernels take 128 atoms per CTA");
   h->tune.members = t->members_per_launch;
   h->tune.atom_block = t->atom_block;
   h->tune.gather_block = t->gather_block;
@@ -2185,6 +2230,8 @@ int nep_set_precision(nep_handle *h, int mode) {
   if (!valid_handle(h)) return NEP_ERR_ARG;
   if (mode < 0 || mode > 2)
     return fail(h, NEP_ERR_ARG, "precision must be 0 (FP32), 1 (BF16 tensor cores) or 2 (split BF16)");
+  if (mode >= 1 && h->generic)
+    return fail(h, NEP_ERR_UNSUPPORTED, "the tensor-core forms need a compiled hyper-parameter shape");
   if (mode >= 1 && !h->d_tc.p) {
     // W0 as the two GEMM operands, K-major no-swizzle UMMA layout, zero padded:
     //   B1 [NP1 x KP1]: (mu, nu) -> w0[mu][nu];  B2 [KP1 x NP1]: (nu, mu) -> w0[mu][nu]

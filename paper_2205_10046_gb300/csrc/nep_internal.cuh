@@ -193,6 +193,10 @@ struct AtomArgs {
   double *heat;            // [N][3] caller order, or null
   // batched serving engine: per-structure kick (phase, time step, FIRE state), or null
   const EngineSlot *slots;
+  // model shape at run time and the FP32 network [w0 | b0 | w1 | b1] on the device: read only
+  // by the kernels that take the shape at run time (shapes without a compiled instantiation)
+  int gR, gKR, gA, gKA, gH, gL3, gL4, gL5, gD;
+  const float *ann;
 };
 
 // Model constants of one handle, FP32.
@@ -222,6 +226,11 @@ struct ShapeOps {
 
 int shape_count();
 const ShapeOps *shape_at(int i);
+// kernels that take the model shape at run time (any shape within these limits)
+constexpr int kGenMaxN = 19;     // n_max^R, n_max^A, N_bas^R, N_bas^A
+constexpr int kGenMaxNeu = 256;  // N_neu
+constexpr int kGenMaxDes = (kGenMaxN + 1) * 7;
+const ShapeOps *shape_generic();
 
 // Host helpers shared by the handle-based and the static-scratch entry points.
 struct Grid;

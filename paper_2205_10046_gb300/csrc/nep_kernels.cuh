@@ -976,6 +976,87 @@ __global__ void __launch_bounds__(AB, 1)
   }
 }
 
+// Epilogue of the gather kernels for atom i: outputs in the caller's order, the squared force
+// error of Eq. loss, the second velocity-Verlet half-kick with the kinetic energy, and the
+// heat current J_i = W_i . v_i (Eq. Ji); part[] collects the block sums.
+__device__ __forceinline__ void gather_epilogue(const AtomArgs &a, int i, const float4 &pi, int ti, int mem,
+                                                float fx, float fy, float fz, const float *w, double *part) {
+  const double Fx = fx, Fy = fy, Fz = fz;
+  const size_t io = mem * a.s_out + (a.perm ? (size_t)a.perm[i] : (size_t)i);
+  if (a.force) {
+    a.force[3 * io] = Fx;
+    a.force[3 * io + 1] = Fy;
+    a.force[3 * io + 2] = Fz;
+  }
+  if (a.virial) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) a.virial[9 * io + c] = (double)w[c];
+  }
+#pragma unroll
+  for (int c = 0; c < 9; ++c) part[2 + c] = (double)w[c];
+  // velocity of the heat current: after the kick below (MD), or given by the caller
+  double vh[3] = {0.0, 0.0, 0.0};
+  if (a.vel_in) {
+    const double *vi = a.vel_in + 3 * (a.perm ? (size_t)a.perm[i] : (size_t)i);
+    vh[0] = vi[0]; vh[1] = vi[1]; vh[2] = vi[2];
+  }
+  if (a.f_tar) {  // squared force error against target forces (the force term of Eq. loss)
+    const double *ft = a.f_tar + 3 * (a.perm ? (size_t)a.perm[i] : (size_t)i);
+    const double ex = Fx - ft[0], ey = Fy - ft[1], ez = Fz - ft[2];
+    part[11] = ex * ex + ey * ey + ez * ez;
+  }
+  bool kick = a.md_kick && !(a.fire && a.fire->converged);
+  double hdt = a.fire ? 0.5 * a.fire->dt : a.half_dt;
+  if (a.slots) {  // batched engine: the structure's own phase and time step
+    const EngineSlot &sl = a.slots[struct_of(pi)];
+    kick = sl.phase == 1 && !(sl.kind == kJobFire && sl.fire.converged);
+    hdt = 0.5 * (sl.kind == kJobFire ? sl.fire.dt : sl.dt);
+  }
+  if (kick) {  // second half-kick of velocity Verlet, kinetic energy
+    double *v = a.vel + 3 * (size_t)i;
+    const double s = hdt * a.inv_mass_kappa[ti];
+    const double vx = v[0] + s * Fx, vy = v[1] + s * Fy, vz = v[2] + s * Fz;
+    v[0] = vx; v[1] = vy; v[2] = vz;
+    part[1] = a.mass_kappa_half[ti] * (vx * vx + vy * vy + vz * vz);
+    vh[0] = vx; vh[1] = vy; vh[2] = vz;
+  } else if (a.md_kick || a.slots) {  // converged FIRE or no step: velocities unchanged
+    const double *v = a.vel + 3 * (size_t)i;
+    part[1] = a.mass_kappa_half[ti] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    vh[0] = v[0]; vh[1] = v[1]; vh[2] = v[2];
+  }
+  // J_i = W_i . v_i, W_i[a][b] in the order xx, yy, zz, xy, xz, yz, yx, zx, zy (Eq. Ji)
+  const double Jx = (double)w[0] * vh[0] + (double)w[3] * vh[1] + (double)w[4] * vh[2];
+  const double Jy = (double)w[6] * vh[0] + (double)w[1] * vh[1] + (double)w[5] * vh[2];
+  const double Jz = (double)w[7] * vh[0] + (double)w[8] * vh[1] + (double)w[2] * vh[2];
+  part[12] = Jx;
+  part[13] = Jy;
+  part[14] = Jz;
+  if (a.heat) {
+    a.heat[3 * io] = Jx;
+    a.heat[3 * io + 1] = Jy;
+    a.heat[3 * io + 2] = Jz;
+  }
+}
+
+// Deterministic block sums of (KE, W[9], force error, J[3]) over a block of GB threads.
+template <int GB>
+__device__ __forceinline__ void gather_block_sums(const AtomArgs &a, int mem, const double *part) {
+  __shared__ double red[GB / 32][kReduceSlots];
+#pragma unroll
+  for (int s = 1; s < kReduceSlots; ++s) {
+    double v = part[s];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][s] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kReduceSlots && threadIdx.x >= 1) {
+    double s = 0.0;
+    for (int wv = 0; wv < GB / 32; ++wv) s += red[wv][threadIdx.x];
+    a.partial_gather[((size_t)mem * gridDim.x + blockIdx.x) * kReduceSlots + threadIdx.x] = s;
+  }
+}
+
 // ------------------------------------------------------------------------ gather kernel
 template <class S, bool BATCH = false, int GB = kGatherBlock>
 __global__ void __launch_bounds__(GB)
@@ -1129,77 +1210,9 @@ __global__ void __launch_bounds__(GB)
         }
       }
     }
-    const double Fx = fx, Fy = fy, Fz = fz;
-    const size_t io = mem * a.s_out + (a.perm ? (size_t)a.perm[i] : (size_t)i);
-    if (a.force) {
-      a.force[3 * io] = Fx;
-      a.force[3 * io + 1] = Fy;
-      a.force[3 * io + 2] = Fz;
-    }
-    if (a.virial) {
-#pragma unroll
-      for (int c = 0; c < 9; ++c) a.virial[9 * io + c] = (double)w[c];
-    }
-#pragma unroll
-    for (int c = 0; c < 9; ++c) part[2 + c] = (double)w[c];
-    // velocity of the heat current: after the kick below (MD), or given by the caller
-    double vh[3] = {0.0, 0.0, 0.0};
-    if (a.vel_in) {
-      const double *vi = a.vel_in + 3 * (a.perm ? (size_t)a.perm[i] : (size_t)i);
-      vh[0] = vi[0]; vh[1] = vi[1]; vh[2] = vi[2];
-    }
-    if (a.f_tar) {  // squared force error against target forces (the force term of Eq. loss)
-      const double *ft = a.f_tar + 3 * (a.perm ? (size_t)a.perm[i] : (size_t)i);
-      const double ex = Fx - ft[0], ey = Fy - ft[1], ez = Fz - ft[2];
-      part[11] = ex * ex + ey * ey + ez * ez;
-    }
-    bool kick = a.md_kick && !(a.fire && a.fire->converged);
-    double hdt = a.fire ? 0.5 * a.fire->dt : a.half_dt;
-    if (a.slots) {  // batched engine: the structure's own phase and time step
-      const EngineSlot &sl = a.slots[struct_of(pi)];
-      kick = sl.phase == 1 && !(sl.kind == kJobFire && sl.fire.converged);
-      hdt = 0.5 * (sl.kind == kJobFire ? sl.fire.dt : sl.dt);
-    }
-    if (kick) {  // second half-kick of velocity Verlet, kinetic energy
-      double *v = a.vel + 3 * (size_t)i;
-      const double s = hdt * a.inv_mass_kappa[ti];
-      const double vx = v[0] + s * Fx, vy = v[1] + s * Fy, vz = v[2] + s * Fz;
-      v[0] = vx; v[1] = vy; v[2] = vz;
-      part[1] = a.mass_kappa_half[ti] * (vx * vx + vy * vy + vz * vz);
-      vh[0] = vx; vh[1] = vy; vh[2] = vz;
-    } else if (a.md_kick || a.slots) {  // converged FIRE or no step: velocities unchanged
-      const double *v = a.vel + 3 * (size_t)i;
-      part[1] = a.mass_kappa_half[ti] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-      vh[0] = v[0]; vh[1] = v[1]; vh[2] = v[2];
-    }
-    // J_i = W_i . v_i, W_i[a][b] in the order xx, yy, zz, xy, xz, yz, yx, zx, zy (Eq. Ji)
-    const double Jx = (double)w[0] * vh[0] + (double)w[3] * vh[1] + (double)w[4] * vh[2];
-    const double Jy = (double)w[6] * vh[0] + (double)w[1] * vh[1] + (double)w[5] * vh[2];
-    const double Jz = (double)w[7] * vh[0] + (double)w[8] * vh[1] + (double)w[2] * vh[2];
-    part[12] = Jx;
-    part[13] = Jy;
-    part[14] = Jz;
-    if (a.heat) {
-      a.heat[3 * io] = Jx;
-      a.heat[3 * io + 1] = Jy;
-      a.heat[3 * io + 2] = Jz;
-    }
+    gather_epilogue(a, i, pi, ti, mem, fx, fy, fz, w, part);
   }
-  // deterministic block sums of (KE, W[9], force error)
-  __shared__ double red[GB / 32][kReduceSlots];
-#pragma unroll
-  for (int s = 1; s < kReduceSlots; ++s) {
-    double v = part[s];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][s] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < kReduceSlots && threadIdx.x >= 1) {
-    double s = 0.0;
-    for (int wv = 0; wv < GB / 32; ++wv) s += red[wv][threadIdx.x];
-    a.partial_gather[((size_t)mem * gridDim.x + blockIdx.x) * kReduceSlots + threadIdx.x] = s;
-  }
+  gather_block_sums<GB>(a, mem, part);
 }
 
 // ------------------------------------------------------------------------ launchers

@@ -18,6 +18,8 @@
 
 namespace nep {
 int check_params(const nep_params *p, const ShapeOps **ops_out, const char **err);
+int n_des_of(const nep_params *p);
+void set_shape_args(AtomArgs &a, const nep_params &p, const float *ann);
 void set_create_error(const char *msg);  // read back by nep_last_error(NULL)
 }
 
@@ -120,7 +122,7 @@ int nep_descriptors_static(const nep_params *params, int n_atoms, const double *
   cudaStream_t s = (cudaStream_t)stream;
   const int N = n_atoms, T = params->n_types;
   const int nR = params->n_max_radial, KR = params->basis_radial, nA = params->n_max_angular,
-            KA = params->basis_angular, H = params->n_neuron, D = ops->n_des;
+            KA = params->basis_angular, H = params->n_neuron, D = n_des_of(params);
   const double skin = params->skin > 0 ? params->skin : 1.0;
 
   // host-side model tables (fixed-size, on the stack)
@@ -238,6 +240,7 @@ int nep_descriptors_static(const nep_params *params, int n_atoms, const double *
   args.c_a = dcA;
   args.perm = a.perm;
   args.q_out = q;
+  set_shape_args(args, *params, nullptr);  // the descriptor pass reads no network
   const cudaError_t e = ops->atom(args, mf, w0, b0, w1, (float)params->b1, 1, s);
   if (e != cudaSuccess) return cuda_err(e, "descriptor kernel");
   return NEP_OK;
