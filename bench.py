@@ -50,7 +50,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["pbte", "si", "si_large"], default="si_large")
+    ap.add_argument("--workload", choices=["pbte", "si", "si_medium", "si_large"], default="si_large",
+                    help="si_medium (40^3 cells, 512,000 atoms) is the profiling case of the si_large kernels")
     ap.add_argument("--pbte-steps", type=int, default=1000, help="timed steps of the extra PbTe key (0: skip)")
     ap.add_argument("--skin", type=float, default=0.4, help="neighbour-list skin (A) of the MD workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -75,12 +76,15 @@ def make_workload(name: str):
         return W.pbte_rocksalt(32, seed=1)
     if name == "si":
         return W.si_diamond(3, seed=0)
+    if name == "si_medium":
+        return W.si_diamond(40, seed=0, n_steps=100, dt_fs=1.0)
     return W.si_diamond(100, seed=0, n_steps=100, dt_fs=1.0)
 
 
 def workload_config(w, name):
     desc = {"pbte": "rocksalt PbTe 32x32x32 conventional cells, a=6.46 A, sigma=0.1 A, 300 K, dt=2 fs",
             "si": "diamond Si 3x3x3 conventional cells, a=5.43 A, sigma=0.05 A, 300 K, dt=1 fs",
+            "si_medium": "diamond Si 40x40x40 conventional cells, a=5.43 A, sigma=0.05 A, 300 K, dt=1 fs",
             "si_large": "diamond Si 100x100x100 conventional cells, a=5.43 A, sigma=0.05 A, 300 K, dt=1 fs"}[name]
     m = w.model
     return {"workload": f"{w.name} ({w.n_atoms} atoms): {desc}", "n_atoms": w.n_atoms,
@@ -311,12 +315,50 @@ def subcell_reference(w, w_name):
         U, F, _ = oracle.compute(w.model, w.pos, w.types, w.box)
         sel, desc = np.arange(w.n_atoms), "the whole periodic box"
     else:
-        reps, cells = (100, 8) if w_name == "si_large" else (32, 4)
+        reps, cells = {"si_large": (100, 8), "si_medium": (40, 8), "pbte": (32, 4)}[w_name]
         cpos, ctypes, cbox, inner, sel = W.subcell_cluster(w, reps, cells)
         U, F, _ = oracle.compute(w.model, cpos, ctypes, cbox, sel=inner)
         desc = (f"{sel.shape[0]} atoms of conventional cells [0,{cells})^3, cut out with every atom within "
                 f"2 r_c^R ({cpos.shape[0]} atoms) as an open cluster, step-0 positions")
     return sel, U, F, desc, time.perf_counter() - t0
+
+
+def _labels_chunk(args):
+    """Oracle energies per atom, forces and virials of a chunk of structures (one thread)."""
+    import numpy as np
+    import oracle
+    model, parts = args
+    out = []
+    for pos, types, box in parts:
+        U, F, Wv = oracle.compute(model, pos, types, box, n_threads=1)
+        out.append((U.sum() / pos.shape[0], F, oracle.virial6(Wv.sum(0))[0] / pos.shape[0]))
+    return out
+
+
+def population_labels(model, batch):
+    """FP64 oracle labels (energy per atom, forces, six virial components per atom) of every
+    structure of `batch`, one structure per task over a spawned process pool on all host cores.
+    Returns (e [S], F [N, 3], w [S, 6], seconds, processes)."""
+    import multiprocessing as mp
+    import numpy as np
+    import oracle
+    oracle.build()
+    nproc = max(1, os.cpu_count() or 1)
+    parts = [batch.structure(s) for s in range(batch.n_struct)]
+    order = np.argsort([-p[0].shape[0] for p in parts], kind="stable")  # largest first
+    chunks = [[parts[k] for k in order[c::nproc * 4]] for c in range(nproc * 4)]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(nproc) as pool:
+        res = pool.map(_labels_chunk, [(model, c) for c in chunks])
+    secs = time.perf_counter() - t0
+    e = np.zeros(batch.n_struct)
+    w = np.zeros((batch.n_struct, 6))
+    F = np.zeros((batch.n_atoms, 3))
+    for c, r in enumerate(res):
+        for k, (ek, Fk, wk) in zip(order[c::nproc * 4], r):
+            a0, a1 = int(batch.offsets[k]), int(batch.offsets[k + 1])
+            e[k], w[k], F[a0:a1] = ek, wk, Fk
+    return e, F, w, secs, nproc
 
 
 def form_errors(step0, ref):
@@ -401,10 +443,10 @@ def _events_timed(fn, calls, warmup, stream, flush):
     return sum(dev_ms) / 1e3, wall
 
 
-def run_batch_forms(args, dev, stream, flush, peak):
+def run_batch_forms(args, dev, stream, flush, peak, oracle_labels=True):
     """The structure batch (4096 structures of 8-512 atoms in one evaluation) and the
-    population evaluation (64 candidate vectors on a fixed 1024-structure subset), FP32 and
-    BF16, with the autotuner's launch shapes."""
+    population evaluation (64 candidate vectors on a fixed 1024-structure subset against FP64
+    oracle labels), FP32 and BF16, with the autotuner's launch shapes."""
     import numpy as np
     import torch
     from paper_2205_10046_gb300 import nep
@@ -423,7 +465,7 @@ def run_batch_forms(args, dev, stream, flush, peak):
     call = lambda: nep.nep_compute_batch(h.h, b.offsets, p, t, b.boxes, None, E, F, None, Wv)
     names = ["neighbor_rebuild", "nep_atom", "nep_gather", "finalize"]
     out = {}
-    for prec in (0, 1):
+    for prec, key in FORMS:
         nep.nep_set_precision(h.h, prec)
         tune = nep.nep_autotune(h.h, b.offsets, p, t, b.boxes, 0)
         dev_s, wall = _events_timed(call, args.batch_calls, 3, stream, flush)
@@ -434,7 +476,6 @@ def run_batch_forms(args, dev, stream, flush, peak):
         st = nep.nep_get_stats(h.h)
         atom_f, gather_f = flop_model(model, model.n_types, st["mean_radial"], st["mean_radial_in_rc"],
                                       st["mean_angular"], st["mean_angular_in_rc"])
-        key = "fp32" if prec == 0 else "bf16"
         out[key] = {
             "value": N * args.batch_calls / dev_s, "unit": "atom-evaluations/s",
             "structures_per_s": S * args.batch_calls / dev_s, "ms_per_call": 1e3 * dev_s / args.batch_calls,
@@ -455,35 +496,46 @@ def run_batch_forms(args, dev, stream, flush, peak):
     out["gpu_launches_per_call"] = nep.nep_get_stats(h.h)["batch_graph_kernels"]
     out["l2"] = "flushed (256 MiB write) before every timed call"
 
-    # population: 64 candidates on the first 1024 structures
+    # population: 64 candidates on the first 1024 structures, against FP64 oracle labels of
+    # the seed-0 model (computed on the host cores before the timed calls)
     sub = b.subset(range(1024))
     Ns = sub.n_atoms
     ps = torch.tensor(sub.pos, device=dev)
     ts = torch.tensor(sub.types, device=dev)
-    nep.nep_set_precision(h.h, 0)
-    nep.nep_set_tuning(h.h, 0, 0, 0)
-    Es = torch.empty(1024, **f64)
-    Fs = torch.empty((Ns, 3), **f64)
-    Ws = torch.empty((1024, 9), **f64)
-    nep.nep_compute_batch(h.h, sub.offsets, ps, ts, sub.boxes, None, Es, Fs, None, Ws)
-    torch.cuda.synchronize()
-    cnt = torch.tensor(np.diff(sub.offsets).astype(np.float64), device=dev)
-    e_tar = Es / cnt
-    w9 = Ws / cnt[:, None]
-    w_tar = torch.stack([w9[:, 0], w9[:, 1], w9[:, 2], 0.5 * (w9[:, 3] + w9[:, 6]), 0.5 * (w9[:, 5] + w9[:, 8]),
-                         0.5 * (w9[:, 4] + w9[:, 7])], 1).contiguous()
+    f64 = dict(dtype=torch.float64, device=dev)
+    if oracle_labels:
+        e_l, f_l, w_l, label_s, label_procs = population_labels(model, sub)
+        label_desc = (f"FP64 oracle energies/forces/virials of the seed-0 model on the 1024 structures "
+                      f"({Ns} atoms), {label_s:.1f} s on {label_procs} host processes")
+    else:  # --no-cpu-baseline: labels from the FP32 batch path (the cost does not depend on them)
+        nep.nep_set_precision(h.h, 0)
+        nep.nep_set_tuning(h.h, 0, 0, 0)
+        Es = torch.empty(1024, **f64)
+        Fs = torch.empty((Ns, 3), **f64)
+        Ws = torch.empty((1024, 9), **f64)
+        nep.nep_compute_batch(h.h, sub.offsets, ps, ts, sub.boxes, None, Es, Fs, None, Ws)
+        torch.cuda.synchronize()
+        cnt = np.diff(sub.offsets).astype(np.float64)
+        e_l, f_l = Es.cpu().numpy() / cnt, Fs.cpu().numpy()
+        w9 = Ws.cpu().numpy() / cnt[:, None]
+        w_l = np.stack([w9[:, 0], w9[:, 1], w9[:, 2], 0.5 * (w9[:, 3] + w9[:, 6]), 0.5 * (w9[:, 5] + w9[:, 8]),
+                        0.5 * (w9[:, 4] + w9[:, 7])], 1)
+        label_desc = "FP32 batch path of the seed-0 model (no oracle run requested)"
+    e_tar = torch.tensor(e_l, **f64)
+    Fs = torch.tensor(f_l, **f64)
+    w_tar = torch.tensor(np.ascontiguousarray(w_l), **f64)
     P = 64
     z = torch.tensor(np.stack([W.mixed_model(100 + k).to_vector() for k in range(P)]), device=dev)
     lam = (1.0, 1.0, 0.1, 0.0, 0.0)
     pop = {}
-    for prec in (0, 1):
+    for prec, key in FORMS:
         nep.nep_set_precision(h.h, prec)
         tune = nep.nep_autotune(h.h, sub.offsets, ps, ts, sub.boxes, P)
         loss = torch.empty((P, 6), **f64)
         fn = lambda: nep.nep_eval_population(h.h, z, sub.offsets, ps, ts, sub.boxes, e_tar, Fs, w_tar, lam, loss)
         dev_s, wall = _events_timed(fn, args.pop_calls, 1, stream, flush)
         l = loss.cpu().numpy()
-        pop["fp32" if prec == 0 else "bf16"] = {
+        pop[key] = {
             "value": P * Ns * args.pop_calls / dev_s, "unit": "member-atom-evaluations/s",
             "candidates_per_s": P * args.pop_calls / dev_s, "ms_per_call": 1e3 * dev_s / args.pop_calls,
             "wall_ms_per_call": 1e3 * wall / args.pop_calls,
@@ -493,9 +545,10 @@ def run_batch_forms(args, dev, stream, flush, peak):
         }
     pop["workload"] = (f"{P} random candidate vectors (seeds 100..{100 + P - 1}) on 1024 structures "
                        f"({Ns} atoms) of the batch; Eq. loss with lambda_e = lambda_f = 1, lambda_v = 0.1")
-    pop["targets"] = ("energies, forces and virials of the seed-0 model from the FP32 batch path; the cost does not "
-                      "depend on the target values, tests/test_gpu_population.py checks the losses against "
-                      "FP64 oracle labels")
+    pop["targets"] = label_desc
+    if oracle_labels:
+        pop["cpu_baseline"] = {"value": Ns / label_s, "unit": "atom-evaluations/s", "cores": label_procs,
+                               "kind": "oracle", "sample": label_desc}
     h.close()
     return out, pop
 
@@ -535,34 +588,58 @@ def serve_pool(n_pool, seed):
     return pool
 
 
-def serve_run(model, pool, reqs, precision, workers):
-    """Submit the requests at their arrival times; collect every result."""
+def serve_sample(pool, reqs):
+    """Requests whose served results are checked against the oracle: the first 12 single
+    points on structures of at most 2500 atoms and the first 3 NVE jobs of at most 50 steps on
+    at most 400 atoms."""
+    sp, nve = [], []
+    for q, (t, k, kind, steps) in enumerate(reqs):
+        n = pool[k][0].shape[0]
+        if kind == 0 and n <= 2500 and len(sp) < 12:
+            sp.append(q)
+        elif kind == 2 and n <= 400 and steps <= 50 and len(nve) < 3:
+            nve.append(q)
+    return set(sp + nve)
+
+
+def serve_run(model, pool, reqs, precision, workers, sample=()):
+    """Submit the requests at their arrival times; collect every result (with the final
+    arrays of the requests in `sample`)."""
     import numpy as np
     from paper_2205_10046_gb300 import nep
     srv = nep.Server(model, memory_budget=SERVE_BUDGET, workers=workers, precision=precision, skin=SERVE_SKIN)
     done = {}
     offered = 0.0
     lag = []
+    kinds, req_of, kept = {}, {}, {}
+    lock = threading.Lock()
 
     def collector():
         while len(done) < len(reqs):
             r = srv.wait(0.5)
             if r is not None:
+                with lock:  # the submitting thread has recorded this job
+                    q = req_of.get(r["id"])
+                if q in sample and r["status"] == 0:
+                    kept[q] = (r["energy"], *srv.arrays(r["id"]))
+                else:
+                    srv.drop(r["id"])
                 done[r["id"]] = r
-                srv.drop(r["id"])
 
     th = threading.Thread(target=collector)
     th.start()
     t0 = time.perf_counter()
-    kinds = {}
-    for (t, k, kind, steps) in reqs:
+    for q, (t, k, kind, steps) in enumerate(reqs):
         delay = t - (time.perf_counter() - t0)
         if delay > 0:
             time.sleep(delay)
         lag.append(max(0.0, -delay))
         pos, types, box, vel = pool[k]
-        jid = srv.submit(kind, pos, types, box, n_steps=steps, dt_fs=1.0, fmax=0.0, vel=vel if kind == 2 else None)
-        kinds[jid] = kind
+        with lock:
+            jid = srv.submit(kind, pos, types, box, n_steps=steps, dt_fs=1.0, fmax=0.0,
+                             vel=vel if kind == 2 else None)
+            kinds[jid] = kind
+            req_of[jid] = q
         offered += pos.shape[0] * (1 if kind == 0 else steps + 2)
     th.join()
     wall = time.perf_counter() - t0
@@ -589,25 +666,68 @@ def serve_run(model, pool, reqs, precision, workers):
         "peak_bytes_reserved": int(st["peak_bytes_reserved"]),
         "submit_lag_ms_p99": float(np.percentile(lag, 99)) * 1e3,
         "errors": sorted({r["message"] for r in res if r["status"] != 0})[:3],
-    }
+    }, kept
+
+
+def serving_errors(model, pool, reqs, kept_by_form):
+    """Force and energy errors of the sampled served results against the FP64 oracle: single
+    points at the submitted positions, NVE jobs after the oracle's own velocity Verlet of the
+    same steps (dt 1 fs) from the submitted positions and velocities."""
+    import numpy as np
+    import oracle
+    t0 = time.perf_counter()
+    refs = {}
+    qs = sorted(set().union(*[set(k) for k in kept_by_form.values()]))
+    for q in qs:
+        t, k, kind, steps = reqs[q]
+        pos, types, box, vel = pool[k]
+        if kind == 0:
+            U, F, _ = oracle.compute(model, pos, types, box)
+            refs[q] = (U.sum(), pos, F)
+        else:
+            p1, v1, th, F = oracle.md(model, pos, vel, types, box, steps, 1.0)
+            refs[q] = (th[-1, 0], p1, F)
+    out = {"sample": f"{sum(1 for q in qs if reqs[q][2] == 0)} single points (<= 2500 atoms) and "
+                     f"{sum(1 for q in qs if reqs[q][2] == 2)} NVE jobs (<= 400 atoms, <= 50 steps) of the "
+                     f"2000 req/s stream; NVE against the oracle's velocity Verlet from the same start",
+           "oracle_seconds": time.perf_counter() - t0}
+    for key, kept in kept_by_form.items():
+        d2, f2, de, n_at, dx = 0.0, 0.0, [], 0, 0.0
+        for q, (E, pos_g, F_g, _) in kept.items():
+            E_ref, pos_ref, F_ref = refs[q]
+            d2 += float(np.sum((F_g - F_ref) ** 2))
+            f2 += float(np.sum(F_ref ** 2))
+            n_at += F_ref.shape[0]
+            de.append(abs(E - E_ref) / F_ref.shape[0])
+            box = pool[reqs[q][1]][2]
+            ds = (pos_g - pos_ref) @ np.linalg.inv(box)
+            dx = max(dx, float(np.abs((ds - np.round(ds)) @ box).max()))
+        out[key] = {"jobs": len(kept), "force_rmse_meV_per_A": 1e3 * float(np.sqrt(d2 / max(3 * n_at, 1))),
+                    "force_relative_rms": float(np.sqrt(d2 / max(f2, 1e-300))),
+                    "energy_error_eV_per_atom_max": float(max(de)) if de else None,
+                    "position_error_A_max": dx}
+    return out
 
 
 def run_serving(args):
     """Config-4 serving: Poisson arrivals of single-point (50%), 50-step FIRE (30%) and NVE
     (20%, 10-1000 steps of 1 fs) jobs on 32-20,000-atom structures, 40 GB admission budget,
-    FP32 and BF16 forms; then both forms again at half the measured FP32 capacity."""
+    FP32 and BF16 forms; then both forms again at half the measured FP32 capacity. Returns
+    (report, the sampled results of the full-rate runs for the oracle check)."""
     from paper_2205_10046_gb300 import workloads as W
     model = W.mixed_model(0)
     pool = serve_pool(256, 4)
     reqs = serve_requests(args.serve_rate, args.serve_seconds, 5, pool)
+    sample = serve_sample(pool, reqs)
     out = {"workload": (f"Poisson {args.serve_rate:.0f} req/s for {args.serve_seconds:.0f} s ({len(reqs)} requests); "
                         f"structures drawn from a pool of 256 (32-20,000 atoms, log-uniform, FCC/BCC/diamond, "
                         f"1-3 of 3 species); 50% single point, 30% 50-step FIRE, 20% NVE U{{10..1000}} steps "
                         f"of 1 fs; NEP rc 5.5/4.0 n_max 8/4 40 neurons; one batch of up to {args.serve_workers} jobs (iteration-level batching), "
                         f"{SERVE_BUDGET >> 30} GB admission budget"),
            "latency": "submission (arrival) to result on the host, server clock"}
+    kept = {}
     for prec, key in ((0, "fp32"), (1, "bf16")):
-        out[key] = serve_run(model, pool, reqs, prec, args.serve_workers)
+        out[key], kept[key] = serve_run(model, pool, reqs, prec, args.serve_workers, sample)
     # a load the server sustains: half the FP32 capacity measured above
     cap = out["fp32"]["throughput_atom_evaluations_per_s"]
     work = out["fp32"]["offered_atom_evaluations_per_s"] / args.serve_rate  # per request
@@ -615,10 +735,8 @@ def run_serving(args):
     reqs2 = serve_requests(rate2, args.serve_seconds, 6, pool)
     out["half_capacity"] = {"rate_req_per_s": rate2, "requests": len(reqs2)}
     for prec, key in ((0, "fp32"), (1, "bf16")):
-        out["half_capacity"][key] = serve_run(model, pool, reqs2, prec, args.serve_workers)
-    out["force_error_vs_fp64_oracle"] = ("FP32 form: relative force RMS <= 1e-5 (tests/test_gpu_serve.py); "
-                                         "BF16 form: force RMSE <= 1 meV/A (tests/test_gpu_bf16.py)")
-    return out
+        out["half_capacity"][key], _ = serve_run(model, pool, reqs2, prec, args.serve_workers)
+    return out, (model, pool, reqs, kept)
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -738,14 +856,17 @@ def run_gb300(args):
     if args.serve_only:
         clk = ClockSampler(torch.cuda.current_device() if world == 1 else local)
         with clk:
-            sv = run_serving(args)
+            sv, sv_sample = run_serving(args)
         if rank == 0:
+            if not args.no_cpu_baseline:
+                sv["force_error_vs_fp64_oracle"] = serving_errors(*sv_sample)
             print(json.dumps({"serving": sv, "clocks": clk.summary()}), flush=True)
         return 0
     if args.batch_only:
         clk = ClockSampler(torch.cuda.current_device() if world == 1 else local)
         with clk:
-            bf, pf = run_batch_forms(args, dev, stream, flush, fp32_peak_2070)
+            bf, pf = run_batch_forms(args, dev, stream, flush, fp32_peak_2070,
+                                     oracle_labels=not args.no_cpu_baseline and world == 1)
         if rank == 0:
             print(json.dumps({"batch_form": bf, "population": pf, "clocks": clk.summary()}), flush=True)
         return 0
@@ -756,6 +877,8 @@ def run_gb300(args):
         err_sel = W.subcell_cluster(w, 100, 8)[4]
     elif args.workload == "pbte":
         err_sel = W.subcell_cluster(w, 32, 4)[4]
+    elif args.workload == "si_medium":
+        err_sel = W.subcell_cluster(w, 40, 8)[4]
     else:
         err_sel = np.arange(N)
     clk = ClockSampler(torch.cuda.current_device() if world == 1 else local)
@@ -805,12 +928,13 @@ def run_gb300(args):
     batch_forms = None
     if not args.no_batch:
         with ClockSampler(torch.cuda.current_device() if world == 1 else local) as bclk:
-            batch_forms = run_batch_forms(args, dev, stream, flush, fp32_peak_2070)
+            batch_forms = run_batch_forms(args, dev, stream, flush, fp32_peak_2070,
+                                          oracle_labels=not args.no_cpu_baseline and world == 1)
         batch_forms[0]["clocks"] = bclk.summary()
     serving = None
     if not args.no_serve and world == 1:
         with ClockSampler(torch.cuda.current_device()) as sclk:
-            serving = run_serving(args)
+            serving, serving_sample = run_serving(args)
         serving["clocks"] = sclk.summary()
     if rank == 0:
         clocks = clk.summary()
@@ -863,6 +987,8 @@ def run_gb300(args):
             line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
             ref = subcell_reference(w, args.workload)
             line["force_error_vs_fp64_oracle"] = form_errors(step0, ref)
+            if serving is not None:
+                serving["force_error_vs_fp64_oracle"] = serving_errors(*serving_sample)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

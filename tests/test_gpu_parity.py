@@ -140,9 +140,9 @@ def test_degenerate_inputs(torch_cuda):
     with pytest.raises(nep.NepError, match="NEP_ERR_ARG"):
         h.compute(pos, torch.zeros(2, dtype=torch.int32, device="cuda"), np.zeros((3, 3)))
     h.close()
-    m2 = W.random_model(dict(W.SI_MODEL, n_neuron=7), 0, [W.MASS_SI])
+    m2 = W.random_model(dict(W.SI_MODEL, n_max_radial=20, basis_radial=20), 0, [W.MASS_SI])
     with pytest.raises(nep.NepError, match="NEP_ERR_UNSUPPORTED"):
-        nep.NEP(m2)
+        nep.NEP(m2)  # beyond the run-time-shape kernels' n_max <= 19
 
 
 def test_deterministic_bitwise(torch_cuda):

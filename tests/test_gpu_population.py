@@ -115,3 +115,33 @@ def test_population_autotuned_shapes(torch_cuda, problem):
     # the force term's block sums follow the gather CTA size: equal up to FP64 summation order
     np.testing.assert_allclose(loss, base, rtol=1e-12, atol=1e-15)
     h.close()
+
+
+def test_population_16_members_on_64_structures(torch_cuda):
+    """A larger sampled case: 16 candidates (the label model and 15 random ones) on 64
+    structures of 8-40 atoms, every loss term against the oracle's Eq. loss, in all three
+    network forms (the tensor-core forms at their force bars)."""
+    torch = torch_cuda
+    from paper_2205_10046_gb300 import nep
+    label = W.mixed_model(0)
+    b = W.batch_structures(64, seed=33, n_max=40)
+    e_t, f_t, w_t = oracle.batch_predictions(label, b.offsets, b.pos, b.types, b.boxes)
+    members = [label] + [W.mixed_model(200 + p) for p in range(15)]
+    z = np.stack([m.to_vector() for m in members])
+    ref = []
+    for m in members:
+        e, f, w = oracle.batch_predictions(m, b.offsets, b.pos, b.types, b.boxes)
+        ref.append(oracle.eq_loss(e, e_t, f, f_t, m.to_vector(), LAMBDAS, w, w_t))
+    ref = np.array(ref)
+    dev = lambda a, dt=torch.float64: torch.tensor(a, dtype=dt, device="cuda")
+    for prec in (0, 1, 2):
+        h = nep.NEP(label, precision=prec)
+        g = nep.nep_eval_population(h.h, dev(z), b.offsets, dev(b.pos), dev(b.types, torch.int32), b.boxes,
+                                    dev(e_t), dev(f_t), dev(w_t), LAMBDAS).cpu().numpy()
+        h.close()
+        np.testing.assert_allclose(g[:, 4:], ref[:, 4:], rtol=1e-12, atol=0)
+        if prec == 1:
+            assert np.all(np.abs(g[:, 2] - ref[:, 2]) <= 1e-3)
+            continue
+        for c in (1, 2, 3):
+            np.testing.assert_allclose(g[:, c], ref[:, c], rtol=1e-5 if prec == 0 else 1e-4, atol=1e-6)
