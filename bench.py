@@ -54,6 +54,8 @@ def parse_args():
                     help="si_medium (40^3 cells, 512,000 atoms) is the profiling case of the si_large kernels")
     ap.add_argument("--pbte-steps", type=int, default=1000, help="timed steps of the extra PbTe key (0: skip)")
     ap.add_argument("--skin", type=float, default=0.4, help="neighbour-list skin (A) of the MD workload")
+    ap.add_argument("--atom-form", type=int, choices=[0, 1, 3], default=0,
+                    help="FP32 per-atom kernel form (nep_tuning.atom_form; 0 = the library's default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=8.0)
     ap.add_argument("--plain-graph", action="store_true",
@@ -795,13 +797,14 @@ def atom_roofline(w, stats, atom_ms, peak, peak_basis, traffic=None):
 
 
 def md_forms(nep, w, name, skin, steps, warmup, stream, flush, world, clk=None, step0_sel=None,
-             plain_graph=False):
+             plain_graph=False, atom_form=0):
     """Every network form of the MD workload w on one handle: optional step-0 evaluations
     (forces and site energies of the atoms step0_sel, for the error against the oracle), then
     `steps` timed MD steps per form from the same start state. Returns (handle, results)."""
     import torch
     dev = flush.device
     h = nep.NEP(w.model, skin=skin)
+    nep.nep_set_tuning(h.h, 0, 0, 0, atom_form)
     pos_d = torch.tensor(w.pos, device=dev)
     types_d = torch.tensor(w.types, device=dev)
     vel_d = torch.tensor(w.vel, device=dev)
@@ -822,7 +825,8 @@ def md_forms(nep, w, name, skin, steps, warmup, stream, flush, world, clk=None, 
         nep.md_init(h.h, pos_d, types_d, w.box, vel_d)
         tot, ktime, rebuilds = timed_md(nep, h, w.dt_fs, steps, warmup, stream, flush, world,
                                         clk if prec == 0 else None)
-        res[key] = {"seconds": tot, "ktime": ktime, "rebuilds": rebuilds, "stats": nep.nep_get_stats(h.h)}
+        res[key] = {"seconds": tot, "ktime": ktime, "rebuilds": rebuilds, "stats": nep.nep_get_stats(h.h),
+                    "atom_form": nep.nep_get_tuning(h.h)["atom_form"]}
     nep.nep_set_precision(h.h, 0)
     del pos_d, types_d, vel_d
     return h, res, step0
@@ -883,7 +887,7 @@ def run_gb300(args):
         err_sel = np.arange(N)
     clk = ClockSampler(torch.cuda.current_device() if world == 1 else local)
     h, md, step0 = md_forms(nep, w, args.workload, args.skin, args.steps, args.warmup, stream, flush, world, clk,
-                            err_sel, args.plain_graph)
+                            err_sel, args.plain_graph, args.atom_form)
     stats = md["fp32"]["stats"]
     total_s, ktime, timed_rebuilds = md["fp32"]["seconds"], md["fp32"]["ktime"], md["fp32"]["rebuilds"]
 
@@ -912,7 +916,8 @@ def run_gb300(args):
     pbte = None
     if args.pbte_steps > 0 and args.workload != "pbte":
         wp = W.pbte_rocksalt(32, seed=1)
-        hp, mp, _ = md_forms(nep, wp, "pbte", args.skin, args.pbte_steps, 20, stream, flush, world)
+        hp, mp, _ = md_forms(nep, wp, "pbte", args.skin, args.pbte_steps, 20, stream, flush, world,
+                             atom_form=args.atom_form)
         hp.close()
         pbte = {"workload": workload_config(wp, "pbte")["workload"], "steps": args.pbte_steps, "warmup": 20}
         for key in mp:
@@ -949,7 +954,7 @@ def run_gb300(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(workload_config(w, args.workload), parallelism=f"replicas x{world}",
-                           neighbour_skin_A=args.skin),
+                           neighbour_skin_A=args.skin, atom_form=md["fp32"]["atom_form"]),
             "roofline": roof,
             "kernel_ms_per_step": {k: v / args.steps for k, v in ktime.items()},
             "gather_roofline": {"achieved": gather_f * N / (ktime["nep_gather"] / args.steps / 1e3) / 1e12,

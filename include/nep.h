@@ -179,6 +179,11 @@ typedef struct {
   int n_tried;            /* out: candidates timed by the last nep_autotune */
   float best_ms;          /* out: time of one evaluation (per member) with the chosen shapes */
   float default_ms;       /* out: the same with 128 / 128 atoms per CTA and one member */
+  int atom_form;          /* FP32 per-atom kernel of nep_compute and md_run: 1 = sums and
+                             dU/dS_nk in registers (two CTAs per SM), 3 = two passes for S_nk and
+                             dU/dS_nk in shared memory (three CTAs per SM; shapes whose
+                             (n_max^A + 1) x 24 sums fit 128 TMEM columns, else as 1); 0 = the
+                             library's default. Results are identical up to FP32 summation order. */
 } nep_tuning;
 
 /* Set or read the launch shapes (NEP_ERR_ARG for values outside the lists above). */

@@ -292,7 +292,11 @@ struct Tuning {
   int last_members = 0;  // members per launch of the last population evaluation
   int n_tried = 0;       // candidates timed by the last autotune
   float best_ms = 0.f, default_ms = 0.f;  // per-evaluation times of the choice and of the defaults
+  int atom_form = 0;     // FP32 per-atom kernel of nep_compute / md_run: 0 default, 1, 3 (AtomArgs.atom_occ)
 };
+
+// The FP32 per-atom kernel form used when the caller chose none.
+constexpr int kDefaultAtomForm = 1;
 
 struct nep_handle {
   // model
@@ -597,7 +601,13 @@ AtomArgs make_args(nep_handle *h, int N) {
   a.gR = h->nR; a.gKR = h->KR; a.gA = h->nA; a.gKA = h->KA; a.gH = h->H;
   a.gL3 = h->L3; a.gL4 = h->L4; a.gL5 = h->L5; a.gD = h->n_des;
   a.ann = h->d_ann.p;
+  a.atom_occ = h->tune.atom_form ? h->tune.atom_form : kDefaultAtomForm;
   return a;
+}
+
+// Identity of the per-atom kernel a captured MD step uses (network form and FP32 kernel form).
+int kernel_form(const nep_handle *h) {
+  return h->precision * 16 + (h->tune.atom_form ? h->tune.atom_form : kDefaultAtomForm);
 }
 
 // Load positions (device, [N][3]) and types, set up the grid and build the lists.
@@ -1640,6 +1650,9 @@ int nep_set_tuning(nep_handle *h, const nep_tuning *t) {
     return fail(h, NEP_ERR_ARG, "gather_block must be 0, 64, 128 or 256");
   if (h->generic && ((t->atom_block != 0 && t->atom_block != 128) || (t->gather_block != 0 && t->gather_block != 128)))
     return fail(h, NEP_ERR_UNSUPPORTED, "the run-time-shape kernels take 128 atoms per CTA");
+  if (t->atom_form != 0 && t->atom_form != 1 && t->atom_form != 3)
+    return fail(h, NEP_ERR_ARG, "atom_form must be 0, 1 or 3");
+  h->tune.atom_form = t->atom_form;
   h->tune.members = t->members_per_launch;
   h->tune.atom_block = t->atom_block;
   h->tune.gather_block = t->gather_block;
@@ -1655,6 +1668,7 @@ int nep_get_tuning(const nep_handle *h, nep_tuning *t) {
   t->n_tried = h->tune.n_tried;
   t->best_ms = h->tune.best_ms;
   t->default_ms = h->tune.default_ms;
+  t->atom_form = h->tune.atom_form ? h->tune.atom_form : kDefaultAtomForm;
   return NEP_OK;
 }
 
@@ -1863,13 +1877,13 @@ int md_queue(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double 
   // staging buffer changed
   cudaGraphExec_t &gx = fire ? h->fire_graph : h->graph;
   if (fire && gx && (h->graph_prof != h->prof || h->graph_thermo != h->thermo_stage.p ||
-                     h->graph_cond_used != h->graph_cond || h->graph_prec != h->precision ||
+                     h->graph_cond_used != h->graph_cond || h->graph_prec != kernel_form(h) ||
                      h->graph_nvt != h->nvt)) {
     cudaGraphExecDestroy(gx);
     gx = nullptr;
   }
   if (!gx || (!fire && h->graph_dt != dt_fs) || h->graph_prof != h->prof || h->graph_thermo != h->thermo_stage.p ||
-      h->graph_cond_used != h->graph_cond || h->graph_prec != h->precision || h->graph_nvt != h->nvt) {
+      h->graph_cond_used != h->graph_cond || h->graph_prec != kernel_form(h) || h->graph_nvt != h->nvt) {
     // the MD and FIRE graphs share the capture settings: drop both when they change
     for (cudaGraphExec_t *g : {&h->graph, &h->fire_graph})
       if (*g) {
@@ -1894,7 +1908,7 @@ int md_queue(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double 
     h->graph_prof = h->prof;
     h->graph_thermo = h->thermo_stage.p;
     h->graph_cond_used = h->graph_cond;
-    h->graph_prec = h->precision;
+    h->graph_prec = kernel_form(h);
     h->graph_nvt = h->nvt;
   }
   for (int st = 0; st < n_steps; ++st) CK(cudaGraphLaunch(gx, s), "graph launch");

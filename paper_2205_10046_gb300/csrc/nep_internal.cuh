@@ -197,6 +197,9 @@ struct AtomArgs {
   // by the kernels that take the shape at run time (shapes without a compiled instantiation)
   int gR, gKR, gA, gKA, gH, gL3, gL4, gL5, gD;
   const float *ann;
+  // FP32 per-atom kernel form: 1 the register-resident form, 3 the low-register form (three
+  // blocks per SM; shapes whose S_nk fit 128 TMEM columns)
+  int atom_occ;
 };
 
 // Model constants of one handle, FP32.

@@ -370,10 +370,17 @@ __device__ __forceinline__ void for_pairs_plain(const unsigned *__restrict__ nl,
 }
 
 // ------------------------------------------------------------------------ per-atom kernel
-template <class S, bool DESC_ONLY, int PREC, bool BATCH = false, int AB = kAtomBlock>
-__global__ void __launch_bounds__(AB, 1)
+// OCC = 3 is the low-register form of the FP32 kernel: S_nk summed in two passes over the
+// angular neighbours, parked in 128 TMEM columns, and dU/dS_nk kept in the thread's shared
+// block instead of registers, so that three blocks (12 warps) fit an SM instead of two.
+template <class S, bool DESC_ONLY, int PREC, bool BATCH = false, int AB = kAtomBlock, int OCC = 1>
+__global__ void __launch_bounds__(AB, OCC)
     atom_kernel(const AtomArgs a, const __grid_constant__ AnnConst<S> w) {
   static_assert(PREC >= 0 && PREC <= 2, "network forms: 0 FP32, 1 BF16, 2 split BF16");
+  constexpr bool LOWREG = OCC > 1;
+  static_assert(!LOWREG || (PREC == 0 && !DESC_ONLY && AB == 128 && S::NS <= 128),
+                "the low-register form: FP32 network, S_nk within 128 TMEM columns");
+  constexpr uint32_t TCOLS = LOWREG ? 128u : (uint32_t)S::TMEM_COLS;
   static_assert(PREC == 0 || !DESC_ONLY, "the descriptor-only kernel has no network");
   static_assert(PREC == 0 || AB == 128, "the tensor-core network works on 128-atom tiles (UMMA M = 128)");
   // S_nk waits for the network in this thread's TMEM lane (128-atom blocks, whole groups of 8
@@ -382,7 +389,7 @@ __global__ void __launch_bounds__(AB, 1)
   static_assert(PREC == 0 || TM, "the tensor-core network keeps S_nk in TMEM");
   // With S_nk parked in TMEM the registers hold all (n_max^A + 1) x 24 sums at once: one pass
   // over the angular neighbours (PbTe: 168 sums); otherwise NPASS passes of NCH values of n.
-  constexpr int NPASS = TM && (S::NA + 1) * S::NK <= 192 ? 1 : S::NPASS;
+  constexpr int NPASS = LOWREG ? ((S::NA + 1) >= 2 ? 2 : 1) : (TM && (S::NA + 1) * S::NK <= 192 ? 1 : S::NPASS);
   constexpr int NCH = (S::NA + 1 + NPASS - 1) / NPASS;
   static_assert(AB % 32 == 0 && AB <= 256, "whole warps, at most 256 atoms per block");
   constexpr int NR = S::NR, KR = S::KR, NA = S::NA, KA = S::KA, NK = S::NK, NDES = S::NDES;
@@ -487,7 +494,7 @@ __global__ void __launch_bounds__(AB, 1)
   if constexpr (TM) {
     if (threadIdx.x < 32) {
       asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tc_tmem)),
-                   "r"(S::TMEM_COLS));
+                   "r"(TCOLS));
       asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -842,11 +849,12 @@ __global__ void __launch_bounds__(AB, 1)
       }
 
       // ---- dU/dS_nk from the explicit 3/4/5-body forms, kept in registers for the force loop
-      float dSr[NA + 1][NKP];
+      // (low-register form: in this thread's shared block, row n at n NKP)
+      float dSr[LOWREG ? 1 : NA + 1][NKP];
 #pragma unroll
       for (int n = 0; n <= NA; ++n) {
         float s[NKP];
-        float *dS = dSr[n];
+        float *dS = dSr[LOWREG ? 0 : n];
         if constexpr (!TM) {
 #pragma unroll
           for (int k4 = 0; k4 < NKP / 4; ++k4) {
@@ -884,6 +892,11 @@ __global__ void __launch_bounds__(AB, 1)
           const float common = 2.f * C[1] * s[0] * s[0] + 4.f * C[2] * s12;
           dS[1] += d5 * common * s[1];
           dS[2] += d5 * common * s[2];
+        }
+        if constexpr (LOWREG) {
+#pragma unroll
+          for (int k4 = 0; k4 < NKP / 4; ++k4)
+            Sme[n * (NKP / 4) + k4] = make_float4(dS[4 * k4], dS[4 * k4 + 1], dS[4 * k4 + 2], dS[4 * k4 + 3]);
         }
       }
 
@@ -923,11 +936,19 @@ __global__ void __launch_bounds__(AB, 1)
             float ak[4] = {0.f, 0.f, 0.f, 0.f}, ck[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int n = 0; n <= NA; ++n) {
+              float dv[4];
+              if constexpr (LOWREG) {
+                const float4 v = Sme[n * (NKP / 4) + k0 / 4];
+                dv[0] = v.x, dv[1] = v.y, dv[2] = v.z, dv[3] = v.w;
+              } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) dv[j] = k0 + j < NK ? dSr[n][k0 + j] : 0.f;
+              }
 #pragma unroll
               for (int j = 0; j < 4; ++j)
                 if (k0 + j < NK) {
-                  ak[j] = __fmaf_rn(dSr[n][k0 + j], g[n], ak[j]);
-                  ck[j] = __fmaf_rn(dSr[n][k0 + j], gp[n], ck[j]);
+                  ak[j] = __fmaf_rn(dv[j], g[n], ak[j]);
+                  ck[j] = __fmaf_rn(dv[j], gp[n], ck[j]);
                 }
             }
             static_for<0, 4>([&](auto jc) {
@@ -971,7 +992,7 @@ __global__ void __launch_bounds__(AB, 1)
     __syncthreads();
     if (threadIdx.x < 32) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc_tmem), "r"(S::TMEM_COLS));
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc_tmem), "r"(TCOLS));
     }
   }
 }
@@ -1298,6 +1319,16 @@ cudaError_t launch_atom(const AtomArgs &a, const ModelF &mf, const float *w0, co
   if (descriptor_only) return go(atom_kernel<S, true, 0>);
   if (a.precision == 1) return go(atom_kernel<S, false, 1>);
   if (a.precision == 2) return go(atom_kernel<S, false, 2>);
+  if constexpr (S::NS <= 128) {
+    if (a.atom_occ == 3) {  // low-register form: the per-thread dU/dS_nk blocks, no TMEM-driven cap
+      auto kern = atom_kernel<S, false, 0, false, 128, 3>;
+      const size_t extra = sizeof(float) * (size_t)S::SPT * kAtomBlock;
+      cudaError_t e = smem_limit_once(kern, atom_smem_bytes<S>(kMaxTypes, 1 << 9, 0) + extra);
+      if (e != cudaSuccess) return e;
+      kern<<<blocks, kAtomBlock, atom_smem_bytes<S>(a.T, a.ncode, 0) + extra, st>>>(a, w);
+      return cudaGetLastError();
+    }
+  }
   return go(atom_kernel<S, false, 0>);
 }
 

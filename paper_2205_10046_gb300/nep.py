@@ -48,7 +48,7 @@ class nep_stats(C.Structure):
 class nep_tuning(C.Structure):
     _fields_ = [("members_per_launch", C.c_int), ("atom_block", C.c_int), ("gather_block", C.c_int),
                 ("last_members", C.c_int), ("n_tried", C.c_int), ("best_ms", C.c_float),
-                ("default_ms", C.c_float)]
+                ("default_ms", C.c_float), ("atom_form", C.c_int)]
 
 
 class md_options(C.Structure):
@@ -311,8 +311,8 @@ def nep_eval_population(h, z, offsets, pos, types, boxes, e_tar, f_tar, w_tar=No
     return loss
 
 
-def nep_set_tuning(h, members_per_launch: int = 0, atom_block: int = 0, gather_block: int = 0):
-    t = nep_tuning(int(members_per_launch), int(atom_block), int(gather_block), 0, 0, 0.0, 0.0)
+def nep_set_tuning(h, members_per_launch: int = 0, atom_block: int = 0, gather_block: int = 0, atom_form: int = 0):
+    t = nep_tuning(int(members_per_launch), int(atom_block), int(gather_block), 0, 0, 0.0, 0.0, int(atom_form))
     _check(load().nep_set_tuning(h, C.byref(t)), h)
 
 

@@ -237,3 +237,30 @@ def test_md_rebuilds_keep_forces_exact(torch_cuda):
     etot = e[:, 0] + e[:, 1]
     assert np.ptp(etot) / w.n_atoms < 1e-4
     h.close()
+
+
+@pytest.mark.parametrize("seed,n", [(0, 8), (3, 64), (5, 150)])
+def test_low_register_atom_form_matches_oracle(torch_cuda, seed, n):
+    """The three-CTAs-per-SM form of the FP32 per-atom kernel (nep_tuning.atom_form = 3) on
+    the mixed model (S_nk in 128 TMEM columns): same bars as the default form, and an MD run
+    whose step graph uses it."""
+    torch = torch_cuda
+    from paper_2205_10046_gb300 import nep
+    pos, types, box = W.random_structure(seed, n)
+    model = W.random_model(W.MIXED_MODEL, seed, [W.MASS_SI, W.MASS_GE, W.MASS_C])
+    h = nep.NEP(model)
+    nep.nep_set_tuning(h.h, 0, 0, 0, 3)
+    assert nep.nep_get_tuning(h.h)["atom_form"] == 3
+    p = torch.tensor(pos, device="cuda")
+    t = torch.tensor(types, device="cuda")
+    g = {k: v.cpu().numpy() for k, v in h.compute(p, t, box, per_atom_virial=True).items()}
+    U, F, Wv = oracle.compute(model, pos, types, box)
+    _check_all(g, U, F, Wv, n)
+    vel = W.maxwell_boltzmann(model.mass[types], 300.0, seed)
+    nep.md_init(h.h, p, t, box, torch.tensor(vel, device="cuda"))
+    th = torch.zeros((10, 4), dtype=torch.float64, device="cuda")
+    nep.md_run(h.h, 10, 1.0, 1, th)
+    torch.cuda.synchronize()
+    h.close()
+    _, _, th_ref, _ = oracle.md(model, pos, vel, types, box, 10, 1.0)
+    assert np.abs(th.cpu().numpy()[:, 0] - th_ref[1:, 0]).max() / n <= 1e-6

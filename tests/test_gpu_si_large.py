@@ -45,13 +45,15 @@ def _rel(a, b):
 
 
 def _gpu(torch, w, precisions):
+    """Per form: FP32 with each per-atom kernel form (keys 0 and 'occ3'), then the BF16 forms."""
     from paper_2205_10046_gb300 import nep
     h = nep.NEP(w.model)
     p = torch.tensor(w.pos, device="cuda")
     t = torch.tensor(w.types, device="cuda")
     out = {}
-    for prec in precisions:
-        nep.nep_set_precision(h.h, prec)
+    for prec in ("occ3",) + tuple(precisions):
+        nep.nep_set_tuning(h.h, 0, 0, 0, 3 if prec == "occ3" else 1)
+        nep.nep_set_precision(h.h, 0 if prec == "occ3" else prec)
         r = h.compute(p, t, w.box, per_atom_virial=True)
         torch.cuda.synchronize()
         out[prec] = {k: v.cpu().numpy() for k, v in r.items()}
@@ -77,7 +79,13 @@ def test_si_8m_subcell_against_oracle(torch_cuda, si8m):
     assert np.abs(g32["F"].sum(0)).max() < 1e-6 * np.abs(g32["F"]).sum() / 3
     assert abs(g32["E"][0] - g32["U"].sum()) < 1e-9 * abs(g32["E"][0])
     np.testing.assert_allclose(g32["W_total"], g32["W"].sum(0), rtol=1e-9, atol=1e-6)
-    for prec in sorted(k for k in g if k != 0):
+    # the low-register FP32 kernel form: same bars
+    g3 = g["occ3"]
+    print(f"FP32 form 3: relative force RMS {_rel(g3['F'][sel], F):.2e}")
+    assert _rel(g3["F"][sel], F) <= REL_F
+    assert abs(g3["U"][sel].sum() - U.sum()) / sel.shape[0] <= DE_ATOM
+    assert _rel(g3["W"][sel], Wv) <= REL_F
+    for prec in sorted(k for k in g if k not in (0, "occ3")):
         gb = g[prec]
         rmse = float(np.sqrt(np.mean((gb["F"][sel] - F) ** 2)))
         print(f"BF16 form {prec}: force RMSE {rmse:.2e} eV/A (relative RMS {_rel(gb['F'][sel], F):.2e}, "
