@@ -183,7 +183,8 @@ typedef struct {
                              dU/dS_nk in registers (two CTAs per SM), 3 = two passes for S_nk and
                              dU/dS_nk in shared memory (three CTAs per SM; shapes whose
                              (n_max^A + 1) x 24 sums fit 128 TMEM columns, else as 1); 0 = the
-                             library's default. Results are identical up to FP32 summation order. */
+                             library's default (3 where it exists). nep_get_tuning returns the
+                             form in use. Results agree to FP32 summation order. */
 } nep_tuning;
 
 /* Set or read the launch shapes (NEP_ERR_ARG for values outside the lists above). */

@@ -377,6 +377,7 @@ const ShapeOps *shape_generic() {
     o.gather_batch = &generic_gather_batch;
     o.atom_blocks = &blocks128;
     o.gather_blocks = &blocks128;
+    o.lowreg = 0;
     return o;
   }();
   return &ops;

@@ -225,6 +225,7 @@ struct ShapeOps {
   cudaError_t (*gather_batch)(const AtomArgs &, int members, int block, cudaStream_t s);
   int (*atom_blocks)(int N);
   int (*gather_blocks)(int N);
+  int lowreg;  // the shape's S_nk fit 128 TMEM columns: the low-register FP32 form (3) exists
 };
 
 int shape_count();

@@ -1414,6 +1414,7 @@ ShapeOps make_ops() {
   o.gather = &launch_gather<S>;
   o.atom_blocks = &atom_blocks<S>;
   o.gather_blocks = &gather_blocks<S>;
+  o.lowreg = S::NS <= 128 ? 1 : 0;
   attach_batch<S>(o);
   return o;
 }
