@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(AB, OCC)
     atom_kernel(const AtomArgs a, const __grid_constant__ AnnConst<S> w) {
   static_assert(PREC >= 0 && PREC <= 2, "network forms: 0 FP32, 1 BF16, 2 split BF16");
   constexpr bool LOWREG = OCC > 1;
-  static_assert(!LOWREG || (PREC == 0 && !DESC_ONLY && AB == 128 && S::NS <= 128),
+  static_assert(!LOWREG || (PREC == 0 && !DESC_ONLY && AB == 128 && S::NS <= 128 && S::NK % 8 == 0),
                 "the low-register form: FP32 network, S_nk within 128 TMEM columns");
   constexpr uint32_t TCOLS = LOWREG ? 128u : (uint32_t)S::TMEM_COLS;
   static_assert(PREC == 0 || !DESC_ONLY, "the descriptor-only kernel has no network");
@@ -582,6 +582,86 @@ __global__ void __launch_bounds__(AB, OCC)
     // ---- angular sums S_nk (Eq. S_nk, b_k(d) r^-l) and the angular descriptor components
     // (Sec. II D): one pass over the angular neighbours, or one chunk of n per pass when the
     // sums do not fit the registers (NPASS above)
+    if constexpr (LOWREG) {
+      // low-register form: two passes split over k, pass 0 the polynomials k < 16 (the 3-body
+      // blocks l = 1..3 and k = 15 of l = 4, the 4- and 5-body terms), pass 1 the rest; every
+      // pass sums all n, so each pair evaluates each b_k once
+      constexpr int KSPL = NK > 16 ? 16 : NK;
+      static_for<0, (NK > KSPL ? 2 : 1)>([&](auto pc) {
+        constexpr int k0 = decltype(pc)::value == 0 ? 0 : KSPL;
+        constexpr int k1 = decltype(pc)::value == 0 ? KSPL : NK;
+        constexpr int NKC = k1 - k0;
+        float Sv[NA + 1][NKC];
+#pragma unroll
+        for (int n = 0; n <= NA; ++n)
+#pragma unroll
+          for (int k = 0; k < NKC; ++k) Sv[n][k] = 0.f;
+        for_pairs(a.nl_a, 0, na, N, i, a.pos4, a.jmask, [&](int, unsigned e, const float4 &pj) {
+          const float3 d = pair_vector(pi, pj, shift(e));
+          const float r2 = norm2(d);
+          if (r2 < rcA2) {
+            const int tj = type_of(pj);
+            const float rinv = rsqrtf(r2);
+            float f[KA + 1];
+            cheb_basis<KA>(r2 * rinv, inv_rcA, f);
+            const float4 *cc = reinterpret_cast<const float4 *>(cA_s + (ti * T + tj) * (NA + 1) * KAP);
+            float g[NA + 1];
+#pragma unroll
+            for (int n = 0; n <= NA; ++n) {
+              float acc = 0.f;
+#pragma unroll
+              for (int k4 = 0; k4 < KAP / 4; ++k4) {
+                const float4 cv = cc[n * (KAP / 4) + k4];
+                const float cw[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                  if (4 * k4 + j <= KA) acc = __fmaf_rn(cw[j], f[4 * k4 + j], acc);
+              }
+              g[n] = acc;
+            }
+            const float rl[5] = {1.f, rinv, rinv * rinv, rinv * rinv * rinv, (rinv * rinv) * (rinv * rinv)};
+            static_for<k0, k1>([&](auto kc) {
+              constexpr int k = decltype(kc)::value;
+              const float b = poly_b<k>(d.x, d.y, d.z, r2) * rl[l_of_k(k)];
+#pragma unroll
+              for (int n = 0; n <= NA; ++n) Sv[n][k - k0] = __fmaf_rn(g[n], b, Sv[n][k - k0]);
+            });
+          }
+        });
+#pragma unroll
+        for (int n = 0; n <= NA; ++n) {
+          // 3-body components: the part of each l block inside [k0, k1)
+          static_for<0, S::L3>([&](auto lc) {
+            constexpr int l = decltype(lc)::value + 1;
+            constexpr int b0 = l == 1 ? 0 : l == 2 ? 3 : l == 3 ? 8 : 15;
+            constexpr int b1 = l == 1 ? 3 : l == 2 ? 8 : l == 3 ? 15 : 24;
+            constexpr int lo = b0 > k0 ? b0 : k0, hi = b1 < k1 ? b1 : k1;
+            if constexpr (lo < hi) {
+              float acc = q[(NR + 1) + (l - 1) * (NA + 1) + n];
+#pragma unroll
+              for (int k = lo; k < hi; ++k) acc = __fmaf_rn(w.m.c3b[k] * Sv[n][k - k0], Sv[n][k - k0], acc);
+              q[(NR + 1) + (l - 1) * (NA + 1) + n] = acc;
+            }
+          });
+          if constexpr (k0 == 0) {
+            if constexpr (S::L4 >= 2) {
+              const float s3 = Sv[n][3], s4 = Sv[n][4], s5 = Sv[n][5], s6 = Sv[n][6], s7 = Sv[n][7];
+              q[S::OFF4 + n] = w.m.c4b[0] * s3 * s3 * s3 + w.m.c4b[1] * s3 * (s4 * s4 + s5 * s5) +
+                               w.m.c4b[2] * s3 * (s6 * s6 + s7 * s7) + w.m.c4b[3] * s6 * (s5 * s5 - s4 * s4) +
+                               w.m.c4b[4] * s4 * s5 * s7;
+            }
+            if constexpr (S::L5 >= 1) {
+              const float s0 = Sv[n][0], s12 = Sv[n][1] * Sv[n][1] + Sv[n][2] * Sv[n][2];
+              q[S::OFF5 + n] = w.m.c5b[0] * s0 * s0 * s0 * s0 + w.m.c5b[1] * s0 * s0 * s12 + w.m.c5b[2] * s12 * s12;
+            }
+          }
+          // park this part of S_n in TMEM, columns n NK + k0 .. n NK + k1 - 1
+          __syncwarp();
+#pragma unroll
+          for (int k8 = 0; k8 < NKC / 8; ++k8) tmem_st8(tmem_row + n * NK + k0 + 8 * k8, &Sv[n][8 * k8]);
+        }
+      });
+    } else
     static_for<0, NPASS>([&](auto pc) {
       constexpr int n0 = decltype(pc)::value * NCH;
       constexpr int n1 = (n0 + NCH < NA + 1) ? n0 + NCH : NA + 1;
@@ -1319,7 +1399,7 @@ cudaError_t launch_atom(const AtomArgs &a, const ModelF &mf, const float *w0, co
   if (descriptor_only) return go(atom_kernel<S, true, 0>);
   if (a.precision == 1) return go(atom_kernel<S, false, 1>);
   if (a.precision == 2) return go(atom_kernel<S, false, 2>);
-  if constexpr (S::NS <= 128) {
+  if constexpr (S::NS <= 128 && S::NK % 8 == 0) {
     if (a.atom_occ == 3) {  // low-register form: the per-thread dU/dS_nk blocks, no TMEM-driven cap
       auto kern = atom_kernel<S, false, 0, false, 128, 3>;
       const size_t extra = sizeof(float) * (size_t)S::SPT * kAtomBlock;
@@ -1414,7 +1494,7 @@ ShapeOps make_ops() {
   o.gather = &launch_gather<S>;
   o.atom_blocks = &atom_blocks<S>;
   o.gather_blocks = &gather_blocks<S>;
-  o.lowreg = S::NS <= 128 ? 1 : 0;
+  o.lowreg = (S::NS <= 128 && S::NK % 8 == 0) ? 1 : 0;
   attach_batch<S>(o);
   return o;
 }
