@@ -801,7 +801,7 @@ BatchKey batch_key(nep_handle *h, int N, const BatchOut &o) {
   k.N = N;
   k.cap_r = h->cap_r;
   k.cap_a = h->cap_a;
-  k.precision = h->precision;
+  k.precision = kernel_form(h);
   k.blocks = atom_block(h) * 1024 + gather_block(h);
   return k;
 }
@@ -1025,7 +1025,7 @@ EngineKey engine_key(nep_handle *h) {
   k.N = h->N;
   k.cap_r = h->cap_r;
   k.cap_a = h->cap_a;
-  k.precision = h->precision;
+  k.precision = kernel_form(h);
   return k;
 }
 

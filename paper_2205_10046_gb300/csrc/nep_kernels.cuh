@@ -1457,6 +1457,16 @@ cudaError_t launch_atom_batch(const AtomArgs &a, const ModelF &mf, const float *
   if (a.precision == 1) return go(atom_kernel<S, false, 1, true, 128>);
   if (a.precision == 2) return go(atom_kernel<S, false, 2, true, 128>);
   if (block == 64) return go(atom_kernel<S, false, 0, true, 64>);
+  if constexpr (S::NS <= 128 && S::NK % 8 == 0) {
+    if (a.atom_occ == 3) {  // the low-register form, as in the single-structure launch
+      auto kern = atom_kernel<S, false, 0, true, 128, 3>;
+      const size_t extra = sizeof(float) * (size_t)S::SPT * 128;
+      cudaError_t e = smem_limit_once(kern, atom_smem_bytes<S>(kMaxTypes, 0, 0, 128) + extra);
+      if (e != cudaSuccess) return e;
+      kern<<<grid, 128, atom_smem_bytes<S>(a.T, 0, 0, 128) + extra, st>>>(a, w);
+      return cudaGetLastError();
+    }
+  }
   return go(atom_kernel<S, false, 0, true, 128>);
 }
 
