@@ -184,7 +184,9 @@ typedef struct {
                              dU/dS_nk in shared memory (three CTAs per SM; shapes whose
                              (n_max^A + 1) x 24 sums fit 128 TMEM columns, else as 1); 0 = the
                              library's default (3 where it exists). nep_get_tuning returns the
-                             form in use. Results agree to FP32 summation order. */
+                             form in use. The form applies to 128-atom CTAs (an atom_block of 64
+                             runs form 1) and nep_autotune keeps it. The two forms agree to FP32
+                             rounding; within one form, results do not depend on the CTA sizes. */
 } nep_tuning;
 
 /* Set or read the launch shapes (NEP_ERR_ARG for values outside the lists above). */

@@ -1600,7 +1600,9 @@ int nep_autotune(nep_handle *h, int n_struct, const int *offsets, const double *
   int best_ab = 128, best_gb = 128;
   const int abs_[2] = {64, 128}, gbs[3] = {64, 128, 256};
   for (int ia = 0; ia < 2 && !rc; ++ia) {
-    if ((h->precision >= 1 || h->generic) && abs_[ia] != 128) continue;
+    // the tensor-core forms, the run-time-shape kernels and the low-register FP32 form work on
+    // 128-atom CTAs only (a 64-atom CTA would change the FP32 form, hence the rounding)
+    if ((h->precision >= 1 || h->generic || atom_form_of(h) == 3) && abs_[ia] != 128) continue;
     for (int ig = 0; ig < 3 && !rc; ++ig) {
       if (h->generic && gbs[ig] != 128) continue;  // one block shape for the run-time-shape kernels
       h->tune.atom_block = abs_[ia];

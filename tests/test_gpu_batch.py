@@ -255,10 +255,14 @@ def test_block_shapes_and_autotune(torch_cuda):
     from paper_2205_10046_gb300 import nep
     b = W.batch_structures(64, seed=5)
     h = nep.NEP(W.mixed_model(0))
+    ref3 = _run_batch(torch, h, b)  # the default: low-register FP32 form on 128-atom CTAs
+    nep.nep_set_tuning(h.h, 0, 0, 0, 1)  # the register-resident form runs on 64 and 128
     ref = _run_batch(torch, h, b)
+    for k in ref:  # the two forms differ only by FP32 rounding
+        np.testing.assert_allclose(ref3[k], ref[k], rtol=1e-6, atol=1e-7, err_msg=k)
     for ab in (64, 128):
         for gb in (64, 128, 256):
-            nep.nep_set_tuning(h.h, 0, ab, gb)
+            nep.nep_set_tuning(h.h, 0, ab, gb, 1)
             g = _run_batch(torch, h, b)
             for k in ref:
                 np.testing.assert_array_equal(g[k], ref[k], err_msg=f"{k} atom_block={ab} gather_block={gb}")
@@ -271,4 +275,11 @@ def test_block_shapes_and_autotune(torch_cuda):
         np.testing.assert_array_equal(g[k], ref[k])
     with pytest.raises(nep.NepError):
         nep.nep_set_tuning(h.h, 0, 96, 128)
+    # the autotuner keeps the handle's form: only 128-atom CTAs for the low-register form
+    nep.nep_set_tuning(h.h, 0, 0, 0, 3)
+    tune = nep.nep_autotune(h.h, b.offsets, p, t, b.boxes, n_pop=0)
+    assert tune["atom_block"] == 128 and tune["n_tried"] == 3 and tune["atom_form"] == 3
+    g = _run_batch(torch, h, b)
+    for k in ref3:
+        np.testing.assert_array_equal(g[k], ref3[k])
     h.close()

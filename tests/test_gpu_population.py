@@ -108,7 +108,8 @@ def test_population_autotuned_shapes(torch_cuda, problem):
     p, t = dev(b.pos), dev(b.types, torch.int32)
     P = problem["z"].shape[0]
     tune = nep.nep_autotune(h.h, b.offsets, p, t, b.boxes, n_pop=P)
-    assert tune["members_per_launch"] in (1, 2, 4) and tune["n_tried"] >= 7
+    # gather CTA shapes (the default low-register form keeps 128-atom CTAs), then members
+    assert tune["members_per_launch"] in (1, 2, 4) and tune["n_tried"] >= 5
     loss = nep.nep_eval_population(h.h, dev(problem["z"]), b.offsets, p, t, b.boxes, dev(problem["e_t"]),
                                    dev(problem["f_t"]), dev(problem["w_t"]), LAMBDAS).cpu().numpy()
     assert nep.nep_get_tuning(h.h)["last_members"] == tune["members_per_launch"]
