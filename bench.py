@@ -53,7 +53,9 @@ def parse_args():
     ap.add_argument("--workload", choices=["pbte", "si", "si_medium", "si_large"], default="si_large",
                     help="si_medium (40^3 cells, 512,000 atoms) is the profiling case of the si_large kernels")
     ap.add_argument("--pbte-steps", type=int, default=1000, help="timed steps of the extra PbTe key (0: skip)")
-    ap.add_argument("--skin", type=float, default=0.4, help="neighbour-list skin (A) of the MD workload")
+    ap.add_argument("--skin", type=float, default=None,
+                    help="neighbour-list skin (A) of the MD workload (default: 0.3 for the Si boxes, 0.4 for PbTe, "
+                         "the fastest of a sweep on each)")
     ap.add_argument("--atom-form", type=int, choices=[0, 1, 3], default=0,
                     help="FP32 per-atom kernel form (nep_tuning.atom_form; 0 = the library's default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -916,10 +918,11 @@ def run_gb300(args):
     pbte = None
     if args.pbte_steps > 0 and args.workload != "pbte":
         wp = W.pbte_rocksalt(32, seed=1)
-        hp, mp, _ = md_forms(nep, wp, "pbte", args.skin, args.pbte_steps, 20, stream, flush, world,
+        hp, mp, _ = md_forms(nep, wp, "pbte", args.pbte_skin, args.pbte_steps, 20, stream, flush, world,
                              atom_form=args.atom_form)
         hp.close()
-        pbte = {"workload": workload_config(wp, "pbte")["workload"], "steps": args.pbte_steps, "warmup": 20}
+        pbte = {"workload": workload_config(wp, "pbte")["workload"], "steps": args.pbte_steps, "warmup": 20,
+                "neighbour_skin_A": args.pbte_skin}
         for key in mp:
             r = mp[key]
             rl, _ = atom_roofline(wp, r["stats"], r["ktime"]["nep_atom"] / args.pbte_steps, fp32_peak_2070,
@@ -1000,8 +1003,14 @@ def run_gb300(args):
     return 0
 
 
+SKIN_DEFAULT = {"si_large": 0.3, "si_medium": 0.3, "si": 0.4, "pbte": 0.4}
+
+
 def main():
     args = parse_args()
+    args.pbte_skin = args.skin if args.skin is not None else SKIN_DEFAULT["pbte"]
+    if args.skin is None:
+        args.skin = SKIN_DEFAULT[args.workload]
     if args.impl == "reference":
         return run_reference(args)
     return run_gb300(args)
