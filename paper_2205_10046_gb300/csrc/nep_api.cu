@@ -14,6 +14,18 @@
 #include "../../include/nep.h"
 #include "nep_internal.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
+namespace nep {
+// A named NVTX range around a host call (for timeline profilers; no cost without one).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace nep
+
 namespace nep {
 void launch_rebuild_condition(cudaGraphConditionalHandle hc, const BuildStatus *st, cudaStream_t s);
 void launch_drift(int N, const AtomState &a, const double *inv_mass_kappa, double dt, double half_skin2,
@@ -1090,6 +1102,7 @@ int engine_queue_iteration(nep_handle *h, cudaStream_t s) {
 // list overflow in any of them undoes them all, grows the lists and runs them again. An
 // unchanged layout replays one captured iteration graph.
 int engine_step(nep_handle *h, cudaStream_t s, int n_iter, bool force_rebuild) {
+  nep::NvtxRange nvtx_range("engine_step");
   const int N = h->N, S = h->nb_struct;
   if (N == 0 || S == 0 || n_iter < 1) return NEP_OK;
   CK(h->ck_F.ensure(3 * (size_t)N), "alloc checkpoint");
@@ -1324,6 +1337,7 @@ int nep_n_des(const nep_handle *h) { return valid_handle(h) ? h->n_des : NEP_ERR
 
 int nep_compute(nep_handle *h, int n_atoms, const double *pos, const int *types, const double *box, double *energy,
                 double *energy_total, double *force, double *virial, double *virial_total, nep_stream_t stream) {
+  nep::NvtxRange nvtx_range("nep_compute");
   if (!valid_handle(h)) return NEP_ERR_ARG;
   h->err.clear();
   cudaStream_t s = (cudaStream_t)stream;
@@ -1354,6 +1368,7 @@ int nep_compute(nep_handle *h, int n_atoms, const double *pos, const int *types,
 int nep_compute_batch(nep_handle *h, int n_struct, const int *offsets, const double *pos, const int *types,
                       const double *boxes, double *energy, double *energy_struct, double *force, double *virial,
                       double *virial_struct, nep_stream_t stream) {
+  nep::NvtxRange nvtx_range("nep_compute_batch");
   if (!valid_handle(h)) return NEP_ERR_ARG;
   h->err.clear();
   cudaStream_t s = (cudaStream_t)stream;
@@ -1434,6 +1449,7 @@ int nep_eval_population(nep_handle *h, int n_pop, const double *z, int n_struct,
                         const double *pos, const int *types, const double *boxes, const double *e_tar,
                         const double *f_tar, const double *w_tar, const double *lambda, double *loss,
                         nep_stream_t stream) {
+  nep::NvtxRange nvtx_range("nep_eval_population");
   if (!valid_handle(h)) return NEP_ERR_ARG;
   h->err.clear();
   cudaStream_t s = (cudaStream_t)stream;
@@ -1539,6 +1555,7 @@ int nep_eval_population(nep_handle *h, int n_pop, const double *z, int n_struct,
 
 int nep_autotune(nep_handle *h, int n_struct, const int *offsets, const double *pos, const int *types,
                  const double *boxes, int n_pop, nep_tuning *out, nep_stream_t stream) {
+  nep::NvtxRange nvtx_range("nep_autotune");
   if (!valid_handle(h)) return NEP_ERR_ARG;
   h->err.clear();
   cudaStream_t s = (cudaStream_t)stream;
@@ -1682,6 +1699,7 @@ int nep_get_tuning(const nep_handle *h, nep_tuning *t) {
 
 int nep_descriptors(nep_handle *h, int n_atoms, const double *pos, const int *types, const double *box, double *q,
                     nep_stream_t stream) {
+  nep::NvtxRange nvtx_range("nep_descriptors");
   if (!valid_handle(h)) return NEP_ERR_ARG;
   h->err.clear();
   cudaStream_t s = (cudaStream_t)stream;
@@ -1745,6 +1763,7 @@ int nep_compute_host(nep_handle *h, int n_atoms, const double *pos, const int *t
 
 int md_init(nep_handle *h, int n_atoms, const double *pos, const int *types, const double *box, const double *vel,
             nep_stream_t stream) {
+  nep::NvtxRange nvtx_range("md_init");
   if (!valid_handle(h)) return NEP_ERR_ARG;
   h->err.clear();
   cudaStream_t s = (cudaStream_t)stream;
@@ -1958,6 +1977,7 @@ namespace {
 // rebuild, replay. A converged relaxation stops at the end of its chunk.
 int run_steps(nep_handle *h, int n_steps, double dt_fs, int thermo_every, double *thermo, cudaStream_t s, bool fire,
               double *heat = nullptr) {
+  nep::NvtxRange nvtx_range("md_run");
   const int N = h->N;
   const size_t b = sizeof(double) * 3 * (size_t)N;
   CK(h->ck_x.ensure(3 * (size_t)N), "alloc checkpoint");

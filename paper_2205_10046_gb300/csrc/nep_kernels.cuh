@@ -1159,12 +1159,11 @@ __device__ __forceinline__ void gather_block_sums(const AtomArgs &a, int mem, co
 }
 
 // ------------------------------------------------------------------------ gather kernel
-// For one structure and N_bas^R <= 8 the gather fits 64 registers: 1024 threads per SM (8 CTAs
-// of 128) instead of 7 hide more of the neighbour gathers' latency (8,000,000 Si atoms: 3.17
-// against 3.52 ms); larger bases, and the batched form, would spill more, so they keep the
-// compiler's choice.
+// For one structure the gather is held to 64 registers for N_bas^R <= 8 (1024 threads per SM:
+// 8 CTAs of 128 instead of 7 hide more of the neighbour gathers' latency; 8,000,000 Si atoms:
+// 3.17 against 3.52 ms) and to 72 above (7 CTAs); the batched form keeps the compiler's choice.
 template <class S, bool BATCH = false, int GB = kGatherBlock>
-__global__ void __launch_bounds__(GB, (!BATCH && S::KR <= 8) ? 1024 / GB : 1)
+__global__ void __launch_bounds__(GB, BATCH ? 1 : (S::KR <= 8 ? 1024 : 896) / GB)
     gather_kernel(const AtomArgs a) {
   constexpr int KR = S::KR, EST = S::EST;
   extern __shared__ float4 smem4[];
