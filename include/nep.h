@@ -290,7 +290,8 @@ int nep_n_des(const nep_handle *h);
 int md_init(nep_handle *h, int n_atoms, const double *pos, const int *types, const double *box,
             const double *vel, nep_stream_t stream);
 
-/* md_init from HOST arrays (synchronous). */
+/* md_init from HOST arrays (synchronous; the legacy default stream). The arrays are copied
+ * straight into the handle's workspace: page-locked host memory gives full-speed copies. */
 int md_init_host(nep_handle *h, int n_atoms, const double *pos, const int *types, const double *box,
                  const double *vel);
 
@@ -362,7 +363,8 @@ int md_status(nep_handle *h, nep_stream_t stream);
  * cell [N][3], velocities [N][3], forces of the current positions [N][3]. */
 int md_get_state(nep_handle *h, double *pos, double *vel, double *force, nep_stream_t stream);
 
-/* md_get_state into HOST arrays (synchronous). */
+/* md_get_state into HOST arrays (synchronous; the legacy default stream), through the
+ * handle's workspace (no temporary device allocation). */
 int md_get_state_host(nep_handle *h, double *pos, double *vel, double *force);
 
 /* Statistics of the last neighbour build and of the MD run so far. */

@@ -1798,27 +1798,19 @@ int md_init_host(nep_handle *h, int n_atoms, const double *pos, const int *types
                  const double *vel) {
   if (!valid_handle(h)) return NEP_ERR_ARG;
   if (n_atoms < 1 || !pos || !types || !box) return fail(h, NEP_ERR_ARG, "md_init needs atoms, types and a box");
-  double *dp = nullptr, *dv = nullptr;
-  int *dt = nullptr;
-  cudaError_t e = cudaMalloc(&dp, 3 * (size_t)n_atoms * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&dt, (size_t)n_atoms * sizeof(int));
-  if (e == cudaSuccess && vel) e = cudaMalloc(&dv, 3 * (size_t)n_atoms * sizeof(double));
-  int rc = NEP_OK;
-  if (e == cudaSuccess) {
-    cudaMemcpy(dp, pos, 3 * (size_t)n_atoms * sizeof(double), cudaMemcpyHostToDevice);
-    if (vel) cudaMemcpy(dv, vel, 3 * (size_t)n_atoms * sizeof(double), cudaMemcpyHostToDevice);
-    e = cudaMemcpy(dt, types, (size_t)n_atoms * sizeof(int), cudaMemcpyHostToDevice);
-  }
-  if (e != cudaSuccess) rc = cuda_fail(h, e, "md_init_host");
-  if (!rc) rc = md_init(h, n_atoms, dp, dt, box, dv, nullptr);
-  if (!rc) {
-    e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) rc = cuda_fail(h, e, "md_init_host");
-  }
-  cudaFree(dp);
-  cudaFree(dt);
-  if (dv) cudaFree(dv);
-  return rc;
+  // the host arrays go straight into the handle's reorder scratch (no temporary device
+  // buffers); md_init copies them on the same stream before the neighbour build reuses it
+  int rc = ensure_atoms(h, n_atoms, nullptr);
+  if (rc) return rc;
+  const size_t b3 = sizeof(double) * 3 * (size_t)n_atoms;
+  CK(cudaMemcpyAsync(h->x2.p, pos, b3, cudaMemcpyHostToDevice, nullptr), "md_init_host");
+  CK(cudaMemcpyAsync(h->types2.p, types, sizeof(int) * (size_t)n_atoms, cudaMemcpyHostToDevice, nullptr),
+     "md_init_host");
+  if (vel) CK(cudaMemcpyAsync(h->v2.p, vel, b3, cudaMemcpyHostToDevice, nullptr), "md_init_host");
+  rc = md_init(h, n_atoms, h->x2.p, h->types2.p, box, vel ? h->v2.p : nullptr, nullptr);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(nullptr), "md_init_host");
+  return NEP_OK;
 }
 
 namespace {
@@ -2170,17 +2162,15 @@ int md_get_state(nep_handle *h, double *pos, double *vel, double *force, nep_str
 int md_get_state_host(nep_handle *h, double *pos, double *vel, double *force) {
   if (!valid_handle(h)) return NEP_ERR_ARG;
   if (!h->md_ready) return fail(h, NEP_ERR_STATE, "no MD state");
+  // exported into the handle's reorder scratch (idle between steps), then copied out
   const size_t b = sizeof(double) * 3 * (size_t)h->N;
-  double *d = nullptr;
-  CK(cudaMalloc(&d, 3 * b), "alloc");
-  int rc = md_get_state(h, pos ? d : nullptr, vel ? d + 3 * (size_t)h->N : nullptr,
-                        force ? d + 6 * (size_t)h->N : nullptr, nullptr);
-  cudaError_t e = cudaDeviceSynchronize();
-  if (!rc && e == cudaSuccess && pos) e = cudaMemcpy(pos, d, b, cudaMemcpyDeviceToHost);
-  if (!rc && e == cudaSuccess && vel) e = cudaMemcpy(vel, d + 3 * (size_t)h->N, b, cudaMemcpyDeviceToHost);
-  if (!rc && e == cudaSuccess && force) e = cudaMemcpy(force, d + 6 * (size_t)h->N, b, cudaMemcpyDeviceToHost);
-  cudaFree(d);
+  int rc = md_get_state(h, pos ? h->x2.p : nullptr, vel ? h->v2.p : nullptr, force ? h->F2.p : nullptr, nullptr);
   if (rc) return rc;
+  cudaError_t e = cudaSuccess;
+  if (pos) e = cudaMemcpyAsync(pos, h->x2.p, b, cudaMemcpyDeviceToHost, nullptr);
+  if (e == cudaSuccess && vel) e = cudaMemcpyAsync(vel, h->v2.p, b, cudaMemcpyDeviceToHost, nullptr);
+  if (e == cudaSuccess && force) e = cudaMemcpyAsync(force, h->F2.p, b, cudaMemcpyDeviceToHost, nullptr);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
   if (e != cudaSuccess) return cuda_fail(h, e, "md_get_state_host");
   return NEP_OK;
 }

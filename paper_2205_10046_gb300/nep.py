@@ -438,10 +438,17 @@ def md_get_state(h, pos=None, vel=None, force=None):
     _check(rc, h)
 
 
-def md_get_state_host(h, n: int):
-    pos = np.zeros((n, 3))
-    vel = np.zeros((n, 3))
-    F = np.zeros((n, 3))
+def md_get_state_host(h, n: int, pos=None, vel=None, F=None):
+    """(pos, vel, F) [n, 3] float64 host arrays; pass preallocated C-contiguous arrays (e.g.
+    views of page-locked memory) to have them filled in place."""
+    out = []
+    for a in (pos, vel, F):
+        if a is None:
+            a = np.zeros((n, 3))
+        elif a.dtype != np.float64 or a.shape != (n, 3) or not a.flags.c_contiguous:
+            raise ValueError("state arrays must be C-contiguous float64 [n, 3]")
+        out.append(a)
+    pos, vel, F = out
     rc = load().md_get_state_host(h, pos.ctypes.data, vel.ctypes.data, F.ctypes.data)
     _check(rc, h)
     return pos, vel, F

@@ -264,3 +264,33 @@ def test_low_register_atom_form_matches_oracle(torch_cuda, seed, n):
     h.close()
     _, _, th_ref, _ = oracle.md(model, pos, vel, types, box, 10, 1.0)
     assert np.abs(th.cpu().numpy()[:, 0] - th_ref[1:, 0]).max() / n <= 1e-6
+
+
+def test_host_md_entry_points_match_device(torch_cuda):
+    """md_init_host / md_get_state_host (host arrays, page-locked or not) give the device
+    entry points' trajectory bit for bit, twice in a row on one handle."""
+    torch = torch_cuda
+    from paper_2205_10046_gb300 import nep
+    w = W.si_diamond(3, seed=0)
+    h = nep.NEP(w.model)
+    nep.md_init(h.h, torch.tensor(w.pos, device="cuda"), torch.tensor(w.types, device="cuda"), w.box,
+                torch.tensor(w.vel, device="cuda"))
+    nep.md_run(h.h, 12, 1.0, 1, None)
+    ref = [torch.zeros((w.n_atoms, 3), dtype=torch.float64, device="cuda") for _ in range(3)]
+    nep.md_get_state(h.h, *ref)
+    torch.cuda.synchronize()
+    ref = [r.cpu().numpy() for r in ref]
+    for pinned in (False, True):
+        if pinned:
+            pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).pin_memory().numpy()
+            pos, types, vel = pin(w.pos, np.float64), pin(w.types, np.int32), pin(w.vel, np.float64)
+            outs = [torch.empty((w.n_atoms, 3), dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
+        else:
+            pos, types, vel, outs = w.pos, w.types, w.vel, [None, None, None]
+        nep.md_init_host(h.h, pos, types, w.box, vel)
+        nep.md_run(h.h, 12, 1.0, 1, None)
+        torch.cuda.synchronize()
+        got = nep.md_get_state_host(h.h, w.n_atoms, *outs)
+        for a, b in zip(got, ref):
+            np.testing.assert_array_equal(a, b)
+    h.close()
