@@ -70,6 +70,8 @@ def parse_args():
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window of each serving run")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (requests/s)")
     ap.add_argument("--serve-workers", type=int, default=1024, help="job slots of the serving batch")
+    ap.add_argument("--serve-compact", type=int, default=0,
+                    help="lazy leaving of finished jobs (nep_server_config.compact_every; 0 = at once)")
     ap.add_argument("--pop-calls", type=int, default=5)
     return ap.parse_args()
 
@@ -606,12 +608,13 @@ def serve_sample(pool, reqs):
     return set(sp + nve)
 
 
-def serve_run(model, pool, reqs, precision, workers, sample=()):
+def serve_run(model, pool, reqs, precision, workers, sample=(), compact_every=0):
     """Submit the requests at their arrival times; collect every result (with the final
     arrays of the requests in `sample`)."""
     import numpy as np
     from paper_2205_10046_gb300 import nep
-    srv = nep.Server(model, memory_budget=SERVE_BUDGET, workers=workers, precision=precision, skin=SERVE_SKIN)
+    srv = nep.Server(model, memory_budget=SERVE_BUDGET, workers=workers, precision=precision, skin=SERVE_SKIN,
+                     compact_every=compact_every)
     done = {}
     offered = 0.0
     lag = []
@@ -670,6 +673,9 @@ def serve_run(model, pool, reqs, precision, workers, sample=()):
         "peak_bytes_reserved": int(st["peak_bytes_reserved"]),
         "submit_lag_ms_p99": float(np.percentile(lag, 99)) * 1e3,
         "errors": sorted({r["message"] for r in res if r["status"] != 0})[:3],
+        "scheduler": {"iterations": int(st["iterations"]), "relayouts": int(st["relayouts"]),
+                      "relayout_s": st["relayout_seconds"], "iteration_s": st["step_seconds"],
+                      "fetch_s": st["fetch_seconds"]},
     }, kept
 
 
@@ -727,11 +733,11 @@ def run_serving(args):
                         f"structures drawn from a pool of 256 (32-20,000 atoms, log-uniform, FCC/BCC/diamond, "
                         f"1-3 of 3 species); 50% single point, 30% 50-step FIRE, 20% NVE U{{10..1000}} steps "
                         f"of 1 fs; NEP rc 5.5/4.0 n_max 8/4 40 neurons; one batch of up to {args.serve_workers} jobs (iteration-level batching), "
-                        f"{SERVE_BUDGET >> 30} GB admission budget"),
+                        f"{SERVE_BUDGET >> 30} GB admission budget, compact_every {args.serve_compact}"),
            "latency": "submission (arrival) to result on the host, server clock"}
     kept = {}
     for prec, key in ((0, "fp32"), (1, "bf16")):
-        out[key], kept[key] = serve_run(model, pool, reqs, prec, args.serve_workers, sample)
+        out[key], kept[key] = serve_run(model, pool, reqs, prec, args.serve_workers, sample, args.serve_compact)
     # a load the server sustains: half the FP32 capacity measured above
     cap = out["fp32"]["throughput_atom_evaluations_per_s"]
     work = out["fp32"]["offered_atom_evaluations_per_s"] / args.serve_rate  # per request
@@ -739,7 +745,8 @@ def run_serving(args):
     reqs2 = serve_requests(rate2, args.serve_seconds, 6, pool)
     out["half_capacity"] = {"rate_req_per_s": rate2, "requests": len(reqs2)}
     for prec, key in ((0, "fp32"), (1, "bf16")):
-        out["half_capacity"][key], _ = serve_run(model, pool, reqs2, prec, args.serve_workers)
+        out["half_capacity"][key], _ = serve_run(model, pool, reqs2, prec, args.serve_workers,
+                                                 compact_every=args.serve_compact)
     return out, (model, pool, reqs, kept)
 
 

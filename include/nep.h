@@ -223,6 +223,11 @@ typedef struct {
   size_t memory_budget; /* bytes of device workspace that running jobs may hold together */
   int workers;          /* job slots of the batch: jobs on the device at once (1..65536) */
   int precision;        /* 0: FP32 network, 1: BF16 / 2: split-BF16 tensor-core network (nep_set_precision) */
+  int compact_every;    /* 0: a finished job leaves the batch at once (one layout change, with a
+                           full neighbour build, per iteration that ends a job); c > 0: finished
+                           jobs stay frozen in the batch (results already delivered) until they
+                           are 1/c of it, and queued jobs join once 1/c of the slots and of the
+                           budget are free, so one layout change serves many jobs */
 } nep_server_config;
 
 typedef struct {
@@ -256,6 +261,10 @@ typedef struct {
   size_t bytes_reserved, peak_bytes_reserved; /* admission estimates of the running jobs */
   size_t peak_workspace_bytes;                /* largest device workspace of the batch */
   double atom_evaluations;                    /* sum over finished jobs of N x force evaluations */
+  long long iterations, relayouts;            /* batch iterations run; layout changes */
+  double relayout_seconds, step_seconds, fetch_seconds; /* scheduler wall time: layout changes,
+                                                 iterations (incl. builds and the state read),
+                                                 copying finished jobs out */
 } nep_server_stats;
 
 /* Start the workers (each creates its handle for `params`, copied). NEP_ERR_ARG for a bad

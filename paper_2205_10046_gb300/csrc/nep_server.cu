@@ -44,6 +44,7 @@ struct Job {
   std::vector<int> types;
   double t_submit = 0, t_start = 0;
   size_t est = 0;
+  bool finished = false;  // results delivered; frozen in the batch until the next layout change
 };
 
 struct Arrays {
@@ -78,6 +79,9 @@ struct __attribute__((visibility("hidden"))) nep_server {
   size_t reserved = 0, peak_reserved = 0, peak_workspace = 0;
   long long completed = 0, failed = 0;
   double atom_evals = 0;
+  // where the scheduler's time goes (host wall clock)
+  long long iterations = 0, relayouts = 0;
+  double t_relayout = 0, t_step = 0, t_fetch = 0;
   std::thread scheduler;
 
   // Device workspace estimate of one job (bytes): its per-atom arrays in the batch,
@@ -118,6 +122,17 @@ void nep_server::scheduler_main() {
   }
   std::vector<Job> active;  // in batch order
   bool relaid = false;      // the layout changed since the last iteration (force a build)
+  // finished jobs have left `active` but not yet the engine's layout: the next layout change
+  // (with the jobs admitted then) keeps only these engine job indices, so one relayout per
+  // iteration serves both the leaving and the joining jobs
+  bool compact = false;
+  std::vector<int> pending_keep;
+  auto timed = [](double &acc, auto &&fn) {
+    const auto a = std::chrono::steady_clock::now();
+    auto r = fn();
+    acc += std::chrono::duration<double>(std::chrono::steady_clock::now() - a).count();
+    return r;
+  };
   for (;;) {
     // 1. admit queued jobs (first in first out) while a job slot and the budget allow
     std::vector<Job> add;
@@ -126,10 +141,22 @@ void nep_server::scheduler_main() {
       if (active.empty()) cv_work.wait(lk, [&] { return stopping || !queue.empty(); });
       if (stopping) break;
       long long batch_atoms = 0;
-      for (const Job &j : active) batch_atoms += j.spec.n_atoms;
-      while (!queue.empty() && (int)(active.size() + add.size()) < cfg.workers &&
+      int live = 0;
+      for (const Job &j : active)
+        if (!j.finished) {
+          batch_atoms += j.spec.n_atoms;
+          ++live;
+        }
+      // lazy leaving (compact_every > 0): while jobs run, admit only once a 1/compact_every
+      // share of the slots and of the budget is free, so that one layout change takes many
+      // jobs in (and the finished ones out)
+      const bool gate_open = cfg.compact_every <= 0 || live == 0 ||
+                             (cfg.workers - live >= std::max(1, cfg.workers / cfg.compact_every) &&
+                              cfg.memory_budget - std::min(reserved, cfg.memory_budget) >=
+                                  cfg.memory_budget / (size_t)cfg.compact_every);
+      while (gate_open && !queue.empty() && live + (int)add.size() < cfg.workers &&
              batch_atoms + queue.front().spec.n_atoms <= kEngineMaxAtoms &&
-             (active.empty() && add.empty() ? true : reserved + queue.front().est <= cfg.memory_budget)) {
+             (live == 0 && add.empty() ? true : reserved + queue.front().est <= cfg.memory_budget)) {
         Job j = std::move(queue.front());
         queue.pop_front();
         batch_atoms += j.spec.n_atoms;
@@ -166,10 +193,25 @@ void nep_server::scheduler_main() {
       fail_jobs(add, rc ? rc : NEP_ERR_STATE, "server has no handle: " + setup_error);
       continue;
     }
-    // 2. new layout: the running jobs, then the admitted ones
-    if (!add.empty()) {
-      std::vector<int> keep(active.size());
-      for (size_t k = 0; k < active.size(); ++k) keep[k] = (int)k;
+    // 2. new layout: the running jobs, then the admitted ones (and the finished jobs out)
+    if (!add.empty() || (compact && !active.empty())) {
+      // any layout change also drops the finished jobs still frozen in the batch
+      std::vector<int> keep;
+      if (compact) keep = pending_keep;
+      else
+        for (size_t k = 0; k < active.size(); ++k) keep.push_back((int)k);
+      {
+        std::vector<int> live_keep;
+        std::vector<Job> still;
+        for (size_t k = 0; k < active.size(); ++k)
+          if (!active[k].finished) {
+            live_keep.push_back(keep[k]);
+            still.push_back(std::move(active[k]));
+          }
+        keep = std::move(live_keep);
+        active = std::move(still);
+      }
+      compact = false;
       std::vector<nep::EngineJob> in;
       for (Job &j : add) {
         nep::EngineJob e{};
@@ -187,55 +229,89 @@ void nep_server::scheduler_main() {
       size_t target = 0;
       for (const Job &j : active) target += j.est;
       for (const Job &j : add) target += j.est;
-      const int r = nep::engine_relayout(h, keep, in, s, target);
+      const int r = timed(t_relayout, [&] { return nep::engine_relayout(h, keep, in, s, target); });
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        ++relayouts;
+      }
       if (r != NEP_OK) {
         // the admitted jobs cannot be laid out: report them and restore the running batch
         const std::string msg = nep_last_error(h);
         fail_jobs(add, r, msg);
         if (nep::engine_relayout(h, keep, {}, s) != NEP_OK) fail_jobs(active, r, msg);
+        relaid = true;
         continue;
       }
       for (Job &j : add) active.push_back(std::move(j));
       add.clear();
       relaid = true;
     }
-    if (active.empty()) continue;
+    if (active.empty()) {
+      if (compact) nep::engine_relayout(h, {}, {}, s);  // the last jobs left: an empty layout
+      compact = false;
+      continue;
+    }
     // 3. a chunk of iterations of every job: one while jobs wait or start (to admit and finish
     // them promptly), else up to the first job's completion (at most 32)
     int n_iter = 32;
     {
+      // one iteration when a queued job could join now (lazy leaving: once the slots and the
+      // budget have the free share that opens admission)
       std::lock_guard<std::mutex> lk(mu);
-      if (!queue.empty()) n_iter = 1;
+      if (!queue.empty()) {
+        int live = 0;
+        for (const Job &j : active) live += j.finished ? 0 : 1;
+        const bool slot_free = cfg.compact_every <= 0
+                                   ? live < cfg.workers
+                                   : cfg.workers - live >= std::max(1, cfg.workers / cfg.compact_every);
+        const bool budget_free = cfg.compact_every <= 0 ||
+                                 cfg.memory_budget - std::min(reserved, cfg.memory_budget) >=
+                                     cfg.memory_budget / (size_t)cfg.compact_every;
+        if (slot_free && budget_free) n_iter = 1;
+      }
     }
     for (size_t k = 0; k < active.size() && n_iter > 1; ++k) {
+      if (active[k].finished) continue;  // frozen until the next layout change
       const nep::EngineSlot &sl = nep::engine_slot(h, (int)k);
       if (sl.phase != 1) n_iter = 1;
       else n_iter = std::max(1, std::min(n_iter, sl.n_steps - sl.steps_done));
     }
-    const int r = nep::engine_step(h, s, n_iter, relaid);
+    const int r = timed(t_step, [&] { return nep::engine_step(h, s, n_iter, relaid); });
     relaid = false;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      iterations += n_iter;
+    }
     {
       const size_t ws = nep::workspace_bytes(h);
       std::lock_guard<std::mutex> lk(mu);
       peak_workspace = std::max(peak_workspace, ws);
     }
     if (r != NEP_OK) {
-      fail_jobs(active, r, nep_last_error(h));
+      std::vector<Job> unfinished;
+      for (Job &j : active)
+        if (!j.finished) unfinished.push_back(std::move(j));
+      active.clear();
+      fail_jobs(unfinished, r, nep_last_error(h));
       nep::engine_relayout(h, {}, {}, s);
+      compact = false;
       continue;
     }
-    // 4. finished jobs leave with their results
-    std::vector<int> keep;
+    const auto t_fetch0 = std::chrono::steady_clock::now();
+    // 4. finished jobs hand over their results at once; they leave the batch at the next
+    // layout change, or now if (lazy leaving) they make up a 1/compact_every share of it
     std::vector<nep_result> out;
     std::vector<std::pair<long long, Arrays>> outa;
     double evals = 0;
+    int n_finished = 0;
     for (size_t k = 0; k < active.size(); ++k) {
-      const nep::EngineSlot &sl = nep::engine_slot(h, (int)k);
-      if (sl.phase != 2) {
-        keep.push_back((int)k);
+      Job &j = active[k];
+      if (j.finished) {
+        ++n_finished;
         continue;
       }
-      Job &j = active[k];
+      const nep::EngineSlot &sl = nep::engine_slot(h, (int)k);
+      if (sl.phase != 2) continue;
       nep_result res{};
       res.id = j.id;
       res.kind = j.spec.kind;
@@ -253,29 +329,20 @@ void nep_server::scheduler_main() {
       if (j.spec.kind == NEP_JOB_NVE) a.vel.resize(n3);
       res.status = nep::engine_fetch(h, (int)k, a.pos.data(), a.force.data(), a.vel.empty() ? nullptr : a.vel.data(), s);
       if (res.status != NEP_OK) std::snprintf(res.message, sizeof(res.message), "%s", nep_last_error(h));
-      // the job's share of the batch workspace, by atoms
-      const int na = std::max(nep::engine_atoms(h), 1);
       res.workspace_used = nep::workspace_bytes(h);
       res.t_done = now_since(t0);
       evals += (double)j.spec.n_atoms * (1 + sl.steps_done);
       out.push_back(res);
       outa.emplace_back(j.id, std::move(a));
+      j.finished = true;
+      ++n_finished;
     }
     if (!out.empty()) {
-      std::vector<Job> still;
-      for (int k : keep) still.push_back(std::move(active[k]));
-      std::vector<size_t> ests;
-      for (const nep_result &res : out) ests.push_back(res.workspace_est);
-      active = std::move(still);
-      size_t target = 0;
-      for (const Job &j : active) target += j.est;
-      if (nep::engine_relayout(h, keep, {}, s, target) != NEP_OK) fail_jobs(active, NEP_ERR_CUDA, nep_last_error(h));
-      relaid = true;
       {
         std::lock_guard<std::mutex> lk(mu);
         for (size_t q = 0; q < out.size(); ++q) {
           --running;
-          reserved -= ests[q];
+          reserved -= out[q].workspace_est;
           if (out[q].status == NEP_OK) {
             ++completed;
             arrays.emplace(outa[q].first, std::move(outa[q].second));
@@ -287,6 +354,24 @@ void nep_server::scheduler_main() {
         atom_evals += evals;
       }
       cv_done.notify_all();
+    }
+    if (n_finished > 0 && (cfg.compact_every <= 0 || n_finished == (int)active.size() ||
+                           n_finished * cfg.compact_every >= (int)active.size())) {
+      // the engine keeps the finished jobs until the next layout change (step 2)
+      std::vector<int> keep;
+      std::vector<Job> still;
+      for (size_t k = 0; k < active.size(); ++k)
+        if (!active[k].finished) {
+          keep.push_back((int)k);
+          still.push_back(std::move(active[k]));
+        }
+      active = std::move(still);
+      pending_keep = std::move(keep);
+      compact = true;
+    }
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      t_fetch += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_fetch0).count();
     }
   }
   if (h) {
@@ -308,8 +393,9 @@ NEP_SERVER_API int nep_server_create(const nep_params *params, const nep_server_
   }
   *out = nullptr;
   if (cfg->workers < 1 || cfg->workers > 65536 || cfg->memory_budget == 0 ||
-      cfg->precision < 0 || cfg->precision > 2) {
-    nep::set_create_error("need 1 <= workers <= 65536, memory_budget > 0, precision 0, 1 or 2");
+      cfg->precision < 0 || cfg->precision > 2 || cfg->compact_every < 0 || cfg->compact_every > 1024) {
+    nep::set_create_error("need 1 <= workers <= 65536, memory_budget > 0, precision 0, 1 or 2, "
+                          "0 <= compact_every <= 1024");
     return NEP_ERR_ARG;
   }
   if (!params->mass) {
@@ -434,6 +520,11 @@ NEP_SERVER_API int nep_server_stats_get(nep_server *s, nep_server_stats *out) {
   out->peak_bytes_reserved = s->peak_reserved;
   out->peak_workspace_bytes = s->peak_workspace;
   out->atom_evaluations = s->atom_evals;
+  out->iterations = s->iterations;
+  out->relayouts = s->relayouts;
+  out->relayout_seconds = s->t_relayout;
+  out->step_seconds = s->t_step;
+  out->fetch_seconds = s->t_fetch;
   return NEP_OK;
 }
 

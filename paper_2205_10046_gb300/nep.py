@@ -57,7 +57,8 @@ class md_options(C.Structure):
 
 
 class nep_server_config(C.Structure):
-    _fields_ = [("memory_budget", C.c_size_t), ("workers", C.c_int), ("precision", C.c_int)]
+    _fields_ = [("memory_budget", C.c_size_t), ("workers", C.c_int), ("precision", C.c_int),
+                ("compact_every", C.c_int)]
 
 
 class nep_job(C.Structure):
@@ -76,7 +77,9 @@ class nep_result(C.Structure):
 class nep_server_stats(C.Structure):
     _fields_ = [("queued", C.c_int), ("running", C.c_int), ("completed", C.c_longlong), ("failed", C.c_longlong),
                 ("bytes_reserved", C.c_size_t), ("peak_bytes_reserved", C.c_size_t),
-                ("peak_workspace_bytes", C.c_size_t), ("atom_evaluations", C.c_double)]
+                ("peak_workspace_bytes", C.c_size_t), ("atom_evaluations", C.c_double),
+                ("iterations", C.c_longlong), ("relayouts", C.c_longlong), ("relayout_seconds", C.c_double),
+                ("step_seconds", C.c_double), ("fetch_seconds", C.c_double)]
 
 
 JOB_SINGLE, JOB_FIRE, JOB_NVE = 0, 1, 2
@@ -553,10 +556,11 @@ class NEP:
 class Server:
     """A running nep_server: submit jobs (host arrays), collect results in completion order."""
 
-    def __init__(self, model, memory_budget: int, workers: int = 16, precision: int = 0, skin: float = 1.0):
+    def __init__(self, model, memory_budget: int, workers: int = 16, precision: int = 0, skin: float = 1.0,
+                 compact_every: int = 0):
         lib = load()
         p, self._keep = _params(model, skin)
-        cfg = nep_server_config(int(memory_budget), int(workers), int(precision))
+        cfg = nep_server_config(int(memory_budget), int(workers), int(precision), int(compact_every))
         h = C.c_void_p()
         _check(lib.nep_server_create(C.byref(p), C.byref(cfg), C.byref(h)), None)
         self.h = h
