@@ -63,7 +63,8 @@ __global__ void __launch_bounds__(128) generic_atom_kernel(const AtomArgs a, con
   const float *c_r = a.c_r + mem * a.s_cr, *c_a = a.c_a + mem * a.s_ca;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double Ublock = 0.0;
-  if (i < N) {
+  // (serving engine) atoms of a finished job frozen in the batch are skipped
+  if (i < N && !(BATCH && a.slots && a.slots[struct_of(a.pos4[i])].phase == 2)) {
     const float4 pi = a.pos4[i];
     const int ti = type_of(pi);
     const float4 *tab = a.dtab + (BATCH ? (size_t)struct_of(pi) * a.ncode : 0);
@@ -271,7 +272,7 @@ __global__ void __launch_bounds__(128) generic_gather_kernel(const AtomArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double part[kReduceSlots];
   for (int s = 0; s < kReduceSlots; ++s) part[s] = 0.0;
-  if (i < N) {
+  if (i < N && !(BATCH && a.slots && a.slots[struct_of(a.pos4[i])].phase == 2)) {
     const float4 pi = a.pos4[i];
     const int ti = type_of(pi);
     const float4 *tab = a.dtab + (BATCH ? (size_t)struct_of(pi) * a.ncode : 0);

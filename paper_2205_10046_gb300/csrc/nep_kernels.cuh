@@ -397,13 +397,14 @@ __global__ void __launch_bounds__(AB, OCC)
   const int T = a.T;
   const int N = a.N;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  // Threads past the last atom run the same code with no neighbours (the tensor-core steps
-  // are block- and warp-collective); they write nothing.
-  const bool active = i < N;
+  // Threads past the last atom, and (serving engine) atoms of a finished job frozen in the
+  // batch, run the same code with no neighbours (the tensor-core steps are block- and
+  // warp-collective); they write nothing.
   // This atom's position, list lengths and first list entries are requested before the
   // block's setup (shared tables, TMEM), which hides their DRAM latency: the counts into
   // registers, the first 16 radial and 2 angular slots into L2.
-  const float4 pi = active ? __ldg(a.pos4 + i) : make_float4(0.f, 0.f, 0.f, __int_as_float(0));
+  const float4 pi = i < N ? __ldg(a.pos4 + i) : make_float4(0.f, 0.f, 0.f, __int_as_float(0));
+  const bool active = i < N && !(BATCH && a.slots && a.slots[struct_of(pi)].phase == 2);
   const int na = active ? __ldg(a.nn_a + i) : 0;
   int cnt_r = active ? __ldg(a.nn_r + i) : 0;
   if (active) {
@@ -1180,7 +1181,8 @@ __global__ void __launch_bounds__(GB, BATCH ? 1 : (S::KR <= 8 ? 1024 : 896) / GB
   double part[kReduceSlots];
 #pragma unroll
   for (int s = 0; s < kReduceSlots; ++s) part[s] = 0.0;
-  if (i < N) {
+  // (serving engine) atoms of a finished job frozen in the batch are skipped
+  if (i < N && !(BATCH && a.slots && a.slots[struct_of(a.pos4[i])].phase == 2)) {
     const float4 pi = a.pos4[i];
     const int ti = type_of(pi);
     const float4 *dtab_b = BATCH ? a.dtab + (size_t)struct_of(pi) * a.ncode : dtab_s;
