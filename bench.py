@@ -70,8 +70,10 @@ def parse_args():
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window of each serving run")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (requests/s)")
     ap.add_argument("--serve-workers", type=int, default=1024, help="job slots of the serving batch")
-    ap.add_argument("--serve-compact", type=int, default=0,
+    ap.add_argument("--serve-compact", type=int, default=8,
                     help="lazy leaving of finished jobs (nep_server_config.compact_every; 0 = at once)")
+    ap.add_argument("--serve-rate2", type=float, default=0.0,
+                    help="arrival rate of the second (sustained-load) serving run; 0 = half the measured FP32 capacity")
     ap.add_argument("--pop-calls", type=int, default=5)
     return ap.parse_args()
 
@@ -738,10 +740,10 @@ def run_serving(args):
     kept = {}
     for prec, key in ((0, "fp32"), (1, "bf16")):
         out[key], kept[key] = serve_run(model, pool, reqs, prec, args.serve_workers, sample, args.serve_compact)
-    # a load the server sustains: half the FP32 capacity measured above
+    # a load the server sustains: half the FP32 capacity measured above (or a given rate)
     cap = out["fp32"]["throughput_atom_evaluations_per_s"]
     work = out["fp32"]["offered_atom_evaluations_per_s"] / args.serve_rate  # per request
-    rate2 = max(10.0, 0.5 * cap / work)
+    rate2 = args.serve_rate2 if args.serve_rate2 > 0 else max(10.0, 0.5 * cap / work)
     reqs2 = serve_requests(rate2, args.serve_seconds, 6, pool)
     out["half_capacity"] = {"rate_req_per_s": rate2, "requests": len(reqs2)}
     for prec, key in ((0, "fp32"), (1, "bf16")):
