@@ -122,6 +122,7 @@ int build_grid(const double *box, double rl, int N, Grid &g, float4 *dtab, doubl
     g.R[a] = (int)std::ceil(rl * g.nc[a] / th[a] - 1e-12);
     if (g.R[a] < 1) g.R[a] = 1;
     rmax = std::max(rmax, g.R[a]);
+    g.reach[a] = (float)((rl + kReachMargin) * g.nc[a] / th[a]);
   }
   if (rmax > kMaxImage) {
     *err = "cell thinner than a third of r_c^R + skin; replicate the cell before calling";

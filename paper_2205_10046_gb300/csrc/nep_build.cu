@@ -211,9 +211,16 @@ __device__ __forceinline__ int floor_div(int x, int n) { return (x + 8 * n) / n 
 // shift S is formed once per run and the distance comes from the FP32 positions in the cell
 // frame: d = (r_j - r_i) + S, exactly antisymmetric like pair_vector. The image code of an
 // entry is the cell offset (ox, oy, oz), as the force kernels' shift tables expect.
+//
+// Cells that cannot hold a pair are skipped: along axis a, atom i sits at the fraction u_a of
+// its cell's width, so every point of the cell at offset o >= 1 lies (o - u_a) cell
+// thicknesses away across the lattice planes, and of the cell at o <= -1, (u_a - o - 1); a
+// cell is visited only if that gap stays below reach_a = (r_c^R + skin + margin) / thickness.
+// The skipped candidates would all fail the distance test, so the lists (and their order)
+// are those of the full (2R+1)^3 scan. pl: atom i's cell-local coordinates (pos4).
 template <class F>
-__device__ __forceinline__ void for_candidates(int i, const float4 &pi, int gid, const Grid &g, const int *start,
-                                               const float4 *posA, F &&f) {
+__device__ __forceinline__ void for_candidates(int i, const float4 &pi, const float4 &pl, int gid, const Grid &g,
+                                               const int *start, const float4 *posA, F &&f) {
   const int id = gid - g.cell_off;
   const int cx = id / (g.nc[1] * g.nc[2]);
   const int cy = (id / g.nc[2]) % g.nc[1];
@@ -223,10 +230,18 @@ __device__ __forceinline__ void for_candidates(int i, const float4 &pi, int gid,
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) Hf[a][b] = (float)g.H[a][b];
-  for (int ox = -g.R[0]; ox <= g.R[0]; ++ox) {
+  int lo[3], hi[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float s = pl.x * (float)g.Hinv[0][a] + pl.y * (float)g.Hinv[1][a] + pl.z * (float)g.Hinv[2][a];
+    const float u = fminf(fmaxf(s * (float)g.nc[a], 0.f), 1.f);
+    hi[a] = min(g.R[a], (int)ceilf(u + g.reach[a]) - 1);
+    lo[a] = max(-g.R[a], 1 - (int)ceilf(1.f - u + g.reach[a]));
+  }
+  for (int ox = lo[0]; ox <= hi[0]; ++ox) {
     const int kx = floor_div(cx + ox, g.nc[0]);
     const int xm = cx + ox - kx * g.nc[0];
-    for (int oy = -g.R[1]; oy <= g.R[1]; ++oy) {
+    for (int oy = lo[1]; oy <= hi[1]; ++oy) {
       const int ky = floor_div(cy + oy, g.nc[1]);
       const int ym = cy + oy - ky * g.nc[1];
       const int col = g.cell_off + (xm * g.nc[1] + ym) * g.nc[2];
@@ -234,11 +249,11 @@ __device__ __forceinline__ void for_candidates(int i, const float4 &pi, int gid,
       const float sy = __fadd_rn(__fmul_rn((float)kx, Hf[0][1]), __fmul_rn((float)ky, Hf[1][1]));
       const float sz = __fadd_rn(__fmul_rn((float)kx, Hf[0][2]), __fmul_rn((float)ky, Hf[1][2]));
       const unsigned code_xy = (unsigned)(ox + g.R[0]) | ((unsigned)(oy + g.R[1]) << g.obits);
-      int z = cz - g.R[2];
-      while (z <= cz + g.R[2]) {
+      int z = cz + lo[2];
+      while (z <= cz + hi[2]) {
         const int kz = floor_div(z, g.nc[2]);
         const int zm = z - kz * g.nc[2];
-        const int run = min(cz + g.R[2] - z, g.nc[2] - 1 - zm) + 1;  // cells of this image
+        const int run = min(cz + hi[2] - z, g.nc[2] - 1 - zm) + 1;  // cells of this image
         const float4 S = make_float4(__fadd_rn(sx, __fmul_rn((float)kz, Hf[2][0])),
                                      __fadd_rn(sy, __fmul_rn((float)kz, Hf[2][1])),
                                      __fadd_rn(sz, __fmul_rn((float)kz, Hf[2][2])), 0.f);
@@ -266,7 +281,7 @@ __device__ __forceinline__ void for_candidates(int i, const float4 &pi, int gid,
 // count_only: record only the length statistics (used to size the lists). TT: the number of
 // atom types (compile time, so the per-type counters of a candidate cost TT compares).
 template <int TT>
-__global__ void build_lists_kernel(int N, const float4 *posA, const int *cell_of, const int *start,
+__global__ void build_lists_kernel(int N, const float4 *posA, const float4 *pos4, const int *cell_of, const int *start,
                                    const Grid g0, const Batch B, float rlR2, float rlA2, float rcR2, float rcA2,
                                    ListBufs L, int count_only, BuildStatus *st) {
   if (!rebuild_pending(st)) return;
@@ -276,6 +291,7 @@ __global__ void build_lists_kernel(int N, const float4 *posA, const int *cell_of
   const int i = active ? i0 : 0;  // a valid index for the idle lanes (N >= 1)
   const Grid &g = grid_of(B, g0, i);
   const float4 pi = posA[i];
+  const float4 pl = pos4[i];
   const int id = cell_of[i];
   // per-type counters stay in registers: every update is unrolled over the types
   int cr0[TT], cr1[TT];
@@ -292,7 +308,7 @@ __global__ void build_lists_kernel(int N, const float4 *posA, const int *cell_of
     // ones, r_c^A <= r_c^R); their groups are counted afterwards from the staged bytes
     unsigned *se = L.stage_e + i;
     unsigned char *sg = L.stage_g + i;
-    for_candidates(i, pi, id, g, start, posA, [&](int, unsigned ent, float r2, int tj) {
+    for_candidates(i, pi, pl, id, g, start, posA, [&](int, unsigned ent, float r2, int tj) {
       if (r2 < rlR2) {
         if (n_seen < L.cap_r) {
           const int ang = r2 < rlA2 ? (r2 < rcA2 ? 1 : 2) : 0;
@@ -324,7 +340,7 @@ __global__ void build_lists_kernel(int N, const float4 *posA, const int *cell_of
     cr1[0] += n_seen - ns;
     ca1 += n_seen - ns;
   } else if (active) {
-    for_candidates(i, pi, id, g, start, posA, [&](int, unsigned ent, float r2, int tj) {
+    for_candidates(i, pi, pl, id, g, start, posA, [&](int, unsigned ent, float r2, int tj) {
       if (r2 < rlR2) {
         const bool core = r2 < rcR2;
 #pragma unroll
@@ -409,7 +425,7 @@ __global__ void build_lists_kernel(int N, const float4 *posA, const int *cell_of
     L.nn_a[i] = nA;
     return;
   }
-  for_candidates(i, pi, id, g, start, posA, [&](int, unsigned ent, float r2, int tj) {
+  for_candidates(i, pi, pl, id, g, start, posA, [&](int, unsigned ent, float r2, int tj) {
     if (r2 < rlR2) {
       const bool core = r2 < rcR2;
       int slot = 0;
@@ -866,7 +882,7 @@ cudaError_t launch_rebuild(int N, int T, const Grid &g, const Batch &B, const fl
   reorder_gather_kernel<<<nb, tb, 0, s>>>(N, L.cell_atoms, a, st);
   reorder_commit_kernel<<<nb, tb, 0, s>>>(N, a, g, B, st);
   auto lists = [&](auto kern) {
-    kern<<<(N + 127) / 128, 128, 0, s>>>(N, a.posA, a.cell_of, L.cell_start, g, B, rlR2, rlA2, rcR2, rcA2, L,
+    kern<<<(N + 127) / 128, 128, 0, s>>>(N, a.posA, a.pos4, a.cell_of, L.cell_start, g, B, rlR2, rlA2, rcR2, rcA2, L,
                                          count_only, st);
   };
   switch (T) {

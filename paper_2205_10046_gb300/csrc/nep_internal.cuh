@@ -10,6 +10,10 @@ namespace nep {
 constexpr int kMaxTypes = 8;
 constexpr int kListBuf = 512;   // largest neighbour-list capacity per atom
 constexpr int kMaxImage = 3;    // largest cell/image offset searched per axis
+// Distance (A) added to r_c^R + skin before a cell is left out of the neighbour search: far
+// above the FP32 rounding of a pair distance, so no candidate that the distance test would
+// accept is left out.
+constexpr double kReachMargin = 2e-3;
 constexpr int kAtomBlock = 128; // threads per block of the per-atom kernel
 constexpr int kGatherBlock = 128;
 constexpr int kReduceSlots = 16; // per-block partial sums: U, KE, W[9], force error, J[3], spare
@@ -27,6 +31,8 @@ struct Grid {
   double H[3][3];     // cell rows
   double Hinv[3][3];  // s = r . Hinv
   double Hc[3][3];    // rows of one grid cell: H[a] / nc[a]
+  float reach[3];     // (r_c^R + skin + kReachMargin) / cell thickness per axis: a cell whose
+                      // gap to an atom's cell position exceeds it along any axis holds no pair
   int cell_off;       // first global cell of this structure (batches; 0 for one structure)
   int dtab_off;       // first shift-table entry of this structure (batches; 0 for one structure)
 };
