@@ -179,14 +179,17 @@ typedef struct {
   int n_tried;            /* out: candidates timed by the last nep_autotune */
   float best_ms;          /* out: time of one evaluation (per member) with the chosen shapes */
   float default_ms;       /* out: the same with 128 / 128 atoms per CTA and one member */
-  int atom_form;          /* FP32 per-atom kernel of nep_compute and md_run: 1 = sums and
+  int atom_form;          /* per-atom kernel form (FP32 and BF16 networks): 1 = sums and
                              dU/dS_nk in registers (two CTAs per SM), 3 = two passes for S_nk and
                              dU/dS_nk in shared memory (three CTAs per SM; shapes whose
-                             (n_max^A + 1) x 24 sums fit 128 TMEM columns, else as 1); 0 = the
-                             library's default (3 where it exists). nep_get_tuning returns the
-                             form in use. The form applies to 128-atom CTAs (an atom_block of 64
-                             runs form 1) and nep_autotune keeps it. The two forms agree to FP32
-                             rounding; within one form, results do not depend on the CTA sizes. */
+                             (n_max^A + 1) x 24 sums fit 128 TMEM columns, else as 1; with the
+                             BF16 network (precision 1) S_nk waits in shared memory and the GEMM
+                             operands and results use 128 TMEM columns); 0 = the library's default
+                             (3 where it exists). The split-BF16 network (precision 2) always runs
+                             form 1. nep_get_tuning returns the form in use. The form applies to
+                             128-atom CTAs (an atom_block of 64 runs form 1) and nep_autotune keeps
+                             it. The two forms agree to FP32 rounding; within one form, results do
+                             not depend on the CTA sizes. */
 } nep_tuning;
 
 /* Set or read the launch shapes (NEP_ERR_ARG for values outside the lists above). */

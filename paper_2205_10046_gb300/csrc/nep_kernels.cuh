@@ -74,6 +74,17 @@ struct Shape {
   static constexpr int TILE_B = NP1 * KP1 * 2;                             // each of B1, B2
   static_assert(DCOL + (NP1 > NP2 ? NP1 : NP2) <= TMEM_COLS, "S and the network results must fit 256 TMEM columns");
   static_assert(NP1 <= 256 && NP2 <= 256, "UMMA N limit");
+  // Low-register form of the tensor-core network: S_nk waits in the thread's shared block
+  // (SPTC floats, later dU/dS_nk in place), the GEMM results take TMEM columns [0, ACOL) and
+  // the A operands (BF16 pairs, one lane per atom) columns [ACOL, ACOL + KP/2): 128 columns a
+  // block. With (SPTC/4) % 4 == 2 the rows are packed without padding and the float4 index is
+  // rotated by ((thread >> 2) & 1), which keeps 8 consecutive threads on 8 distinct bank groups.
+  static constexpr int ACOL = NP1 > NP2 ? NP1 : NP2;
+  static constexpr bool TCLR_OK =
+      NS <= 128 && NK % 8 == 0 && ACOL + (KP1 > KP2 ? KP1 : KP2) / 2 <= 128;
+  static constexpr int SW = (NA + 1) * NKP / 4;  // float4s of one thread's S_nk block
+  static constexpr bool SROT = SW % 4 == 2;
+  static constexpr int SPTC = SROT ? 4 * SW : SPT;
 };
 
 template <class S>
@@ -217,6 +228,22 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float *v) {
                "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
                "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
                "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+               : "memory");
+}
+
+// The same MMA with the A operand read from tensor memory (lane m = row m, K packed along the
+// columns: two BF16 values per 32-bit column, the lower K index in the low half).
+__device__ __forceinline__ void umma_bf16_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t db, uint32_t idesc,
+                                             uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tmem_st8u(uint32_t taddr, const uint32_t *v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
+               "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
                : "memory");
 }
 
@@ -378,15 +405,20 @@ __global__ void __launch_bounds__(AB, OCC)
     atom_kernel(const AtomArgs a, const __grid_constant__ AnnConst<S> w) {
   static_assert(PREC >= 0 && PREC <= 2, "network forms: 0 FP32, 1 BF16, 2 split BF16");
   constexpr bool LOWREG = OCC > 1;
-  static_assert(!LOWREG || (PREC == 0 && !DESC_ONLY && AB == 128 && S::NS <= 128 && S::NK % 8 == 0),
-                "the low-register form: FP32 network, S_nk within 128 TMEM columns");
+  static_assert(!LOWREG || (PREC <= 1 && !DESC_ONLY && AB == 128 && S::NS <= 128 && S::NK % 8 == 0),
+                "the low-register form: FP32 or BF16 network, S_nk within 128 TMEM columns");
+  // TCLR: the low-register form with the BF16 tensor-core network. S_nk then waits in the
+  // thread's shared block (not in TMEM), whose 128 columns hold the GEMM operands and results.
+  constexpr bool TCLR = LOWREG && PREC == 1;
+  static_assert(!TCLR || S::TCLR_OK, "the tensor-core network within 128 TMEM columns");
   constexpr uint32_t TCOLS = LOWREG ? 128u : (uint32_t)S::TMEM_COLS;
   static_assert(PREC == 0 || !DESC_ONLY, "the descriptor-only kernel has no network");
   static_assert(PREC == 0 || AB == 128, "the tensor-core network works on 128-atom tiles (UMMA M = 128)");
   // S_nk waits for the network in this thread's TMEM lane (128-atom blocks, whole groups of 8
   // columns), else in a per-thread block of shared memory
   constexpr bool TM = !DESC_ONLY && AB == 128 && S::NK % 8 == 0;
-  static_assert(PREC == 0 || TM, "the tensor-core network keeps S_nk in TMEM");
+  static_assert(PREC == 0 || TM, "the tensor-core network works in TMEM");
+  constexpr bool STM = TM && !TCLR;  // S_nk parked in TMEM during the network
   // With S_nk parked in TMEM the registers hold all (n_max^A + 1) x 24 sums at once: one pass
   // over the angular neighbours (PbTe: 168 sums); otherwise NPASS passes of NCH values of n.
   constexpr int NPASS = LOWREG ? ((S::NA + 1) >= 2 ? 2 : 1) : (TM && (S::NA + 1) * S::NK <= 192 ? 1 : S::NPASS);
@@ -421,7 +453,7 @@ __global__ void __launch_bounds__(AB, OCC)
   const int mem = BATCH ? (int)blockIdx.y : 0;
   const float *pw = (BATCH && a.pop_ann) ? a.pop_ann + mem * a.s_ann : nullptr;
   float4 *dtab_s = smem4;                                        // [ncode] (one structure)
-  constexpr int KAP = S::KAP, NKP = S::NKP, SPT = S::SPT;
+  constexpr int KAP = S::KAP, NKP = S::NKP, SPT = TCLR ? S::SPTC : S::SPT;
   float *w0_s = reinterpret_cast<float *>(smem4 + (BATCH ? 0 : a.ncode));  // [H][NDP] (FP32 network)
   float *b0_s = w0_s + S::off_b0(PREC);                          // [H]
   float *w1_s = b0_s + S::H;                                     // [H]
@@ -463,10 +495,11 @@ __global__ void __launch_bounds__(AB, OCC)
   unsigned char *tileA = nullptr, *tileB1 = nullptr, *tileB2 = nullptr;
   unsigned char *tileAlo = nullptr, *tileB1lo = nullptr, *tileB2lo = nullptr;
   if constexpr (PREC >= 1) {
-    unsigned char *base = reinterpret_cast<unsigned char *>(S_s);
+    // (TCLR: after the per-thread S_nk blocks, and no A tile: the A operands are in TMEM)
+    unsigned char *base = reinterpret_cast<unsigned char *>(S_s + (TCLR ? AB * SPT : 0));
     base += (128u - (smem_addr(base) & 127u)) & 127u;
     tileA = base;
-    tileB1 = tileA + S::TILE_A;
+    tileB1 = tileA + (TCLR ? 0 : S::TILE_A);
     tileB2 = tileB1 + S::TILE_B;
     if constexpr (SPLIT) {
       tileB1lo = tileB2 + S::TILE_B;
@@ -506,6 +539,13 @@ __global__ void __launch_bounds__(AB, OCC)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     tmem_row = tc_tmem + ((uint32_t)((threadIdx.x >> 5) * 32) << 16);
   }
+  // this thread's shared block of S_nk, later dU/dS_nk: float4 v of [n][NKP / 4]
+  float4 *const Sblk = reinterpret_cast<float4 *>(S_s + threadIdx.x * SPT);
+  const int srot = (TCLR && S::SROT) ? ((threadIdx.x >> 2) & 1) : 0;
+  auto sref = [&](int v) -> float4 & {
+    if constexpr (TCLR && S::SROT) return v == S::SW - 1 ? Sblk[srot ? 0 : S::SW - 1] : Sblk[v + srot];
+    else return Sblk[v];
+  };
 
   double Ublock = 0.0;
   {
@@ -656,10 +696,18 @@ __global__ void __launch_bounds__(AB, OCC)
               q[S::OFF5 + n] = w.m.c5b[0] * s0 * s0 * s0 * s0 + w.m.c5b[1] * s0 * s0 * s12 + w.m.c5b[2] * s12 * s12;
             }
           }
-          // park this part of S_n in TMEM, columns n NK + k0 .. n NK + k1 - 1
-          __syncwarp();
+          if constexpr (TCLR) {
+            // park this part of S_n in the thread's shared block (TMEM serves the network)
 #pragma unroll
-          for (int k8 = 0; k8 < NKC / 8; ++k8) tmem_st8(tmem_row + n * NK + k0 + 8 * k8, &Sv[n][8 * k8]);
+            for (int k4 = 0; k4 < NKC / 4; ++k4)
+              sref(n * (NKP / 4) + k0 / 4 + k4) =
+                  make_float4(Sv[n][4 * k4], Sv[n][4 * k4 + 1], Sv[n][4 * k4 + 2], Sv[n][4 * k4 + 3]);
+          } else {
+            // park this part of S_n in TMEM, columns n NK + k0 .. n NK + k1 - 1
+            __syncwarp();
+#pragma unroll
+            for (int k8 = 0; k8 < NKC / 8; ++k8) tmem_st8(tmem_row + n * NK + k0 + 8 * k8, &Sv[n][8 * k8]);
+          }
         }
       });
     } else
@@ -753,7 +801,6 @@ __global__ void __launch_bounds__(AB, OCC)
         for (int v = 0; v < NDES; ++v) a.q_out[io * NDES + v] = (double)q[v];
       }
     } else {
-      float4 *Sme = reinterpret_cast<float4 *>(S_s + threadIdx.x * SPT);  // [n][NKP / 4]
       if constexpr (TM) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 
       // ---- network, Eq. Ui, and dU/dq
@@ -837,55 +884,130 @@ __global__ void __launch_bounds__(AB, OCC)
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           return true;
         };
-        // q row -> operand tile A (bf16, K-major)
+        if constexpr (TCLR) {
+          // Low-register form: the A operands go to TMEM columns ACOL.. as BF16 pairs (one lane
+          // per atom, no shared-memory tile), the results to columns 0..; B tiles as above.
+          constexpr uint32_t ACOL = S::ACOL;
 #pragma unroll
-        for (int kc = 0; kc < KC1; ++kc) {
-          float x[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) x[j] = 8 * kc + j < NDES ? q[8 * kc + j] : 0.f;
-          put8(tileA, tileAlo, umma_off(r, 8 * kc, KC1), x);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (threadIdx.x == 0)  // GEMM1: z = q . W0^T into TMEM columns DCOL ..
-          gemm(tileA, tileAlo, tileB1, tileB1lo, S::KP1 / 16, KC1, umma_idesc_bf16<kAtomBlock, S::NP1>());
-        __syncwarp();
-        if (tc_wait(0)) {
-          // tanh layer from this row of z; beta = w1 (1 - h^2) -> operand tile A (reused)
-#pragma unroll
-          for (int c8 = 0; c8 < S::NP1 / 8; ++c8) {
-            float z[8];
-            tmem_ld8(tmem_row + S::DCOL + 8 * c8, z);
-            float bt[8];
+          for (int c8 = 0; c8 < S::KP1 / 16; ++c8) {  // q row -> A (16 values per store)
+            uint32_t u[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-              const int mu = 8 * c8 + j;
-              bt[j] = 0.f;
-              if (mu < S::H) {
-                const float h = tanhf(z[j] - b0_s[mu]);
-                U = __fmaf_rn(w1_s[mu], h, U);
-                bt[j] = w1_s[mu] * (1.f - h * h);
+              const int v0 = 16 * c8 + 2 * j;
+              u[j] = pack_bf16x2(v0 < NDES ? q[v0] : 0.f, v0 + 1 < NDES ? q[v0 + 1] : 0.f);
+            }
+            tmem_st8u(tmem_row + ACOL + 8 * c8, u);
+          }
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncthreads();
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          if (threadIdx.x == 0) {  // GEMM1: z = q . W0^T into columns 0 .. NP1 - 1
+            for (int st = 0; st < S::KP1 / 16; ++st)
+              umma_bf16_ts(tc_tmem, tc_tmem + ACOL + 8 * st, umma_desc(smem_addr(tileB1) + 256 * st, 128, KC1 * 128),
+                           umma_idesc_bf16<kAtomBlock, S::NP1>(), st > 0 ? 1u : 0u);
+            umma_commit(&tc_mbar);
+          }
+          __syncwarp();
+          if (tc_wait(0)) {
+            // tanh layer from this row of z; beta = w1 (1 - h^2) -> A (16 hidden units per store;
+            // the GEMM that read q has completed)
+#pragma unroll
+            for (int c16 = 0; c16 < S::NP1 / 16; ++c16) {
+              float z[16];
+              tmem_ld8(tmem_row + 16 * c16, z);
+              tmem_ld8(tmem_row + 16 * c16 + 8, z + 8);
+              float bt[16];
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                const int mu = 16 * c16 + j;
+                bt[j] = 0.f;
+                if (mu < S::H) {
+                  const float h = tanhf(z[j] - b0_s[mu]);
+                  U = __fmaf_rn(w1_s[mu], h, U);
+                  bt[j] = w1_s[mu] * (1.f - h * h);
+                }
+              }
+              uint32_t u[8];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) u[j] = pack_bf16x2(bt[2 * j], bt[2 * j + 1]);
+              tmem_st8u(tmem_row + ACOL + 8 * c16, u);
+            }
+            // every lane has read its z (tcgen05.ld waited) before GEMM2 overwrites the columns
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (threadIdx.x == 0) {  // GEMM2: dq = beta . W0 into columns 0 .. NP2 - 1
+              for (int st = 0; st < S::KP2 / 16; ++st)
+                umma_bf16_ts(tc_tmem, tc_tmem + ACOL + 8 * st,
+                             umma_desc(smem_addr(tileB2) + 256 * st, 128, KC2 * 128),
+                             umma_idesc_bf16<kAtomBlock, S::NP2>(), st > 0 ? 1u : 0u);
+              umma_commit(&tc_mbar);
+            }
+            __syncwarp();
+            if (tc_wait(1)) {
+#pragma unroll
+              for (int c8 = 0; c8 < S::NP2 / 8; ++c8) {
+                float v[8];
+                tmem_ld8(tmem_row + 8 * c8, v);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                  if (8 * c8 + j < NDES) dq[8 * c8 + j] = v[j];
               }
             }
-            put8(tileA, tileAlo, umma_off(r, 8 * c8, KC2), bt);
+          }
+        } else {
+          // q row -> operand tile A (bf16, K-major)
+#pragma unroll
+          for (int kc = 0; kc < KC1; ++kc) {
+            float x[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) x[j] = 8 * kc + j < NDES ? q[8 * kc + j] : 0.f;
+            put8(tileA, tileAlo, umma_off(r, 8 * kc, KC1), x);
           }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           __syncthreads();
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          if (threadIdx.x == 0)  // GEMM2: dq = beta . W0 into the same TMEM columns
-            gemm(tileA, tileAlo, tileB2, tileB2lo, S::KP2 / 16, KC2, umma_idesc_bf16<kAtomBlock, S::NP2>());
+          if (threadIdx.x == 0)  // GEMM1: z = q . W0^T into TMEM columns DCOL ..
+            gemm(tileA, tileAlo, tileB1, tileB1lo, S::KP1 / 16, KC1, umma_idesc_bf16<kAtomBlock, S::NP1>());
           __syncwarp();
-          if (tc_wait(1)) {
+          if (tc_wait(0)) {
+            // tanh layer from this row of z; beta = w1 (1 - h^2) -> operand tile A (reused)
 #pragma unroll
-            for (int c8 = 0; c8 < S::NP2 / 8; ++c8) {
-              float v[8];
-              tmem_ld8(tmem_row + S::DCOL + 8 * c8, v);
+            for (int c8 = 0; c8 < S::NP1 / 8; ++c8) {
+              float z[8];
+              tmem_ld8(tmem_row + S::DCOL + 8 * c8, z);
+              float bt[8];
 #pragma unroll
-              for (int j = 0; j < 8; ++j)
-                if (8 * c8 + j < NDES) dq[8 * c8 + j] = v[j];
+              for (int j = 0; j < 8; ++j) {
+                const int mu = 8 * c8 + j;
+                bt[j] = 0.f;
+                if (mu < S::H) {
+                  const float h = tanhf(z[j] - b0_s[mu]);
+                  U = __fmaf_rn(w1_s[mu], h, U);
+                  bt[j] = w1_s[mu] * (1.f - h * h);
+                }
+              }
+              put8(tileA, tileAlo, umma_off(r, 8 * c8, KC2), bt);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (threadIdx.x == 0)  // GEMM2: dq = beta . W0 into the same TMEM columns
+              gemm(tileA, tileAlo, tileB2, tileB2lo, S::KP2 / 16, KC2, umma_idesc_bf16<kAtomBlock, S::NP2>());
+            __syncwarp();
+            if (tc_wait(1)) {
+#pragma unroll
+              for (int c8 = 0; c8 < S::NP2 / 8; ++c8) {
+                float v[8];
+                tmem_ld8(tmem_row + S::DCOL + 8 * c8, v);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                  if (8 * c8 + j < NDES) dq[8 * c8 + j] = v[j];
+              }
             }
           }
         }
@@ -936,10 +1058,10 @@ __global__ void __launch_bounds__(AB, OCC)
       for (int n = 0; n <= NA; ++n) {
         float s[NKP];
         float *dS = dSr[LOWREG ? 0 : n];
-        if constexpr (!TM) {
+        if constexpr (!STM) {
 #pragma unroll
           for (int k4 = 0; k4 < NKP / 4; ++k4) {
-            const float4 v = Sme[n * (NKP / 4) + k4];
+            const float4 v = sref(n * (NKP / 4) + k4);
             s[4 * k4] = v.x, s[4 * k4 + 1] = v.y, s[4 * k4 + 2] = v.z, s[4 * k4 + 3] = v.w;
           }
         } else {
@@ -977,7 +1099,7 @@ __global__ void __launch_bounds__(AB, OCC)
         if constexpr (LOWREG) {
 #pragma unroll
           for (int k4 = 0; k4 < NKP / 4; ++k4)
-            Sme[n * (NKP / 4) + k4] = make_float4(dS[4 * k4], dS[4 * k4 + 1], dS[4 * k4 + 2], dS[4 * k4 + 3]);
+            sref(n * (NKP / 4) + k4) = make_float4(dS[4 * k4], dS[4 * k4 + 1], dS[4 * k4 + 2], dS[4 * k4 + 3]);
         }
       }
 
@@ -1019,7 +1141,7 @@ __global__ void __launch_bounds__(AB, OCC)
             for (int n = 0; n <= NA; ++n) {
               float dv[4];
               if constexpr (LOWREG) {
-                const float4 v = Sme[n * (NKP / 4) + k0 / 4];
+                const float4 v = sref(n * (NKP / 4) + k0 / 4);
                 dv[0] = v.x, dv[1] = v.y, dv[2] = v.z, dv[3] = v.w;
               } else {
 #pragma unroll
@@ -1340,11 +1462,12 @@ cudaError_t smem_limit_once(K kern, size_t bound) {
 }
 
 template <class S>
-size_t atom_smem_bytes(int T, int ncode, int prec, int ab = kAtomBlock) {
-  // the last region: BF16 operand tiles (tensor-core network), nothing (S_nk in TMEM) or the
-  // per-thread S_nk blocks
+size_t atom_smem_bytes(int T, int ncode, int prec, int ab = kAtomBlock, bool tclr = false) {
+  // the last region: BF16 operand tiles (tensor-core network; tclr: the per-thread S_nk blocks
+  // and the B tiles), nothing (S_nk in TMEM) or the per-thread S_nk blocks
   const bool tm = ab == 128 && S::NK % 8 == 0;
-  const size_t last = prec == 1   ? (size_t)S::TILE_A + 2 * S::TILE_B + 128
+  const size_t last = tclr        ? sizeof(float) * (size_t)S::SPTC * ab + 128 + 2 * (size_t)S::TILE_B
+                      : prec == 1 ? (size_t)S::TILE_A + 2 * S::TILE_B + 128
                       : prec == 2 ? 2 * (size_t)S::TILE_A + 4 * S::TILE_B + 128
                       : tm        ? 0
                                   : sizeof(float) * S::SPT * ab;
@@ -1402,6 +1525,15 @@ cudaError_t launch_atom(const AtomArgs &a, const ModelF &mf, const float *w0, co
     return cudaGetLastError();
   };
   if (descriptor_only) return go(atom_kernel<S, true, 0>);
+  if constexpr (S::TCLR_OK) {
+    if (a.precision == 1 && a.atom_occ == 3) {  // low-register form of the tensor-core network
+      auto kern = atom_kernel<S, false, 1, false, 128, 3>;
+      cudaError_t e = smem_limit_once(kern, atom_smem_bytes<S>(kMaxTypes, 1 << 9, 1, 128, true));
+      if (e != cudaSuccess) return e;
+      kern<<<blocks, kAtomBlock, atom_smem_bytes<S>(a.T, a.ncode, 1, 128, true), st>>>(a, w);
+      return cudaGetLastError();
+    }
+  }
   if (a.precision == 1) return go(atom_kernel<S, false, 1>);
   if (a.precision == 2) return go(atom_kernel<S, false, 2>);
   if constexpr (S::NS <= 128 && S::NK % 8 == 0) {
@@ -1459,6 +1591,15 @@ cudaError_t launch_atom_batch(const AtomArgs &a, const ModelF &mf, const float *
     kern<<<grid, block, smem, st>>>(a, w);
     return cudaGetLastError();
   };
+  if constexpr (S::TCLR_OK) {
+    if (a.precision == 1 && a.atom_occ == 3) {  // the low-register tensor-core form
+      auto kern = atom_kernel<S, false, 1, true, 128, 3>;
+      cudaError_t e = smem_limit_once(kern, atom_smem_bytes<S>(kMaxTypes, 0, 1, 128, true));
+      if (e != cudaSuccess) return e;
+      kern<<<grid, 128, atom_smem_bytes<S>(a.T, 0, 1, 128, true), st>>>(a, w);
+      return cudaGetLastError();
+    }
+  }
   if (a.precision == 1) return go(atom_kernel<S, false, 1, true, 128>);
   if (a.precision == 2) return go(atom_kernel<S, false, 2, true, 128>);
   if (block == 64) return go(atom_kernel<S, false, 0, true, 64>);
