@@ -183,10 +183,10 @@ typedef struct {
                              dU/dS_nk in registers (two CTAs per SM), 3 = two passes for S_nk and
                              dU/dS_nk in shared memory (three CTAs per SM; shapes whose
                              (n_max^A + 1) x 24 sums fit 128 TMEM columns, else as 1; with the
-                             BF16 network (precision 1) S_nk waits in shared memory and the GEMM
-                             operands and results use 128 TMEM columns); 0 = the library's default
-                             (3 where it exists). The split-BF16 network (precision 2) always runs
-                             form 1. nep_get_tuning returns the form in use. The form applies to
+                             BF16 networks (precision 1 and 2) S_nk waits in shared memory and
+                             the GEMM operands and results use 128 TMEM columns); 0 = the
+                             library's default (3 where it exists). nep_get_tuning returns the
+                             form in use. The form applies to
                              128-atom CTAs (an atom_block of 64 runs form 1) and nep_autotune keeps
                              it. The two forms agree to FP32 rounding; within one form, results do
                              not depend on the CTA sizes. */

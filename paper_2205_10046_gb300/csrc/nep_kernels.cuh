@@ -79,9 +79,11 @@ struct Shape {
   // the A operands (BF16 pairs, one lane per atom) columns [ACOL, ACOL + KP/2): 128 columns a
   // block. With (SPTC/4) % 4 == 2 the rows are packed without padding and the float4 index is
   // rotated by ((thread >> 2) & 1), which keeps 8 consecutive threads on 8 distinct bank groups.
+  // The split form keeps the A_lo operands after the A ones, at column ALO.
   static constexpr int ACOL = NP1 > NP2 ? NP1 : NP2;
-  static constexpr bool TCLR_OK =
-      NS <= 128 && NK % 8 == 0 && ACOL + (KP1 > KP2 ? KP1 : KP2) / 2 <= 128;
+  static constexpr int ALO = ACOL + (KP1 > KP2 ? KP1 : KP2) / 2;
+  static constexpr bool TCLR_OK = NS <= 128 && NK % 8 == 0 && ALO <= 128;
+  static constexpr bool TCLR2_OK = TCLR_OK && ALO + (KP1 > KP2 ? KP1 : KP2) / 2 <= 128;
   static constexpr int SW = (NA + 1) * NKP / 4;  // float4s of one thread's S_nk block
   static constexpr bool SROT = SW % 4 == 2;
   static constexpr int SPTC = SROT ? 4 * SW : SPT;
@@ -186,6 +188,14 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
 template <int M, int N>
 __host__ __device__ constexpr uint32_t umma_idesc_bf16() {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// The same with B read MN-major (transpose-B bit): core matrices of 8 K-rows x 16 bytes of
+// consecutive N, SBO the step along N and LBO the step along K. A K-major tile of W0 for
+// D = A.W0^T read this way is W0 itself as the K x N operand of D = A.W0.
+template <int M, int N>
+__host__ __device__ constexpr uint32_t umma_idesc_bf16_bmn() {
+  return umma_idesc_bf16<M, N>() | (1u << 16);
 }
 
 __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
@@ -405,12 +415,12 @@ __global__ void __launch_bounds__(AB, OCC)
     atom_kernel(const AtomArgs a, const __grid_constant__ AnnConst<S> w) {
   static_assert(PREC >= 0 && PREC <= 2, "network forms: 0 FP32, 1 BF16, 2 split BF16");
   constexpr bool LOWREG = OCC > 1;
-  static_assert(!LOWREG || (PREC <= 1 && !DESC_ONLY && AB == 128 && S::NS <= 128 && S::NK % 8 == 0),
-                "the low-register form: FP32 or BF16 network, S_nk within 128 TMEM columns");
-  // TCLR: the low-register form with the BF16 tensor-core network. S_nk then waits in the
-  // thread's shared block (not in TMEM), whose 128 columns hold the GEMM operands and results.
-  constexpr bool TCLR = LOWREG && PREC == 1;
-  static_assert(!TCLR || S::TCLR_OK, "the tensor-core network within 128 TMEM columns");
+  static_assert(!LOWREG || (!DESC_ONLY && AB == 128 && S::NS <= 128 && S::NK % 8 == 0),
+                "the low-register form: S_nk within 128 TMEM columns");
+  // TCLR: the low-register form with a tensor-core network. S_nk then waits in the thread's
+  // shared block (not in TMEM), whose 128 columns hold the GEMM operands and results.
+  constexpr bool TCLR = LOWREG && PREC >= 1;
+  static_assert(!TCLR || (PREC == 1 ? S::TCLR_OK : S::TCLR2_OK), "the tensor-core network within 128 TMEM columns");
   constexpr uint32_t TCOLS = LOWREG ? 128u : (uint32_t)S::TMEM_COLS;
   static_assert(PREC == 0 || !DESC_ONLY, "the descriptor-only kernel has no network");
   static_assert(PREC == 0 || AB == 128, "the tensor-core network works on 128-atom tiles (UMMA M = 128)");
@@ -506,6 +516,10 @@ __global__ void __launch_bounds__(AB, OCC)
       tileB2lo = tileB1lo + S::TILE_B;
       tileAlo = tileB2lo + S::TILE_B;
     }
+    if constexpr (TCLR) {  // one W0 tile (and its lo part) serves both GEMMs
+      tileB1lo = tileB1 + S::TILE_B;
+      tileB2 = tileB2lo = tileA = tileAlo = nullptr;
+    }
     // W0 tiles in global memory: B1, B2, then (split form) B1_lo, B2_lo
     const uint4 *b1t = a.tc_b1, *b2t = a.tc_b2;
     if (BATCH && a.pop_tc) {
@@ -514,10 +528,10 @@ __global__ void __launch_bounds__(AB, OCC)
     }
     for (int v = threadIdx.x; v < S::TILE_B / 16; v += blockDim.x) {
       reinterpret_cast<uint4 *>(tileB1)[v] = b1t[v];
-      reinterpret_cast<uint4 *>(tileB2)[v] = b2t[v];
+      if constexpr (!TCLR) reinterpret_cast<uint4 *>(tileB2)[v] = b2t[v];
       if constexpr (SPLIT) {
         reinterpret_cast<uint4 *>(tileB1lo)[v] = b1t[v + 2 * (S::TILE_B / 16)];
-        reinterpret_cast<uint4 *>(tileB2lo)[v] = b2t[v + 2 * (S::TILE_B / 16)];
+        if constexpr (!TCLR) reinterpret_cast<uint4 *>(tileB2lo)[v] = b2t[v + 2 * (S::TILE_B / 16)];
       }
     }
     if (threadIdx.x == 0) {
@@ -886,28 +900,54 @@ __global__ void __launch_bounds__(AB, OCC)
         };
         if constexpr (TCLR) {
           // Low-register form: the A operands go to TMEM columns ACOL.. as BF16 pairs (one lane
-          // per atom, no shared-memory tile), the results to columns 0..; B tiles as above.
-          constexpr uint32_t ACOL = S::ACOL;
-#pragma unroll
-          for (int c8 = 0; c8 < S::KP1 / 16; ++c8) {  // q row -> A (16 values per store)
-            uint32_t u[8];
+          // per atom, no shared-memory tile; split form: their lo parts at ALO..), the results
+          // to columns 0... GEMM2 reads the GEMM1 tile of W0 MN-major (B = W0).
+          constexpr uint32_t ACOL = S::ACOL, ALO = S::ALO;
+          // 16 values -> A (and A_lo) columns col .. col + 7
+          auto put16 = [&](uint32_t col, const float *x) {
+            uint32_t u[8], ul[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-              const int v0 = 16 * c8 + 2 * j;
-              u[j] = pack_bf16x2(v0 < NDES ? q[v0] : 0.f, v0 + 1 < NDES ? q[v0 + 1] : 0.f);
+              const __nv_bfloat162 bh = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
+              u[j] = *reinterpret_cast<const uint32_t *>(&bh);
+              if constexpr (SPLIT)
+                ul[j] = pack_bf16x2(x[2 * j] - __low2float(bh), x[2 * j + 1] - __high2float(bh));
             }
-            tmem_st8u(tmem_row + ACOL + 8 * c8, u);
-          }
-          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-          __syncthreads();
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          if (threadIdx.x == 0) {  // GEMM1: z = q . W0^T into columns 0 .. NP1 - 1
-            for (int st = 0; st < S::KP1 / 16; ++st)
-              umma_bf16_ts(tc_tmem, tc_tmem + ACOL + 8 * st, umma_desc(smem_addr(tileB1) + 256 * st, 128, KC1 * 128),
-                           umma_idesc_bf16<kAtomBlock, S::NP1>(), st > 0 ? 1u : 0u);
+            tmem_st8u(tmem_row + ACOL + col, u);
+            if constexpr (SPLIT) tmem_st8u(tmem_row + ALO + col, ul);
+          };
+          // operands written by every thread -> visible to the MMA issued by thread 0
+          auto to_mma = [&]() {
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          };
+          // D = A.B over K steps of 16 (+ A_lo.B + A.B_lo in the split form, in the order of
+          // the two-CTA form); B step st at byte offset st * bstep, descriptors (lbo, sbo)
+          auto gemm_t = [&](const unsigned char *B, const unsigned char *Blo, int ksteps, uint32_t bstep,
+                            uint32_t lbo, uint32_t sbo, uint32_t idesc) {
+            for (int st = 0; st < ksteps; ++st) {
+              const uint64_t db = umma_desc(smem_addr(B) + bstep * st, lbo, sbo);
+              umma_bf16_ts(tc_tmem, tc_tmem + ACOL + 8 * st, db, idesc, st > 0 ? 1u : 0u);
+              if constexpr (SPLIT) {
+                umma_bf16_ts(tc_tmem, tc_tmem + ALO + 8 * st, db, idesc, 1u);
+                umma_bf16_ts(tc_tmem, tc_tmem + ACOL + 8 * st, umma_desc(smem_addr(Blo) + bstep * st, lbo, sbo),
+                             idesc, 1u);
+              }
+            }
             umma_commit(&tc_mbar);
+          };
+#pragma unroll
+          for (int c8 = 0; c8 < S::KP1 / 16; ++c8) {  // q row -> A
+            float x[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) x[j] = 16 * c8 + j < NDES ? q[16 * c8 + j] : 0.f;
+            put16(8 * c8, x);
           }
+          to_mma();
+          if (threadIdx.x == 0)  // GEMM1: z = q . W0^T into columns 0 .. NP1 - 1
+            gemm_t(tileB1, tileB1lo, S::KP1 / 16, 256, 128, KC1 * 128, umma_idesc_bf16<kAtomBlock, S::NP1>());
           __syncwarp();
           if (tc_wait(0)) {
             // tanh layer from this row of z; beta = w1 (1 - h^2) -> A (16 hidden units per store;
@@ -928,23 +968,16 @@ __global__ void __launch_bounds__(AB, OCC)
                   bt[j] = w1_s[mu] * (1.f - h * h);
                 }
               }
-              uint32_t u[8];
-#pragma unroll
-              for (int j = 0; j < 8; ++j) u[j] = pack_bf16x2(bt[2 * j], bt[2 * j + 1]);
-              tmem_st8u(tmem_row + ACOL + 8 * c16, u);
+              put16(8 * c16, bt);
             }
             // every lane has read its z (tcgen05.ld waited) before GEMM2 overwrites the columns
-            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (threadIdx.x == 0) {  // GEMM2: dq = beta . W0 into columns 0 .. NP2 - 1
-              for (int st = 0; st < S::KP2 / 16; ++st)
-                umma_bf16_ts(tc_tmem, tc_tmem + ACOL + 8 * st,
-                             umma_desc(smem_addr(tileB2) + 256 * st, 128, KC2 * 128),
-                             umma_idesc_bf16<kAtomBlock, S::NP2>(), st > 0 ? 1u : 0u);
-              umma_commit(&tc_mbar);
-            }
+            to_mma();
+            // GEMM2: dq = beta . W0 into columns 0 .. NP2 - 1; B = W0 (K = hidden units, N =
+            // descriptor components) MN-major from the GEMM1 tile, 16 hidden units (two row
+            // groups of KC1 core matrices) per step
+            if (threadIdx.x == 0)
+              gemm_t(tileB1, tileB1lo, S::KP2 / 16, 2 * KC1 * 128, KC1 * 128, 128,
+                     umma_idesc_bf16_bmn<kAtomBlock, S::NP2>());
             __syncwarp();
             if (tc_wait(1)) {
 #pragma unroll
@@ -1466,7 +1499,7 @@ size_t atom_smem_bytes(int T, int ncode, int prec, int ab = kAtomBlock, bool tcl
   // the last region: BF16 operand tiles (tensor-core network; tclr: the per-thread S_nk blocks
   // and the B tiles), nothing (S_nk in TMEM) or the per-thread S_nk blocks
   const bool tm = ab == 128 && S::NK % 8 == 0;
-  const size_t last = tclr        ? sizeof(float) * (size_t)S::SPTC * ab + 128 + 2 * (size_t)S::TILE_B
+  const size_t last = tclr        ? sizeof(float) * (size_t)S::SPTC * ab + 128 + (prec == 2 ? 2 : 1) * (size_t)S::TILE_B
                       : prec == 1 ? (size_t)S::TILE_A + 2 * S::TILE_B + 128
                       : prec == 2 ? 2 * (size_t)S::TILE_A + 4 * S::TILE_B + 128
                       : tm        ? 0
@@ -1525,15 +1558,17 @@ cudaError_t launch_atom(const AtomArgs &a, const ModelF &mf, const float *w0, co
     return cudaGetLastError();
   };
   if (descriptor_only) return go(atom_kernel<S, true, 0>);
-  if constexpr (S::TCLR_OK) {
-    if (a.precision == 1 && a.atom_occ == 3) {  // low-register form of the tensor-core network
-      auto kern = atom_kernel<S, false, 1, false, 128, 3>;
-      cudaError_t e = smem_limit_once(kern, atom_smem_bytes<S>(kMaxTypes, 1 << 9, 1, 128, true));
-      if (e != cudaSuccess) return e;
-      kern<<<blocks, kAtomBlock, atom_smem_bytes<S>(a.T, a.ncode, 1, 128, true), st>>>(a, w);
-      return cudaGetLastError();
-    }
-  }
+  // low-register form of the tensor-core networks (BF16, split BF16)
+  auto go_tclr = [&](auto kern, int prec) -> cudaError_t {
+    cudaError_t e = smem_limit_once(kern, atom_smem_bytes<S>(kMaxTypes, 1 << 9, prec, 128, true));
+    if (e != cudaSuccess) return e;
+    kern<<<blocks, kAtomBlock, atom_smem_bytes<S>(a.T, a.ncode, prec, 128, true), st>>>(a, w);
+    return cudaGetLastError();
+  };
+  if constexpr (S::TCLR_OK)
+    if (a.precision == 1 && a.atom_occ == 3) return go_tclr(atom_kernel<S, false, 1, false, 128, 3>, 1);
+  if constexpr (S::TCLR2_OK)
+    if (a.precision == 2 && a.atom_occ == 3) return go_tclr(atom_kernel<S, false, 2, false, 128, 3>, 2);
   if (a.precision == 1) return go(atom_kernel<S, false, 1>);
   if (a.precision == 2) return go(atom_kernel<S, false, 2>);
   if constexpr (S::NS <= 128 && S::NK % 8 == 0) {
@@ -1591,15 +1626,17 @@ cudaError_t launch_atom_batch(const AtomArgs &a, const ModelF &mf, const float *
     kern<<<grid, block, smem, st>>>(a, w);
     return cudaGetLastError();
   };
-  if constexpr (S::TCLR_OK) {
-    if (a.precision == 1 && a.atom_occ == 3) {  // the low-register tensor-core form
-      auto kern = atom_kernel<S, false, 1, true, 128, 3>;
-      cudaError_t e = smem_limit_once(kern, atom_smem_bytes<S>(kMaxTypes, 0, 1, 128, true));
-      if (e != cudaSuccess) return e;
-      kern<<<grid, 128, atom_smem_bytes<S>(a.T, 0, 1, 128, true), st>>>(a, w);
-      return cudaGetLastError();
-    }
-  }
+  // the low-register tensor-core forms
+  auto go_tclr = [&](auto kern, int prec) -> cudaError_t {
+    cudaError_t e = smem_limit_once(kern, atom_smem_bytes<S>(kMaxTypes, 0, prec, 128, true));
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 128, atom_smem_bytes<S>(a.T, 0, prec, 128, true), st>>>(a, w);
+    return cudaGetLastError();
+  };
+  if constexpr (S::TCLR_OK)
+    if (a.precision == 1 && a.atom_occ == 3) return go_tclr(atom_kernel<S, false, 1, true, 128, 3>, 1);
+  if constexpr (S::TCLR2_OK)
+    if (a.precision == 2 && a.atom_occ == 3) return go_tclr(atom_kernel<S, false, 2, true, 128, 3>, 2);
   if (a.precision == 1) return go(atom_kernel<S, false, 1, true, 128>);
   if (a.precision == 2) return go(atom_kernel<S, false, 2, true, 128>);
   if (block == 64) return go(atom_kernel<S, false, 0, true, 64>);
