@@ -843,6 +843,44 @@ def md_forms(nep, w, name, skin, steps, warmup, stream, flush, world, clk=None, 
     return h, res, step0
 
 
+# MD steps of the configuration's own run, by workload (the 8,000,000-atom box: 100 NVE steps)
+CONFIG_STEPS = {"si_large": 100}
+
+
+def config_run(nep, h, w, steps, stream, flush, world):
+    """The configuration's own MD run in every network form: md_init from the initial state,
+    then `steps` steps in one md_run_async call (no warm-up), timed with CUDA events on the
+    launching stream (L2 flushed once before). Leaves the handle in the FP32 form."""
+    import torch
+    dev = flush.device
+    pos_d, types_d, vel_d = (torch.tensor(a, device=dev) for a in (w.pos, w.types, w.vel))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"steps": steps, "from": "md_init of the initial state, no warm-up, one md_run_async call"}
+    for prec, key in FORMS:
+        nep.nep_set_precision(h.h, prec)
+        nep.md_init(h.h, pos_d, types_d, w.box, vel_d)
+        r0 = nep.nep_get_stats(h.h)["n_rebuilds"]
+        flush.fill_(prec)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        nep.md_run_async(h.h, steps, w.dt_fs, steps, None, stream.cuda_stream)
+        ev1.record(stream)
+        ev1.synchronize()
+        nep.md_status(h.h)
+        sec = ev0.elapsed_time(ev1) / 1e3
+        if world > 1:
+            t = torch.tensor([sec], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            sec = float(t.item())
+        out[key] = {"value": world * w.n_atoms * steps / sec, "unit": UNIT, "ms_per_step": 1e3 * sec / steps,
+                    "rebuilds": nep.nep_get_stats(h.h)["n_rebuilds"] - r0}
+    nep.nep_set_precision(h.h, 0)
+    return out
+
+
 def run_gb300(args):
     import numpy as np
     import torch
@@ -901,6 +939,9 @@ def run_gb300(args):
                             err_sel, args.plain_graph, args.atom_form)
     stats = md["fp32"]["stats"]
     total_s, ktime, timed_rebuilds = md["fp32"]["seconds"], md["fp32"]["ktime"], md["fp32"]["rebuilds"]
+    nep.nep_set_profiling(h.h, False)
+    crun = config_run(nep, h, w, CONFIG_STEPS[args.workload], stream, flush, world) \
+        if args.workload in CONFIG_STEPS else None
 
     # end-to-end through the host-pointer entry points: upload from page-locked host memory,
     # run, read the state back into page-locked host memory
@@ -998,6 +1039,8 @@ def run_gb300(args):
                 "atom_kernel_ms": r["ktime"]["nep_atom"] / args.steps,
                 "atom_kernel_frac_of_fp32_peak": rl["frac"],
                 "network": NETWORK[prec]}
+        if crun is not None:
+            line["config_run"] = crun
         if pbte is not None:
             line["pbte"] = pbte
         if batch_forms is not None:
