@@ -676,6 +676,7 @@ def serve_run(model, pool, reqs, precision, workers, sample=(), compact_every=0)
         "submit_lag_ms_p99": float(np.percentile(lag, 99)) * 1e3,
         "errors": sorted({r["message"] for r in res if r["status"] != 0})[:3],
         "scheduler": {"iterations": int(st["iterations"]), "relayouts": int(st["relayouts"]),
+                      "builds": int(st["builds"]),
                       "relayout_s": st["relayout_seconds"], "iteration_s": st["step_seconds"],
                       "fetch_s": st["fetch_seconds"]},
     }, kept

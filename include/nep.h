@@ -268,6 +268,8 @@ typedef struct {
   double relayout_seconds, step_seconds, fetch_seconds; /* scheduler wall time: layout changes,
                                                  iterations (incl. builds and the state read),
                                                  copying finished jobs out */
+  long long builds;                           /* neighbour builds of the batch (layout changes
+                                                 and skin-triggered rebuilds, overflow replays) */
 } nep_server_stats;
 
 /* Start the workers (each creates its handle for `params`, copied). NEP_ERR_ARG for a bad

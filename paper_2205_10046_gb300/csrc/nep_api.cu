@@ -292,7 +292,7 @@ struct BatchKey {
 
 // Identity of a captured engine iteration: every array it touches and the list capacities.
 struct EngineKey {
-  const void *p[24];
+  const void *p[25];
   long long gen;
   int N, cap_r, cap_a, precision;
 };
@@ -350,6 +350,7 @@ struct nep_handle {
   std::vector<EngineSlot> e_slots_h;            // host mirror (after the last iteration)
   std::vector<double> e_energy_h, e_virial_h;   // per job, after the last iteration
   DevBuf<EngineSlot> e_slots, e_slots_ck;
+  DevBuf<int> e_sflag;  // per-job build requests of the drift kernel (partial builds)
   DevBuf<double> e_energy, e_virial, e_u, e_w, e_xck, e_vck;
   DevBuf<int4> e_table;
   cudaGraphExec_t e_graph = nullptr;            // one captured iteration of the current layout
@@ -545,6 +546,7 @@ int rebuild_lists(nep_handle *h, int N, cudaStream_t s, const Batch &B = Batch{n
     CK(wait_stream(s), "sync");
     reset_status_counts(h);
     h->h_status->rebuild = 1;
+    h->h_status->full = 1;
     CK(cudaMemcpyAsync(h->status.p, h->h_status, sizeof(BuildStatus), cudaMemcpyHostToDevice, s), "status");
     CK(launch_rebuild(N, h->T, g, B, h->dtab.p, rlR * rlR, rlA * rlA, h->rcR2f(), h->rcA2f(), atom_state(h),
                       list_bufs(h), count_only ? 1 : 0, h->status.p, s),
@@ -1007,6 +1009,8 @@ int engine_relayout(nep_handle *h, const std::vector<int> &keep, const std::vect
   if (rc) return rc;
   CK(h->e_slots.ensure(S_new), "alloc");
   CK(h->e_slots_ck.ensure(S_new), "alloc");
+  CK(h->e_sflag.ensure(S_new), "alloc");
+  CK(cudaMemsetAsync(h->e_sflag.p, 0, sizeof(int) * S_new, s), "clear build requests");
   CK(h->e_energy.ensure(S_new), "alloc");
   CK(h->e_virial.ensure(9 * (size_t)S_new), "alloc");
   CK(h->e_u.ensure(n), "alloc");
@@ -1031,7 +1035,7 @@ EngineKey engine_key(nep_handle *h) {
   const void *p[] = {h->x.p, h->v.p, h->F.p, h->x_ref.p, h->origin.p, h->types.p, h->perm.p, h->pos4.p, h->posA.p,
                      h->nl_r.p, h->nl_a.p, h->rev_a.p, h->p_ang.p, h->e_rad.p, h->e_u.p, h->e_w.p, h->e_slots.p,
                      h->e_energy.p, h->d_grids.p, h->d_sid.p, h->dtab.p, h->cell_start.p, h->stage_e.p,
-                     h->partial_gather.p};
+                     h->partial_gather.p, h->e_sflag.p};
   static_assert(sizeof(p) / sizeof(p[0]) == sizeof(k.p) / sizeof(k.p[0]), "key size");
   for (size_t c = 0; c < sizeof(p) / sizeof(p[0]); ++c) k.p[c] = p[c];
   k.gen = h->b_gen;
@@ -1077,9 +1081,12 @@ int engine_queue_iteration(nep_handle *h, cudaStream_t s) {
   const int N = h->N, S = h->nb_struct;
   const float rlR = (float)(h->rcR + h->skin), rlA = (float)(h->rcA + h->skin);
   launch_engine_drift(N, atom_state(h), h->d_sid.p, h->e_slots.p, h->d_inv_mk.p, 0.25 * h->skin * h->skin,
-                      h->status.p, s);
-  cudaError_t e = launch_rebuild(N, h->T, h->grid, batch_of(h), h->dtab.p, rlR * rlR, rlA * rlA, h->rcR2f(),
-                                 h->rcA2f(), atom_state(h), list_bufs(h), 0, h->status.p, s);
+                      h->e_sflag.p, h->status.p, s);
+  // a build requested by the drift re-lists only the flagged jobs; a forced one every job
+  Batch B = batch_of(h);
+  B.sflag = h->e_sflag.p;
+  cudaError_t e = launch_rebuild(N, h->T, h->grid, B, h->dtab.p, rlR * rlR, rlA * rlA, h->rcR2f(), h->rcA2f(),
+                                 atom_state(h), list_bufs(h), 0, h->status.p, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "engine rebuild");
   AtomArgs a = make_args(h, N);
   a.perm = nullptr;  // every output in the internal order
@@ -1174,6 +1181,8 @@ int engine_step(nep_handle *h, cudaStream_t s, int n_iter, bool force_rebuild) {
   h->e_slots_h = sl;
   return NEP_OK;
 }
+
+long long engine_builds(const nep_handle *h) { return h->h_status ? h->h_status->n_rebuilds : 0; }
 
 // Final arrays of job k in its own atom order: positions wrapped into its cell, forces,
 // velocities (HOST buffers [n][3], any may be null).

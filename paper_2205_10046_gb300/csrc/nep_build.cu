@@ -33,6 +33,13 @@ __device__ __forceinline__ bool rebuild_pending(const BuildStatus *st) {
   return *(volatile const int *)&st->rebuild != 0;
 }
 
+// Atom (or internal position) i belongs to a structure that this build leaves as it is: a
+// build requested by the serving engine's drift kernel, not forced, and i's structure not
+// flagged. Such atoms keep their cell, their place in the order, their lists and x_ref.
+__device__ __forceinline__ bool kept_by_build(const Batch &B, const BuildStatus *st, int i) {
+  return B.sflag && !*(volatile const int *)&st->full && B.sflag[B.sid[i]] == 0;
+}
+
 __global__ void zero_cells_kernel(int ncell, int *count, int *cursor, BuildStatus *st) {
   if (!rebuild_pending(st)) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) {  // per-build sums (the maxima are kept over the run)
@@ -50,6 +57,10 @@ __global__ void bin_atoms_kernel(int N, int T, AtomState a, int *count, const Gr
   if (!rebuild_pending(st)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  if (kept_by_build(B, st, i)) {  // counted in its old cell: its structure's order stays
+    atomicAdd(count + a.cell_of[i], 1);
+    return;
+  }
   const Grid &g = grid_of(B, g0, i);
   double *x = a.x + 3 * (size_t)i;
   double r[3] = {x[0], x[1], x[2]};
@@ -132,10 +143,10 @@ __global__ void scan_cells_kernel(int ncell, const int *count, int *start, const
 }
 
 __global__ void scatter_atoms_kernel(int N, const int *cell_of, const int *start, int *cursor, int *cell_atoms,
-                                     const BuildStatus *st) {
+                                     const Batch B, const BuildStatus *st) {
   if (!rebuild_pending(st)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+  if (i >= N || kept_by_build(B, st, i)) return;
   const int c = cell_of[i];
   cell_atoms[start[c] + atomicAdd(cursor + c, 1)] = i;
 }
@@ -157,10 +168,11 @@ __global__ void sort_cells_kernel(int ncell, const int *start, int *cell_atoms, 
 }
 
 // Internal atom p takes the data of atom cell_atoms[p] (into the scratch arrays).
-__global__ void reorder_gather_kernel(int N, const int *cell_atoms, AtomState a, const BuildStatus *st) {
+__global__ void reorder_gather_kernel(int N, const int *cell_atoms, AtomState a, const Batch B,
+                                      const BuildStatus *st) {
   if (!rebuild_pending(st)) return;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= N) return;
+  if (p >= N || kept_by_build(B, st, p)) return;
   const int o = cell_atoms[p];
   for (int b = 0; b < 3; ++b) {
     a.x2[3 * (size_t)p + b] = a.x[3 * (size_t)o + b];
@@ -176,7 +188,7 @@ __global__ void reorder_gather_kernel(int N, const int *cell_atoms, AtomState a,
 __global__ void reorder_commit_kernel(int N, AtomState a, const Grid g0, const Batch B, const BuildStatus *st) {
   if (!rebuild_pending(st)) return;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= N) return;
+  if (p >= N || kept_by_build(B, st, p)) return;
   // cells are numbered structure by structure, so atom p stays inside its structure's range
   const Grid &g = grid_of(B, g0, p);
   const int gid = a.cell2[p];
@@ -286,8 +298,9 @@ __global__ void build_lists_kernel(int N, const float4 *posA, const float4 *pos4
                                    ListBufs L, int count_only, BuildStatus *st) {
   if (!rebuild_pending(st)) return;
   const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
-  // lanes past the last atom stay until the warp-level statistics below
-  const bool active = i0 < N;
+  // lanes past the last atom (and atoms of structures this build keeps) stay until the
+  // warp-level statistics below
+  const bool active = i0 < N && !kept_by_build(B, st, i0);
   const int i = active ? i0 : 0;  // a valid index for the idle lanes (N >= 1)
   const Grid &g = grid_of(B, g0, i);
   const float4 pi = posA[i];
@@ -447,7 +460,7 @@ __global__ void build_lists_kernel(int N, const float4 *posA, const float4 *pos4
 __global__ void build_rev_kernel(int N, const ListBufs L, const Grid g0, const Batch B, BuildStatus *st) {
   if (!rebuild_pending(st)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+  if (i >= N || kept_by_build(B, st, i)) return;
   const Grid &g = grid_of(B, g0, i);
   const unsigned om = (1u << g.obits) - 1u;
   const int na = L.nn_a[i];
@@ -478,8 +491,15 @@ __global__ void build_rev_kernel(int N, const ListBufs L, const Grid g0, const B
 __global__ void finish_build_kernel(BuildStatus *st) {
   if (st->rebuild) {
     st->rebuild = 0;
+    st->full = 0;
     st->n_rebuilds += 1;
   }
+}
+
+// The per-structure build requests are served: clear them (before finish_build_kernel).
+__global__ void clear_sflags_kernel(int n_struct, int *sflag, const BuildStatus *st) {
+  if (!rebuild_pending(st)) return;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_struct; s += gridDim.x * blockDim.x) sflag[s] = 0;
 }
 
 // Sets the condition of the graph's rebuild node from the drift kernel's request.
@@ -708,6 +728,7 @@ __global__ void arm_rebuild_kernel(BuildStatus *st) {
   st->bad_input = 0;
   st->tc_timeout = 0;
   st->rebuild = 1;
+  st->full = 1;
 }
 
 // ------------------------------------------------------------------ population evaluation
@@ -877,9 +898,9 @@ cudaError_t launch_rebuild(int N, int T, const Grid &g, const Batch &B, const fl
   zero_cells_kernel<<<cb < 1024 ? cb : 1024, tb, 0, s>>>(g.ncell, L.cell_count, L.cell_cursor, st);
   bin_atoms_kernel<<<nb, tb, 0, s>>>(N, T, a, L.cell_count, g, B, st);
   scan_cells_kernel<<<1, 1024, 0, s>>>(g.ncell, L.cell_count, L.cell_start, st);
-  scatter_atoms_kernel<<<nb, tb, 0, s>>>(N, a.cell_of, L.cell_start, L.cell_cursor, L.cell_atoms, st);
+  scatter_atoms_kernel<<<nb, tb, 0, s>>>(N, a.cell_of, L.cell_start, L.cell_cursor, L.cell_atoms, B, st);
   sort_cells_kernel<<<cb, tb, 0, s>>>(g.ncell, L.cell_start, L.cell_atoms, st);
-  reorder_gather_kernel<<<nb, tb, 0, s>>>(N, L.cell_atoms, a, st);
+  reorder_gather_kernel<<<nb, tb, 0, s>>>(N, L.cell_atoms, a, B, st);
   reorder_commit_kernel<<<nb, tb, 0, s>>>(N, a, g, B, st);
   auto lists = [&](auto kern) {
     kern<<<(N + 127) / 128, 128, 0, s>>>(N, a.posA, a.pos4, a.cell_of, L.cell_start, g, B, rlR2, rlA2, rcR2, rcA2, L,
@@ -896,6 +917,10 @@ cudaError_t launch_rebuild(int N, int T, const Grid &g, const Batch &B, const fl
     default: lists(build_lists_kernel<8>); break;
   }
   if (!count_only) build_rev_kernel<<<nb, tb, 0, s>>>(N, L, g, B, st);
+  if (B.sflag && B.n > 0) {
+    const int sb = (B.n + 255) / 256;
+    clear_sflags_kernel<<<sb < 256 ? sb : 256, 256, 0, s>>>(B.n, B.sflag, st);
+  }
   finish_build_kernel<<<1, 1, 0, s>>>(st);
   return cudaGetLastError();
 }
@@ -993,7 +1018,7 @@ void launch_fire_mix(int N, const AtomState &a, FireState *fire, int check_only,
 // First half of the velocity-Verlet step of the stepping jobs: v += dt/2 F/m, x += dt v.
 // A neighbour build is requested when an atom moved more than skin/2 since the last one.
 __global__ void engine_drift_kernel(int N, AtomState a, const int *sid, const EngineSlot *slots,
-                                    const double *inv_mass_kappa, double half_skin2, BuildStatus *st) {
+                                    const double *inv_mass_kappa, double half_skin2, int *sflag, BuildStatus *st) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const EngineSlot &sl = slots[sid[i]];
@@ -1016,7 +1041,11 @@ __global__ void engine_drift_kernel(int N, AtomState a, const int *sid, const En
   p.y = (float)(r[1] - a.origin[3 * (size_t)i + 1]);
   p.z = (float)(r[2] - a.origin[3 * (size_t)i + 2]);
   a.pos4[i] = p;
-  if (d2 > half_skin2) st->rebuild = 1;
+  // a build of this structure (also for a non-finite displacement, which the build reports)
+  if (!(d2 <= half_skin2)) {
+    if (sflag) sflag[sid[i]] = 1;
+    st->rebuild = 1;
+  }
 }
 
 // Clears the error flags of a chunk of iterations (a build is not requested).
@@ -1126,8 +1155,10 @@ __global__ void engine_relayout_kernel(const int4 *table, AtomState src, AtomSta
 }
 
 void launch_engine_drift(int N, const AtomState &a, const int *sid, const EngineSlot *slots,
-                         const double *inv_mass_kappa, double half_skin2, BuildStatus *st, cudaStream_t s) {
-  if (N > 0) engine_drift_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, a, sid, slots, inv_mass_kappa, half_skin2, st);
+                         const double *inv_mass_kappa, double half_skin2, int *sflag, BuildStatus *st,
+                         cudaStream_t s) {
+  if (N > 0)
+    engine_drift_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, a, sid, slots, inv_mass_kappa, half_skin2, sflag, st);
 }
 
 void launch_engine_fire(int n_struct, const int *offsets, const AtomState &a, EngineSlot *slots, cudaStream_t s) {

@@ -43,6 +43,10 @@ struct Batch {
   const Grid *grids;
   const int *sid;
   int n;
+  // serving engine: per-structure build requests of the drift kernel. A build that is not
+  // forced (BuildStatus::full == 0) then re-sorts and re-lists only the flagged structures;
+  // every other structure keeps its atom order, cells, lists and reference positions.
+  int *sflag = nullptr;
 };
 
 // Per-atom device arrays. Internally atoms are kept in cell order (re-sorted at every
@@ -78,6 +82,8 @@ struct BuildStatus {
   unsigned long long sum_r, sum_a;  // total list entries
   unsigned long long in_r, in_a;    // entries with r < r_c (at build time)
   int rebuild;         // a rebuild is pending (set by the drift kernel or the host)
+  int full;            // the pending build covers every structure (forced); else, with
+                       // per-structure flags, only the flagged ones
   int bad_input;       // bit 0: type out of range, bit 1: non-finite position
   int tc_timeout;      // a tensor-core completion wait ran out (results invalid)
   long long n_rebuilds;
@@ -265,7 +271,8 @@ void launch_arm_rebuild(BuildStatus *st, cudaStream_t s);
 void launch_fire_mix(int N, const AtomState &a, FireState *fire, int check_only, cudaStream_t s);
 // batched serving engine
 void launch_engine_drift(int N, const AtomState &a, const int *sid, const EngineSlot *slots,
-                         const double *inv_mass_kappa, double half_skin2, BuildStatus *st, cudaStream_t s);
+                         const double *inv_mass_kappa, double half_skin2, int *sflag, BuildStatus *st,
+                         cudaStream_t s);
 void launch_clear_flags(BuildStatus *st, cudaStream_t s);
 void launch_engine_fire(int n_struct, const int *offsets, const AtomState &a, EngineSlot *slots, cudaStream_t s);
 void launch_engine_advance(int n_struct, EngineSlot *slots, cudaStream_t s);
@@ -290,6 +297,8 @@ namespace nep {
 int engine_relayout(nep_handle *h, const std::vector<int> &keep, const std::vector<EngineJob> &add, cudaStream_t s,
                     size_t target_bytes = 0);
 int engine_step(nep_handle *h, cudaStream_t s, int n_iter, bool force_rebuild);
+// neighbour builds of the engine's batch so far (read with the status after every chunk)
+long long engine_builds(const nep_handle *h);
 int engine_fetch(nep_handle *h, int k, double *pos, double *force, double *vel, cudaStream_t s);
 int engine_jobs(const nep_handle *h);
 int engine_atoms(const nep_handle *h);

@@ -80,7 +80,7 @@ struct __attribute__((visibility("hidden"))) nep_server {
   long long completed = 0, failed = 0;
   double atom_evals = 0;
   // where the scheduler's time goes (host wall clock)
-  long long iterations = 0, relayouts = 0;
+  long long iterations = 0, relayouts = 0, builds = 0;
   double t_relayout = 0, t_step = 0, t_fetch = 0;
   std::thread scheduler;
 
@@ -281,6 +281,7 @@ void nep_server::scheduler_main() {
     {
       std::lock_guard<std::mutex> lk(mu);
       iterations += n_iter;
+      builds = nep::engine_builds(h);
     }
     {
       const size_t ws = nep::workspace_bytes(h);
@@ -525,6 +526,7 @@ NEP_SERVER_API int nep_server_stats_get(nep_server *s, nep_server_stats *out) {
   out->relayout_seconds = s->t_relayout;
   out->step_seconds = s->t_step;
   out->fetch_seconds = s->t_fetch;
+  out->builds = s->builds;
   return NEP_OK;
 }
 

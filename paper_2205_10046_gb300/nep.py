@@ -79,7 +79,7 @@ class nep_server_stats(C.Structure):
                 ("bytes_reserved", C.c_size_t), ("peak_bytes_reserved", C.c_size_t),
                 ("peak_workspace_bytes", C.c_size_t), ("atom_evaluations", C.c_double),
                 ("iterations", C.c_longlong), ("relayouts", C.c_longlong), ("relayout_seconds", C.c_double),
-                ("step_seconds", C.c_double), ("fetch_seconds", C.c_double)]
+                ("step_seconds", C.c_double), ("fetch_seconds", C.c_double), ("builds", C.c_longlong)]
 
 
 JOB_SINGLE, JOB_FIRE, JOB_NVE = 0, 1, 2

@@ -208,3 +208,30 @@ def test_memory_budget_admission_and_failures(torch_cuda):
         s.submit(0, np.zeros((n_big, 3)), np.zeros(n_big, np.int32), np.eye(3) * 2000.0)
     assert ei.value.code == -6
     s.close()
+
+
+def test_partial_builds_keep_every_job_exact(torch_cuda):
+    """Hot NVE jobs of different lengths in one batch: a job whose atom moved more than skin/2
+    has its own neighbour lists rebuilt while the other jobs keep their atom order and lists.
+    Every job's final state equals the oracle's velocity Verlet run of that job alone."""
+    from paper_2205_10046_gb300 import nep
+    model = W.mixed_model(0)
+    jobs = []
+    for k, (n, steps) in enumerate([(40, 30), (64, 12), (100, 25), (150, 8), (200, 30), (300, 18)]):
+        pos, types, box = W.random_structure(60 + k, n)
+        vel = W.maxwell_boltzmann(model.mass[types], 1000.0, 900 + k)
+        jobs.append(dict(kind=2, pos=pos, types=types, box=box, n_steps=steps, dt_fs=1.0, fmax=0.0, vel=vel))
+    s = nep.Server(model, memory_budget=8 << 30, workers=8, skin=0.2)
+    out = _run(s, jobs)
+    st = s.stats()
+    s.close()
+    assert st["completed"] == len(jobs) and st["failed"] == 0
+    assert st["builds"] >= 1
+    for (r, a), j in zip(out, jobs):
+        assert r["status"] == 0, r["message"]
+        xo, vo, thermo, fo = oracle.md(model, j["pos"], j["vel"], j["types"], j["box"], j["n_steps"], 1.0)
+        n = j["pos"].shape[0]
+        assert np.abs(_min_image(a[0] - xo, j["box"])).max() <= 1e-5
+        assert np.abs(a[2] - vo).max() <= 1e-6
+        assert np.linalg.norm(a[1] - fo) <= 1e-5 * np.linalg.norm(fo)
+        assert abs(r["energy"] - thermo[-1, 0]) / n <= 1e-6
