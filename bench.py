@@ -72,6 +72,8 @@ def parse_args():
     ap.add_argument("--serve-workers", type=int, default=1024, help="job slots of the serving batch")
     ap.add_argument("--serve-compact", type=int, default=8,
                     help="lazy leaving of finished jobs (nep_server_config.compact_every; 0 = at once)")
+    ap.add_argument("--serve-min-chunk", type=int, default=4,
+                    help="least iterations between two reads of the job states (nep_server_config.min_chunk)")
     ap.add_argument("--serve-rate2", type=float, default=0.0,
                     help="arrival rate of the second (sustained-load) serving run; 0 = half the measured FP32 capacity")
     ap.add_argument("--pop-calls", type=int, default=5)
@@ -610,13 +612,13 @@ def serve_sample(pool, reqs):
     return set(sp + nve)
 
 
-def serve_run(model, pool, reqs, precision, workers, sample=(), compact_every=0):
+def serve_run(model, pool, reqs, precision, workers, sample=(), compact_every=0, min_chunk=0):
     """Submit the requests at their arrival times; collect every result (with the final
     arrays of the requests in `sample`)."""
     import numpy as np
     from paper_2205_10046_gb300 import nep
     srv = nep.Server(model, memory_budget=SERVE_BUDGET, workers=workers, precision=precision, skin=SERVE_SKIN,
-                     compact_every=compact_every)
+                     compact_every=compact_every, min_chunk=min_chunk)
     done = {}
     offered = 0.0
     lag = []
@@ -736,11 +738,13 @@ def run_serving(args):
                         f"structures drawn from a pool of 256 (32-20,000 atoms, log-uniform, FCC/BCC/diamond, "
                         f"1-3 of 3 species); 50% single point, 30% 50-step FIRE, 20% NVE U{{10..1000}} steps "
                         f"of 1 fs; NEP rc 5.5/4.0 n_max 8/4 40 neurons; one batch of up to {args.serve_workers} jobs (iteration-level batching), "
-                        f"{SERVE_BUDGET >> 30} GB admission budget, compact_every {args.serve_compact}"),
+                        f"{SERVE_BUDGET >> 30} GB admission budget, compact_every {args.serve_compact}, "
+                        f"min_chunk {args.serve_min_chunk}"),
            "latency": "submission (arrival) to result on the host, server clock"}
     kept = {}
     for prec, key in ((0, "fp32"), (1, "bf16")):
-        out[key], kept[key] = serve_run(model, pool, reqs, prec, args.serve_workers, sample, args.serve_compact)
+        out[key], kept[key] = serve_run(model, pool, reqs, prec, args.serve_workers, sample, args.serve_compact,
+                                        args.serve_min_chunk)
     # a load the server sustains: half the FP32 capacity measured above (or a given rate)
     cap = out["fp32"]["throughput_atom_evaluations_per_s"]
     work = out["fp32"]["offered_atom_evaluations_per_s"] / args.serve_rate  # per request
@@ -749,7 +753,7 @@ def run_serving(args):
     out["half_capacity"] = {"rate_req_per_s": rate2, "requests": len(reqs2)}
     for prec, key in ((0, "fp32"), (1, "bf16")):
         out["half_capacity"][key], _ = serve_run(model, pool, reqs2, prec, args.serve_workers,
-                                                 compact_every=args.serve_compact)
+                                                 compact_every=args.serve_compact, min_chunk=args.serve_min_chunk)
     return out, (model, pool, reqs, kept)
 
 

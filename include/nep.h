@@ -231,6 +231,11 @@ typedef struct {
                            jobs stay frozen in the batch (results already delivered) until they
                            are 1/c of it, and queued jobs join once 1/c of the slots and of the
                            budget are free, so one layout change serves many jobs */
+  int min_chunk;        /* iterations between two reads of the job states (0 or 1: a single
+                           iteration whenever a job starts or could join, else up to the first
+                           completion); k > 1 runs at least k (at most 32): jobs that finish
+                           inside a chunk stay frozen until it ends, which spreads the per-chunk
+                           host work (checkpoint, status and state reads) over k iterations */
 } nep_server_config;
 
 typedef struct {

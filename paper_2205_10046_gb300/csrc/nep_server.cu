@@ -276,6 +276,9 @@ void nep_server::scheduler_main() {
       if (sl.phase != 1) n_iter = 1;
       else n_iter = std::max(1, std::min(n_iter, sl.n_steps - sl.steps_done));
     }
+    // at least min_chunk iterations: a job that finishes earlier is frozen (phase 2: no drift,
+    // no kick, its energy, forces and state unchanged) until the chunk ends
+    n_iter = std::max(n_iter, std::min(cfg.min_chunk, 32));
     const int r = timed(t_step, [&] { return nep::engine_step(h, s, n_iter, relaid); });
     relaid = false;
     {
@@ -394,9 +397,10 @@ NEP_SERVER_API int nep_server_create(const nep_params *params, const nep_server_
   }
   *out = nullptr;
   if (cfg->workers < 1 || cfg->workers > 65536 || cfg->memory_budget == 0 ||
-      cfg->precision < 0 || cfg->precision > 2 || cfg->compact_every < 0 || cfg->compact_every > 1024) {
+      cfg->precision < 0 || cfg->precision > 2 || cfg->compact_every < 0 || cfg->compact_every > 1024 ||
+      cfg->min_chunk < 0 || cfg->min_chunk > 32) {
     nep::set_create_error("need 1 <= workers <= 65536, memory_budget > 0, precision 0, 1 or 2, "
-                          "0 <= compact_every <= 1024");
+                          "0 <= compact_every <= 1024, 0 <= min_chunk <= 32");
     return NEP_ERR_ARG;
   }
   if (!params->mass) {

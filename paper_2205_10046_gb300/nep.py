@@ -58,7 +58,7 @@ class md_options(C.Structure):
 
 class nep_server_config(C.Structure):
     _fields_ = [("memory_budget", C.c_size_t), ("workers", C.c_int), ("precision", C.c_int),
-                ("compact_every", C.c_int)]
+                ("compact_every", C.c_int), ("min_chunk", C.c_int)]
 
 
 class nep_job(C.Structure):
@@ -557,10 +557,10 @@ class Server:
     """A running nep_server: submit jobs (host arrays), collect results in completion order."""
 
     def __init__(self, model, memory_budget: int, workers: int = 16, precision: int = 0, skin: float = 1.0,
-                 compact_every: int = 0):
+                 compact_every: int = 0, min_chunk: int = 0):
         lib = load()
         p, self._keep = _params(model, skin)
-        cfg = nep_server_config(int(memory_budget), int(workers), int(precision), int(compact_every))
+        cfg = nep_server_config(int(memory_budget), int(workers), int(precision), int(compact_every), int(min_chunk))
         h = C.c_void_p()
         _check(lib.nep_server_create(C.byref(p), C.byref(cfg), C.byref(h)), None)
         self.h = h
