@@ -79,3 +79,17 @@ def test_descriptor_output_shape_is_checked_before_the_library_is_called(monkeyp
         q = torch.zeros(bad, dtype=torch.float64)
         with pytest.raises(ValueError, match="q has shape"):
             nep.nep_descriptors_static(w.model, pos, types, w.box, q)
+
+
+def test_server_configuration_is_checked_without_gpu(lib):
+    """nep_server_create refuses configurations outside the documented ranges before it
+    touches a device (workers, precision, compact_every, min_chunk)."""
+    from paper_2205_10046_gb300 import nep, workloads as W
+    model = W.mixed_model(0)
+    for bad in (dict(min_chunk=33), dict(min_chunk=-1), dict(compact_every=-1), dict(compact_every=1025),
+                dict(workers=0), dict(precision=3)):
+        kw = dict(memory_budget=1 << 30, workers=4)
+        kw.update(bad)
+        with pytest.raises(nep.NepError) as ei:
+            nep.Server(model, **kw)
+        assert ei.value.code == -1, bad

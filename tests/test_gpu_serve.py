@@ -106,10 +106,11 @@ def _run(server, jobs):
     return [(res[i], arr[i]) for i in ids]
 
 
-@pytest.mark.parametrize("compact_every", [0, 4])
-def test_results_are_the_same_alone_and_in_a_mix(torch_cuda, compact_every):
+@pytest.mark.parametrize("compact_every,min_chunk", [(0, 0), (4, 0), (4, 4)])
+def test_results_are_the_same_alone_and_in_a_mix(torch_cuda, compact_every, min_chunk):
     """compact_every = 4: finished jobs stay frozen in the batch until they are a quarter of it
-    (lazy leaving); the results are the same."""
+    (lazy leaving); min_chunk = 4: at least four iterations between two reads of the job
+    states (a job finishing inside a chunk waits frozen); the results are the same."""
     from paper_2205_10046_gb300 import nep
     model = W.mixed_model(0)
     targets = _targets()
@@ -120,7 +121,7 @@ def test_results_are_the_same_alone_and_in_a_mix(torch_cuda, compact_every):
         s.close()
     mix = _jobs(3)
     order = mix[:4] + [targets[0]] + mix[4:9] + [targets[1]] + mix[9:13] + [targets[2]] + mix[13:]
-    s = nep.Server(model, memory_budget=8 << 30, workers=8, compact_every=compact_every)
+    s = nep.Server(model, memory_budget=8 << 30, workers=8, compact_every=compact_every, min_chunk=min_chunk)
     out = _run(s, order)
     st = s.stats()
     s.close()
