@@ -1076,7 +1076,7 @@ int capture_engine(nep_handle *h, cudaStream_t s) {
 
 // Queue one iteration of every job: drift (requesting a neighbour build when an atom moved
 // more than skin/2 since the last one), the build (its kernels return at once unless one is
-// pending), forces, kick, structure sums, FIRE update, bookkeeping.
+// pending), forces, kick, FIRE update, bookkeeping (the per-job sums follow once per chunk).
 int engine_queue_iteration(nep_handle *h, cudaStream_t s) {
   const int N = h->N, S = h->nb_struct;
   const float rlR = (float)(h->rcR + h->skin), rlA = (float)(h->rcA + h->skin);
@@ -1098,7 +1098,6 @@ int engine_queue_iteration(nep_handle *h, cudaStream_t s) {
   e = h->ops->atom_batch(a, h->mf, h->w0.data(), h->b0.data(), h->w1.data(), h->b1, 1, atom_block(h), s);
   if (e == cudaSuccess) e = h->ops->gather_batch(a, 1, gather_block(h), s);
   if (e != cudaSuccess) return cuda_fail(h, e, "engine kernels");
-  launch_struct_sums(S, 1, h->d_offsets.p, N, h->e_u.p, h->e_w.p, h->e_energy.p, h->e_virial.p, s);
   launch_engine_fire(S, h->d_offsets.p, atom_state(h), h->e_slots.p, s);
   launch_engine_advance(S, h->e_slots.p, s);
   CK(cudaGetLastError(), "engine step");
@@ -1151,6 +1150,9 @@ int engine_step(nep_handle *h, cudaStream_t s, int n_iter, bool force_rebuild) {
       if (rc) return rc;
     }
     h->e_last = key;
+    // the jobs' energies and virials, once per chunk: only a job that finished (frozen since,
+    // its per-atom values unchanged) or the chunk's last state is ever read
+    launch_struct_sums(S, 1, h->d_offsets.p, N, h->e_u.p, h->e_w.p, h->e_energy.p, h->e_virial.p, s);
     CK(cudaMemcpyAsync(h->h_status, h->status.p, sizeof(BuildStatus), cudaMemcpyDeviceToHost, s), "status");
     CK(wait_stream(s), "sync");
     const BuildStatus st = *h->h_status;
