@@ -252,6 +252,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(seconds: float, device, world: int) -> float:
+    """The slowest rank's time (every rank gets it): the replicas' job ends when the last one
+    does. One process: the time itself."""
+    if world <= 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput of `world` independent replicas that each processed
+    `units_per_rank` units, over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 # ----------------------------------------------------------------------------- CPU oracle
 def oracle_sample(w_name: str):
     """A bounded sample of the same workload for the FP64 oracle: the same lattice, model,
@@ -795,12 +813,7 @@ def timed_md(nep, h, dt, steps, warmup, stream, flush, world, sampler=None):
                 nep.md_status(h.h, stream.cuda_stream)  # list health, outside the timed events
     nep.md_status(h.h)
     torch.cuda.synchronize()
-    tot = sum(step_ms) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([tot], device=flush.device, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot = float(t.item())
+    tot = max_over_ranks(sum(step_ms) / 1e3, flush.device, world)
     return tot, ktime, nep.nep_get_stats(h.h)["n_rebuilds"] - r0
 
 
@@ -875,12 +888,8 @@ def config_run(nep, h, w, steps, stream, flush, world):
         ev1.record(stream)
         ev1.synchronize()
         nep.md_status(h.h)
-        sec = ev0.elapsed_time(ev1) / 1e3
-        if world > 1:
-            t = torch.tensor([sec], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            sec = float(t.item())
-        out[key] = {"value": world * w.n_atoms * steps / sec, "unit": UNIT, "ms_per_step": 1e3 * sec / steps,
+        sec = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, dev, world)
+        out[key] = {"value": replica_rate(world, w.n_atoms * steps, sec), "unit": UNIT, "ms_per_step": 1e3 * sec / steps,
                     "rebuilds": nep.nep_get_stats(h.h)["n_rebuilds"] - r0}
     nep.nep_set_precision(h.h, 0)
     return out
@@ -962,11 +971,7 @@ def run_gb300(args):
     nep.md_status(h.h)
     th_host = th.cpu()
     p_out, v_out, f_out = nep.md_get_state_host(h.h, N, *out_h)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev, world)
     h2d = N * (24 + 4 + 24) + 72
     d2h = N * 72 + th_host.numel() * 8
     etot = (th_host[:, 0] + th_host[:, 1]).numpy()
@@ -1010,7 +1015,7 @@ def run_gb300(args):
         basis = f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"
         roof, gather_f = atom_roofline(w, stats, ktime["nep_atom"] / args.steps, peak, basis,
                                        profiled_traffic(args.workload))
-        value = world * N * args.steps / total_s
+        value = replica_rate(world, N * args.steps, total_s)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
