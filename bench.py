@@ -315,9 +315,26 @@ def _oracle_md_rate(s, seconds, n_threads):
     return s.n_atoms * steps / el, steps, el
 
 
+def oracle_tiny_run():
+    """The tiny configuration as stated, on the oracle: the 216-atom Si diamond box (3x3x3
+    cells), one energy/force/virial evaluation, then 100 velocity-Verlet NVE steps of 1 fs, on
+    all host cores."""
+    import oracle
+    from paper_2205_10046_gb300 import workloads as W
+    w = W.si_diamond(3, seed=0)
+    t0 = time.perf_counter()
+    oracle.compute(w.model, w.pos, w.types, w.box)
+    t1 = time.perf_counter()
+    oracle.md(w.model, w.pos, w.vel, w.types, w.box, 100, w.dt_fs)
+    t2 = time.perf_counter()
+    return {"workload": f"{w.name} ({w.n_atoms} atoms): one evaluation, then 100 NVE steps of {w.dt_fs} fs",
+            "evaluation_s": t1 - t0, "md_s": t2 - t1, "value": w.n_atoms * 100 / (t2 - t1), "unit": UNIT,
+            "cores": oracle.max_threads()}
+
+
 def cpu_baseline(w_name: str, seconds: float):
     """The oracle as it stands, on the host cores: all threads (the reported value) and one
-    thread, on a bounded periodic sample of the workload."""
+    thread, on a bounded periodic sample of the workload; and the tiny configuration's own run."""
     import oracle
     s, desc = oracle_sample(w_name)
     value, steps, el = _oracle_md_rate(s, seconds, 0)
@@ -327,6 +344,7 @@ def cpu_baseline(w_name: str, seconds: float):
                       f"FP64, OpenMP over atoms",
             "single_thread": {"value": one, "unit": UNIT, "cores": 1,
                               "sample": f"same sample, {steps1} steps in {el1:.1f} s on one thread"},
+            "tiny_configuration": oracle_tiny_run(),
             "cpu_model": cpu_model()}
 
 
