@@ -693,46 +693,54 @@ __global__ void shift_tables_kernel(int n_struct, const Grid *grids, int ncode, 
   dtab[g.dtab_off + code] = D;
 }
 
-// Per-structure sums of the per-atom energies and virials (FP64), one block per (member,
-// structure): every thread adds a fixed stride of the structure's atoms, then a fixed-order
-// reduction (warp shuffles, then the warp totals in warp order), so a sum depends only on the
-// structure's atom range, not on how many structures or members share the launch.
-constexpr int kSumThreads = 256;
-__global__ void __launch_bounds__(kSumThreads) struct_sums_kernel(int n_struct, int members, const int *offsets,
-                                                                   int N, const double *e_atom, const double *w_atom,
-                                                                   double *e_struct, double *w_struct) {
-  const long long b = blockIdx.x;
-  if (b >= (long long)n_struct * members) return;  // uniform over the block
-  const int m = (int)(b / n_struct), s = (int)(b % n_struct);
+// Per-structure sums E_s = sum U_i and W_s = sum W_i (FP64, fixed order): one warp per (member,
+// structure). Lane l adds atoms l, l + 32, l + 64, ... into four partial sums by round (round
+// mod 4): four independent chains, so a structure of 20,000 atoms is not one long FP64 add
+// chain per lane. The partial sums are combined in a fixed order, then a fixed shuffle tree: the
+// result depends only on the structure's atom range.
+__global__ void struct_sums_kernel(int n_struct, int members, const int *offsets, int N, const double *e_atom,
+                                   const double *w_atom, double *e_struct, double *w_struct) {
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= (long long)n_struct * members) return;
+  const int m = (int)(wid / n_struct), s = (int)(wid % n_struct);
   const size_t base = (size_t)m * N;
-  const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5;
-  double acc[10];
+  const int a1 = offsets[s + 1];
+  double acc[4][10];
 #pragma unroll
-  for (int c = 0; c < 10; ++c) acc[c] = 0.0;
-  for (int i = offsets[s] + threadIdx.x; i < offsets[s + 1]; i += kSumThreads) {
-    if (e_atom) acc[0] += e_atom[base + i];
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 10; ++c) acc[r][c] = 0.0;
+  auto add = [&](double *a, size_t k) {
+    if (e_atom) a[0] += e_atom[k];
     if (w_atom)
 #pragma unroll
-      for (int c = 0; c < 9; ++c) acc[1 + c] += w_atom[9 * (base + i) + c];
+      for (int c = 0; c < 9; ++c) a[1 + c] += w_atom[9 * k + c];
+  };
+  int i = offsets[s] + lane;
+  for (; i + 96 < a1; i += 128) {  // four rounds at a time
+#pragma unroll
+    for (int r = 0; r < 4; ++r) add(acc[r], base + i + 32 * r);
   }
-  __shared__ double red[kSumThreads / 32][10];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)  // at most three rounds left
+    if (i < a1) {
+      add(acc[r], base + i);
+      i += 32;
+    }
+  double tot[10];
 #pragma unroll
   for (int c = 0; c < 10; ++c) {
-    double v = acc[c];
+    tot[c] = (acc[0][c] + acc[1][c]) + (acc[2][c] + acc[3][c]);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) red[wv][c] = v;
+    for (int o = 16; o > 0; o >>= 1) tot[c] += __shfl_down_sync(0xffffffffu, tot[c], o);
   }
-  __syncthreads();
-  if (threadIdx.x < 10) {
-    double t = 0.0;
-    for (int w = 0; w < kSumThreads / 32; ++w) t += red[w][threadIdx.x];
+  if (lane == 0) {
     const size_t o = (size_t)m * n_struct + s;
-    if (threadIdx.x == 0) {
-      if (e_struct) e_struct[o] = t;
-    } else if (w_struct) {
-      w_struct[9 * o + threadIdx.x - 1] = t;
-    }
+    if (e_struct) e_struct[o] = tot[0];
+    if (w_struct)
+#pragma unroll
+      for (int c = 0; c < 9; ++c) w_struct[9 * o + c] = tot[1 + c];
   }
 }
 
@@ -900,10 +908,10 @@ void launch_shift_tables(int n_struct, const Grid *grids, int ncode, int obits, 
 
 void launch_struct_sums(int n_struct, int members, const int *offsets, int N, const double *e_atom,
                         const double *w_atom, double *e_struct, double *w_struct, cudaStream_t s) {
-  const long long blocks = (long long)n_struct * members;
-  if (blocks > 0)
-    struct_sums_kernel<<<(unsigned)blocks, kSumThreads, 0, s>>>(n_struct, members, offsets, N, e_atom, w_atom,
-                                                                 e_struct, w_struct);
+  const long long warps = (long long)n_struct * members;
+  if (warps > 0)
+    struct_sums_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(n_struct, members, offsets, N, e_atom,
+                                                                             w_atom, e_struct, w_struct);
 }
 
 // ------------------------------------------------------------------ host launchers
