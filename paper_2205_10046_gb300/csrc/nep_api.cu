@@ -738,6 +738,13 @@ int setup_batch(nep_handle *h, int n_struct, const int *offsets, const double *b
   return NEP_OK;
 }
 
+// The largest structure of the batch layout (atoms).
+int max_struct_atoms(const nep_handle *h) {
+  int mx = 0;
+  for (size_t k = 1; k < h->b_offsets.size(); ++k) mx = std::max(mx, h->b_offsets[k] - h->b_offsets[k - 1]);
+  return mx;
+}
+
 Batch batch_of(nep_handle *h) {
   Batch B;
   B.grids = h->d_grids.p;
@@ -799,7 +806,7 @@ int batch_kernels(nep_handle *h, int N, const BatchOut &o, cudaStream_t s, bool 
   ev_record(h, SLOT_FINAL, 0, s, capturing);
   if (o.e_struct || o.w_struct)
     launch_struct_sums(h->nb_struct, 1, h->d_offsets.p, N, o.e_struct ? o.e_atom : nullptr,
-                       o.w_struct ? o.w_atom : nullptr, o.e_struct, o.w_struct, s);
+                       o.w_struct ? o.w_atom : nullptr, o.e_struct, o.w_struct, max_struct_atoms(h), s);
   ev_record(h, SLOT_FINAL, 1, s, capturing);
   CK(cudaGetLastError(), "structure sums");
   return NEP_OK;
@@ -1152,7 +1159,8 @@ int engine_step(nep_handle *h, cudaStream_t s, int n_iter, bool force_rebuild) {
     h->e_last = key;
     // the jobs' energies and virials, once per chunk: only a job that finished (frozen since,
     // its per-atom values unchanged) or the chunk's last state is ever read
-    launch_struct_sums(S, 1, h->d_offsets.p, N, h->e_u.p, h->e_w.p, h->e_energy.p, h->e_virial.p, s);
+    launch_struct_sums(S, 1, h->d_offsets.p, N, h->e_u.p, h->e_w.p, h->e_energy.p, h->e_virial.p,
+                       max_struct_atoms(h), s);
     CK(cudaMemcpyAsync(h->h_status, h->status.p, sizeof(BuildStatus), cudaMemcpyDeviceToHost, s), "status");
     CK(wait_stream(s), "sync");
     const BuildStatus st = *h->h_status;
@@ -1554,7 +1562,7 @@ int nep_eval_population(nep_handle *h, int n_pop, const double *z, int n_struct,
     ev_record(h, SLOT_GATHER, 1, s, false);
     ev_record(h, SLOT_FINAL, 0, s, false);
     launch_struct_sums(n_struct, m, h->d_offsets.p, N, h->b_e.p, w_tar ? h->b_w.p : nullptr, h->pop_es.p,
-                       w_tar ? h->pop_ws.p : nullptr, s);
+                       w_tar ? h->pop_ws.p : nullptr, max_struct_atoms(h), s);
     launch_population_loss(m, n_struct, h->d_offsets.p, h->pop_es.p, w_tar ? h->pop_ws.p : nullptr, e_tar, w_tar,
                            h->partial_gather.p, nb_g, N, h->pop_reg.p + 2 * (size_t)p0, n_par, lambda,
                            loss + 6 * (size_t)p0, s);

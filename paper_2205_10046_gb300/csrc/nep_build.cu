@@ -693,19 +693,25 @@ __global__ void shift_tables_kernel(int n_struct, const Grid *grids, int ncode, 
   dtab[g.dtab_off + code] = D;
 }
 
-// Per-structure sums E_s = sum U_i and W_s = sum W_i (FP64, fixed order): one warp per (member,
-// structure). Lane l adds atoms l, l + 32, l + 64, ... into four partial sums by round (round
-// mod 4): four independent chains, so a structure of 20,000 atoms is not one long FP64 add
-// chain per lane. The partial sums are combined in a fixed order, then a fixed shuffle tree: the
-// result depends only on the structure's atom range.
+// Per-structure sums E_s = sum U_i and W_s = sum W_i (FP64, fixed order). A structure of at
+// most kWideSum atoms takes one warp (WIDE = false); a larger one one block of kSumThreads
+// threads (WIDE = true), so its FP64 additions run on eight warps. Every thread adds a fixed
+// stride of the structure's atoms into four partial sums by round (round mod 4: independent
+// chains), combined in a fixed order, then a fixed shuffle tree (and, wide, the warp totals in
+// warp order): the result depends only on the structure's atom range.
+constexpr int kWideSum = 2048;
+constexpr int kSumThreads = 256;
+template <bool WIDE>
 __global__ void struct_sums_kernel(int n_struct, int members, const int *offsets, int N, const double *e_atom,
                                    const double *w_atom, double *e_struct, double *w_struct) {
-  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (wid >= (long long)n_struct * members) return;
-  const int m = (int)(wid / n_struct), s = (int)(wid % n_struct);
+  const long long unit = WIDE ? (long long)blockIdx.x : ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (unit >= (long long)n_struct * members) return;  // uniform over the warp (block, WIDE)
+  const int m = (int)(unit / n_struct), s = (int)(unit % n_struct);
+  const int a0 = offsets[s], a1 = offsets[s + 1];
+  if ((a1 - a0 > kWideSum) != WIDE) return;  // the other form takes this structure
   const size_t base = (size_t)m * N;
-  const int a1 = offsets[s + 1];
+  const int t = WIDE ? (int)threadIdx.x : lane, nt = WIDE ? kSumThreads : 32;
   double acc[4][10];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
@@ -717,16 +723,16 @@ __global__ void struct_sums_kernel(int n_struct, int members, const int *offsets
 #pragma unroll
       for (int c = 0; c < 9; ++c) a[1 + c] += w_atom[9 * k + c];
   };
-  int i = offsets[s] + lane;
-  for (; i + 96 < a1; i += 128) {  // four rounds at a time
+  int i = a0 + t;
+  for (; i + 3 * nt < a1; i += 4 * nt) {  // four rounds at a time
 #pragma unroll
-    for (int r = 0; r < 4; ++r) add(acc[r], base + i + 32 * r);
+    for (int r = 0; r < 4; ++r) add(acc[r], base + i + (size_t)nt * r);
   }
 #pragma unroll
   for (int r = 0; r < 3; ++r)  // at most three rounds left
     if (i < a1) {
       add(acc[r], base + i);
-      i += 32;
+      i += nt;
     }
   double tot[10];
 #pragma unroll
@@ -735,8 +741,23 @@ __global__ void struct_sums_kernel(int n_struct, int members, const int *offsets
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) tot[c] += __shfl_down_sync(0xffffffffu, tot[c], o);
   }
-  if (lane == 0) {
-    const size_t o = (size_t)m * n_struct + s;
+  const size_t o = (size_t)m * n_struct + s;
+  if constexpr (WIDE) {
+    __shared__ double red[kSumThreads / 32][10];
+    if (lane == 0)
+#pragma unroll
+      for (int c = 0; c < 10; ++c) red[threadIdx.x >> 5][c] = tot[c];
+    __syncthreads();
+    if (threadIdx.x < 10) {
+      double v = 0.0;
+      for (int w = 0; w < kSumThreads / 32; ++w) v += red[w][threadIdx.x];
+      if (threadIdx.x == 0) {
+        if (e_struct) e_struct[o] = v;
+      } else if (w_struct) {
+        w_struct[9 * o + threadIdx.x - 1] = v;
+      }
+    }
+  } else if (lane == 0) {
     if (e_struct) e_struct[o] = tot[0];
     if (w_struct)
 #pragma unroll
@@ -907,11 +928,15 @@ void launch_shift_tables(int n_struct, const Grid *grids, int ncode, int obits, 
 }
 
 void launch_struct_sums(int n_struct, int members, const int *offsets, int N, const double *e_atom,
-                        const double *w_atom, double *e_struct, double *w_struct, cudaStream_t s) {
-  const long long warps = (long long)n_struct * members;
-  if (warps > 0)
-    struct_sums_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(n_struct, members, offsets, N, e_atom,
-                                                                             w_atom, e_struct, w_struct);
+                        const double *w_atom, double *e_struct, double *w_struct, int max_atoms, cudaStream_t s) {
+  const long long units = (long long)n_struct * members;
+  if (units > 0) {
+    struct_sums_kernel<false><<<(unsigned)((units * 32 + 255) / 256), 256, 0, s>>>(n_struct, members, offsets, N,
+                                                                                    e_atom, w_atom, e_struct, w_struct);
+    if (max_atoms > kWideSum)
+      struct_sums_kernel<true><<<(unsigned)units, kSumThreads, 0, s>>>(n_struct, members, offsets, N, e_atom, w_atom,
+                                                                      e_struct, w_struct);
+  }
 }
 
 // ------------------------------------------------------------------ host launchers

@@ -265,8 +265,9 @@ void launch_export_lists(int N, int T, const float4 *pos4, const int *perm, cons
 // per-structure sums of per-atom energies and virials (caller order, per member)
 void launch_struct_ids(int n_struct, const int *offsets, int *sid, cudaStream_t s);
 void launch_shift_tables(int n_struct, const Grid *grids, int ncode, int obits, float4 *dtab, cudaStream_t s);
+// max_atoms: the largest structure (structures above kWideSum atoms are summed by a block)
 void launch_struct_sums(int n_struct, int members, const int *offsets, int N, const double *e_atom,
-                        const double *w_atom, double *e_struct, double *w_struct, cudaStream_t s);
+                        const double *w_atom, double *e_struct, double *w_struct, int max_atoms, cudaStream_t s);
 void launch_arm_rebuild(BuildStatus *st, cudaStream_t s);
 void launch_fire_mix(int N, const AtomState &a, FireState *fire, int check_only, cudaStream_t s);
 // batched serving engine
