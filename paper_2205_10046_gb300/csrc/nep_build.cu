@@ -17,7 +17,9 @@
 //                  of j, so forces are gathered without atomics (Algorithm 4's "index
 //                  manipulations").
 // Every builder returns early unless a rebuild is pending, so the whole sequence sits in the
-// captured MD step graph and only works when an atom moved more than skin/2.
+// captured MD step graph and only works when an atom moved more than skin/2. In the serving
+// engine's batch a build that was not forced covers only the structures whose atoms moved that
+// far (per-structure flags); the others keep their cells, atom order, lists and x_ref.
 #include <cuda_bf16.h>
 
 #include "nep_internal.cuh"
